@@ -1,0 +1,184 @@
+/*
+ * kubo.h -- C ABI of the GB300 Kubo-formula anomalous Hall conductivity library.
+ *
+ * The library evaluates, for every k-point of a uniform Brillouin-zone mesh, the four
+ * steps of the paper's baseline algorithm (Sec. 2.2, List 1; batched form Sec. 2.3,
+ * List 2 and Eq. 4) and the k-sum of Eq. 2:
+ *
+ *   (1) H(k) = sum_R e^{i k.R} H(R),  d_a H(k) = sum_R i R_a e^{i k.R} H(R), a = x, y
+ *   (2) H(k) = U diag(E) U^dagger                     (Hermitian eigendecomposition)
+ *   (3) v^a  = U^dagger d_a H U                       ("convert" to the eigenbasis)
+ *   (4) Omega_n = -2 sum_{m != n} Im(v^x_nm v^y_mn) / ((E_n - E_m)^2 + eta^2)   (Eq. 3)
+ *   S(E_F) = (1/N_k) sum_k sum_n occ(E_n(k); E_F) Omega_n(k)                      (Eq. 2)
+ *
+ * occ is theta(E_F - E_n) (occupied iff E_n < E_F) for kT = 0, else the Fermi-Dirac
+ * factor 1/(1 + exp((E_n - E_F)/kT)).  S is dimensionless (lattice units, integer R);
+ * for one 2-D layer the Chern number is 2 pi S, and the 3-D conductivity is
+ * sigma_xy = -(e^2/hbar) S / V_cell (conversion left to the caller).  The paper's
+ * Eq. 3 omits eta; eta > 0 regularises near-degenerate pairs.  With eta = 0, pairs with
+ * |E_n - E_m| <= 1e-12 max|E| are skipped.
+ *
+ * Memory conventions.
+ *   - complex128 arrays are interleaved (re, im) doubles, row-major.
+ *   - H_R: [N_R][W][W] complex128 with H(-R) = H(R)^dagger; R_vecs: [N_R][3] int32,
+ *     closed under R -> -R and containing R = 0.
+ *   - k-point linear index: (j1*N2 + j2)*N3 + j3 for k = 2 pi (j1/N1, j2/N2, j3/N3).
+ *   - "packed Hermitian" (W*W doubles) P of a Hermitian A: P[i][j] = Re A_ij for i <= j
+ *     and P[i][j] = Im A_ji for i > j.
+ *   - The caller owns every buffer; the library never frees caller memory.
+ *
+ * Errors.  Every entry point validates its arguments on the host before any launch and
+ * returns a kubo_status; no C++ exception crosses the ABI.  Entry points that take H_R
+ * also check Hermitian pairing on the device (max |H(-R) - H(R)^dagger| <= 1e-12 max|H|,
+ * all entries finite).  Calls are stream-ordered on opt->stream and return after that
+ * stream has completed the call's work (the device status word is read back), so the
+ * returned status covers device-detected errors too.  Outputs are written only when the
+ * call returns KUBO_OK.
+ */
+#ifndef KUBO_H
+#define KUBO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KUBO_OK = 0,
+  KUBO_ERR_INVALID_ARG = 1,     /* bad size, null pointer, non-finite eta/kT/E_F, ... */
+  KUBO_ERR_NOT_HERMITIAN = 2,   /* H(-R) != H(R)^dagger beyond 1e-12 max|H|, or non-finite H */
+  KUBO_ERR_R_NOT_CLOSED = 3,    /* some -R missing, R = 0 missing, or duplicate R */
+  KUBO_ERR_UNSUPPORTED = 4,     /* W or precision outside what this build supports */
+  KUBO_ERR_OOM = 5,             /* device allocation failed */
+  KUBO_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+  KUBO_ERR_NO_CONVERGENCE = 7,  /* eigensolver hit its iteration cap at some k-point */
+  KUBO_ERR_WORKSPACE = 8        /* caller workspace smaller than kubo_workspace_size() */
+} kubo_status;
+
+typedef enum {
+  KUBO_FP64 = 0,   /* every step in FP64 */
+  KUBO_MIXED = 1   /* steps (1) and (3) on the tensor cores with split-BF16 operands and
+                      FP32 accumulation; eigensolver, denominators and k-sum in FP64 */
+} kubo_precision;
+
+/* Pipeline stages, for the optional per-stage timing in kubo_profile. */
+enum {
+  KUBO_STAGE_PREP = 0,          /* Hermitian check, twiddles, packed Fourier basis */
+  KUBO_STAGE_FOURIER = 1,       /* step (1) */
+  KUBO_STAGE_TRIDIAG = 2,       /* step (2): Householder tridiagonalisation */
+  KUBO_STAGE_QL = 3,            /* step (2): implicit QL on the tridiagonals */
+  KUBO_STAGE_BACKTRANSFORM = 4, /* step (2): eigenvectors U = Q D Z */
+  KUBO_STAGE_BERRY = 5,         /* steps (3)-(4) */
+  KUBO_STAGE_KSUM = 6,          /* k-sum of Eq. 2 */
+  KUBO_N_STAGES = 7
+};
+
+/* Per-stage kernel launch counts and summed device time (CUDA events recorded on the call's
+ * stream around each launch).  The library adds to the fields; the caller zeroes them. */
+typedef struct kubo_profile {
+  int64_t launches[KUBO_N_STAGES];
+  double ms[KUBO_N_STAGES];
+} kubo_profile;
+
+typedef struct kubo_options {
+  int precision;            /* kubo_precision; default KUBO_FP64 */
+  int n_eta;                /* > 0: evaluate every broadening in etas (host array) */
+  const double* etas;       /*       and write out as [n_eta][n_EF]; 0: use the eta arg */
+  double kT;                /* 0: step occupation; > 0: Fermi-Dirac temperature (energy units) */
+  int64_t k_begin, k_end;   /* sub-range [k_begin, k_end) of linear mesh indices; both 0 =
+                               whole mesh.  The weight stays 1/N_k, so results over a
+                               partition of the mesh add up to the full-mesh result. */
+  void* stream;             /* cudaStream_t; NULL = legacy default stream */
+  void* workspace;          /* device scratch of workspace_bytes; NULL = the library
+                               allocates (cudaMallocAsync) and frees it inside the call */
+  size_t workspace_bytes;
+  int chunk_k;              /* k-points per internal batch; 0 = automatic */
+  kubo_profile* profile;    /* non-NULL: accumulate per-stage launch counts and times */
+} kubo_options;
+
+/* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,
+ * library-managed workspace, automatic batch size). */
+void kubo_options_init(kubo_options* opt);
+
+/* Human-readable name of a status code (static storage). */
+const char* kubo_status_string(kubo_status s);
+
+/* Largest orbital count W supported by this build for the given precision. */
+int kubo_max_orbitals(int precision);
+
+/*
+ * Anomalous Hall sum S(E_F) over the k-mesh (Eq. 2 with the integrand of Eq. 3; the
+ * steps of List 1 / List 2 evaluated for every mesh point).
+ *   H_R    device, complex128 [N_R][W][W]
+ *   R_vecs host,   int32 [N_R][3]
+ *   kmesh  host,   int32 [3], each >= 1
+ *   E_F    device, double [n_EF]  (any order)
+ *   out    device, double [n_eta][n_EF]  (n_eta = opt->n_eta if > 0, else 1 with eta)
+ * Returns KUBO_OK or an error; on error out is untouched.
+ */
+kubo_status kubo_ahc(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                     const int32_t* kmesh, const double* E_F, int n_EF, double eta,
+                     double* out, const kubo_options* opt);
+
+/*
+ * Same computation as kubo_ahc with HOST buffers for H_R, E_F and out: the library copies
+ * H_R and E_F to the device and out back to the host inside the call.
+ */
+kubo_status kubo_ahc_host(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                          const int32_t* kmesh, const double* E_F, int n_EF, double eta,
+                          double* out, const kubo_options* opt);
+
+/*
+ * Per-k results for a list of mesh points (steps (1)-(4) of List 1 without the k-sum):
+ *   kidx   device, int64 [n_k] linear mesh indices (each in [0, N_k))
+ *   E      device, double [n_k][W]            eigenvalues, ascending
+ *   Omega  device, double [n_eta][n_k][W]     band Berry curvatures
+ * opt->k_begin/k_end are ignored.
+ */
+kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                       const int32_t* kmesh, const int64_t* kidx, int64_t n_k, double eta,
+                       double* E, double* Omega, const kubo_options* opt);
+
+/*
+ * Step (1) alone ("define_matrices" of List 1/2): packed Hermitian H(k), d_x H(k), d_y H(k)
+ * for the listed mesh points.
+ *   Hk, dHx, dHy  device, double [n_k][W*W] each (packed Hermitian)
+ */
+kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                       const int32_t* kmesh, const int64_t* kidx, int64_t n_k,
+                       double* Hk, double* dHx, double* dHy, const kubo_options* opt);
+
+/*
+ * Step (2) alone: batched Hermitian eigendecomposition ("diagonalize" of List 2, the
+ * batched EISPACK-style solver of Sec. 2.3) in FP64.
+ *   A  device, double [n][W*W] packed Hermitian matrices
+ *   E  device, double [n][W] ascending eigenvalues
+ *   U  device, complex128 [n][W][W]; column j is the eigenvector of E[j] (U may be NULL
+ *      to compute eigenvalues only)
+ */
+kubo_status kubo_eigh_batched(const double* A, int W, int64_t n, double* E, double* U,
+                              const kubo_options* opt);
+
+/*
+ * Steps (3)-(4) alone ("convert" + "evaluate" of List 1/2): band Berry curvatures from
+ * eigenpairs and velocity matrices.
+ *   E        device, double [n][W]
+ *   U        device, complex128 [n][W][W] (columns = eigenvectors)
+ *   dHx, dHy device, double [n][W*W] packed Hermitian
+ *   Omega    device, double [n_eta][n][W]
+ */
+kubo_status kubo_berry_batched(const double* E, const double* U, const double* dHx,
+                               const double* dHy, int W, int64_t n, double eta,
+                               double* Omega, const kubo_options* opt);
+
+/* Device bytes of scratch a kubo_ahc / kubo_ahc_k call with these sizes needs. */
+size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
+                           const kubo_options* opt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KUBO_H */

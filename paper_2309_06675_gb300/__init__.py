@@ -1,0 +1,326 @@
+"""GB300-native Kubo-formula anomalous Hall conductivity (Yahagi & Kato, arXiv 2309.06675).
+
+Thin Python binding over the C ABI of ``libkubo.so`` (declared in include/kubo.h).  Every
+step of the computation runs in the library's CUDA kernels; this module only marshals
+arguments (device pointers of PyTorch tensors, host arrays, the current CUDA stream) and
+maps status codes to exceptions.  There is no CPU fallback: if the library is missing
+the import of a compute function raises.
+
+Entry points (same names as the C ABI, without the ``kubo_`` prefix):
+  ahc(H_R, R, kmesh, E_F, eta=..., etas=None, kT=0, ...)       -> S [n_eta, n_EF]
+  ahc_host(H_R_np, R, kmesh, E_F_np, ...)                       -> numpy S (host in/out)
+  ahc_k(H_R, R, kmesh, kidx, eta=..., etas=None)                -> (E [n_k, W], Omega [n_eta, n_k, W])
+  bloch(H_R, R, kmesh, kidx)                                    -> packed H, dHx, dHy
+  eigh_batched(A_packed, W)                                     -> (E, U)
+  berry_batched(E, U, dHx_packed, dHy_packed, eta | etas)       -> Omega
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "KuboError", "lib", "ahc", "ahc_host", "ahc_k", "bloch", "eigh_batched", "berry_batched",
+    "workspace_size", "max_orbitals", "pack_hermitian", "unpack_hermitian", "FP64", "MIXED",
+    "LIB_PATH", "Profile", "Options", "STAGES",
+]
+
+FP64 = 0
+MIXED = 1
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libkubo.so")
+
+_STATUS = {
+    0: "KUBO_OK", 1: "KUBO_ERR_INVALID_ARG", 2: "KUBO_ERR_NOT_HERMITIAN",
+    3: "KUBO_ERR_R_NOT_CLOSED", 4: "KUBO_ERR_UNSUPPORTED", 5: "KUBO_ERR_OOM",
+    6: "KUBO_ERR_CUDA", 7: "KUBO_ERR_NO_CONVERGENCE", 8: "KUBO_ERR_WORKSPACE",
+}
+
+
+class KuboError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = _STATUS.get(code, str(code))
+
+
+STAGES = ("prep", "fourier", "tridiag", "ql", "backtransform", "berry", "ksum")
+
+
+class Profile(ctypes.Structure):
+    """Per-stage launch counts and device milliseconds (kubo_profile of include/kubo.h)."""
+    _fields_ = [("launches", ctypes.c_int64 * len(STAGES)), ("ms", ctypes.c_double * len(STAGES))]
+
+    def as_dict(self):
+        return {s: {"launches": int(self.launches[i]), "ms": float(self.ms[i])}
+                for i, s in enumerate(STAGES)}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("n_eta", ctypes.c_int),
+        ("etas", ctypes.POINTER(ctypes.c_double)),
+        ("kT", ctypes.c_double),
+        ("k_begin", ctypes.c_int64),
+        ("k_end", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("chunk_k", ctypes.c_int),
+        ("profile", ctypes.POINTER(Profile)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libkubo (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libkubo.so not found at {LIB_PATH}; build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D, V = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                           ctypes.c_void_p)
+        OPT = ctypes.POINTER(Options)
+        sig = {
+            "kubo_options_init": (None, [OPT]),
+            "kubo_status_string": (ctypes.c_char_p, [I]),
+            "kubo_max_orbitals": (I, [I]),
+            "kubo_workspace_size": (ctypes.c_size_t, [I, I, P, I, OPT]),
+            "kubo_ahc": (I, [P, P, I, I, P, P, I, D, P, OPT]),
+            "kubo_ahc_host": (I, [P, P, I, I, P, P, I, D, P, OPT]),
+            "kubo_ahc_k": (I, [P, P, I, I, P, P, I64, D, P, P, OPT]),
+            "kubo_bloch": (I, [P, P, I, I, P, P, I64, P, P, P, OPT]),
+            "kubo_eigh_batched": (I, [P, I, I64, P, P, OPT]),
+            "kubo_berry_batched": (I, [P, P, P, P, I, I64, D, P, OPT]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        msg = lib().kubo_status_string(code).decode()
+        raise KuboError(code, f"{what}: {msg}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host_int32(a, shape_last=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    if shape_last is not None and arr.shape[-1] != shape_last:
+        raise ValueError(f"expected trailing dimension {shape_last}, got {arr.shape}")
+    return arr
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk_k=0,
+             workspace=None, keep=None, profile=None):
+    o = Options()
+    lib().kubo_options_init(ctypes.byref(o))
+    o.precision = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    if etas is not None:
+        e = np.ascontiguousarray(np.asarray(etas, dtype=np.float64).ravel())
+        if keep is not None:
+            keep.append(e)
+        o.n_eta = int(e.size)
+        o.etas = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o.kT = float(kT)
+    if k_range is not None:
+        o.k_begin, o.k_end = int(k_range[0]), int(k_range[1])
+    o.stream = _stream_ptr(stream)
+    o.chunk_k = int(chunk_k)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    if profile is not None:
+        o.profile = ctypes.pointer(profile)
+    return o
+
+
+def max_orbitals(precision=FP64) -> int:
+    return int(lib().kubo_max_orbitals({"fp64": FP64, "mixed": MIXED}.get(precision, precision)))
+
+
+def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range=None,
+                   chunk_k=0) -> int:
+    km = _host_int32(kmesh)
+    keep = []
+    o = Options()
+    lib().kubo_options_init(ctypes.byref(o))
+    o.precision = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    if n_eta > 1:
+        e = np.full(n_eta, 1e-3)
+        keep.append(e)
+        o.n_eta = n_eta
+        o.etas = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o.kT = kT
+    if k_range is not None:
+        o.k_begin, o.k_end = k_range
+    o.chunk_k = chunk_k
+    return int(lib().kubo_workspace_size(int(W), int(N_R), km.ctypes.data_as(ctypes.c_void_p),
+                                         int(n_EF), ctypes.byref(o)))
+
+
+def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
+        stream=None, chunk_k=0, workspace=None, out=None, profile=None):
+    """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
+
+    H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
+    """
+    torch = _torch()
+    Rh = _host_int32(R, 3)
+    km = _host_int32(kmesh)
+    N_R, W = int(H_R.shape[0]), int(H_R.shape[1])
+    n_EF = int(E_F.numel())
+    n_eta = 1 if etas is None else int(np.asarray(etas).size)
+    if out is None:
+        out = torch.empty((n_eta, n_EF), dtype=torch.float64, device=H_R.device)
+    keep = []
+    o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
+    code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
+                          W, N_R, km.ctypes.data_as(ctypes.c_void_p),
+                          _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),
+                          _dev(out, torch.float64, "out"), ctypes.byref(o))
+    _check(code, "kubo_ahc")
+    return out
+
+
+def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
+             stream=None, chunk_k=0, workspace=None, profile=None):
+    """Host-buffer variant: H_R complex128 numpy [N_R, W, W], E_F float64 numpy -> numpy S."""
+    H = np.ascontiguousarray(H_R, dtype=np.complex128)
+    EF = np.ascontiguousarray(E_F, dtype=np.float64).ravel()
+    Rh = _host_int32(R, 3)
+    km = _host_int32(kmesh)
+    N_R, W = H.shape[0], H.shape[1]
+    n_eta = 1 if etas is None else int(np.asarray(etas).size)
+    out = np.empty((n_eta, EF.size), dtype=np.float64)
+    keep = []
+    o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
+    code = lib().kubo_ahc_host(H.ctypes.data_as(ctypes.c_void_p), Rh.ctypes.data_as(ctypes.c_void_p),
+                               W, N_R, km.ctypes.data_as(ctypes.c_void_p),
+                               EF.ctypes.data_as(ctypes.c_void_p), int(EF.size), float(eta),
+                               out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o))
+    _check(code, "kubo_ahc_host")
+    return out
+
+
+def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None, chunk_k=0):
+    """Per-k eigenvalues and band curvatures for the listed mesh points."""
+    torch = _torch()
+    Rh = _host_int32(R, 3)
+    km = _host_int32(kmesh)
+    N_R, W = int(H_R.shape[0]), int(H_R.shape[1])
+    n_k = int(kidx.numel())
+    n_eta = 1 if etas is None else int(np.asarray(etas).size)
+    E = torch.empty((n_k, W), dtype=torch.float64, device=H_R.device)
+    Om = torch.empty((n_eta, n_k, W), dtype=torch.float64, device=H_R.device)
+    keep = []
+    o = _options(precision, etas, 0.0, None, stream, chunk_k, None, keep)
+    code = lib().kubo_ahc_k(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
+                            W, N_R, km.ctypes.data_as(ctypes.c_void_p),
+                            _dev(kidx, torch.int64, "kidx"), n_k, float(eta),
+                            _dev(E, torch.float64, "E"), _dev(Om, torch.float64, "Omega"),
+                            ctypes.byref(o))
+    _check(code, "kubo_ahc_k")
+    return E, Om
+
+
+def bloch(H_R, R, kmesh, kidx, stream=None):
+    """Packed Hermitian H(k), d_x H(k), d_y H(k) [n_k, W*W] each (float64 CUDA)."""
+    torch = _torch()
+    Rh = _host_int32(R, 3)
+    km = _host_int32(kmesh)
+    N_R, W = int(H_R.shape[0]), int(H_R.shape[1])
+    n_k = int(kidx.numel())
+    outs = [torch.empty((n_k, W * W), dtype=torch.float64, device=H_R.device) for _ in range(3)]
+    o = _options(stream=stream)
+    code = lib().kubo_bloch(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
+                            W, N_R, km.ctypes.data_as(ctypes.c_void_p),
+                            _dev(kidx, torch.int64, "kidx"), n_k,
+                            *[_dev(x, torch.float64, "out") for x in outs], ctypes.byref(o))
+    _check(code, "kubo_bloch")
+    return tuple(outs)
+
+
+def eigh_batched(A, W, vectors=True, stream=None, chunk_k=0):
+    """Batched FP64 Hermitian eigh of packed matrices A [n, W*W] -> (E [n, W], U [n, W, W] or None)."""
+    torch = _torch()
+    n = int(A.shape[0])
+    E = torch.empty((n, W), dtype=torch.float64, device=A.device)
+    U = torch.empty((n, W, W), dtype=torch.complex128, device=A.device) if vectors else None
+    o = _options(stream=stream, chunk_k=chunk_k)
+    code = lib().kubo_eigh_batched(_dev(A, torch.float64, "A"), int(W), n, _dev(E, torch.float64, "E"),
+                                   _dev(U, torch.complex128, "U") if vectors else None,
+                                   ctypes.byref(o))
+    _check(code, "kubo_eigh_batched")
+    return E, U
+
+
+def berry_batched(E, U, dHx, dHy, eta=1e-3, etas=None, stream=None):
+    """Band Berry curvatures [n_eta, n, W] from eigenpairs and packed velocity matrices."""
+    torch = _torch()
+    n, W = int(E.shape[0]), int(E.shape[1])
+    n_eta = 1 if etas is None else int(np.asarray(etas).size)
+    Om = torch.empty((n_eta, n, W), dtype=torch.float64, device=E.device)
+    keep = []
+    o = _options(etas=etas, stream=stream, keep=keep)
+    code = lib().kubo_berry_batched(_dev(E, torch.float64, "E"), _dev(U, torch.complex128, "U"),
+                                    _dev(dHx, torch.float64, "dHx"), _dev(dHy, torch.float64, "dHy"),
+                                    W, n, float(eta), _dev(Om, torch.float64, "Omega"),
+                                    ctypes.byref(o))
+    _check(code, "kubo_berry_batched")
+    return Om
+
+
+def pack_hermitian(A):
+    """Packed Hermitian layout of include/kubo.h: P[i][j] = Re A_ij (i <= j), Im A_ji (i > j)."""
+    torch = _torch()
+    W = A.shape[-1]
+    iu = torch.triu(torch.ones(W, W, dtype=torch.bool, device=A.device))
+    re = A.real
+    im_t = A.imag.transpose(-1, -2)
+    return torch.where(iu, re, im_t).reshape(*A.shape[:-2], W * W).contiguous()
+
+
+def unpack_hermitian(P, W):
+    """Inverse of pack_hermitian: complex128 [..., W, W]."""
+    torch = _torch()
+    P = P.reshape(*P.shape[:-1], W, W)
+    iu = torch.triu(torch.ones(W, W, dtype=torch.bool, device=P.device), diagonal=1)
+    diag = torch.eye(W, dtype=torch.bool, device=P.device)
+    Pt = P.transpose(-1, -2)
+    re = torch.where(iu, P, torch.where(diag, P, Pt))
+    im = torch.where(iu, Pt, torch.where(diag, torch.zeros_like(P), -P))
+    return torch.complex(re, im)

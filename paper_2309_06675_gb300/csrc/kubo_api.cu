@@ -1,0 +1,687 @@
+// C ABI of libkubo (include/kubo.h): argument validation, analysis of the R set, workspace
+// planning and the batched k-point pipeline (the paper's List 2 loop over batches).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "kubo_internal.cuh"
+
+using namespace kubo;
+
+namespace {
+
+constexpr int MAX_W = 64;
+constexpr int MAX_ETA = 8;
+constexpr int KSUM_KPB = 256;        // k-points per deterministic k-sum block
+constexpr size_t ALIGN = 256;
+
+// ------------------------------------------------------------------ options
+kubo_options defaults() {
+  kubo_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.precision = KUBO_FP64;
+  return o;
+}
+
+// ------------------------------------------------------------------ R set
+struct RInfo {
+  std::vector<int> neg;     // [N_R] index of -R
+  std::vector<int> pairs;   // [N_h][2] (index of R_h, index of -R_h), canonical R_h
+  std::vector<int> Rh;      // [N_h][3]
+  int idx0 = -1;
+  int N_h = 0;
+};
+
+kubo_status analyze_R(const int32_t* R, int N_R, RInfo& info) {
+  std::map<std::array<int, 3>, int> idx;
+  for (int i = 0; i < N_R; ++i) {
+    std::array<int, 3> key{R[3 * i], R[3 * i + 1], R[3 * i + 2]};
+    if (!idx.emplace(key, i).second) return KUBO_ERR_R_NOT_CLOSED;   // duplicate
+  }
+  auto z = idx.find({0, 0, 0});
+  if (z == idx.end()) return KUBO_ERR_R_NOT_CLOSED;
+  info.idx0 = z->second;
+  info.neg.assign(N_R, -1);
+  for (int i = 0; i < N_R; ++i) {
+    auto it = idx.find({-R[3 * i], -R[3 * i + 1], -R[3 * i + 2]});
+    if (it == idx.end()) return KUBO_ERR_R_NOT_CLOSED;
+    info.neg[i] = it->second;
+    const int r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+    const bool canon = r0 > 0 || (r0 == 0 && (r1 > 0 || (r1 == 0 && r2 > 0)));
+    if (canon) {
+      info.pairs.push_back(i);
+      info.pairs.push_back(it->second);
+      info.Rh.push_back(r0);
+      info.Rh.push_back(r1);
+      info.Rh.push_back(r2);
+    }
+  }
+  info.N_h = (int)info.pairs.size() / 2;
+  if (1 + 2 * info.N_h != N_R) return KUBO_ERR_R_NOT_CLOSED;
+  return KUBO_OK;
+}
+
+// ------------------------------------------------------------------ workspace plan
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + ALIGN - 1) / ALIGN * ALIGN;
+    return o;
+  }
+};
+
+struct Plan {
+  int W = 0, N_R = 0, N_h = 0, K = 0, n_EF = 0, n_eta = 1, chunk = 0, cap = 0;
+  bool model = false;   // needs the prepared Fourier basis
+  bool eigh = false;    // needs eigensolver buffers
+  bool berry = false;   // needs velocity / curvature buffers
+  bool ksum = false;    // needs k-sum buffers
+  Mesh mesh{1, 1, 1, 1};
+  size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
+         o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
+         o_ph = 0, o_refl = 0, o_tau = 0, o_rot = 0, o_rcol = 0, o_nrot = 0, o_part = 0,
+         o_HR = 0, o_EF = 0, o_out = 0;
+  size_t total = 0;
+};
+
+int rot_capacity(int W) { return 3 * W * W + 64; }
+
+size_t bytes_per_k(int W, int n_eta) {
+  size_t WW = (size_t)W * W;
+  return 3 * WW * 8 + WW * 16 /*U*/ + WW * 16 /*refl*/ + (size_t)rot_capacity(W) * 18 +
+         (size_t)W * (8 * 4 + 16) + (size_t)n_eta * W * 8 + 64;
+}
+
+int auto_chunk(int W, int n_eta, int64_t n_total) {
+  const size_t budget = (size_t)12 << 30;
+  int64_t c = (int64_t)(budget / bytes_per_k(W, n_eta));
+  c = std::max<int64_t>(1024, std::min<int64_t>(c, 65536));
+  c = c / 1024 * 1024;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(c, n_total));
+}
+
+void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
+  (void)n_list_outputs_unused;
+  Bump b;
+  const size_t WW = (size_t)p.W * p.W;
+  p.o_status = b.take(sizeof(DevStatus));
+  p.o_etas = b.take(sizeof(double) * MAX_ETA);
+  if (p.model) {
+    p.o_neg = b.take(sizeof(int) * p.N_R);
+    p.o_pairs = b.take(sizeof(int) * 2 * std::max(1, p.N_h));
+    p.o_Rh = b.take(sizeof(int) * 3 * std::max(1, p.N_h));
+    p.o_tab = b.take(sizeof(double2) * (p.mesh.N1 + p.mesh.N2 + p.mesh.N3));
+    p.o_Bp = b.take(sizeof(double) * (size_t)p.K * WW);
+    p.o_Hp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+    p.o_Xp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+    p.o_Yp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+  }
+  if (p.eigh) {
+    p.o_d = b.take(sizeof(double) * (size_t)p.chunk * p.W);
+    p.o_e = b.take(sizeof(double) * (size_t)p.chunk * p.W);
+    p.o_ph = b.take(sizeof(double2) * (size_t)p.chunk * p.W);
+    p.o_tau = b.take(sizeof(double) * (size_t)p.chunk * p.W);
+    p.o_refl = b.take(sizeof(double2) * (size_t)p.chunk * WW);
+    p.o_rot = b.take(sizeof(double2) * (size_t)p.chunk * p.cap);
+    p.o_rcol = b.take(sizeof(short) * (size_t)p.chunk * p.cap);
+    p.o_nrot = b.take(sizeof(int) * (size_t)p.chunk);
+  }
+  if (p.berry) {
+    p.o_E = b.take(sizeof(double) * (size_t)p.chunk * p.W);
+    p.o_U = b.take(sizeof(double2) * (size_t)p.chunk * WW);
+    p.o_Om = b.take(sizeof(double) * (size_t)p.chunk * p.W * p.n_eta);
+  }
+  if (p.ksum) {
+    const int n_out = p.n_eta * p.n_EF;
+    p.o_acc = b.take(sizeof(double2) * n_out);
+    p.o_part = b.take(sizeof(double2) * (size_t)n_out * ((p.chunk + KSUM_KPB - 1) / KSUM_KPB));
+  }
+  if (host_io) {
+    p.o_HR = b.take(sizeof(double2) * (size_t)p.N_R * WW);
+    p.o_EF = b.take(sizeof(double) * p.n_EF);
+    p.o_out = b.take(sizeof(double) * (size_t)p.n_eta * p.n_EF);
+  }
+  p.total = b.off;
+}
+
+// ------------------------------------------------------------------ call context
+struct Call {
+  cudaStream_t s = nullptr;
+  char* ws = nullptr;
+  bool owned = false;
+  Plan p;
+  kubo_status st = KUBO_OK;
+  // optional per-stage timing: event pairs recorded around launches, read after the sync
+  struct Ev { int stage, launches; cudaEvent_t a, b; };
+  kubo_profile* prof = nullptr;
+  std::vector<Ev> evs;
+
+  ~Call() { collect(); }
+  void collect() {
+    if (evs.empty()) return;
+    cudaStreamSynchronize(s);
+    for (auto& e : evs) {
+      float ms = 0.f;
+      if (prof && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+        prof->ms[e.stage] += ms;
+        prof->launches[e.stage] += e.launches;
+      }
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    evs.clear();
+    cudaGetLastError();
+  }
+
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+
+  kubo_status acquire(const kubo_options& o) {
+    if (o.workspace) {
+      if (o.workspace_bytes < p.total) return KUBO_ERR_WORKSPACE;
+      ws = (char*)o.workspace;
+      return KUBO_OK;
+    }
+    if (cudaMallocAsync((void**)&ws, p.total, s) != cudaSuccess) {
+      cudaGetLastError();
+      ws = nullptr;
+      return KUBO_ERR_OOM;
+    }
+    owned = true;
+    return KUBO_OK;
+  }
+  void release() {
+    if (owned && ws) cudaFreeAsync(ws, s);
+    ws = nullptr;
+    owned = false;
+  }
+};
+
+// Records a CUDA event pair on the call's stream around the launches of one stage.
+struct StageTimer {
+  Call& c;
+  Call::Ev ev{0, 0, nullptr, nullptr};
+  StageTimer(Call& call, int stage, int launches) : c(call) {
+    if (!c.prof) return;
+    ev.stage = stage;
+    ev.launches = launches;
+    if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+      cudaGetLastError();
+      ev.a = ev.b = nullptr;
+      return;
+    }
+    cudaEventRecord(ev.a, c.s);
+  }
+  ~StageTimer() {
+    if (!c.prof || !ev.a) return;
+    cudaEventRecord(ev.b, c.s);
+    c.evs.push_back(ev);
+  }
+};
+
+#define KCHECK(expr)                                  \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) {                          \
+      cudaGetLastError();                             \
+      return KUBO_ERR_CUDA;                           \
+    }                                                 \
+  } while (0)
+
+kubo_status bits_to_status(unsigned bits) {
+  if (bits & (ST_NOT_HERMITIAN | ST_NONFINITE)) return KUBO_ERR_NOT_HERMITIAN;
+  if (bits & (ST_NO_CONVERGENCE | ST_LOG_OVERFLOW)) return KUBO_ERR_NO_CONVERGENCE;
+  return KUBO_OK;
+}
+
+kubo_status read_status(Call& c) {
+  DevStatus h;
+  KCHECK(cudaMemcpyAsync(&h, c.at<DevStatus>(c.p.o_status), sizeof(h), cudaMemcpyDeviceToHost, c.s));
+  KCHECK(cudaStreamSynchronize(c.s));
+  return bits_to_status(h.bits);
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_options& o,
+                            int& n_eta) {
+  if (W < 1 || N_R < 1 || !kmesh) return KUBO_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (kmesh[a] < 1) return KUBO_ERR_INVALID_ARG;
+  if (o.precision != KUBO_FP64) return KUBO_ERR_UNSUPPORTED;
+  if (W > MAX_W) return KUBO_ERR_UNSUPPORTED;
+  if (!finite_nonneg(o.kT)) return KUBO_ERR_INVALID_ARG;
+  if (o.n_eta < 0) return KUBO_ERR_INVALID_ARG;
+  if (o.n_eta > 0) {
+    if (!o.etas) return KUBO_ERR_INVALID_ARG;
+    if (o.n_eta > MAX_ETA) return KUBO_ERR_UNSUPPORTED;
+    for (int e = 0; e < o.n_eta; ++e)
+      if (!finite_nonneg(o.etas[e])) return KUBO_ERR_INVALID_ARG;
+  }
+  if (o.chunk_k < 0) return KUBO_ERR_INVALID_ARG;
+  n_eta = o.n_eta > 0 ? o.n_eta : 1;
+  return KUBO_OK;
+}
+
+// Prepare the model (status reset, Hermitian check, twiddles, packed basis) and return the
+// Hermitian verdict (one host sync).
+kubo_status prepare_model(Call& c, const double* H_R, const RInfo& ri) {
+  Plan& p = c.p;
+  KCHECK(cudaMemsetAsync(c.at<char>(p.o_status), 0, sizeof(DevStatus), c.s));
+  KCHECK(cudaMemcpyAsync(c.at<int>(p.o_neg), ri.neg.data(), sizeof(int) * p.N_R, cudaMemcpyHostToDevice, c.s));
+  if (p.N_h > 0) {
+    KCHECK(cudaMemcpyAsync(c.at<int>(p.o_pairs), ri.pairs.data(), sizeof(int) * 2 * p.N_h, cudaMemcpyHostToDevice, c.s));
+    KCHECK(cudaMemcpyAsync(c.at<int>(p.o_Rh), ri.Rh.data(), sizeof(int) * 3 * p.N_h, cudaMemcpyHostToDevice, c.s));
+  }
+  DevStatus* st = c.at<DevStatus>(p.o_status);
+  {
+    StageTimer tm(c, KUBO_STAGE_PREP, 4);
+    KCHECK(launch_check_hermitian((const double2*)H_R, c.at<int>(p.o_neg), p.N_R, p.W, st, c.s));
+    KCHECK(launch_hermitian_verdict(st, c.s));
+    KCHECK(launch_twiddles(c.at<double2>(p.o_tab), p.mesh.N1, p.mesh.N2, p.mesh.N3, c.s));
+    KCHECK(launch_pack_basis((const double2*)H_R, c.at<int>(p.o_pairs), ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s));
+  }
+  return read_status(c);
+}
+
+Model make_model(const Call& c) {
+  Model md;
+  md.W = c.p.W;
+  md.N_R = c.p.N_R;
+  md.N_h = c.p.N_h;
+  md.K = c.p.K;
+  md.Bp = c.at<double>(c.p.o_Bp);
+  md.Rh = c.at<int>(c.p.o_Rh);
+  md.tab = c.at<double2>(c.p.o_tab);
+  md.tab_off[0] = 0;
+  md.tab_off[1] = c.p.mesh.N1;
+  md.tab_off[2] = c.p.mesh.N1 + c.p.mesh.N2;
+  return md;
+}
+
+EighBufs make_eigh_bufs(const Call& c) {
+  EighBufs b;
+  b.d = c.at<double>(c.p.o_d);
+  b.e = c.at<double>(c.p.o_e);
+  b.phase = c.at<double2>(c.p.o_ph);
+  b.refl = c.at<double2>(c.p.o_refl);
+  b.tau = c.at<double>(c.p.o_tau);
+  b.rot = c.at<double2>(c.p.o_rot);
+  b.rcol = c.at<short>(c.p.o_rcol);
+  b.nrot = c.at<int>(c.p.o_nrot);
+  b.perm = nullptr;
+  b.cap = c.p.cap;
+  return b;
+}
+
+// Steps (1)-(4) for one batch [t0, t0+n) of a k-list; E and U go to the chunk buffers, Omega
+// to Om (eta stride om_stride).  Eout may redirect the sorted eigenvalues.
+kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
+                      int64_t om_stride) {
+  Plan& p = c.p;
+  double* Hp = c.at<double>(p.o_Hp);
+  double* Xp = c.at<double>(p.o_Xp);
+  double* Yp = c.at<double>(p.o_Yp);
+  EighBufs eb = make_eigh_bufs(c);
+  DevStatus* st = c.at<DevStatus>(p.o_status);
+  double2* U = c.at<double2>(p.o_U);
+  {
+    StageTimer tm(c, KUBO_STAGE_FOURIER, 1);
+    KCHECK(launch_fourier_fp64(md, p.mesh, kl, Hp, Xp, Yp, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
+    KCHECK(launch_tridiag(Hp, p.W, kl.n, eb, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_QL, 1);
+    KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
+    KCHECK(launch_backtransform(p.W, kl.n, eb, Eout, U, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_BERRY, 1);
+    KCHECK(launch_berry_fp64(Eout, U, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+  }
+  return KUBO_OK;
+}
+
+kubo_status upload_etas(Call& c, const kubo_options& o, double eta) {
+  double h[MAX_ETA] = {0};
+  if (o.n_eta > 0) for (int e = 0; e < o.n_eta; ++e) h[e] = o.etas[e];
+  else h[0] = eta;
+  KCHECK(cudaMemcpyAsync(c.at<double>(c.p.o_etas), h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+  return KUBO_OK;
+}
+
+// Shared body of kubo_ahc and kubo_ahc_host (device pointers by now).
+kubo_status ahc_device(Call& c, const kubo_options& o, const double* H_R, const RInfo& ri,
+                       const double* E_F, double eta, double* out, int64_t kb, int64_t ke) {
+  Plan& p = c.p;
+  kubo_status r = upload_etas(c, o, eta);
+  if (r != KUBO_OK) return r;
+  r = prepare_model(c, H_R, ri);
+  if (r != KUBO_OK) return r;
+  const int n_out = p.n_eta * p.n_EF;
+  KCHECK(cudaMemsetAsync(c.at<char>(p.o_acc), 0, sizeof(double2) * n_out, c.s));
+  const Model md = make_model(c);
+  double* E = c.at<double>(p.o_E);
+  double* Om = c.at<double>(p.o_Om);
+  double2* part = c.at<double2>(p.o_part);
+  double2* acc = c.at<double2>(p.o_acc);
+  for (int64_t base = kb; base < ke; base += p.chunk) {
+    KList kl{nullptr, base, (int)std::min<int64_t>(p.chunk, ke - base)};
+    r = run_batch(c, md, kl, E, Om, (int64_t)kl.n * p.W);
+    if (r != KUBO_OK) return r;
+    StageTimer tm(c, KUBO_STAGE_KSUM, 2);
+    KCHECK(launch_ksum_partial(E, Om, p.W, kl.n, p.n_eta, (int64_t)kl.n * p.W, E_F, p.n_EF, o.kT, part, KSUM_KPB, c.s));
+    KCHECK(launch_ksum_fold(part, (kl.n + KSUM_KPB - 1) / KSUM_KPB, n_out, acc, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_KSUM, 1);
+    KCHECK(launch_ksum_final(acc, n_out, 1.0 / (double)p.mesh.Nk, c.at<DevStatus>(p.o_status), out, c.s));
+  }
+  return read_status(c);
+}
+
+kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int W, int N_R,
+                      const int32_t* kmesh, int n_EF, RInfo& ri, int64_t& kb, int64_t& ke,
+                      bool host_io) {
+  int n_eta = 1;
+  kubo_status r = validate_common(W, N_R, kmesh, o, n_eta);
+  if (r != KUBO_OK) return r;
+  if (!R_vecs || n_EF < 1) return KUBO_ERR_INVALID_ARG;
+  r = analyze_R(R_vecs, N_R, ri);
+  if (r != KUBO_OK) return r;
+  Plan& p = c.p;
+  p.W = W; p.N_R = N_R; p.N_h = ri.N_h; p.K = N_R; p.n_EF = n_EF; p.n_eta = n_eta;
+  p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
+  kb = o.k_begin; ke = o.k_end;
+  if (kb == 0 && ke == 0) ke = p.mesh.Nk;
+  if (kb < 0 || ke > p.mesh.Nk || kb > ke) return KUBO_ERR_INVALID_ARG;
+  p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
+  p.cap = rot_capacity(W);
+  p.model = p.eigh = p.berry = p.ksum = true;
+  plan_layout(p, host_io, 0);
+  c.s = (cudaStream_t)o.stream;
+  c.prof = o.profile;
+  return KUBO_OK;
+}
+
+}  // namespace
+
+// ====================================================================== public ABI
+extern "C" {
+
+void kubo_options_init(kubo_options* opt) {
+  if (opt) *opt = defaults();
+}
+
+const char* kubo_status_string(kubo_status s) {
+  switch (s) {
+    case KUBO_OK: return "KUBO_OK";
+    case KUBO_ERR_INVALID_ARG: return "KUBO_ERR_INVALID_ARG: invalid argument";
+    case KUBO_ERR_NOT_HERMITIAN: return "KUBO_ERR_NOT_HERMITIAN: H(-R) != H(R)^dagger or non-finite H(R)";
+    case KUBO_ERR_R_NOT_CLOSED: return "KUBO_ERR_R_NOT_CLOSED: R set not closed under -R, missing R=0, or duplicate R";
+    case KUBO_ERR_UNSUPPORTED: return "KUBO_ERR_UNSUPPORTED: size or precision not supported by this build";
+    case KUBO_ERR_OOM: return "KUBO_ERR_OOM: device allocation failed";
+    case KUBO_ERR_CUDA: return "KUBO_ERR_CUDA: CUDA runtime error";
+    case KUBO_ERR_NO_CONVERGENCE: return "KUBO_ERR_NO_CONVERGENCE: eigensolver iteration cap reached";
+    case KUBO_ERR_WORKSPACE: return "KUBO_ERR_WORKSPACE: workspace smaller than kubo_workspace_size()";
+  }
+  return "KUBO_ERR_UNKNOWN";
+}
+
+int kubo_max_orbitals(int precision) { return precision == KUBO_FP64 ? MAX_W : 0; }
+
+size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
+                           const kubo_options* opt) {
+  kubo_options o = opt ? *opt : defaults();
+  int n_eta = 1;
+  if (validate_common(W, N_R, kmesh, o, n_eta) != KUBO_OK || n_EF < 1) return 0;
+  Plan p;
+  p.W = W; p.N_R = N_R; p.N_h = (N_R - 1) / 2; p.K = N_R; p.n_EF = n_EF; p.n_eta = n_eta;
+  p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
+  int64_t kb = o.k_begin, ke = o.k_end;
+  if (kb == 0 && ke == 0) ke = p.mesh.Nk;
+  p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
+  p.cap = rot_capacity(W);
+  p.model = p.eigh = p.berry = p.ksum = true;
+  plan_layout(p, false, 0);
+  return p.total;
+}
+
+kubo_status kubo_ahc(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                     const int32_t* kmesh, const double* E_F, int n_EF, double eta, double* out,
+                     const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!H_R || !E_F || !out) return KUBO_ERR_INVALID_ARG;
+    if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
+    Call c;
+    RInfo ri;
+    int64_t kb, ke;
+    kubo_status r = setup_ahc(c, o, R_vecs, W, N_R, kmesh, n_EF, ri, kb, ke, false);
+    if (r != KUBO_OK) return r;
+    r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    r = ahc_device(c, o, H_R, ri, E_F, eta, out, kb, ke);
+    c.release();
+    if (r == KUBO_OK && cudaStreamSynchronize(c.s) != cudaSuccess) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (const std::bad_alloc&) {
+    return KUBO_ERR_OOM;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_ahc_host(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                          const int32_t* kmesh, const double* E_F, int n_EF, double eta,
+                          double* out, const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!H_R || !E_F || !out) return KUBO_ERR_INVALID_ARG;
+    if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
+    Call c;
+    RInfo ri;
+    int64_t kb, ke;
+    kubo_status r = setup_ahc(c, o, R_vecs, W, N_R, kmesh, n_EF, ri, kb, ke, true);
+    if (r != KUBO_OK) return r;
+    r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    const Plan& p = c.p;
+    const size_t hr_bytes = sizeof(double2) * (size_t)N_R * W * W;
+    if (cudaMemcpyAsync(c.at<char>(p.o_HR), H_R, hr_bytes, cudaMemcpyHostToDevice, c.s) != cudaSuccess ||
+        cudaMemcpyAsync(c.at<char>(p.o_EF), E_F, sizeof(double) * n_EF, cudaMemcpyHostToDevice, c.s) != cudaSuccess) {
+      cudaGetLastError();
+      c.release();
+      return KUBO_ERR_CUDA;
+    }
+    r = ahc_device(c, o, c.at<double>(p.o_HR), ri, c.at<double>(p.o_EF), eta, c.at<double>(p.o_out), kb, ke);
+    if (r == KUBO_OK) {
+      if (cudaMemcpyAsync(out, c.at<double>(p.o_out), sizeof(double) * p.n_eta * n_EF, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+          cudaStreamSynchronize(c.s) != cudaSuccess) {
+        cudaGetLastError();
+        r = KUBO_ERR_CUDA;
+      }
+    }
+    c.release();
+    if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (const std::bad_alloc&) {
+    return KUBO_ERR_OOM;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                       const int32_t* kmesh, const int64_t* kidx, int64_t n_k, double eta,
+                       double* E, double* Omega, const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!H_R || !kidx || !E || !Omega || n_k < 1) return KUBO_ERR_INVALID_ARG;
+    if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
+    o.k_begin = o.k_end = 0;
+    Call c;
+    RInfo ri;
+    int64_t kb, ke;
+    kubo_status r = setup_ahc(c, o, R_vecs, W, N_R, kmesh, 1, ri, kb, ke, false);
+    if (r != KUBO_OK) return r;
+    // per-k mode: no k-sum, batches over the list
+    Plan& p = c.p;
+    p.ksum = false;
+    p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, p.n_eta, n_k);
+    plan_layout(p, false, 0);
+    r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    r = upload_etas(c, o, eta);
+    if (r == KUBO_OK) r = prepare_model(c, H_R, ri);
+    if (r == KUBO_OK) {
+      const Model md = make_model(c);
+      for (int64_t t0 = 0; t0 < n_k && r == KUBO_OK; t0 += p.chunk) {
+        KList kl{kidx + t0, 0, (int)std::min<int64_t>(p.chunk, n_k - t0)};
+        r = run_batch(c, md, kl, E + t0 * W, Omega + t0 * W, n_k * W);
+      }
+      if (r == KUBO_OK) r = read_status(c);
+    }
+    c.release();
+    if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (const std::bad_alloc&) {
+    return KUBO_ERR_OOM;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                       const int32_t* kmesh, const int64_t* kidx, int64_t n_k, double* Hk,
+                       double* dHx, double* dHy, const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!H_R || !kidx || !Hk || !dHx || !dHy || n_k < 1) return KUBO_ERR_INVALID_ARG;
+    int n_eta = 1;
+    kubo_status r = validate_common(W, N_R, kmesh, o, n_eta);
+    if (r != KUBO_OK) return r;
+    if (!R_vecs) return KUBO_ERR_INVALID_ARG;
+    RInfo ri;
+    r = analyze_R(R_vecs, N_R, ri);
+    if (r != KUBO_OK) return r;
+    Call c;
+    Plan& p = c.p;
+    p.W = W; p.N_R = N_R; p.N_h = ri.N_h; p.K = N_R; p.n_EF = 1; p.n_eta = 1;
+    p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
+    p.chunk = 0;
+    p.model = true;
+    plan_layout(p, false, 0);
+    c.s = (cudaStream_t)o.stream;
+    c.prof = o.profile;
+    r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    r = prepare_model(c, H_R, ri);
+    if (r == KUBO_OK) {
+      const Model md = make_model(c);
+      const size_t WW = (size_t)W * W;
+      const int64_t step = 1 << 19;   // keeps grid.y = step / 16 within 65535
+      for (int64_t t0 = 0; t0 < n_k && r == KUBO_OK; t0 += step) {
+        KList kl{kidx + t0, 0, (int)std::min<int64_t>(step, n_k - t0)};
+        if (launch_fourier_fp64(md, p.mesh, kl, Hk + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, c.s) != cudaSuccess) {
+          cudaGetLastError();
+          r = KUBO_ERR_CUDA;
+        }
+      }
+      if (r == KUBO_OK) r = read_status(c);
+    }
+    c.release();
+    if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_eigh_batched(const double* A, int W, int64_t n, double* E, double* U,
+                              const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!A || !E || n < 1 || W < 1) return KUBO_ERR_INVALID_ARG;
+    if (W > MAX_W) return KUBO_ERR_UNSUPPORTED;
+    Call c;
+    Plan& p = c.p;
+    p.W = W; p.n_eta = 1; p.n_EF = 1;
+    p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, 1, n);
+    p.cap = rot_capacity(W);
+    p.eigh = true;
+    plan_layout(p, false, 0);
+    c.s = (cudaStream_t)o.stream;
+    kubo_status r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    if (cudaMemsetAsync(c.at<char>(p.o_status), 0, sizeof(DevStatus), c.s) != cudaSuccess) r = KUBO_ERR_CUDA;
+    EighBufs eb = make_eigh_bufs(c);
+    DevStatus* st = c.at<DevStatus>(p.o_status);
+    const size_t WW = (size_t)W * W;
+    for (int64_t t0 = 0; t0 < n && r == KUBO_OK; t0 += p.chunk) {
+      int nn = (int)std::min<int64_t>(p.chunk, n - t0);
+      if (launch_tridiag(A + t0 * WW, W, nn, eb, c.s) != cudaSuccess ||
+          launch_ql(W, nn, eb, st, c.s) != cudaSuccess ||
+          launch_backtransform(W, nn, eb, E + t0 * W, U ? (double2*)U + t0 * WW : nullptr, c.s) != cudaSuccess) {
+        cudaGetLastError();
+        r = KUBO_ERR_CUDA;
+      }
+    }
+    if (r == KUBO_OK) r = read_status(c);
+    c.release();
+    if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_berry_batched(const double* E, const double* U, const double* dHx,
+                               const double* dHy, int W, int64_t n, double eta, double* Omega,
+                               const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!E || !U || !dHx || !dHy || !Omega || n < 1 || W < 1) return KUBO_ERR_INVALID_ARG;
+    if (W > MAX_W) return KUBO_ERR_UNSUPPORTED;
+    if (o.n_eta > MAX_ETA) return KUBO_ERR_UNSUPPORTED;
+    if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
+    for (int e = 0; e < o.n_eta; ++e)
+      if (!o.etas || !finite_nonneg(o.etas[e])) return KUBO_ERR_INVALID_ARG;
+    Call c;
+    Plan& p = c.p;
+    p.W = W; p.n_eta = o.n_eta > 0 ? o.n_eta : 1; p.n_EF = 1;
+    plan_layout(p, false, 0);
+    c.s = (cudaStream_t)o.stream;
+    kubo_status r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    r = upload_etas(c, o, eta);
+    const size_t WW = (size_t)W * W;
+    const int64_t step = 1 << 30;
+    for (int64_t t0 = 0; t0 < n && r == KUBO_OK; t0 += step) {
+      int nn = (int)std::min<int64_t>(step, n - t0);
+      if (launch_berry_fp64(E + t0 * W, (const double2*)U + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, W, nn,
+                            c.at<double>(p.o_etas), p.n_eta, Omega + t0 * W, n * W, c.s) != cudaSuccess) {
+        cudaGetLastError();
+        r = KUBO_ERR_CUDA;
+      }
+    }
+    c.release();
+    if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations shared by the CUDA translation units of libkubo.
+// Nothing here is part of the public ABI (see include/kubo.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kubo.h"
+
+namespace kubo {
+
+// ---------------------------------------------------------------- device status word
+// Bits OR-ed into the status word by kernels; read back by the host at the end of a call.
+enum : unsigned {
+  ST_NOT_HERMITIAN = 1u,   // H(-R) != H(R)^dagger beyond tolerance
+  ST_NONFINITE = 2u,       // NaN/Inf in H(R)
+  ST_NO_CONVERGENCE = 4u,  // QL iteration cap reached at some k
+  ST_LOG_OVERFLOW = 8u,    // rotation log capacity exceeded at some k
+};
+
+struct DevStatus {
+  unsigned int bits;
+  unsigned int pad;
+  unsigned long long herm_dev_bits;  // max |H(-R)_ji - conj H(R)_ij| as double bits
+  unsigned long long herm_max_bits;  // max |H(R)_ij| as double bits
+  unsigned long long pad2;
+};
+
+// ---------------------------------------------------------------- batch of k-points
+// Local index t of a batch maps to the linear mesh index idx[t] (list) or base + t (range).
+struct KList {
+  const int64_t* idx;
+  int64_t base;
+  int n;
+};
+
+__device__ __forceinline__ int64_t klist_get(const KList& l, int t) {
+  return l.idx ? l.idx[t] : l.base + t;
+}
+
+struct Mesh {
+  int N1, N2, N3;
+  int64_t Nk;
+};
+
+// ---------------------------------------------------------------- prepared model (device)
+// H(k) = P0 + sum_h [cos(th_h) A_h + sin(th_h) B_h]
+// d_a H(k) = sum_h R_h,a [cos(th_h) B_h - sin(th_h) A_h]
+// with A_h = H(R_h) + H(-R_h), B_h = i (H(R_h) - H(-R_h)) over the canonical half set
+// (first non-zero component of R_h positive).  Rows of Bp: 0 -> P0, 1+2h -> A_h, 2+2h -> B_h,
+// each packed Hermitian (W*W doubles).
+struct Model {
+  int W, N_R, N_h, K;
+  const double* Bp;       // [K][W*W]
+  const int* Rh;          // [N_h][3]
+  const double2* tab;     // twiddles: tab[tab_off[a] + j] = e^{2 pi i j / N_a}
+  int tab_off[3];
+};
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+
+// e^{i k.R} from per-axis twiddle tables with exact integer argument reduction.
+__device__ __forceinline__ double2 mesh_phase(const double2* __restrict__ tab, const int* off,
+                                              const Mesh& m, int j1, int j2, int j3, int r1,
+                                              int r2, int r3) {
+  int a1 = (int)(((long long)j1 * r1) % m.N1); if (a1 < 0) a1 += m.N1;
+  int a2 = (int)(((long long)j2 * r2) % m.N2); if (a2 < 0) a2 += m.N2;
+  int a3 = (int)(((long long)j3 * r3) % m.N3); if (a3 < 0) a3 += m.N3;
+  double2 p = cmul(tab[off[0] + a1], tab[off[1] + a2]);
+  return cmul(p, tab[off[2] + a3]);
+}
+
+__device__ __forceinline__ void mesh_coords(const Mesh& m, int64_t k, int& j1, int& j2, int& j3) {
+  j3 = (int)(k % m.N3);
+  int64_t q = k / m.N3;
+  j2 = (int)(q % m.N2);
+  j1 = (int)(q / m.N2);
+}
+
+// ---------------------------------------------------------------- eigensolver buffers
+// Per-k intermediate layout of the three eigensolver kernels (all device memory).
+struct EighBufs {
+  double* d;        // [n][W]  diagonal of the real tridiagonal T; later eigenvalues
+  double* e;        // [n][W]  off-diagonal |beta_i| (e[W-1] unused)
+  double2* phase;   // [n][W]  D of T_complex = D T D^dagger
+  double2* refl;    // [n][W*W] Householder vectors v_i stored in column i, rows i+1..W-1
+  double* tau;      // [n][W]
+  double2* rot;     // [n][cap] Givens rotations (c, s) of the QL sweeps
+  short* rcol;      // [n][cap] column index i of each rotation (acts on columns i, i+1)
+  int* nrot;        // [n] number of rotations logged
+  int* perm;        // [n][W] ascending order of eigenvalues
+  int cap;
+};
+
+// ---------------------------------------------------------------- launchers
+// All launchers are asynchronous on `s` and return the launch error (cudaSuccess on success).
+cudaError_t launch_check_hermitian(const double2* H_R, const int* neg, int N_R, int W,
+                                   DevStatus* st, cudaStream_t s);
+cudaError_t launch_hermitian_verdict(DevStatus* st, cudaStream_t s);
+cudaError_t launch_pack_basis(const double2* H_R, const int* pairs, int idx0, int N_h, int W,
+                              double* Bp, cudaStream_t s);
+cudaError_t launch_twiddles(double2* tab, int N1, int N2, int N3, cudaStream_t s);
+
+cudaError_t launch_fourier_fp64(const Model& md, const Mesh& mesh, const KList& kl, double* Hp,
+                                double* Xp, double* Yp, cudaStream_t s);
+
+cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s);
+cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
+cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
+                                 cudaStream_t s);
+
+cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
+                              const double* Yp, int W, int n, const double* etas, int n_eta,
+                              double* Om, int64_t eta_stride, cudaStream_t s);
+
+cudaError_t launch_ksum_partial(const double* E, const double* Om, int W, int n, int n_eta,
+                                int64_t eta_stride, const double* E_F, int n_EF, double kT,
+                                double2* part, int k_per_block, cudaStream_t s);
+cudaError_t launch_ksum_fold(const double2* part, int n_blocks, int n_out, double2* acc,
+                             cudaStream_t s);
+cudaError_t launch_ksum_final(const double2* acc, int n_out, double inv_Nk,
+                              const DevStatus* st, double* out, cudaStream_t s);
+
+size_t tridiag_smem(int W);
+size_t backtransform_smem(int W);
+size_t ql_smem(int W);
+size_t berry_fp64_smem(int W, int n_eta);
+
+}  // namespace kubo
