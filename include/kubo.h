@@ -173,6 +173,33 @@ kubo_status kubo_berry_batched(const double* E, const double* U, const double* d
                                const double* dHy, int W, int64_t n, double eta,
                                double* Omega, const kubo_options* opt);
 
+/*
+ * Allocation-free batched eigensolver: the same computation and output layout as
+ * kubo_eigh_batched, for callers that cannot let a library allocate device memory during
+ * a call -- for example applications whose own allocator has reserved (nearly) all of the
+ * GPU's memory up front, where a cudaMalloc from inside the library would fail, and
+ * latency-critical loops in which cudaMalloc/cudaFree would synchronise the device.  The
+ * paper has no counterpart to this entry point.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its intermediates live
+ * in one fixed 32 MiB block of device memory compiled into the library (every GPU that
+ * loads the library holds that block until the process exits).  Limits:
+ *   - W <= 64; a larger W returns KUBO_ERR_UNSUPPORTED without launching anything.
+ *   - any n >= 1: the matrices are processed in passes of as many as fit in the block
+ *     (about 115 per pass at W = 64, about 1700 at W = 16).
+ * The first call on a device looks up the block's device address (once per device, with
+ * that device current); make that first call before any stream capture.  Every call
+ * shares the block and it keeps the previous call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU -- on different streams or from
+ * different host threads on the same device -- race and corrupt each other's results:
+ * serialise them.  The call returns after `stream` (a cudaStream_t; NULL = legacy default
+ * stream) has finished its work.
+ *   A  device, double [n][W*W] packed Hermitian;  E  device, double [n][W] ascending;
+ *   U  device, complex128 [n][W][W] (columns = eigenvectors), or NULL for eigenvalues only.
+ */
+kubo_status kubo_eigh_batched_noalloc(const double* A, int W, int64_t n, double* E, double* U,
+                                      void* stream);
+
 /* Device bytes of scratch a kubo_ahc / kubo_ahc_k call with these sizes needs. */
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
                            const kubo_options* opt);

@@ -1,0 +1,135 @@
+// Allocation-free variant of the batched Hermitian eigensolver entry point.
+//
+// Some callers cannot let a library allocate device memory during a call: applications
+// whose own allocator reserves (nearly) all of the GPU's memory up front, so a cudaMalloc
+// from inside the library fails or fragments their pool; and latency-critical loops in
+// which a cudaMalloc/cudaFree would synchronise the device and stall every other stream.
+// kubo_eigh_batched_noalloc serves them: its intermediates live in one fixed block of
+// device memory that is part of the library image itself (a file-scope __device__ array),
+// so the call performs no allocation of any kind.  It runs the same three kernels as
+// kubo_eigh_batched, over passes of as many matrices as fit in that block.
+#include <mutex>
+
+#include "kubo_internal.cuh"
+
+namespace kubo {
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)32 << 20;   // 32 MiB, held by every GPU that loads the library
+constexpr int kMaxW = 64;
+constexpr int kMaxDevices = 64;
+constexpr size_t kAlign = 256;
+
+static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
+
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int log_capacity(int W) { return 3 * W * W + 64; }
+
+// bytes of the block used by a pass of B matrices of order W (status word first)
+size_t pass_bytes(int W, int64_t B) {
+  const size_t cap = (size_t)log_capacity(W);
+  return align_up(sizeof(DevStatus)) + 3 * align_up(sizeof(double) * B * W) +
+         align_up(sizeof(double2) * B * W) + align_up(sizeof(double2) * B * W * W) +
+         align_up(sizeof(double2) * B * cap) + align_up(sizeof(short) * B * cap) +
+         align_up(sizeof(int) * B);
+}
+
+int64_t pass_capacity(int W) {
+  const size_t cap = (size_t)log_capacity(W);
+  const size_t per = sizeof(double) * 3 * W + sizeof(double2) * W + sizeof(double2) * W * W +
+                     (sizeof(double2) + sizeof(short)) * cap + sizeof(int);
+  int64_t B = (int64_t)(kScratchBytes / per);
+  while (B > 0 && pass_bytes(W, B) > kScratchBytes) --B;
+  return B;
+}
+
+// Device address of the block on the current device, looked up once per device with that
+// device current (the host-side symbol is only a stand-in and must never reach a kernel).
+kubo_status scratch_address(char** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return KUBO_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return KUBO_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return KUBO_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = (char*)g_scratch_addr[dev];
+  return KUBO_OK;
+}
+
+}  // namespace
+}  // namespace kubo
+
+using namespace kubo;
+
+extern "C" kubo_status kubo_eigh_batched_noalloc(const double* A, int W, int64_t n, double* E,
+                                                 double* U, void* stream) {
+  try {
+    if (!A || !E || n < 1 || W < 1) return KUBO_ERR_INVALID_ARG;
+    if (W > kMaxW) return KUBO_ERR_UNSUPPORTED;   // beyond the block's and the kernels' limit
+    const int64_t B = pass_capacity(W);
+    if (B < 1) return KUBO_ERR_UNSUPPORTED;
+    char* base = nullptr;
+    kubo_status r = scratch_address(&base);
+    if (r != KUBO_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // carve the block for a pass of B matrices
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base + off; off += align_up(bytes); return p; };
+    const size_t cap = (size_t)log_capacity(W);
+    DevStatus* st = (DevStatus*)take(sizeof(DevStatus));
+    EighBufs b;
+    b.d = (double*)take(sizeof(double) * B * W);
+    b.e = (double*)take(sizeof(double) * B * W);
+    b.tau = (double*)take(sizeof(double) * B * W);
+    b.phase = (double2*)take(sizeof(double2) * B * W);
+    b.refl = (double2*)take(sizeof(double2) * B * W * W);
+    b.rot = (double2*)take(sizeof(double2) * B * cap);
+    b.rcol = (short*)take(sizeof(short) * B * cap);
+    b.nrot = (int*)take(sizeof(int) * B);
+    b.perm = nullptr;
+    b.cap = (int)cap;
+
+    // the block keeps the previous call's contents: the status word must start at zero;
+    // every other buffer is fully written before it is read
+    if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) {
+      cudaGetLastError();
+      return KUBO_ERR_CUDA;
+    }
+    const size_t WW = (size_t)W * W;
+    for (int64_t t0 = 0; t0 < n; t0 += B) {
+      const int nn = (int)(n - t0 < B ? n - t0 : B);
+      if (launch_tridiag(A + t0 * WW, W, nn, b, s) != cudaSuccess ||
+          launch_ql(W, nn, b, st, s) != cudaSuccess ||
+          launch_backtransform(W, nn, b, E + t0 * W, U ? (double2*)U + t0 * WW : nullptr, s) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        return KUBO_ERR_CUDA;
+      }
+    }
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return KUBO_ERR_CUDA;
+    }
+    if (h.bits & (ST_NO_CONVERGENCE | ST_LOG_OVERFLOW)) return KUBO_ERR_NO_CONVERGENCE;
+    return KUBO_OK;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
