@@ -44,6 +44,7 @@ def stage_flops(W, N_R):
         "berry": 24.0 * W ** 3,           # two Hermitian rotations U^H dH U
         "ksum": 2.0 * W * 64,
         "prep": 0.0,
+        "fixup": 0.0,
     }
 
 
@@ -53,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kubo", choices=["kubo", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--planes", type=int, default=4, help="k_1-planes of the 128^3 mesh per step")
     ap.add_argument("--cpu-sample", type=int, default=768, help="k-points for the CPU oracle baseline")
     ap.add_argument("--chunk", type=int, default=0, help="k-points per internal batch (0 = auto)")
@@ -162,6 +163,14 @@ def cpu_baseline(model, kmesh, E_F, eta, kT, n):
             "sample": f"{n} seeded random k-points of the 128^3 mesh ({dt:.1f} s), numpy/LAPACK FP64"}
 
 
+def stage_table(st, fl, k_total):
+    tot = max(1e-9, sum(x["ms"] for x in st.values()))
+    return {s: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / tot, 4),
+                "tflops": round(fl[s] * k_total / (v["ms"] / 1e3) / 1e12, 4)
+                if v["ms"] > 0 and fl[s] > 0 else None}
+            for s, v in st.items()}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -185,43 +194,51 @@ def main():
     k_per_step = args.planes * plane
     H = torch.from_numpy(model.H_R).to(dev)
     EF = torch.from_numpy(E_F).to(dev)
-    out = torch.empty((1, E_F.size), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
 
     def slab(step):
         s = (rank * (args.warmup + args.steps) + step) % n_slabs
         return (s * k_per_step, (s + 1) * k_per_step)
 
-    def one_step(step, prof=None):
-        flush.fill_(step & 0xFF)   # evict L2 (256 MiB > 135 MB) before every step
-        kubo.ahc(H, model.R, kmesh, EF, eta=eta, kT=kT, precision=args.precision,
-                 k_range=slab(step), out=out, profile=prof, chunk_k=args.chunk)
+    def timed(prec):
+        outs = []
+        def one_step(step, prof=None):
+            flush.fill_(step & 0xFF)   # evict L2 (256 MiB > 135 MB) before every step
+            o = torch.empty((1, E_F.size), dtype=torch.float64, device=dev)
+            kubo.ahc(H, model.R, kmesh, EF, eta=eta, kT=kT, precision=prec, k_range=slab(step),
+                     out=o, profile=prof, chunk_k=args.chunk)
+            return o
+        for s in range(args.warmup):
+            one_step(s)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        prof = kubo.Profile()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for s in range(args.steps):
+            outs.append(one_step(args.warmup + s, prof))
+        ev1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        d = prof.as_dict()
+        d["_fixup_k"] = int(prof.fixup_k)
+        return ms, d, clk, torch.cat(outs).cpu().numpy()
 
-    for s in range(args.warmup):
-        one_step(s)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    prof = kubo.Profile()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record()
-    for s in range(args.steps):
-        one_step(args.warmup + s, prof)
-    ev1.record()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = world * args.steps * k_per_step / (ms / 1e3)
+    res = {p: timed(p) for p in precisions}
 
-    # ---- end to end through the host-buffer entry point (pinned host memory)
+    # ---- end to end through the host-buffer entry point (pinned host memory), headline path
+    head = precisions[0]
     e2e = None
     if not args.no_e2e:
         H_pin = torch.from_numpy(model.H_R).pin_memory()
@@ -229,7 +246,7 @@ def main():
         h2d = H_pin.numel() * 16 + EF_pin.numel() * 8
         d2h = E_F.size * 8
         kubo.ahc_host(H_pin.numpy(), model.R, kmesh, EF_pin.numpy(), eta=eta, kT=kT,
-                      precision=args.precision, k_range=slab(0))
+                      precision=head, k_range=slab(0))
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -237,7 +254,7 @@ def main():
         for s in range(args.steps):
             flush.fill_(s & 0xFF)
             kubo.ahc_host(H_pin.numpy(), model.R, kmesh, EF_pin.numpy(), eta=eta, kT=kT,
-                          precision=args.precision, k_range=slab(args.warmup + s))
+                          precision=head, k_range=slab(args.warmup + s))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if dist:
@@ -245,44 +262,65 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         e2e = {"value": world * args.steps * k_per_step / dt, "unit": "k-points/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "precision": head}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    st = prof.as_dict()
     fl = stage_flops(model.W, model.N_R)
+    k_total = args.steps * k_per_step
+    paths = {}
+    fixup_k = {p: r[1].pop("_fixup_k") for p, r in res.items()}
+    for p, (ms, st, clk, outs) in res.items():
+        paths[p] = {"value": world * k_total / (ms / 1e3), "ms_per_step": ms / args.steps,
+                    "stages": stage_table(st, fl, k_total),
+                    "gpu_launches": int(sum(v["launches"] for v in st.values())), "clocks": clk}
+    ms, st, clk, outs = res[head]
     dom = max((s for s in st if st[s]["launches"] > 0), key=lambda s: st[s]["ms"])
     launches = st[dom]["launches"]
-    k_per_launch = args.steps * k_per_step / launches if dom != "prep" else 0
-    achieved = fl[dom] * k_per_launch / (st[dom]["ms"] / launches / 1e3) / 1e12 if launches else 0.0
+    k_per_launch = k_total / launches
+    achieved = fl[dom] * k_per_launch / (st[dom]["ms"] / launches / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk/SM (one DFMA warp instruction per 16 "
-                             "cycles, measured) x 2.07 GHz; measured DFMA loop 1.199 TFLOP/s"}
-    stages = {s: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                  "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in st.values())), 4),
-                  "tflops": round(fl[s] * args.steps * k_per_step / (v["ms"] / 1e3) / 1e12, 4)
-                  if v["ms"] > 0 and fl[s] > 0 else None}
-              for s, v in st.items()}
+                             "cycles, measured) x 2.07 GHz (derived; measured DFMA loop 1.199 TFLOP/s)"}
     line = {
-        "metric": METRIC, "value": value, "unit": "k-points/s", "n_gpus": world,
+        "metric": METRIC, "value": paths[head]["value"], "unit": "k-points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-slices(Ozaki)+f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded random TB model, tbgen.random_tb)",
         "config": {"workload": WORKLOAD, "W": model.W, "N_R": model.N_R, "kmesh": list(kmesh),
-                   "n_EF": int(E_F.size), "eta": eta, "precision": args.precision,
+                   "n_EF": int(E_F.size), "eta": eta, "precision": head,
                    "k_per_step": k_per_step, "chunk_k": args.chunk or "auto",
                    "parallelism": f"k-slabs x{world}",
                    "l2": "flushed (256 MiB write) before every step; per-step working set >> L2"},
         "roofline": roofline,
-        "stages": stages,
-        "gpu_launches": int(sum(v["launches"] for v in st.values())),
+        "stages": paths[head]["stages"],
+        "gpu_launches": paths[head]["gpu_launches"],
         "clocks": clk,
         "e2e": e2e,
     }
+    if "mixed" in res and "fp64" in res:
+        om, of = res["mixed"][3], res["fp64"][3]
+        rel = float(np.max(np.abs(om - of) / np.maximum(np.max(np.abs(of), axis=1, keepdims=True), 1e-300)))
+        tc = res["mixed"][1]["fourier"]
+        # 15 slice-pair products x 2 flops x padded K (1344) x padded 3 W^2 (12288) per k-point
+        issued = 15.0 * 2 * 1344 * 12288
+        line["mixed_vs_fp64"] = {
+            "speedup": paths["mixed"]["value"] / paths["fp64"]["value"],
+            "fixup_fraction": fixup_k["mixed"] / k_total,
+            "rel_err_max_over_steps": rel,
+            "fp64": {k: paths["fp64"][k] for k in ("value", "ms_per_step", "stages", "gpu_launches")},
+            "tensor_core_fourier": {
+                "useful_tflops": fl["fourier"] * k_total / (tc["ms"] / 1e3) / 1e12,
+                "issued_bf16_tflops": issued * k_total / (tc["ms"] / 1e3) / 1e12,
+                "bf16_peak_tflops_measured": 1930.6,
+                "note": "stage = coef_slice + fourier_tc (tcgen05, fixed-point BF16 slices, "
+                        "15 slice-pair products, exact FP32 block sums)"},
+        }
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(model, kmesh, E_F, eta, kT, args.cpu_sample)
     print(json.dumps(line))

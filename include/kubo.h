@@ -54,13 +54,17 @@ typedef enum {
   KUBO_ERR_OOM = 5,             /* device allocation failed */
   KUBO_ERR_CUDA = 6,            /* a CUDA runtime call failed */
   KUBO_ERR_NO_CONVERGENCE = 7,  /* eigensolver hit its iteration cap at some k-point */
-  KUBO_ERR_WORKSPACE = 8        /* caller workspace smaller than kubo_workspace_size() */
+  KUBO_ERR_WORKSPACE = 8,       /* caller workspace smaller than kubo_workspace_size() */
+  KUBO_ERR_TIMEOUT = 9          /* a bounded device-side wait (tensor-core pipeline) gave up */
 } kubo_status;
 
 typedef enum {
-  KUBO_FP64 = 0,   /* every step in FP64 */
-  KUBO_MIXED = 1   /* steps (1) and (3) on the tensor cores with split-BF16 operands and
-                      FP32 accumulation; eigensolver, denominators and k-sum in FP64 */
+  KUBO_FP64 = 0,            /* every step in FP64 */
+  KUBO_MIXED = 1,           /* step (1) on the tensor cores (fixed-point BF16 slices with exact
+                               FP32 block accumulation, ~40-bit result), step (3) in FP32;
+                               eigensolver, denominators, curvature sums and k-sum in FP64 */
+  KUBO_MIXED_FOURIER = 2,   /* error-budget mode: only step (1) mixed, step (3) in FP64 */
+  KUBO_MIXED_ROTATION = 3   /* error-budget mode: only step (3) mixed (FP32), step (1) in FP64 */
 } kubo_precision;
 
 /* Pipeline stages, for the optional per-stage timing in kubo_profile. */
@@ -72,7 +76,8 @@ enum {
   KUBO_STAGE_BACKTRANSFORM = 4, /* step (2): eigenvectors U = Q D Z */
   KUBO_STAGE_BERRY = 5,         /* steps (3)-(4) */
   KUBO_STAGE_KSUM = 6,          /* k-sum of Eq. 2 */
-  KUBO_N_STAGES = 7
+  KUBO_STAGE_FIXUP = 7,         /* mixed precision: FP64 redo of k-points with a level near E_F */
+  KUBO_N_STAGES = 8
 };
 
 /* Per-stage kernel launch counts and summed device time (CUDA events recorded on the call's
@@ -80,6 +85,7 @@ enum {
 typedef struct kubo_profile {
   int64_t launches[KUBO_N_STAGES];
   double ms[KUBO_N_STAGES];
+  int64_t fixup_k;          /* k-points re-evaluated in FP64 by the mixed-precision fix-up */
 } kubo_profile;
 
 typedef struct kubo_options {
@@ -96,6 +102,12 @@ typedef struct kubo_options {
   size_t workspace_bytes;
   int chunk_k;              /* k-points per internal batch; 0 = automatic */
   kubo_profile* profile;    /* non-NULL: accumulate per-stage launch counts and times */
+  double mixed_fixup_rel;   /* KUBO_MIXED / KUBO_MIXED_FOURIER, k-summed entry points; > 0
+                               enables an FP64 redo of every k-point with some
+                               |E_n - E_F| < rel * max_n |E_n| (occupations that a reduced-
+                               precision energy could flip) and of the 0.5 % of each batch with
+                               the largest ||Omega(k)||_inf (near-degenerate pairs).  <= 0 (the
+                               default) = no fix-up. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,

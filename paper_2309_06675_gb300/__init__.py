@@ -29,6 +29,10 @@ __all__ = [
 
 FP64 = 0
 MIXED = 1
+MIXED_FOURIER = 2     # error-budget mode: only the Fourier sum on the tensor cores
+MIXED_ROTATION = 3    # error-budget mode: only the rotations in FP32
+_PREC = {"fp64": FP64, "mixed": MIXED, "mixed_fourier": MIXED_FOURIER,
+         "mixed_rotation": MIXED_ROTATION}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libkubo.so")
 
@@ -36,6 +40,7 @@ _STATUS = {
     0: "KUBO_OK", 1: "KUBO_ERR_INVALID_ARG", 2: "KUBO_ERR_NOT_HERMITIAN",
     3: "KUBO_ERR_R_NOT_CLOSED", 4: "KUBO_ERR_UNSUPPORTED", 5: "KUBO_ERR_OOM",
     6: "KUBO_ERR_CUDA", 7: "KUBO_ERR_NO_CONVERGENCE", 8: "KUBO_ERR_WORKSPACE",
+    9: "KUBO_ERR_TIMEOUT",
 }
 
 
@@ -46,12 +51,13 @@ class KuboError(RuntimeError):
         self.name = _STATUS.get(code, str(code))
 
 
-STAGES = ("prep", "fourier", "tridiag", "ql", "backtransform", "berry", "ksum")
+STAGES = ("prep", "fourier", "tridiag", "ql", "backtransform", "berry", "ksum", "fixup")
 
 
 class Profile(ctypes.Structure):
     """Per-stage launch counts and device milliseconds (kubo_profile of include/kubo.h)."""
-    _fields_ = [("launches", ctypes.c_int64 * len(STAGES)), ("ms", ctypes.c_double * len(STAGES))]
+    _fields_ = [("launches", ctypes.c_int64 * len(STAGES)), ("ms", ctypes.c_double * len(STAGES)),
+                ("fixup_k", ctypes.c_int64)]
 
     def as_dict(self):
         return {s: {"launches": int(self.launches[i]), "ms": float(self.ms[i])}
@@ -71,6 +77,7 @@ class Options(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("chunk_k", ctypes.c_int),
         ("profile", ctypes.POINTER(Profile)),
+        ("mixed_fixup_rel", ctypes.c_double),
     ]
 
 
@@ -148,7 +155,7 @@ def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk
              workspace=None, keep=None, profile=None):
     o = Options()
     lib().kubo_options_init(ctypes.byref(o))
-    o.precision = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    o.precision = _PREC.get(precision, precision)
     if etas is not None:
         e = np.ascontiguousarray(np.asarray(etas, dtype=np.float64).ravel())
         if keep is not None:
@@ -169,7 +176,7 @@ def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk
 
 
 def max_orbitals(precision=FP64) -> int:
-    return int(lib().kubo_max_orbitals({"fp64": FP64, "mixed": MIXED}.get(precision, precision)))
+    return int(lib().kubo_max_orbitals(_PREC.get(precision, precision)))
 
 
 def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range=None,
@@ -178,7 +185,7 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
     keep = []
     o = Options()
     lib().kubo_options_init(ctypes.byref(o))
-    o.precision = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    o.precision = _PREC.get(precision, precision)
     if n_eta > 1:
         e = np.full(n_eta, 1e-3)
         keep.append(e)
@@ -193,7 +200,7 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
-        stream=None, chunk_k=0, workspace=None, out=None, profile=None):
+        stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
@@ -208,6 +215,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
         out = torch.empty((n_eta, n_EF), dtype=torch.float64, device=H_R.device)
     keep = []
     o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
+    o.mixed_fixup_rel = float(fixup_rel)
     code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                           W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                           _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),
@@ -257,15 +265,17 @@ def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None,
     return E, Om
 
 
-def bloch(H_R, R, kmesh, kidx, stream=None):
-    """Packed Hermitian H(k), d_x H(k), d_y H(k) [n_k, W*W] each (float64 CUDA)."""
+def bloch(H_R, R, kmesh, kidx, precision=FP64, stream=None):
+    """Packed Hermitian H(k), d_x H(k), d_y H(k) [n_k, W*W] each (float64 CUDA).
+
+    precision="mixed" evaluates the sum on the tensor cores (split-BF16, FP32 accumulation)."""
     torch = _torch()
     Rh = _host_int32(R, 3)
     km = _host_int32(kmesh)
     N_R, W = int(H_R.shape[0]), int(H_R.shape[1])
     n_k = int(kidx.numel())
     outs = [torch.empty((n_k, W * W), dtype=torch.float64, device=H_R.device) for _ in range(3)]
-    o = _options(stream=stream)
+    o = _options(precision=precision, stream=stream)
     code = lib().kubo_bloch(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                             W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                             _dev(kidx, torch.int64, "kidx"), n_k,

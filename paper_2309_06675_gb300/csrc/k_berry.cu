@@ -63,22 +63,93 @@ __device__ __forceinline__ void store_tile(double2* C, int W, int LD, int ty, in
     }
 }
 
-__device__ __forceinline__ void unpack_hermitian(const double* __restrict__ P, double2* A, int W,
+template <typename TIn>
+__device__ __forceinline__ void unpack_hermitian(const TIn* __restrict__ P, double2* A, int W,
                                                  int LD, int t) {
   for (int idx = t; idx < W * W; idx += NT) {
     int i = idx / W, j = idx % W;
     double2 a;
-    if (i < j) a = make_double2(P[i * W + j], P[j * W + i]);
-    else if (i > j) a = make_double2(P[j * W + i], -P[i * W + j]);
-    else a = make_double2(P[i * W + i], 0.0);
+    if (i < j) a = make_double2((double)P[i * W + j], (double)P[j * W + i]);
+    else if (i > j) a = make_double2((double)P[j * W + i], -(double)P[i * W + j]);
+    else a = make_double2((double)P[i * W + i], 0.0);
     A[i * LD + j] = a;
   }
 }
 
+// Curvature epilogue shared by both precisions.  Every pair is evaluated once (n < m) and
+// enters Omega_n with +T_nm and Omega_m with -T_nm, so the antisymmetry T_mn = -T_nm that
+// makes occupied-occupied pairs cancel holds exactly even when v is only Hermitian to FP32
+// rounding.  Per-thread row / column partials go to `red` (2 * n_eta * W * 16 doubles, may
+// alias sVx: a barrier separates the last read of sVx from the first write of red) and are
+// summed in a fixed order (deterministic).
+template <typename V>
+__device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[TM][TM],
+                                                   const double* sE, const double* sEta,
+                                                   int n_eta, double emax, int W, int LD, int ty,
+                                                   int tx, int t, double* red,
+                                                   double* __restrict__ Om, int64_t eta_stride,
+                                                   int64_t k) {
+  double num[TM][TM], d2[TM][TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int n = ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < TM; ++j) {
+      const int m = tx + 16 * j;
+      num[i][j] = 0.0;
+      d2[i][j] = -1.0;   // marks "no pair"
+      if (n < W && m < W && n < m) {
+        const V vx = sVx[n * LD + m];
+        num[i][j] = -2.0 * ((double)vx.y * (double)vy[i][j].x - (double)vx.x * (double)vy[i][j].y);
+        const double dE = sE[n] - sE[m];
+        d2[i][j] = dE * dE;
+      }
+    }
+  }
+  __syncthreads();
+  const double thr2 = (1e-12 * emax) * (1e-12 * emax);
+  for (int e = 0; e < n_eta; ++e) {
+    const double eta = sEta[e];
+    double rp[TM], cp[TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) { rp[i] = 0.0; cp[i] = 0.0; }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TM; ++j) {
+        if (d2[i][j] < 0.0) continue;
+        if (eta == 0.0 && d2[i][j] <= thr2) continue;
+        const double T = num[i][j] / fma(eta, eta, d2[i][j]);
+        rp[i] += T;
+        cp[j] -= T;
+      }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int n = ty + 16 * i;
+      if (n < W) red[((size_t)(e * W + n) * 2) * 16 + tx] = rp[i];
+      const int m = tx + 16 * i;
+      if (m < W) red[((size_t)(e * W + m) * 2 + 1) * 16 + ty] = cp[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = t; idx < n_eta * W; idx += NT) {
+    const int e = idx / W, n = idx % W;
+    const double* p = red + (size_t)idx * 2 * 16;
+    double sr = 0.0, sc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { sr += p[q]; sc += p[16 + q]; }
+    Om[e * eta_stride + k * W + n] = sr + sc;
+  }
+}
+
+// X and Y: packed Hermitian rows of leading dimension ld (FP64 rows of the FP64 Fourier
+// kernel, or FP32 rows of the tensor-core one).
+template <typename TIn>
 __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict__ E,
                                                         const double2* __restrict__ U,
-                                                        const double* __restrict__ Xp,
-                                                        const double* __restrict__ Yp, int W,
+                                                        const TIn* __restrict__ Xp,
+                                                        const TIn* __restrict__ Yp, int64_t ld,
+                                                        int W,
                                                         const double* __restrict__ etas,
                                                         int n_eta, double* __restrict__ Om,
                                                         int64_t eta_stride) {
@@ -87,7 +158,7 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
   double2* sU = sm;
   double2* sA = sU + W * LD;
   double2* sB = sA + W * LD;
-  double* red = (double*)sB;   // reused after the last product
+  double* red = (double*)sA;   // reused (sA and beyond) after the pair terms are formed
   __shared__ double sE[64];
   __shared__ double sEta[MAXE];
   __shared__ double s_emax;
@@ -97,7 +168,7 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
   const size_t WW = (size_t)W * W;
 
   for (int idx = t; idx < W * W; idx += NT) sU[(idx / W) * LD + idx % W] = U[k * WW + idx];
-  unpack_hermitian(Xp + k * WW, sA, W, LD, t);
+  unpack_hermitian(Xp + k * ld, sA, W, LD, t);
   for (int j = t; j < W; j += NT) sE[j] = E[k * W + j];
   if (t < n_eta) sEta[t] = etas[t];
   __syncthreads();
@@ -115,61 +186,150 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
   cgemm_tile<true>(sU, sA, W, LD, ty, tx, acc);         // v^x = U^H T
   __syncthreads();
   store_tile(sA, W, LD, ty, tx, acc);
-  unpack_hermitian(Yp + k * WW, sB, W, LD, t);
+  unpack_hermitian(Yp + k * ld, sB, W, LD, t);
   __syncthreads();
   cgemm_tile<false>(sB, sU, W, LD, ty, tx, acc);        // T = Y U
   __syncthreads();
   store_tile(sB, W, LD, ty, tx, acc);
   __syncthreads();
   cgemm_tile<true>(sU, sB, W, LD, ty, tx, acc);         // v^y = U^H T
-  __syncthreads();                                      // sB is free from here on
+  curvature_epilogue<double2>(sA, acc, sE, sEta, n_eta, s_emax, W, LD, ty, tx, t, red, Om,
+                              eta_stride, k);
+}
 
-  const double emax = s_emax;
-  double rp[MAXE][TM];
+// ------------------------------------------------------------------ mixed precision
+// The two rotations in FP32 on the FP32 pipe (64x the FP64 rate on GB300): operands U
+// (rounded from FP64) and the FP32 tensor-core Fourier output; the energy denominators,
+// the pair terms and the band sums stay FP64.
+template <bool ADJ>
+__device__ __forceinline__ void cgemm_tile_f32(const float2* __restrict__ A,
+                                               const float2* __restrict__ B, int W, int LD,
+                                               int ty, int tx, float2 (&acc)[TM][TM]) {
 #pragma unroll
-  for (int e = 0; e < MAXE; ++e)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int i = 0; i < TM; ++i) rp[e][i] = 0.0;
-#pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    int n = ty + 16 * i;
-    if (n >= W) continue;
-    double En = sE[n];
-#pragma unroll
-    for (int j = 0; j < TM; ++j) {
-      int m = tx + 16 * j;
-      if (m >= W || m == n) continue;
-      double2 vx = sA[n * LD + m];
-      double2 vy = acc[i][j];
-      double num = -2.0 * fma(vx.y, vy.x, -vx.x * vy.y);   // -2 Im(vx conj(vy))
-      double dE = En - sE[m];
-      double d2 = dE * dE;
-#pragma unroll
-      for (int e = 0; e < MAXE; ++e) {
-        if (e >= n_eta) break;
-        double eta = sEta[e];
-        if (eta == 0.0 && fabs(dE) <= 1e-12 * emax) continue;
-        rp[e][i] += num / fma(eta, eta, d2);
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < MAXE; ++e) {
-    if (e >= n_eta) break;
+    for (int j = 0; j < TM; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int q = 0; q < W; ++q) {
+    float2 a[TM], bb[TM];
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      int n = ty + 16 * i;
-      if (n < W) red[(e * W + n) * 16 + tx] = rp[e][i];
+      int r = ty + 16 * i;
+      float2 v = make_float2(0.f, 0.f);
+      if (r < W) {
+        if (ADJ) { v = A[q * LD + r]; v.y = -v.y; }
+        else v = A[r * LD + q];
+      }
+      a[i] = v;
     }
-  }
-  __syncthreads();
-  for (int idx = t; idx < n_eta * W; idx += NT) {
-    int e = idx / W, n = idx % W;
-    const double* p = red + (size_t)idx * 16;
-    double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) s += p[q];
-    Om[e * eta_stride + k * W + n] = s;
+    for (int j = 0; j < TM; ++j) {
+      int c = tx + 16 * j;
+      bb[j] = c < W ? B[q * LD + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TM; ++j) {
+        acc[i][j].x = fmaf(a[i].x, bb[j].x, acc[i][j].x);
+        acc[i][j].x = fmaf(-a[i].y, bb[j].y, acc[i][j].x);
+        acc[i][j].y = fmaf(a[i].x, bb[j].y, acc[i][j].y);
+        acc[i][j].y = fmaf(a[i].y, bb[j].x, acc[i][j].y);
+      }
+  }
+}
+
+__device__ __forceinline__ void store_tile_f32(float2* C, int W, int LD, int ty, int tx,
+                                               const float2 (&acc)[TM][TM]) {
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) {
+      int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < W && c < W) C[r * LD + c] = acc[i][j];
+    }
+}
+
+template <typename TIn>
+__device__ __forceinline__ void unpack_hermitian_f32(const TIn* __restrict__ P, float2* A, int W,
+                                                     int LD, int t) {
+  for (int idx = t; idx < W * W; idx += NT) {
+    int i = idx / W, j = idx % W;
+    float2 a;
+    if (i < j) a = make_float2((float)P[i * W + j], (float)P[j * W + i]);
+    else if (i > j) a = make_float2((float)P[j * W + i], -(float)P[i * W + j]);
+    else a = make_float2((float)P[i * W + i], 0.f);
+    A[i * LD + j] = a;
+  }
+}
+
+// X and Y: packed Hermitian rows of leading dimension ld.
+template <typename TIn>
+__global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restrict__ E,
+                                                         const double2* __restrict__ U,
+                                                         const TIn* __restrict__ Xp,
+                                                         const TIn* __restrict__ Yp, int64_t ld,
+                                                         int W, const double* __restrict__ etas,
+                                                         int n_eta, double* __restrict__ Om,
+                                                         int64_t eta_stride) {
+  extern __shared__ float2 smf[];
+  const int LD = W + 1;
+  float2* sU = smf;
+  float2* sA = sU + W * LD;
+  float2* sB = sA + W * LD;
+  double* red = (double*)(sB + W * LD);   // separate region (FP32 operands are small)
+  __shared__ double sE[64];
+  __shared__ double sEta[MAXE];
+  __shared__ double s_emax;
+
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int64_t k = blockIdx.x;
+  const size_t WW = (size_t)W * W;
+
+  for (int idx = t; idx < W * W; idx += NT) {
+    double2 u = U[k * WW + idx];
+    sU[(idx / W) * LD + idx % W] = make_float2((float)u.x, (float)u.y);
+  }
+  unpack_hermitian_f32(Xp + k * ld, sA, W, LD, t);
+  for (int j = t; j < W; j += NT) sE[j] = E[k * W + j];
+  if (t < n_eta) sEta[t] = etas[t];
+  __syncthreads();
+  if (t == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
+    s_emax = mx;
+  }
+
+  float2 acc[TM][TM];
+  cgemm_tile_f32<false>(sA, sU, W, LD, ty, tx, acc);   // T = X U
+  __syncthreads();
+  store_tile_f32(sA, W, LD, ty, tx, acc);
+  __syncthreads();
+  cgemm_tile_f32<true>(sU, sA, W, LD, ty, tx, acc);    // v^x = U^H T
+  __syncthreads();
+  store_tile_f32(sA, W, LD, ty, tx, acc);
+  unpack_hermitian_f32(Yp + k * ld, sB, W, LD, t);
+  __syncthreads();
+  cgemm_tile_f32<false>(sB, sU, W, LD, ty, tx, acc);   // T = Y U
+  __syncthreads();
+  store_tile_f32(sB, W, LD, ty, tx, acc);
+  __syncthreads();
+  cgemm_tile_f32<true>(sU, sB, W, LD, ty, tx, acc);    // v^y = U^H T
+  curvature_epilogue<float2>(sA, acc, sE, sEta, n_eta, s_emax, W, LD, ty, tx, t, red, Om,
+                             eta_stride, k);
+}
+
+__global__ void unpack_rows_kernel(const double* __restrict__ C, int64_t ld, int W, int n,
+                                   double* __restrict__ H, double* __restrict__ X,
+                                   double* __restrict__ Y) {
+  const int64_t WW = (int64_t)W * W;
+  const int64_t total = (int64_t)n * WW;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / WW, q = t % WW;
+    const double* r = C + k * ld;
+    H[t] = r[q];
+    X[t] = r[WW + q];
+    Y[t] = r[2 * WW + q];
   }
 }
 
@@ -177,18 +337,76 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
 
 size_t berry_fp64_smem(int W, int n_eta) {
   size_t mat = (size_t)W * (W + 1) * sizeof(double2);
-  size_t red = (size_t)n_eta * W * 16 * sizeof(double);
-  return 2 * mat + (mat > red ? mat : red);
+  size_t red = (size_t)n_eta * W * 2 * 16 * sizeof(double);
+  return mat + (2 * mat > red ? 2 * mat : red);
+}
+
+template <typename TIn>
+cudaError_t launch_berry_fp64_t(const double* E, const double2* U, const TIn* Xp, const TIn* Yp,
+                                int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
+                                int64_t eta_stride, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  size_t sm = berry_fp64_smem(W, n_eta);
+  cudaError_t e = cudaFuncSetAttribute(berry_fp64_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  berry_fp64_kernel<TIn><<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
                               const double* Yp, int W, int n, const double* etas, int n_eta,
                               double* Om, int64_t eta_stride, cudaStream_t s) {
+  return launch_berry_fp64_t<double>(E, U, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
+                                     eta_stride, s);
+}
+
+cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const double* C,
+                                   int64_t ld, int W, int n, const double* etas, int n_eta,
+                                   double* Om, int64_t eta_stride, cudaStream_t s) {
+  const int64_t WW = (int64_t)W * W;
+  return launch_berry_fp64_t<double>(E, U, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
+                                     eta_stride, s);
+}
+
+size_t berry_mixed_smem(int W, int n_eta) {
+  return 3 * (size_t)W * (W + 1) * sizeof(float2) + (size_t)n_eta * W * 2 * 16 * sizeof(double);
+}
+
+template <typename TIn>
+cudaError_t launch_berry_mixed_t(const double* E, const double2* U, const TIn* Xp, const TIn* Yp,
+                                 int64_t ld, int W, int n, const double* etas, int n_eta,
+                                 double* Om, int64_t eta_stride, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  size_t sm = berry_fp64_smem(W, n_eta);
-  cudaError_t e = cudaFuncSetAttribute(berry_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  size_t sm = berry_mixed_smem(W, n_eta);
+  cudaError_t e = cudaFuncSetAttribute(berry_mixed_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  berry_fp64_kernel<<<n, NT, sm, s>>>(E, U, Xp, Yp, W, etas, n_eta, Om, eta_stride);
+  berry_mixed_kernel<TIn><<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const double* C,
+                                    int64_t ld, int W, int n, const double* etas, int n_eta,
+                                    double* Om, int64_t eta_stride, cudaStream_t s) {
+  const int64_t WW = (int64_t)W * W;
+  return launch_berry_mixed_t<double>(E, U, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
+                                      eta_stride, s);
+}
+
+cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
+                                        const double* Yp, int W, int n, const double* etas,
+                                        int n_eta, double* Om, int64_t eta_stride,
+                                        cudaStream_t s) {
+  return launch_berry_mixed_t<double>(E, U, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
+                                      eta_stride, s);
+}
+
+cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,
+                               double* Y, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t total = (int64_t)n * W * W;
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 64) b = 152 * 64;
+  unpack_rows_kernel<<<(int)b, 256, 0, s>>>(C, ld, W, n, H, X, Y);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------ K2a: tridiagonalise
-__global__ void __launch_bounds__(NT) tridiag_kernel(const double* __restrict__ Hp, int W,
+// Packed rows of leading dimension ld (W*W for the FP64 Fourier kernel, the padded row of
+// H | dxH | dyH for the tensor-core one).  The reduction is FP64.
+template <typename T>
+__global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
                                                      EighBufs b) {
   extern __shared__ double2 smem2[];
   const int LDA = W + 1;
@@ -48,14 +51,14 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const double* __restrict__ 
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t k = blockIdx.x;
-  const double* P = Hp + (size_t)k * W * W;
+  const T* P = Hp + (size_t)k * ld;
 
   for (int idx = t; idx < W * W; idx += NT) {
     int i = idx / W, j = idx % W;
     double2 a;
-    if (i < j) a = make_double2(P[i * W + j], P[j * W + i]);
-    else if (i > j) a = make_double2(P[j * W + i], -P[i * W + j]);
-    else a = make_double2(P[i * W + i], 0.0);
+    if (i < j) a = make_double2((double)P[i * W + j], (double)P[j * W + i]);
+    else if (i > j) a = make_double2((double)P[j * W + i], -(double)P[i * W + j]);
+    else a = make_double2((double)P[i * W + i], 0.0);
     A[i * LDA + j] = a;
   }
   __syncthreads();
@@ -380,9 +383,19 @@ size_t ql_smem(int W) { return (size_t)2 * 2 * W * 32 * sizeof(double); }
 cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   size_t sm = tridiag_smem(W);
-  cudaError_t e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  tridiag_kernel<<<n, NT, sm, s>>>(Hp, W, b);
+  tridiag_kernel<double><<<n, NT, sm, s>>>(Hp, (int64_t)W * W, W, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  size_t sm = tridiag_smem(W);
+  cudaError_t e = cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  tridiag_kernel<double><<<n, NT, sm, s>>>(Hp, ld, W, b);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,497 @@
+// Step (1) of List 1/2 on the 5th-generation tensor cores.
+//
+// The three outputs of the Fourier sum share one real coefficient row per k-point,
+//   coef(k) = [cos th_0, sin th_0, cos th_1, sin th_1, ..., cos th_{N_h-1}, sin th_{N_h-1}, 1],
+// once the derivative weights are moved into the basis:
+//   H   = sum_h c_h A_h + s_h B_h + P0
+//   d_a H = sum_h c_h (R_h,a B_h) + s_h (-R_h,a A_h)
+// so the whole step is ONE dense contraction C[n_k x 3W^2] = Coef[n_k x N_R] . Basis[N_R x 3W^2]
+// with the stacked basis [B^H | B^X | B^Y].
+//
+// Arithmetic: fixed-point slicing (the Ozaki scheme) on BF16 MMAs.  Every coefficient
+// (|c| <= 1) and every basis entry (scaled by 2^-e_n, e_n the exponent of its column's
+// largest magnitude) is written as x = sum_{i<5} s_i 2^(-7-8i) with integer slices
+// |s_i| <= 128, exact in BF16.  A product of slices is an integer below 2^14, so the sum of one
+// 64-wide K block of all slice pairs of one level l = i + j (at most 5 pairs) stays an integer
+// below 2^24 and is EXACT in the FP32 tensor-memory accumulator, whatever rounding the tensor
+// core applies.  The epilogue converts each level to int32 (exact), accumulates the K blocks in
+// integers (exact), and combines the levels l <= 4 (15 slice pairs) in FP64:
+//   C = 2^e_n sum_l 2^(-14-8l) I_l.
+// The result carries ~40 significant bits relative to the operand scales (FP64 phases, FP64
+// basis), versus ~24 for a split-BF16 product with FP32 accumulation.
+//
+// Kernels:
+//   basis_scale_kernel  once per call: column exponents e_n of the stacked basis
+//   basis_slice_kernel  once per call: stacked basis -> Bt[5 slices][Npad][Kp] (K-major, bf16)
+//   coef_slice_kernel   per batch: FP64 phases with exact argument reduction -> A[5][Mpad][Kp]
+//   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, N=32, K=16), operands staged
+//                       by TMA (128-byte swizzle, 2-stage mbarrier pipeline), 5 level
+//                       accumulators x 2 buffers in TMEM, integer epilogue, FP64 rows in HBM.
+//
+// Every mbarrier wait is bounded; on timeout the CTA records ST_TIMEOUT, drains its own
+// copies (bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "kubo_internal.cuh"
+
+namespace kubo {
+
+namespace {
+
+constexpr int BM = 128;           // k-points per tile (UMMA M)
+constexpr int BN = 32;            // output columns per tile (UMMA N)
+constexpr int BK = 64;            // K per stage (one 128-byte swizzle row of bf16) = one exact chunk
+constexpr int NSTAGE = 2;
+constexpr int NSLICE = 5;         // slices per operand: 7 + 4 x 8 = 39 fractional bits
+constexpr int NLEVEL = 5;         // levels l = i + j <= 4 kept: 15 slice pairs
+constexpr int NPAIR = 15;
+constexpr int NACC = 2;           // level-accumulator sets in flight (double buffer)
+constexpr int TILE_A_BYTES = BM * BK * 2;            // 16 KB per slice
+constexpr int TILE_B_BYTES = BN * BK * 2;            // 4 KB per slice
+constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 100 KB
+constexpr int TC_THREADS = 192;                      // 6 warps
+constexpr int TMEM_COLS = 512;                       // >= NACC * NLEVEL * BN = 320, power of 2
+constexpr uint32_t WAIT_LIMIT = 1u << 26;
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row atoms of 1024 B.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                             // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                             // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                             // swizzle: 128 B
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 32.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Fixed-point slices of x (|x| <= 1): x = sum_i s_i 2^(-7-8i) + O(2^-47), |s_i| <= 128.
+// All operations are exact in FP64 (scaling by powers of two, subtracting integers).
+__device__ __forceinline__ void slice5(double x, __nv_bfloat16 (&sl)[NSLICE]) {
+  double r = x * 128.0;
+#pragma unroll
+  for (int i = 0; i < NSLICE; ++i) {
+    const double q = rint(r);
+    sl[i] = __float2bfloat16_rn((float)q);   // integer with |q| <= 128: exact in BF16
+    r = (r - q) * 256.0;
+  }
+}
+
+// ------------------------------------------------------------------ operand preparation
+// value of the stacked basis at (output column n < 3 W^2, K index k)
+__device__ __forceinline__ double stacked_basis(const double* __restrict__ Bp,
+                                                const int* __restrict__ Rh, int N_h, int WW, int n,
+                                                int k) {
+  const int alpha = n / WW, q = n % WW;
+  if (k < 2 * N_h) {
+    const int h = k >> 1;
+    const bool is_sin = k & 1;
+    const double Ah = Bp[(size_t)(1 + 2 * h) * WW + q];
+    const double Bh = Bp[(size_t)(2 + 2 * h) * WW + q];
+    if (alpha == 0) return is_sin ? Bh : Ah;
+    const double r = (double)Rh[3 * h + (alpha - 1)];
+    return is_sin ? -r * Ah : r * Bh;
+  }
+  if (k == 2 * N_h && alpha == 0) return Bp[q];
+  return 0.0;
+}
+
+// e[n]: exponent with max_k |basis(n, k)| < 2^e[n] (0 for an all-zero column)
+__global__ void basis_scale_kernel(const double* __restrict__ Bp, const int* __restrict__ Rh,
+                                   int N_h, int W, int Npad, int* __restrict__ e) {
+  const int WW = W * W;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < Npad; n += gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    if (n < 3 * WW)
+      for (int k = 0; k <= 2 * N_h; ++k) mx = fmax(mx, fabs(stacked_basis(Bp, Rh, N_h, WW, n, k)));
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);   // mx = f 2^ex, f in [0.5, 1)
+    e[n] = ex;
+  }
+}
+
+// Bt[s][n][k] (n < Npad rows, k < Kp contiguous): slices of basis(n, k) * 2^-e[n]
+__global__ void basis_slice_kernel(const double* __restrict__ Bp, const int* __restrict__ Rh,
+                                   const int* __restrict__ e, int N_h, int W, int Npad, int Kp,
+                                   __nv_bfloat16* __restrict__ Bt) {
+  const int WW = W * W;
+  const int64_t plane = (int64_t)Npad * Kp;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < plane;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t / Kp), k = (int)(t % Kp);
+    double v = 0.0;
+    if (n < 3 * WW && k <= 2 * N_h) v = ldexp(stacked_basis(Bp, Rh, N_h, WW, n, k), -e[n]);
+    __nv_bfloat16 sl[NSLICE];
+    slice5(v, sl);
+#pragma unroll
+    for (int i = 0; i < NSLICE; ++i) Bt[i * plane + t] = sl[i];
+  }
+}
+
+// A[s][m][k] for m < Mpad (rows >= n are zero), k < Kp.  One thread per (m, h).
+__global__ void coef_slice_kernel(Model md, Mesh mesh, KList kl, int Mpad, int Kp,
+                                  __nv_bfloat16* __restrict__ A) {
+  const int npair = Kp / 2;
+  const int64_t total = (int64_t)Mpad * npair;
+  const int64_t plane = (int64_t)Mpad * Kp;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t / npair), h = (int)(t % npair);
+    double c = 0.0, s = 0.0;
+    if (m < kl.n) {
+      if (h < md.N_h) {
+        int j1, j2, j3;
+        mesh_coords(mesh, klist_get(kl, m), j1, j2, j3);
+        const int* r = md.Rh + 3 * h;
+        const double2 e = mesh_phase(md.tab, md.tab_off, mesh, j1, j2, j3, r[0], r[1], r[2]);
+        c = e.x;
+        s = e.y;
+      } else if (h == md.N_h) {
+        c = 1.0;   // the R = 0 term (column 2 N_h); its partner column stays 0
+      }
+    }
+    __nv_bfloat16 cs[NSLICE], ss[NSLICE];
+    slice5(c, cs);
+    slice5(s, ss);
+    const int64_t o = (int64_t)m * Kp + 2 * h;
+#pragma unroll
+    for (int i = 0; i < NSLICE; ++i)
+      *reinterpret_cast<__nv_bfloat162*>(A + i * plane + o) = __halves2bfloat162(cs[i], ss[i]);
+  }
+}
+
+// slice pairs (i, j) with i + j <= 4, grouped by level l = i + j
+__constant__ int c_pi[NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+__constant__ int c_pj[NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+__constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4};
+
+// ------------------------------------------------------------------ the tcgen05 GEMM
+// grid: (Npad / BN, Mpad / BM); out: FP64 [n rows][ldc], rows >= n_rows not written.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                      const __grid_constant__ CUtensorMap mapB, const int* __restrict__ col_exp,
+                      int Mpad, int Npad, int nkb, int n_rows, double* __restrict__ out, int ldc,
+                      DevStatus* st) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t acc_full[NACC], acc_empty[NACC], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < NACC; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 128);   // every epilogue thread arrives
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  auto stageA = [&](int s, int sl) { return base + (size_t)s * STAGE_BYTES + (size_t)sl * TILE_A_BYTES; };
+  auto stageB = [&](int s, int sl) {
+    return base + (size_t)s * STAGE_BYTES + NSLICE * TILE_A_BYTES + (size_t)sl * TILE_B_BYTES;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % NSTAGE;
+        const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
+        if (abort_sh) break;
+        if (kb >= NSTAGE && !mbar_wait(&empty_bar[s], ph ^ 1u)) {
+          atomicOr(&st->bits, ST_TIMEOUT);
+          abort_sh = 1;
+          break;
+        }
+        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        for (int sl = 0; sl < NSLICE; ++sl)
+          tma_load_2d(stageA(s, sl), &mapA, &full_bar[s], kb * BK, sl * Mpad + m0);
+        for (int sl = 0; sl < NSLICE; ++sl)
+          tma_load_2d(stageB(s, sl), &mapB, &full_bar[s], kb * BK, sl * Npad + n0);
+        ++issued;
+      }
+      // drain: every issued stage's copies must have landed before the CTA may exit
+      for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % NSTAGE], (uint32_t)(kb / NSTAGE) & 1u);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: stage kb accumulates each level into accumulator set kb % NACC
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb && !abort_sh; ++kb) {
+        const int s = kb % NSTAGE;
+        const int a = kb % NACC;
+        if (kb >= NACC && !mbar_wait(&acc_empty[a], (uint32_t)(kb / NACC - 1) & 1u)) {
+          atomicOr(&st->bits, ST_TIMEOUT);
+          abort_sh = 1;
+          break;
+        }
+        if (!mbar_wait(&full_bar[s], (uint32_t)(kb / NSTAGE) & 1u)) {
+          atomicOr(&st->bits, ST_TIMEOUT);
+          abort_sh = 1;
+          break;
+        }
+        tc_fence_after();
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          int seen = 0;   // bit l set once level l has been written in this K block
+          for (int p = 0; p < NPAIR; ++p) {
+            const int l = c_pl[p];
+            const uint32_t acc = (kk > 0 || (seen >> l) & 1) ? 1u : 0u;
+            seen |= 1 << l;
+            const uint64_t da = umma_desc_sw128(smem_u32(stageA(s, c_pi[p])) + kk * 32);
+            const uint64_t db = umma_desc_sw128(smem_u32(stageB(s, c_pj[p])) + kk * 32);
+            umma_bf16(tmem + (uint32_t)((a * NLEVEL + l) * BN), da, db, acc);
+          }
+        }
+        umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
+        umma_commit(&acc_full[a]);    // level sums of this K block complete
+      }
+      umma_commit(&done_bar);         // all issued MMAs complete
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 own TMEM lanes 32 * (warp % 4) .. + 31
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int grow = m0 + row;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    // One exact integer per column: sum over K blocks and levels of I_l 2^(32 - 8 l).  A block's
+    // level sum is below 2^23 in magnitude, so the total stays below 2^57 (no overflow).
+    long long isum[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) isum[j] = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int a = kb % NACC;
+      ok = mbar_wait(&acc_full[a], (uint32_t)(kb / NACC) & 1u);
+      ok = __all_sync(0xffffffffu, ok && !abort_sh);   // tcgen05.ld is warp-collective
+      if (!ok) break;
+      tc_fence_after();
+#pragma unroll
+      for (int l = 0; l < NLEVEL; ++l) {
+        uint32_t r[32];
+        tmem_ld32(lane_addr + (uint32_t)((a * NLEVEL + l) * BN), r);
+#pragma unroll
+        for (int j = 0; j < BN; ++j)
+          isum[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[a]);
+    }
+    if (!ok) {
+      atomicOr(&st->bits, ST_TIMEOUT);
+      abort_sh = 1;
+    } else if (grow < n_rows) {
+      // C = 2^e_n * isum * 2^(-14 - 32): a power-of-two scale, exact apart from the final
+      // rounding of the 57-bit integer to FP64
+      double* dst = out + (size_t)grow * ldc + n0;
+#pragma unroll
+      for (int j = 0; j < BN; j += 2) {
+        const double s0 = __longlong_as_double((long long)(1023 - 46 + col_exp[n0 + j]) << 52);
+        const double s1 = __longlong_as_double((long long)(1023 - 46 + col_exp[n0 + j + 1]) << 52);
+        *reinterpret_cast<double2*>(dst + j) =
+            make_double2((double)isum[j] * s0, (double)isum[j + 1] * s1);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (lane == 0) mbar_wait(&done_bar, 0);   // no MMA may still be writing TMEM
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* map, const void* gptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+               uint32_t box_outer) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};   // bytes between rows
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(gptr), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int tc_pad_m(int n) { return (n + BM - 1) / BM * BM; }
+int tc_pad_n(int W) { return (3 * W * W + BN - 1) / BN * BN; }
+int tc_pad_k(int N_R) { return (N_R + BK - 1) / BK * BK; }
+int tc_slices() { return NSLICE; }
+size_t fourier_tc_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
+
+cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, int Npad, int Kp,
+                               int* col_exp, void* Bt, cudaStream_t s) {
+  basis_scale_kernel<<<grid_for(Npad, 128), 128, 0, s>>>(Bp, Rh, N_h, W, Npad, col_exp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  basis_slice_kernel<<<grid_for((int64_t)Npad * Kp, 256), 256, 0, s>>>(Bp, Rh, col_exp, N_h, W, Npad,
+                                                                        Kp, (__nv_bfloat16*)Bt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl, int Mpad, int Kp,
+                              void* A, cudaStream_t s) {
+  coef_slice_kernel<<<grid_for((int64_t)Mpad * (Kp / 2), 256), 256, 0, s>>>(md, mesh, kl, Mpad, Kp,
+                                                                             (__nv_bfloat16*)A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
+                              int Kp, int n_rows, double* out, int ldc, DevStatus* st,
+                              cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  if (Mpad % BM || Npad % BN || Kp % BK || ldc % 2) return cudaErrorInvalidValue;
+  CUtensorMap mA, mB;
+  if (!encode_2d(&mA, A, (uint64_t)Kp, (uint64_t)NSLICE * Mpad, BK, BM)) return cudaErrorInvalidValue;
+  if (!encode_2d(&mB, Bt, (uint64_t)Kp, (uint64_t)NSLICE * Npad, BK, BN)) return cudaErrorInvalidValue;
+  const size_t sm = fourier_tc_smem();
+  cudaError_t e = cudaFuncSetAttribute(fourier_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(Npad / BN, Mpad / BM);
+  fourier_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out,
+                                                 ldc, st);
+  return cudaGetLastError();
+}
+
+}  // namespace kubo

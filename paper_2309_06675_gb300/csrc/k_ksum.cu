@@ -1,6 +1,8 @@
 // k-sum of Eq. 2 (with Eq. 4's batching): S(E_F) = (1/N_k) sum_k sum_n occ(E_n(k)) Omega_n(k)
 // for every (eta, E_F) pair.  Deterministic: every block sums a fixed k-range in order with
 // Neumaier compensation, blocks are folded in index order, batches in call order.
+#include <algorithm>
+
 #include "kubo_internal.cuh"
 
 namespace kubo {
@@ -64,6 +66,111 @@ __global__ void ksum_final_kernel(const double2* __restrict__ acc, int n_out, do
     out[o] = (acc[o].x + acc[o].y) * inv_Nk;
 }
 
+// ------------------------------------------------------------------ mixed-precision fix-up
+// Two kinds of k-point carry most of the mixed path's error and are redone in FP64:
+//  * a level within tau_k = rel * max_n |E_n(k)| of some Fermi level (its occupation could
+//    flip under the FP32-level energy error);
+//  * the spiky tail: ||Omega(k)||_inf among the largest `frac` of the batch (near-degenerate
+//    pairs, whose curvature error ~ |Omega| dE / gap dominates the k-sum).
+// Pass 1 (this kernel): per k the near-E_F flag and the bin of log2 ||Omega(k)||_inf.
+constexpr int NBIN = 512;            // quarter-octave bins of log2 |Omega|
+constexpr int BIN_OFFSET = 256;      // bin of |Omega| = 1
+
+__global__ void fixup_flag_kernel(const double* __restrict__ E, const double* __restrict__ Om,
+                                  int W, int n, int n_eta, int64_t eta_stride,
+                                  const double* __restrict__ E_F, int n_EF, double rel,
+                                  int* __restrict__ flag, int* __restrict__ bin) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double* Ek = E + (size_t)k * W;
+    double mx = 0.0;
+    for (int q = 0; q < W; ++q) mx = fmax(mx, fabs(Ek[q]));
+    const double tau = rel * mx;
+    int f = 0;
+    for (int j = 0; j < n_EF && !f; ++j) {
+      const double ef = E_F[j];
+      for (int q = 0; q < W; ++q)
+        if (fabs(Ek[q] - ef) < tau) { f = 1; break; }
+    }
+    double om = 0.0;
+    for (int e = 0; e < n_eta; ++e)
+      for (int q = 0; q < W; ++q) om = fmax(om, fabs(Om[e * eta_stride + (size_t)k * W + q]));
+    int b = 0;
+    if (om > 0.0) {
+      b = (int)floorf(4.0f * log2f((float)om)) + BIN_OFFSET;
+      b = b < 0 ? 0 : (b >= NBIN ? NBIN - 1 : b);
+    }
+    flag[k] = f;
+    bin[k] = b;
+  }
+}
+
+// Pass 2 (one block): integer histogram of the bins -> threshold bin of the top `frac`
+// (deterministic), then order-preserving compaction: pos[c] = local index, kid[c] = mesh index
+// of the c-th flagged k-point, *count = number flagged.
+__global__ void fixup_compact_kernel(const int* __restrict__ flag, const int* __restrict__ bin,
+                                     int n, double frac, KList kl, int* __restrict__ pos,
+                                     int64_t* __restrict__ kid, int* __restrict__ count) {
+  __shared__ int hist[NBIN];
+  __shared__ int warp_tot[32];
+  __shared__ int base_sh, thr_sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = threadIdx.x; b < NBIN; b += blockDim.x) hist[b] = 0;
+  if (threadIdx.x == 0) base_sh = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n; t += blockDim.x) atomicAdd(&hist[bin[t]], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int budget = (int)(frac * (double)n);
+    int acc = 0, thr = NBIN;          // no k-point flagged by curvature when budget == 0
+    for (int b = NBIN - 1; b > 0; --b) {
+      if (acc + hist[b] > budget) break;
+      acc += hist[b];
+      thr = b;
+    }
+    thr_sh = thr;
+  }
+  __syncthreads();
+  const int thr = thr_sh;
+  for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+    const int t = c0 + threadIdx.x;
+    const int f = t < n ? (flag[t] | (bin[t] >= thr ? 1 : 0)) : 0;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    const int within = __popc(b & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(b);
+    __syncthreads();
+    int off = base_sh;
+    for (int w = 0; w < warp; ++w) off += warp_tot[w];
+    if (f) {
+      pos[off + within] = t;
+      kid[off + within] = klist_get(kl, t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < nw; ++w) tot += warp_tot[w];
+      base_sh += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base_sh;
+}
+
+// E[pos[c]] = Efix[c], Om[e][pos[c]] = Omfix[e][c]
+__global__ void fixup_scatter_kernel(const int* __restrict__ pos, int cnt, int W, int n_eta,
+                                     const double* __restrict__ Efix,
+                                     const double* __restrict__ Omfix, int64_t fix_eta_stride,
+                                     double* __restrict__ E, double* __restrict__ Om,
+                                     int64_t eta_stride) {
+  const int64_t total = (int64_t)cnt * W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / W), q = (int)(t % W);
+    const int64_t k = pos[c];
+    E[k * W + q] = Efix[t];
+    for (int e = 0; e < n_eta; ++e) Om[e * eta_stride + k * W + q] = Omfix[e * fix_eta_stride + t];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_ksum_partial(const double* E, const double* Om, int W, int n, int n_eta,
@@ -85,6 +192,33 @@ cudaError_t launch_ksum_fold(const double2* part, int n_blocks, int n_out, doubl
 cudaError_t launch_ksum_final(const double2* acc, int n_out, double inv_Nk, const DevStatus* st,
                               double* out, cudaStream_t s) {
   ksum_final_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(acc, n_out, inv_Nk, st, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_flag(const double* E, const double* Om, int W, int n, int n_eta,
+                              int64_t eta_stride, const double* E_F, int n_EF, double rel,
+                              int* flag, int* bin, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fixup_flag_kernel<<<(n + 255) / 256, 256, 0, s>>>(E, Om, W, n, n_eta, eta_stride, E_F, n_EF, rel,
+                                                    flag, bin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_compact(const int* flag, const int* bin, int n, double frac,
+                                 const KList& kl, int* pos, int64_t* kid, int* count,
+                                 cudaStream_t s) {
+  fixup_compact_kernel<<<1, 1024, 0, s>>>(flag, bin, n, frac, kl, pos, kid, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_scatter(const int* pos, int cnt, int W, int n_eta, const double* Efix,
+                                 const double* Omfix, int64_t fix_eta_stride, double* E, double* Om,
+                                 int64_t eta_stride, cudaStream_t s) {
+  if (cnt <= 0) return cudaSuccess;
+  int64_t total = (int64_t)cnt * W;
+  int b = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  fixup_scatter_kernel<<<b, 256, 0, s>>>(pos, cnt, W, n_eta, Efix, Omfix, fix_eta_stride, E, Om,
+                                         eta_stride);
   return cudaGetLastError();
 }
 

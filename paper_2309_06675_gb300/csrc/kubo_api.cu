@@ -17,6 +17,8 @@ namespace {
 constexpr int MAX_W = 64;
 constexpr int MAX_ETA = 8;
 constexpr int KSUM_KPB = 256;        // k-points per deterministic k-sum block
+// mixed precision: share of each batch (largest ||Omega(k)||_inf) redone in FP64
+constexpr double kFixupSpikyFraction = 0.005;
 constexpr size_t ALIGN = 256;
 
 // ------------------------------------------------------------------ options
@@ -75,8 +77,14 @@ struct Bump {
   }
 };
 
+// precision modes whose step (1) runs on the tensor cores / whose step (3) runs in FP32
+bool tc_fourier(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_FOURIER; }
+bool f32_rotation(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_ROTATION; }
+
 struct Plan {
   int W = 0, N_R = 0, N_h = 0, K = 0, n_EF = 0, n_eta = 1, chunk = 0, cap = 0;
+  int precision = KUBO_FP64;
+  int Npad = 0, Kp = 0, Mpad = 0;   // tensor-core operand padding (mixed precision)
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -85,7 +93,12 @@ struct Plan {
   size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
          o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
          o_ph = 0, o_refl = 0, o_tau = 0, o_rot = 0, o_rcol = 0, o_nrot = 0, o_part = 0,
-         o_HR = 0, o_EF = 0, o_out = 0;
+         o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0;
+  // mixed-precision fix-up buffers
+  bool fixup = false;
+  int fix_cap = 0;
+  size_t o_flag = 0, o_bin = 0, o_pos = 0, o_kid = 0, o_cnt = 0, o_fHp = 0, o_fXp = 0, o_fYp = 0,
+         o_fE = 0, o_fOm = 0;
   size_t total = 0;
 };
 
@@ -117,9 +130,19 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_Rh = b.take(sizeof(int) * 3 * std::max(1, p.N_h));
     p.o_tab = b.take(sizeof(double2) * (p.mesh.N1 + p.mesh.N2 + p.mesh.N3));
     p.o_Bp = b.take(sizeof(double) * (size_t)p.K * WW);
-    p.o_Hp = b.take(sizeof(double) * (size_t)p.chunk * WW);
-    p.o_Xp = b.take(sizeof(double) * (size_t)p.chunk * WW);
-    p.o_Yp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+    if (tc_fourier(p.precision)) {
+      p.Npad = tc_pad_n(p.W);
+      p.Kp = tc_pad_k(p.N_R);
+      p.Mpad = tc_pad_m(std::max(1, p.chunk));
+      p.o_Bt = b.take((size_t)2 * tc_slices() * p.Npad * p.Kp);
+      p.o_cexp = b.take(sizeof(int) * (size_t)p.Npad);
+      p.o_A = b.take((size_t)2 * tc_slices() * p.Mpad * p.Kp);
+      p.o_C64 = b.take(sizeof(double) * (size_t)p.chunk * p.Npad);
+    } else {
+      p.o_Hp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+      p.o_Xp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+      p.o_Yp = b.take(sizeof(double) * (size_t)p.chunk * WW);
+    }
   }
   if (p.eigh) {
     p.o_d = b.take(sizeof(double) * (size_t)p.chunk * p.W);
@@ -135,6 +158,19 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_E = b.take(sizeof(double) * (size_t)p.chunk * p.W);
     p.o_U = b.take(sizeof(double2) * (size_t)p.chunk * WW);
     p.o_Om = b.take(sizeof(double) * (size_t)p.chunk * p.W * p.n_eta);
+  }
+  if (p.fixup) {
+    p.fix_cap = std::min(std::max(1, p.chunk), std::max(256, p.chunk / 8));
+    p.o_flag = b.take(sizeof(int) * (size_t)p.chunk);
+    p.o_bin = b.take(sizeof(int) * (size_t)p.chunk);
+    p.o_pos = b.take(sizeof(int) * (size_t)p.chunk);
+    p.o_kid = b.take(sizeof(int64_t) * (size_t)p.chunk);
+    p.o_cnt = b.take(sizeof(int));
+    p.o_fHp = b.take(sizeof(double) * (size_t)p.fix_cap * WW);
+    p.o_fXp = b.take(sizeof(double) * (size_t)p.fix_cap * WW);
+    p.o_fYp = b.take(sizeof(double) * (size_t)p.fix_cap * WW);
+    p.o_fE = b.take(sizeof(double) * (size_t)p.fix_cap * p.W);
+    p.o_fOm = b.take(sizeof(double) * (size_t)p.fix_cap * p.W * p.n_eta);
   }
   if (p.ksum) {
     const int n_out = p.n_eta * p.n_EF;
@@ -235,6 +271,7 @@ struct StageTimer {
 
 kubo_status bits_to_status(unsigned bits) {
   if (bits & (ST_NOT_HERMITIAN | ST_NONFINITE)) return KUBO_ERR_NOT_HERMITIAN;
+  if (bits & ST_TIMEOUT) return KUBO_ERR_TIMEOUT;
   if (bits & (ST_NO_CONVERGENCE | ST_LOG_OVERFLOW)) return KUBO_ERR_NO_CONVERGENCE;
   return KUBO_OK;
 }
@@ -253,7 +290,7 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
   if (W < 1 || N_R < 1 || !kmesh) return KUBO_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a)
     if (kmesh[a] < 1) return KUBO_ERR_INVALID_ARG;
-  if (o.precision != KUBO_FP64) return KUBO_ERR_UNSUPPORTED;
+  if (o.precision < KUBO_FP64 || o.precision > KUBO_MIXED_ROTATION) return KUBO_ERR_UNSUPPORTED;
   if (W > MAX_W) return KUBO_ERR_UNSUPPORTED;
   if (!finite_nonneg(o.kT)) return KUBO_ERR_INVALID_ARG;
   if (o.n_eta < 0) return KUBO_ERR_INVALID_ARG;
@@ -264,6 +301,7 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
       if (!finite_nonneg(o.etas[e])) return KUBO_ERR_INVALID_ARG;
   }
   if (o.chunk_k < 0) return KUBO_ERR_INVALID_ARG;
+  if (!std::isfinite(o.mixed_fixup_rel)) return KUBO_ERR_INVALID_ARG;
   n_eta = o.n_eta > 0 ? o.n_eta : 1;
   return KUBO_OK;
 }
@@ -285,6 +323,10 @@ kubo_status prepare_model(Call& c, const double* H_R, const RInfo& ri) {
     KCHECK(launch_hermitian_verdict(st, c.s));
     KCHECK(launch_twiddles(c.at<double2>(p.o_tab), p.mesh.N1, p.mesh.N2, p.mesh.N3, c.s));
     KCHECK(launch_pack_basis((const double2*)H_R, c.at<int>(p.o_pairs), ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s));
+  }
+  if (tc_fourier(p.precision)) {
+    StageTimer tm(c, KUBO_STAGE_PREP, 1);
+    KCHECK(launch_basis_split(c.at<double>(p.o_Bp), c.at<int>(p.o_Rh), p.N_h, p.W, p.Npad, p.Kp, c.at<int>(p.o_cexp), c.at<char>(p.o_Bt), c.s));
   }
   return read_status(c);
 }
@@ -321,9 +363,47 @@ EighBufs make_eigh_bufs(const Call& c) {
 
 // Steps (1)-(4) for one batch [t0, t0+n) of a k-list; E and U go to the chunk buffers, Omega
 // to Om (eta stride om_stride).  Eout may redirect the sorted eigenvalues.
+// Mixed precision: step (1) on the tensor cores into rows [H | dxH | dyH], the eigensolver
+// in FP64 from those rows, the rotations in FP32 (or FP64) with FP64 denominators.
+kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
+                            int64_t om_stride) {
+  Plan& p = c.p;
+  EighBufs eb = make_eigh_bufs(c);
+  DevStatus* st = c.at<DevStatus>(p.o_status);
+  double2* U = c.at<double2>(p.o_U);
+  double* C64 = c.at<double>(p.o_C64);
+  const int Mb = tc_pad_m(kl.n);
+  {
+    StageTimer tm(c, KUBO_STAGE_FOURIER, 2);
+    KCHECK(launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s));
+    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
+    KCHECK(launch_tridiag_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_QL, 1);
+    KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
+    KCHECK(launch_backtransform(p.W, kl.n, eb, Eout, U, c.s));
+  }
+  {
+    StageTimer tm(c, KUBO_STAGE_BERRY, 1);
+    if (f32_rotation(p.precision))
+      KCHECK(launch_berry_mixed_rows(Eout, U, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    else
+      KCHECK(launch_berry_fp64_rows(Eout, U, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+  }
+  return KUBO_OK;
+}
+
 kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
                       int64_t om_stride) {
   Plan& p = c.p;
+  if (tc_fourier(p.precision)) return run_batch_mixed(c, md, kl, Eout, Om, om_stride);
   double* Hp = c.at<double>(p.o_Hp);
   double* Xp = c.at<double>(p.o_Xp);
   double* Yp = c.at<double>(p.o_Yp);
@@ -348,7 +428,10 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
   }
   {
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    KCHECK(launch_berry_fp64(Eout, U, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    if (f32_rotation(p.precision))
+      KCHECK(launch_berry_mixed_from_f64(Eout, U, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    else
+      KCHECK(launch_berry_fp64(Eout, U, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
   }
   return KUBO_OK;
 }
@@ -358,6 +441,45 @@ kubo_status upload_etas(Call& c, const kubo_options& o, double eta) {
   if (o.n_eta > 0) for (int e = 0; e < o.n_eta; ++e) h[e] = o.etas[e];
   else h[0] = eta;
   KCHECK(cudaMemcpyAsync(c.at<double>(c.p.o_etas), h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+  return KUBO_OK;
+}
+
+// Mixed precision: re-evaluate in FP64 the k-points of this batch that have a level within
+// tau_k = rel * max|E(k)| of a Fermi level, and overwrite their E and Omega in place (the
+// k-sum order is unchanged, so the result stays deterministic).
+kubo_status fixup_batch(Call& c, const Model& md, const KList& kl, const double* E_F, double rel,
+                        double frac, double* E, double* Om) {
+  Plan& p = c.p;
+  int* flag = c.at<int>(p.o_flag);
+  int* pos = c.at<int>(p.o_pos);
+  int64_t* kid = c.at<int64_t>(p.o_kid);
+  int cnt = 0;
+  {
+    StageTimer tm(c, KUBO_STAGE_FIXUP, 2);
+    KCHECK(launch_fixup_flag(E, Om, p.W, kl.n, p.n_eta, (int64_t)kl.n * p.W, E_F, p.n_EF, rel, flag, c.at<int>(p.o_bin), c.s));
+    KCHECK(launch_fixup_compact(flag, c.at<int>(p.o_bin), kl.n, frac, kl, pos, kid, c.at<int>(p.o_cnt), c.s));
+  }
+  KCHECK(cudaMemcpyAsync(&cnt, c.at<int>(p.o_cnt), sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  KCHECK(cudaStreamSynchronize(c.s));
+  if (c.prof) c.prof->fixup_k += cnt;
+  if (cnt <= 0) return KUBO_OK;
+  EighBufs eb = make_eigh_bufs(c);
+  DevStatus* st = c.at<DevStatus>(p.o_status);
+  double2* U = c.at<double2>(p.o_U);
+  double* fE = c.at<double>(p.o_fE);
+  double* fOm = c.at<double>(p.o_fOm);
+  const int64_t fstride = (int64_t)p.fix_cap * p.W;
+  for (int c0 = 0; c0 < cnt; c0 += p.fix_cap) {
+    const int nf = std::min(p.fix_cap, cnt - c0);
+    KList fl{kid + c0, 0, nf};
+    StageTimer tm(c, KUBO_STAGE_FIXUP, 6);
+    KCHECK(launch_fourier_fp64(md, p.mesh, fl, c.at<double>(p.o_fHp), c.at<double>(p.o_fXp), c.at<double>(p.o_fYp), c.s));
+    KCHECK(launch_tridiag(c.at<double>(p.o_fHp), p.W, nf, eb, c.s));
+    KCHECK(launch_ql(p.W, nf, eb, st, c.s));
+    KCHECK(launch_backtransform(p.W, nf, eb, fE, U, c.s));
+    KCHECK(launch_berry_fp64(fE, U, c.at<double>(p.o_fXp), c.at<double>(p.o_fYp), p.W, nf, c.at<double>(p.o_etas), p.n_eta, fOm, fstride, c.s));
+    KCHECK(launch_fixup_scatter(pos + c0, nf, p.W, p.n_eta, fE, fOm, fstride, E, Om, (int64_t)kl.n * p.W, c.s));
+  }
   return KUBO_OK;
 }
 
@@ -380,6 +502,10 @@ kubo_status ahc_device(Call& c, const kubo_options& o, const double* H_R, const 
     KList kl{nullptr, base, (int)std::min<int64_t>(p.chunk, ke - base)};
     r = run_batch(c, md, kl, E, Om, (int64_t)kl.n * p.W);
     if (r != KUBO_OK) return r;
+    if (p.fixup) {
+      r = fixup_batch(c, md, kl, E_F, o.mixed_fixup_rel, kFixupSpikyFraction, E, Om);
+      if (r != KUBO_OK) return r;
+    }
     StageTimer tm(c, KUBO_STAGE_KSUM, 2);
     KCHECK(launch_ksum_partial(E, Om, p.W, kl.n, p.n_eta, (int64_t)kl.n * p.W, E_F, p.n_EF, o.kT, part, KSUM_KPB, c.s));
     KCHECK(launch_ksum_fold(part, (kl.n + KSUM_KPB - 1) / KSUM_KPB, n_out, acc, c.s));
@@ -402,6 +528,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   if (r != KUBO_OK) return r;
   Plan& p = c.p;
   p.W = W; p.N_R = N_R; p.N_h = ri.N_h; p.K = N_R; p.n_EF = n_EF; p.n_eta = n_eta;
+  p.precision = o.precision;
   p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
   kb = o.k_begin; ke = o.k_end;
   if (kb == 0 && ke == 0) ke = p.mesh.Nk;
@@ -409,6 +536,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
   p.cap = rot_capacity(W);
   p.model = p.eigh = p.berry = p.ksum = true;
+  p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   plan_layout(p, host_io, 0);
   c.s = (cudaStream_t)o.stream;
   c.prof = o.profile;
@@ -435,11 +563,14 @@ const char* kubo_status_string(kubo_status s) {
     case KUBO_ERR_CUDA: return "KUBO_ERR_CUDA: CUDA runtime error";
     case KUBO_ERR_NO_CONVERGENCE: return "KUBO_ERR_NO_CONVERGENCE: eigensolver iteration cap reached";
     case KUBO_ERR_WORKSPACE: return "KUBO_ERR_WORKSPACE: workspace smaller than kubo_workspace_size()";
+    case KUBO_ERR_TIMEOUT: return "KUBO_ERR_TIMEOUT: a bounded device-side wait gave up";
   }
   return "KUBO_ERR_UNKNOWN";
 }
 
-int kubo_max_orbitals(int precision) { return precision == KUBO_FP64 ? MAX_W : 0; }
+int kubo_max_orbitals(int precision) {
+  return (precision >= KUBO_FP64 && precision <= KUBO_MIXED_ROTATION) ? MAX_W : 0;
+}
 
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
                            const kubo_options* opt) {
@@ -448,12 +579,14 @@ size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
   if (validate_common(W, N_R, kmesh, o, n_eta) != KUBO_OK || n_EF < 1) return 0;
   Plan p;
   p.W = W; p.N_R = N_R; p.N_h = (N_R - 1) / 2; p.K = N_R; p.n_EF = n_EF; p.n_eta = n_eta;
+  p.precision = o.precision;
   p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
   int64_t kb = o.k_begin, ke = o.k_end;
   if (kb == 0 && ke == 0) ke = p.mesh.Nk;
   p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
   p.cap = rot_capacity(W);
   p.model = p.eigh = p.berry = p.ksum = true;
+  p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   plan_layout(p, false, 0);
   return p.total;
 }
@@ -539,6 +672,7 @@ kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
     // per-k mode: no k-sum, batches over the list
     Plan& p = c.p;
     p.ksum = false;
+    p.fixup = false;   // per-k results carry no Fermi level to protect
     p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, p.n_eta, n_k);
     plan_layout(p, false, 0);
     r = c.acquire(o);
@@ -579,8 +713,9 @@ kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
     Call c;
     Plan& p = c.p;
     p.W = W; p.N_R = N_R; p.N_h = ri.N_h; p.K = N_R; p.n_EF = 1; p.n_eta = 1;
+    p.precision = o.precision;
     p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
-    p.chunk = 0;
+    p.chunk = tc_fourier(o.precision) ? (int)std::min<int64_t>(n_k, o.chunk_k > 0 ? o.chunk_k : 8192) : 0;
     p.model = true;
     plan_layout(p, false, 0);
     c.s = (cudaStream_t)o.stream;
@@ -591,8 +726,23 @@ kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
     if (r == KUBO_OK) {
       const Model md = make_model(c);
       const size_t WW = (size_t)W * W;
-      const int64_t step = 1 << 19;   // keeps grid.y = step / 16 within 65535
-      for (int64_t t0 = 0; t0 < n_k && r == KUBO_OK; t0 += step) {
+      if (tc_fourier(p.precision)) {
+        DevStatus* st = c.at<DevStatus>(p.o_status);
+        double* C64 = c.at<double>(p.o_C64);
+        for (int64_t t0 = 0; t0 < n_k && r == KUBO_OK; t0 += p.chunk) {
+          KList kl{kidx + t0, 0, (int)std::min<int64_t>(p.chunk, n_k - t0)};
+          const int Mb = tc_pad_m(kl.n);
+          if (launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s) != cudaSuccess ||
+              launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s) != cudaSuccess ||
+              launch_unpack_rows(C64, p.Npad, W, kl.n, Hk + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, c.s) != cudaSuccess) {
+            cudaGetLastError();
+            r = KUBO_ERR_CUDA;
+          }
+        }
+        if (r == KUBO_OK) r = read_status(c);
+      }
+      const int64_t step = 1 << 19;   // grid.y = step / 16 <= 65535
+      for (int64_t t0 = 0; t0 < n_k && r == KUBO_OK && !tc_fourier(p.precision); t0 += step) {
         KList kl{kidx + t0, 0, (int)std::min<int64_t>(step, n_k - t0)};
         if (launch_fourier_fp64(md, p.mesh, kl, Hk + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, c.s) != cudaSuccess) {
           cudaGetLastError();

@@ -16,6 +16,7 @@ enum : unsigned {
   ST_NONFINITE = 2u,       // NaN/Inf in H(R)
   ST_NO_CONVERGENCE = 4u,  // QL iteration cap reached at some k
   ST_LOG_OVERFLOW = 8u,    // rotation log capacity exceeded at some k
+  ST_TIMEOUT = 16u,        // a bounded device-side wait gave up
 };
 
 struct DevStatus {
@@ -112,6 +113,9 @@ cudaError_t launch_fourier_fp64(const Model& md, const Mesh& mesh, const KList& 
                                 double* Xp, double* Yp, cudaStream_t s);
 
 cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s);
+// same reduction reading packed H from rows of leading dimension ld (tensor-core output)
+cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
+                                cudaStream_t s);
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
                                  cudaStream_t s);
@@ -120,6 +124,37 @@ cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* X
                               const double* Yp, int W, int n, const double* etas, int n_eta,
                               double* Om, int64_t eta_stride, cudaStream_t s);
 
+// rotations from packed dH rows of leading dimension ld (d_x H at column offset W*W, d_y H at
+// 2*W*W, as written by the tensor-core Fourier kernel): in FP32 (mixed) or in FP64
+cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const double* C,
+                                    int64_t ld, int W, int n, const double* etas, int n_eta,
+                                    double* Om, int64_t eta_stride, cudaStream_t s);
+cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const double* C,
+                                   int64_t ld, int W, int n, const double* etas, int n_eta,
+                                   double* Om, int64_t eta_stride, cudaStream_t s);
+
+// FP32 rotation from FP64 packed arrays (error-budget mode)
+cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
+                                        const double* Yp, int W, int n, const double* etas,
+                                        int n_eta, double* Om, int64_t eta_stride,
+                                        cudaStream_t s);
+
+// tensor-core Fourier sum (k_fourier_tc.cu)
+int tc_pad_m(int n);
+int tc_pad_n(int W);
+int tc_pad_k(int N_R);
+int tc_slices();
+cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, int Npad, int Kp,
+                               int* col_exp, void* Bt, cudaStream_t s);
+cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl, int Mpad, int Kp,
+                              void* A, cudaStream_t s);
+cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
+                              int Kp, int n_rows, double* out, int ldc, DevStatus* st,
+                              cudaStream_t s);
+// rows [n][ld] (H | dxH | dyH packed) -> three packed arrays [n][W*W]
+cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,
+                               double* Y, cudaStream_t s);
+
 cudaError_t launch_ksum_partial(const double* E, const double* Om, int W, int n, int n_eta,
                                 int64_t eta_stride, const double* E_F, int n_EF, double kT,
                                 double2* part, int k_per_block, cudaStream_t s);
@@ -127,6 +162,17 @@ cudaError_t launch_ksum_fold(const double2* part, int n_blocks, int n_out, doubl
                              cudaStream_t s);
 cudaError_t launch_ksum_final(const double2* acc, int n_out, double inv_Nk,
                               const DevStatus* st, double* out, cudaStream_t s);
+
+// mixed-precision fix-up (k_ksum.cu)
+cudaError_t launch_fixup_flag(const double* E, const double* Om, int W, int n, int n_eta,
+                              int64_t eta_stride, const double* E_F, int n_EF, double rel,
+                              int* flag, int* bin, cudaStream_t s);
+cudaError_t launch_fixup_compact(const int* flag, const int* bin, int n, double frac,
+                                 const KList& kl, int* pos, int64_t* kid, int* count,
+                                 cudaStream_t s);
+cudaError_t launch_fixup_scatter(const int* pos, int cnt, int W, int n_eta, const double* Efix,
+                                 const double* Omfix, int64_t fix_eta_stride, double* E, double* Om,
+                                 int64_t eta_stride, cudaStream_t s);
 
 size_t tridiag_smem(int W);
 size_t backtransform_smem(int W);

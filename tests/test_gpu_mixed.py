@@ -1,0 +1,142 @@
+"""Mixed-precision path (tensor-core Fourier sum with fixed-point BF16 slices, FP32 rotations,
+FP64 eigensolver, denominators and k-sum) against the FP64 oracle and the FP64 GPU path.
+
+Tolerance: relative 1e-5 on S(E_F) (max over E_F of |diff| / max |S_ref|).  The tensor-core
+Fourier sum itself is exact up to its ~40-bit slicing: 1e-10 relative to max |H|.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import tbgen
+from oracle import kubo_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+REL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def kubo():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_06675_gb300 import _build
+    _build.build()
+    import paper_2309_06675_gb300 as k
+    k.lib()
+    return k
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def cuda(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def m64():
+    return tbgen.random_tb(64, 5, 1.5, 0)
+
+
+@pytest.mark.parametrize("W,hw,n", [(16, 2, 37), (8, 1, 130), (20, 1, 129), (64, 5, 200)])
+def test_tensor_core_fourier_sum(kubo, torch, W, hw, n):
+    """Step (1) on tcgen05 vs the oracle: ragged k counts (not multiples of the 128-row tile),
+    orders whose 3 W^2 columns are not multiples of the 128-column tile."""
+    m = tbgen.random_tb(W, hw, 1.5, seed=W)
+    kmesh = (17, 11, 13)
+    kidx = tbgen.k_sample(kmesh, n, seed=3)
+    got = kubo.bloch(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, kidx), precision="mixed")
+    ref = O.bloch(m.H_R, m.R, kmesh, kidx)
+    for g, r in zip(got, ref):
+        G = kubo.unpack_hermitian(g, W).cpu().numpy()
+        assert rel_err(G, r) < 1e-10, rel_err(G, r)
+
+
+def test_mixed_w16_full_mesh_vs_golden(kubo, torch):
+    g = json.load(open(os.path.join(GOLDEN, "w16_r125_k24.json")))
+    m = tbgen.random_tb(16, 2, 1.0, 0)
+    S = kubo.ahc(cuda(torch, m.H_R), m.R, (24, 24, 24), cuda(torch, np.array(g["E_F"])),
+                 etas=g["etas"], precision="mixed").cpu().numpy()
+    assert rel_err(S, np.array(g["S"])) < REL_MIXED
+
+
+def test_mixed_per_k_w64(kubo, torch, m64):
+    kmesh = (128, 128, 128)
+    kidx = tbgen.k_sample(kmesh, 200, seed=21)
+    E, Om = kubo.ahc_k(cuda(torch, m64.H_R), m64.R, kmesh, cuda(torch, kidx), eta=1e-3,
+                       precision="mixed")
+    E_ref, Om_ref = O.kubo_per_k(m64.H_R, m64.R, kmesh, kidx, [1e-3])
+    E, Om = E.cpu().numpy(), Om.cpu().numpy()[0]
+    assert np.max(np.abs(E - E_ref)) <= 1e-6 * np.max(np.abs(E_ref))
+    scale = np.max(np.abs(Om_ref[0]), axis=-1)
+    err = np.max(np.abs(Om - Om_ref[0]), axis=-1) / scale
+    assert np.max(err) < 1e-3, np.max(err)
+    assert np.median(err) < 1e-5, np.median(err)
+
+
+def test_mixed_vs_fp64_on_a_mesh_plane_w64(kubo, torch, m64):
+    """One k1-plane (16,384 k-points) of the 128^3 mesh, 64 Fermi levels: the benchmark's
+    batch configuration, mixed vs FP64 GPU."""
+    kmesh = (128, 128, 128)
+    EF = np.linspace(-1.0, 1.0, 64)
+    H = cuda(torch, m64.H_R)
+    EFt = cuda(torch, EF)
+    rng = (37 * 16384, 38 * 16384)
+    S64 = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng).cpu().numpy()
+    Smx = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng, precision="mixed").cpu().numpy()
+    assert rel_err(Smx, S64) < REL_MIXED, rel_err(Smx, S64)
+    # the tensor-core Fourier sum alone is FP64-grade: only the FP32 rotations remain
+    Sfo = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng,
+                   precision="mixed_fourier").cpu().numpy()
+    assert rel_err(Sfo, S64) < 1e-8, rel_err(Sfo, S64)
+
+
+def test_mixed_fixup_redoes_flagged_k_points_in_fp64(kubo, torch, m64):
+    """Opt-in fix-up: k-points with a level near a Fermi level, or in the top 0.5 % of
+    ||Omega(k)||, are recomputed on the FP64 path and overwrite their mixed results."""
+    kmesh = (128, 128, 128)
+    EF = np.linspace(-1.0, 1.0, 64)
+    H = cuda(torch, m64.H_R)
+    EFt = cuda(torch, EF)
+    rng = (90 * 16384, 90 * 16384 + 5000)
+    S64 = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng).cpu().numpy()
+    prof = kubo.Profile()
+    Sfx = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng, precision="mixed",
+                   profile=prof, fixup_rel=4e-6, chunk_k=1500).cpu().numpy()
+    assert 0 < prof.fixup_k < 0.1 * 5000
+    assert prof.launches[kubo.STAGES.index("fixup")] > 0
+    assert rel_err(Sfx, S64) < REL_MIXED
+
+
+def test_mixed_multi_eta_fermi_dirac_ragged(kubo, torch):
+    m = tbgen.random_tb(12, 1, 1.0, 5)
+    kmesh = (7, 6, 5)
+    EF = np.array([-0.3, 0.2, 1e3])
+    etas = [1e-3, 5e-3, 1e-2]
+    for kT in (0.0, 0.025):
+        S = kubo.ahc(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, EF), etas=etas, kT=kT,
+                     precision="mixed", chunk_k=61).cpu().numpy()
+        S_ref = O.ahc(m.H_R, m.R, kmesh, EF, etas=etas, kT=kT)
+        assert rel_err(S, S_ref) < REL_MIXED
+
+
+def test_mixed_haldane_chern(kubo, torch):
+    """Quantised Chern number through the mixed path (single layer, eta = 0; exactly degenerate
+    stacked copies at eta = 0 are ill-conditioned once H carries FP32-level errors)."""
+    m = tbgen.haldane()
+    S = kubo.ahc(cuda(torch, m.H_R), m.R, (96, 96, 1), cuda(torch, np.array([0.0])), eta=0.0,
+                 precision="mixed")
+    C = 2 * np.pi * S.cpu().numpy()[0, 0]
+    assert abs(abs(C) - 1) < 1e-5
