@@ -35,31 +35,35 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------ K2a: tridiagonalise
+// The Hermitian matrix is held as its lower triangle, packed by rows: element (r, c <= r) at
+// r (r + 1) / 2 + c (33 KB at W = 64), so that several CTAs share an SM and hide each
+// other's scalar Householder steps.
+__device__ __forceinline__ int tri(int r, int c) { return (r * (r + 1) >> 1) + c; }
+
 // Packed rows of leading dimension ld (W*W for the FP64 Fourier kernel, the padded row of
 // H | dxH | dyH for the tensor-core one).  The reduction is FP64.
 template <typename T>
-__global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
+__global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
                                                      EighBufs b) {
   extern __shared__ double2 smem2[];
-  const int LDA = W + 1;
-  double2* A = smem2;                 // [W][LDA]
-  double2* vb = A + (size_t)W * LDA;  // [W] reflector (contiguous copy)
-  double2* pb = vb + W;               // [W] p, then w
-  double2* be = pb + W;               // [W] complex sub-diagonal beta_i
-  double* tb = (double*)(be + W);     // [W] tau_i
+  double2* A = smem2;                              // lower triangle, packed by rows
+  double2* vb = A + (size_t)W * (W + 1) / 2;       // [W] reflector (contiguous copy)
+  double2* pb = vb + W;                            // [W] p, then w
+  double2* be = pb + W;                            // [W] complex sub-diagonal beta_i
+  double* tb = (double*)(be + W);                  // [W] tau_i
   __shared__ double s_tau, s_K;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t k = blockIdx.x;
   const T* P = Hp + (size_t)k * ld;
 
-  for (int idx = t; idx < W * W; idx += NT) {
-    int i = idx / W, j = idx % W;
-    double2 a;
-    if (i < j) a = make_double2((double)P[i * W + j], (double)P[j * W + i]);
-    else if (i > j) a = make_double2((double)P[j * W + i], -(double)P[i * W + j]);
-    else a = make_double2((double)P[i * W + i], 0.0);
-    A[i * LDA + j] = a;
+  for (int idx = t; idx < W * (W + 1) / 2; idx += NT) {
+    int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while (tri(r, 0) > idx) --r;
+    while (tri(r + 1, 0) <= idx) ++r;
+    const int c = idx - tri(r, 0);
+    A[idx] = r == c ? make_double2((double)P[r * W + r], 0.0)
+                    : make_double2((double)P[c * W + r], -(double)P[r * W + c]);   // conj(A_cr)
   }
   __syncthreads();
 
@@ -69,23 +73,25 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
     if (warp == 0) {
       double s2 = 0.0;
       for (int r = o + 1 + lane; r < W; r += 32) {
-        double2 x = A[r * LDA + i];
+        double2 x = A[tri(r, i)];
         s2 = fma(x.x, x.x, fma(x.y, x.y, s2));
       }
       s2 = warp_sum(s2);
       if (lane == 0) {
-        double2 al = A[o * LDA + i];
+        double2 al = A[tri(o, i)];
         double tau = 0.0;
         double2 beta = al;
         if (s2 != 0.0) {
-          double aa = hypot(al.x, al.y);
-          double nrm = sqrt(fma(aa, aa, s2));
+          // H = I - tau v v^H with v = x - beta e1, beta = -e^{i arg alpha} |x|:
+          // v0 = alpha + e^{i arg alpha} |x|, tau = 2 / v^H v = 1 / (|x| (|x| + |alpha|))
+          const double aa2 = fma(al.x, al.x, al.y * al.y);
+          const double aa = sqrt(aa2);
+          const double nrm = sqrt(aa2 + s2);
           double pr = 1.0, pi = 0.0;
-          if (aa > 0.0) { pr = al.x / aa; pi = al.y / aa; }
+          if (aa > 0.0) { const double ia = 1.0 / aa; pr = al.x * ia; pi = al.y * ia; }
           beta = make_double2(-pr * nrm, -pi * nrm);
-          double2 v0 = make_double2(fma(pr, nrm, al.x), fma(pi, nrm, al.y));
-          tau = 2.0 / fma(v0.x, v0.x, fma(v0.y, v0.y, s2));
-          A[o * LDA + i] = v0;
+          A[tri(o, i)] = make_double2(fma(pr, nrm, al.x), fma(pi, nrm, al.y));
+          tau = 1.0 / (nrm * (nrm + aa));
         }
         s_tau = tau;
         be[i] = beta;
@@ -95,29 +101,30 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
     __syncthreads();
     const double tau = s_tau;
     if (tau != 0.0) {
-      for (int r = t; r < m; r += NT) vb[r] = A[(o + r) * LDA + i];
+      for (int r = t; r < m; r += NT) vb[r] = A[tri(o + r, i)];
       __syncthreads();
       // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r)
       for (int r = t; r < m; r += NT) {
         double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+        const int rowb = tri(o + r, o);
         int c = 0;
         for (; c + 1 < m; c += 2) {
-          int i0 = c <= r ? (o + r) * LDA + o + c : (o + c) * LDA + o + r;
-          int i1 = c + 1 <= r ? (o + r) * LDA + o + c + 1 : (o + c + 1) * LDA + o + r;
+          const int i0 = c <= r ? rowb + c : tri(o + c, o + r);
+          const int i1 = c + 1 <= r ? rowb + c + 1 : tri(o + c + 1, o + r);
           double2 a0 = A[i0], a1 = A[i1];
           if (c > r) a0.y = -a0.y;
           if (c + 1 > r) a1.y = -a1.y;
-          double2 v0 = vb[c], v1 = vb[c + 1];
+          const double2 v0 = vb[c], v1 = vb[c + 1];
           ax = fma(a0.x, v0.x, ax); ax = fma(-a0.y, v0.y, ax);
           ay = fma(a0.x, v0.y, ay); ay = fma(a0.y, v0.x, ay);
           bx = fma(a1.x, v1.x, bx); bx = fma(-a1.y, v1.y, bx);
           by = fma(a1.x, v1.y, by); by = fma(a1.y, v1.x, by);
         }
         if (c < m) {
-          int i0 = c <= r ? (o + r) * LDA + o + c : (o + c) * LDA + o + r;
+          const int i0 = c <= r ? rowb + c : tri(o + c, o + r);
           double2 a0 = A[i0];
           if (c > r) a0.y = -a0.y;
-          double2 v0 = vb[c];
+          const double2 v0 = vb[c];
           ax = fma(a0.x, v0.x, ax); ax = fma(-a0.y, v0.y, ax);
           ay = fma(a0.x, v0.y, ay); ay = fma(a0.y, v0.x, ay);
         }
@@ -125,18 +132,18 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
       }
       __syncthreads();
       if (warp == 0) {
-        double s = 0.0;   // Re(v^H p)
+        double sum = 0.0;   // Re(v^H p)
         for (int r = lane; r < m; r += 32) {
-          double2 v = vb[r], p = pb[r];
-          s = fma(v.x, p.x, fma(v.y, p.y, s));
+          const double2 v = vb[r], p = pb[r];
+          sum = fma(v.x, p.x, fma(v.y, p.y, sum));
         }
-        s = warp_sum(s);
-        if (lane == 0) s_K = 0.5 * tau * s;
+        sum = warp_sum(sum);
+        if (lane == 0) s_K = 0.5 * tau * sum;
       }
       __syncthreads();
       const double K = s_K;
       for (int r = t; r < m; r += NT) {
-        double2 p = pb[r], v = vb[r];
+        const double2 p = pb[r], v = vb[r];
         pb[r] = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
       }
       __syncthreads();
@@ -146,9 +153,9 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
         int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
         while (r * (r + 1) / 2 > idx) --r;
         while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-        int c = idx - r * (r + 1) / 2;
-        double2 vr = vb[r], wr = pb[r], vc = vb[c], wc = pb[c];
-        double2 a = A[(o + r) * LDA + o + c];
+        const int c = idx - r * (r + 1) / 2;
+        const double2 vr = vb[r], wr = pb[r], vc = vb[c], wc = pb[c];
+        double2 a = A[tri(o + r, o + c)];
         // v_r conj(w_c) + w_r conj(v_c)
         a.x = fma(-vr.x, wc.x, a.x); a.x = fma(-vr.y, wc.y, a.x);
         a.x = fma(-wr.x, vc.x, a.x); a.x = fma(-wr.y, vc.y, a.x);
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
           a.y = fma(-vr.y, wc.x, a.y); a.y = fma(vr.x, wc.y, a.y);
           a.y = fma(-wr.y, vc.x, a.y); a.y = fma(wr.x, vc.y, a.y);
         }
-        A[(o + r) * LDA + o + c] = a;
+        A[tri(o + r, o + c)] = a;
       }
     }
     __syncthreads();
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
   double2* phout = b.phase + k * W;
   double* tout = b.tau + k * W;
   if (t == 0) {
-    if (W >= 2) be[W - 2] = A[(W - 1) * LDA + (W - 2)];
+    if (W >= 2) be[W - 2] = A[tri(W - 1, W - 2)];
     double2 D = make_double2(1.0, 0.0);
     phout[0] = D;
     for (int j = 0; j + 1 < W; ++j) {
@@ -183,13 +190,13 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(const T* __restrict__ Hp, i
     eout[W - 1] = 0.0;
   }
   for (int j = t; j < W; j += NT) {
-    dout[j] = A[j * LDA + j].x;
+    dout[j] = A[tri(j, j)].x;
     tout[j] = j < W - 2 ? tb[j] : 0.0;
   }
   double2* rout = b.refl + (size_t)k * W * W;
   for (int idx = t; idx < W * W; idx += NT) {
     int r = idx / W, c = idx % W;
-    rout[idx] = r > c ? A[r * LDA + c] : make_double2(0.0, 0.0);
+    rout[idx] = r > c ? A[tri(r, c)] : make_double2(0.0, 0.0);
   }
 }
 
@@ -268,13 +275,28 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// Log chunk staged in shared memory while the rows replay the previous one
+constexpr int LOG_CHUNK = 1024;
+
+// double2 slots of the U region: the W x (W+1) matrix, or two log chunks ((c, s) + indices)
+__host__ __device__ __forceinline__ size_t bt_u_slots(int W) {
+  const size_t mat = (size_t)W * (W + 1);
+  const size_t logs = 2 * LOG_CHUNK + (2 * LOG_CHUNK * sizeof(short) + 15) / 16;
+  return mat > logs ? mat : logs;
+}
+
 __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, double* __restrict__ Eout,
                                                            double2* __restrict__ Uout) {
   extern __shared__ double2 smem2[];
   const int LDU = W + 1;
   double2* U = smem2;                               // [W][LDU] complex
-  double* Z = (double*)(U + (size_t)W * LDU);       // [W][LDU] real
+  double* Z = (double*)(U + bt_u_slots(W));         // [W][LDU] real
   int* rank = (int*)(Z + (size_t)W * LDU);          // [W]
+  // during the replay U's space holds two log chunks: (c, s) pairs, then column indices
+  double2* logcs = U;                               // [2][LOG_CHUNK]
+  short* logi = (short*)(U + 2 * LOG_CHUNK);        // [2][LOG_CHUNK]
+  // after U = D Z, Z's space holds the reflectors: column j (rows j+1..W-1) at tri(W-2-j) offsets
+  double2* Rs = (double2*)Z;
 
   const int t = threadIdx.x;
   const int64_t k = blockIdx.x;
@@ -297,25 +319,60 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
     int r = idx / W, c = idx % W;
     Z[r * LDU + c] = r == c ? 1.0 : 0.0;
   }
-  __syncthreads();
 
-  // replay the QL rotations: row r of Z is owned by thread r
+  // Replay the QL rotations: row r of Z is owned by thread r (< W); the other threads stage the
+  // next chunk of the log.  Rotation i acts on columns (i, i+1); within a sweep the indices
+  // descend, so column i of one rotation is column i+1 of the next and is carried in a
+  // register (`cur`, column `ci`): two dependent FP64 operations per rotation.
   const int nr = min(b.nrot[k], b.cap);
   const double2* rot = b.rot + k * b.cap;
   const short* rc = b.rcol + k * b.cap;
-  for (int r = t; r < W; r += NT) {
-    double* zr = Z + r * LDU;
-    for (int q = 0; q < nr; ++q) {
-      double2 cs = rot[q];
-      int i = rc[q];
-      double zi = zr[i], f = zr[i + 1];
-      zr[i + 1] = fma(cs.y, zi, cs.x * f);
-      zr[i] = fma(cs.x, zi, -cs.y * f);
-    }
+  const int nchunk = (nr + LOG_CHUNK - 1) / LOG_CHUNK;
+  for (int q = t; q < min(nr, LOG_CHUNK); q += NT) {
+    logcs[q] = rot[q];
+    logi[q] = rc[q];
   }
   __syncthreads();
+  double cur = 0.0;
+  int ci = -2;   // no carried column
+  double* zr = Z + (t < W ? t : 0) * LDU;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int buf = ch & 1;
+    const int q0 = ch * LOG_CHUNK;
+    const int qn = min(LOG_CHUNK, nr - q0);
+    if (t < W) {
+      const double2* cs_b = logcs + buf * LOG_CHUNK;
+      const short* i_b = logi + buf * LOG_CHUNK;
+      for (int q = 0; q < qn; ++q) {
+        const double2 cs = cs_b[q];
+        const int i = i_b[q];
+        double f;                  // column i+1
+        if (ci == i + 1) {
+          f = cur;
+        } else {
+          if (ci >= 0) zr[ci] = cur;
+          f = zr[i + 1];
+        }
+        const double zi = zr[i];
+        zr[i + 1] = fma(cs.y, zi, cs.x * f);
+        cur = fma(cs.x, zi, -cs.y * f);
+        ci = i;
+      }
+    } else if (ch + 1 < nchunk) {
+      const int nb = buf ^ 1;
+      const int q1 = q0 + LOG_CHUNK;
+      const int qn1 = min(LOG_CHUNK, nr - q1);
+      for (int q = t - W; q < qn1; q += NT - W) {
+        logcs[nb * LOG_CHUNK + q] = rot[q1 + q];
+        logi[nb * LOG_CHUNK + q] = rc[q1 + q];
+      }
+    }
+    __syncthreads();
+  }
+  if (t < W && ci >= 0) zr[ci] = cur;
+  __syncthreads();
 
-  // U = D Z
+  // U = D Z (overwrites the log buffers)
   const double2* ph = b.phase + k * W;
   for (int idx = t; idx < W * W; idx += NT) {
     int r = idx / W, c = idx % W;
@@ -325,8 +382,16 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
   }
   __syncthreads();
 
-  // U <- H_j U for j = W-3 .. 0; 4 threads per column, rows strided by 4
+  // stage the reflectors in Z's space: reflector j (length m = W-1-j) at offset roff(j)
   const double2* R = b.refl + (size_t)k * W * W;
+  auto roff = [&](int j) { return j * (W - 1) - (j * (j - 1)) / 2; };   // sum_{j'<j} (W-1-j')
+  for (int idx = t; idx < W * W; idx += NT) {
+    const int r = idx / W, c = idx % W;
+    if (r > c && c < W - 2) Rs[roff(c) + (r - c - 1)] = R[idx];
+  }
+  __syncthreads();
+
+  // U <- H_j U for j = W-3 .. 0; 4 threads per column, rows strided by 4
   const double* tau = b.tau + k * W;
   const int q = t & 3;
   for (int c0 = 0; c0 < W; c0 += NT / 4) {
@@ -336,10 +401,11 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
       const double tj = tau[j];
       if (tj == 0.0) continue;
       const int o = j + 1, m = W - 1 - j;
+      const double2* v_j = Rs + roff(j);
       double sx = 0.0, sy = 0.0;
       if (act) {
         for (int r = q; r < m; r += 4) {
-          double2 v = R[(o + r) * W + j];
+          double2 v = v_j[r];
           double2 u = U[(o + r) * LDU + c];
           sx = fma(v.x, u.x, fma(v.y, u.y, sx));     // conj(v) u
           sy = fma(v.x, u.y, fma(-v.y, u.x, sy));
@@ -352,7 +418,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
       sx *= tj; sy *= tj;
       if (act) {
         for (int r = q; r < m; r += 4) {
-          double2 v = R[(o + r) * W + j];
+          double2 v = v_j[r];
           double2 u = U[(o + r) * LDU + c];
           u.x = fma(-sx, v.x, fma(sy, v.y, u.x));    // u -= s v
           u.y = fma(-sx, v.y, fma(-sy, v.x, u.y));
@@ -373,10 +439,11 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
 }  // namespace
 
 size_t tridiag_smem(int W) {
-  return ((size_t)W * (W + 1) + 3 * (size_t)W) * sizeof(double2) + (size_t)W * sizeof(double);
+  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W) * sizeof(double2) + (size_t)W * sizeof(double);
 }
 size_t backtransform_smem(int W) {
-  return (size_t)W * (W + 1) * (sizeof(double2) + sizeof(double)) + (size_t)W * sizeof(int);
+  return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
+         (size_t)W * sizeof(int);
 }
 size_t ql_smem(int W) { return (size_t)2 * 2 * W * 32 * sizeof(double); }
 

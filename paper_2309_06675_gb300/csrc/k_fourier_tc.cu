@@ -10,23 +10,24 @@
 //
 // Arithmetic: fixed-point slicing (the Ozaki scheme) on BF16 MMAs.  Every coefficient
 // (|c| <= 1) and every basis entry (scaled by 2^-e_n, e_n the exponent of its column's
-// largest magnitude) is written as x = sum_{i<5} s_i 2^(-7-8i) with integer slices
+// largest magnitude) is written as x = sum_{i<4} s_i 2^(-7-8i) with integer slices
 // |s_i| <= 128, exact in BF16.  A product of slices is an integer below 2^14, so the sum of one
-// 64-wide K block of all slice pairs of one level l = i + j (at most 5 pairs) stays an integer
-// below 2^24 and is EXACT in the FP32 tensor-memory accumulator, whatever rounding the tensor
-// core applies.  The epilogue converts each level to int32 (exact), accumulates the K blocks in
-// integers (exact), and combines the levels l <= 4 (15 slice pairs) in FP64:
-//   C = 2^e_n sum_l 2^(-14-8l) I_l.
-// The result carries ~40 significant bits relative to the operand scales (FP64 phases, FP64
+// 64-wide K block of all slice pairs of one level l = i + j (at most 4 pairs) stays an integer
+// below 2^22 and is EXACT in the FP32 tensor-memory accumulator, whatever rounding the tensor
+// core applies.  The epilogue converts each level to an integer (exact), accumulates the K
+// blocks and levels exactly in one int64 per column, and scales once in FP64:
+//   C = 2^e_n sum_l 2^(-14-8l) I_l   (levels l <= 3: 10 slice pairs).
+// The result carries ~31 fractional bits relative to the operand scales (FP64 phases, FP64
 // basis), versus ~24 for a split-BF16 product with FP32 accumulation.
 //
 // Kernels:
 //   basis_scale_kernel  once per call: column exponents e_n of the stacked basis
-//   basis_slice_kernel  once per call: stacked basis -> Bt[5 slices][Npad][Kp] (K-major, bf16)
-//   coef_slice_kernel   per batch: FP64 phases with exact argument reduction -> A[5][Mpad][Kp]
-//   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, N=32, K=16), operands staged
-//                       by TMA (128-byte swizzle, 2-stage mbarrier pipeline), 5 level
-//                       accumulators x 2 buffers in TMEM, integer epilogue, FP64 rows in HBM.
+//   basis_slice_kernel  once per call: stacked basis -> Bt[4 slices][Npad][Kp] (K-major, bf16)
+//   coef_slice_kernel   per batch: FP64 phases with exact argument reduction -> A[4][Mpad][Kp]
+//   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, N=64, K=16), operands staged
+//                       by TMA (128-byte swizzle, 2-stage mbarrier pipeline), 4 level
+//                       accumulators x 2 buffers filling the 512 TMEM columns, integer
+//                       epilogue, FP64 rows in HBM.
 //
 // Every mbarrier wait is bounded; on timeout the CTA records ST_TIMEOUT, drains its own
 // copies (bounded), frees its TMEM and returns.
@@ -41,18 +42,18 @@ namespace kubo {
 namespace {
 
 constexpr int BM = 128;           // k-points per tile (UMMA M)
-constexpr int BN = 32;            // output columns per tile (UMMA N)
+constexpr int BN = 64;            // output columns per tile (UMMA N)
 constexpr int BK = 64;            // K per stage (one 128-byte swizzle row of bf16) = one exact chunk
 constexpr int NSTAGE = 2;
-constexpr int NSLICE = 5;         // slices per operand: 7 + 4 x 8 = 39 fractional bits
-constexpr int NLEVEL = 5;         // levels l = i + j <= 4 kept: 15 slice pairs
-constexpr int NPAIR = 15;
+constexpr int NSLICE = 4;         // slices per operand: 7 + 3 x 8 = 31 fractional bits
+constexpr int NLEVEL = 4;         // levels l = i + j <= 3 kept: 10 slice pairs
+constexpr int NPAIR = 10;
 constexpr int NACC = 2;           // level-accumulator sets in flight (double buffer)
 constexpr int TILE_A_BYTES = BM * BK * 2;            // 16 KB per slice
-constexpr int TILE_B_BYTES = BN * BK * 2;            // 4 KB per slice
-constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 100 KB
+constexpr int TILE_B_BYTES = BN * BK * 2;            // 8 KB per slice
+constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 96 KB
 constexpr int TC_THREADS = 192;                      // 6 warps
-constexpr int TMEM_COLS = 512;                       // >= NACC * NLEVEL * BN = 320, power of 2
+constexpr int TMEM_COLS = 512;                       // = NACC * NLEVEL * BN
 constexpr uint32_t WAIT_LIMIT = 1u << 26;
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -113,7 +114,7 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 32.
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 64.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -154,7 +155,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Fixed-point slices of x (|x| <= 1): x = sum_i s_i 2^(-7-8i) + O(2^-47), |s_i| <= 128.
+// 32 lanes x 16 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Fixed-point slices of x (|x| <= 1): x = sum_i s_i 2^(-7-8i) + O(2^-39), |s_i| <= 128.
 // All operations are exact in FP64 (scaling by powers of two, subtracting integers).
 __device__ __forceinline__ void slice5(double x, __nv_bfloat16 (&sl)[NSLICE]) {
   double r = x * 128.0;
@@ -249,10 +262,10 @@ __global__ void coef_slice_kernel(Model md, Mesh mesh, KList kl, int Mpad, int K
   }
 }
 
-// slice pairs (i, j) with i + j <= 4, grouped by level l = i + j
-__constant__ int c_pi[NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
-__constant__ int c_pj[NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
-__constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4};
+// slice pairs (i, j) with i + j <= 3, grouped by level l = i + j
+__constant__ int c_pi[NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+__constant__ int c_pj[NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+__constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 
 // ------------------------------------------------------------------ the tcgen05 GEMM
 // grid: (Npad / BN, Mpad / BM); out: FP64 [n rows][ldc], rows >= n_rows not written.
@@ -365,7 +378,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int grow = m0 + row;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     // One exact integer per column: sum over K blocks and levels of I_l 2^(32 - 8 l).  A block's
-    // level sum is below 2^23 in magnitude, so the total stays below 2^57 (no overflow).
+    // level sum is below 2^22 in magnitude, so the total stays below 2^57 (no overflow).
     long long isum[BN];
 #pragma unroll
     for (int j = 0; j < BN; ++j) isum[j] = 0;
@@ -378,11 +391,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_after();
 #pragma unroll
       for (int l = 0; l < NLEVEL; ++l) {
-        uint32_t r[32];
-        tmem_ld32(lane_addr + (uint32_t)((a * NLEVEL + l) * BN), r);
 #pragma unroll
-        for (int j = 0; j < BN; ++j)
-          isum[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(lane_addr + (uint32_t)((a * NLEVEL + l) * BN + c0), r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            isum[c0 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
+        }
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[a]);

@@ -2,7 +2,8 @@
 FP64 eigensolver, denominators and k-sum) against the FP64 oracle and the FP64 GPU path.
 
 Tolerance: relative 1e-5 on S(E_F) (max over E_F of |diff| / max |S_ref|).  The tensor-core
-Fourier sum itself is exact up to its ~40-bit slicing: 1e-10 relative to max |H|.
+Fourier sum itself is exact up to its 31-bit fixed-point slicing: 2e-8 relative to max |H|
+(split-BF16 products with FP32 accumulation reach ~3e-7 on the same workload).
 """
 import json
 import os
@@ -61,7 +62,7 @@ def test_tensor_core_fourier_sum(kubo, torch, W, hw, n):
     ref = O.bloch(m.H_R, m.R, kmesh, kidx)
     for g, r in zip(got, ref):
         G = kubo.unpack_hermitian(g, W).cpu().numpy()
-        assert rel_err(G, r) < 1e-10, rel_err(G, r)
+        assert rel_err(G, r) < 2e-8, rel_err(G, r)
 
 
 def test_mixed_w16_full_mesh_vs_golden(kubo, torch):
@@ -100,7 +101,7 @@ def test_mixed_vs_fp64_on_a_mesh_plane_w64(kubo, torch, m64):
     # the tensor-core Fourier sum alone is FP64-grade: only the FP32 rotations remain
     Sfo = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng,
                    precision="mixed_fourier").cpu().numpy()
-    assert rel_err(Sfo, S64) < 1e-8, rel_err(Sfo, S64)
+    assert rel_err(Sfo, S64) < 1e-6, rel_err(Sfo, S64)
 
 
 def test_mixed_fixup_redoes_flagged_k_points_in_fp64(kubo, torch, m64):
