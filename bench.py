@@ -40,7 +40,7 @@ def stage_flops(W, N_R):
         "fourier": 6.0 * N_R * W * W,     # real contraction [3 x N_R] . [N_R x W^2]
         "tridiag": 16.0 / 3.0 * W ** 3,   # complex Householder reduction
         "ql": 25.0 * 1.2 * W * W,         # ~1.2 W^2 Givens steps of ~25 flops
-        "backtransform": 7.2 * W ** 3 + 8.0 * W ** 3,   # rotation replay + reflectors
+        "backtransform": 8.0 * W ** 3 + 42.0 * W * W,   # reflectors U = Q D Z + inverse iteration
         "berry": 24.0 * W ** 3,           # two Hermitian rotations U^H dH U
         "ksum": 2.0 * W * 64,
         "prep": 0.0,

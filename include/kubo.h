@@ -198,7 +198,7 @@ kubo_status kubo_berry_batched(const double* E, const double* U, const double* d
  * loads the library holds that block until the process exits).  Limits:
  *   - W <= 64; a larger W returns KUBO_ERR_UNSUPPORTED without launching anything.
  *   - any n >= 1: the matrices are processed in passes of as many as fit in the block
- *     (about 115 per pass at W = 64, about 1700 at W = 16).
+ *     (about 480 per pass at W = 64, about 6900 at W = 16).
  * The first call on a device looks up the block's device address (once per device, with
  * that device current); make that first call before any stream capture.  Every call
  * shares the block and it keeps the previous call's contents (the call clears what must

@@ -201,7 +201,9 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
 }
 
 // ------------------------------------------------------------------ K2b: QL, lane per k
-// Smem per warp: d and e as [W][32] (lane-interleaved: conflict-free for any index mix).
+// Eigenvalues of the real symmetric tridiagonal T by implicit QL with Wilkinson shifts, one
+// k-point per lane.  Smem per warp: d and e as [W][32] (lane-interleaved: conflict-free for
+// any mix of indices across lanes).  Iterations per eigenvalue are capped (-> ST_NO_CONVERGENCE).
 __global__ void __launch_bounds__(64) ql_kernel(int W, int n, EighBufs b, DevStatus* st) {
   extern __shared__ double qsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -213,10 +215,6 @@ __global__ void __launch_bounds__(64) ql_kernel(int W, int n, EighBufs b, DevSta
     D[i * 32] = b.d[(size_t)k * W + i];
     E[i * 32] = b.e[(size_t)k * W + i];
   }
-  const int cap = b.cap;
-  double2* rot = b.rot + (size_t)k * cap;
-  short* rc = b.rcol + (size_t)k * cap;
-  int nrot = 0;
   bool fail = false;
   const double eps = 2.220446049250313e-16;
   for (int l = 0; l < W && !fail; ++l) {
@@ -254,8 +252,6 @@ __global__ void __launch_bounds__(64) ql_kernel(int W, int n, EighBufs b, DevSta
         p = s * rr;
         D[(i + 1) * 32] = gi + p;
         g = fma(c, rr, -bb);
-        if (nrot < cap) { rot[nrot] = make_double2(c, s); rc[nrot] = (short)i; }
-        ++nrot;
       }
       if (early) continue;
       D[l * 32] -= p;
@@ -263,116 +259,181 @@ __global__ void __launch_bounds__(64) ql_kernel(int W, int n, EighBufs b, DevSta
       E[m * 32] = 0.0;
     }
   }
-  for (int i = 0; i < W; ++i) b.d[(size_t)k * W + i] = D[i * 32];
-  b.nrot[k] = nrot;
+  for (int i = 0; i < W; ++i) b.lam[(size_t)k * W + i] = D[i * 32];
   if (fail) atomicOr(&st->bits, ST_NO_CONVERGENCE);
-  if (nrot > cap) atomicOr(&st->bits, ST_LOG_OVERFLOW);
 }
 
-// ------------------------------------------------------------------ K2c: replay + back-transform
+// ------------------------------------------------------------------ K2c: eigenvectors + back-transform
+// Eigenvectors of T by inverse iteration, then U = Q D Z.
+//   * eigenvalues are sorted (rank by integer keys); clusters are runs of sorted eigenvalues
+//     closer than 1e-3 ||T||_1; one thread handles one cluster (almost always one vector).
+//   * for each eigenvalue: LU of T - lambda I with partial pivoting (row interchanges), 3
+//     solves from a fixed pseudo-random start, modified Gram-Schmidt against the cluster's
+//     previous vectors, normalisation.  Coincident eigenvalues are separated by 10 eps ||T||_1.
+//   * a warp at a time: the factors of 32 vectors live lane-interleaved in the U region;
+//     the iterate lives in its column of Z.
 __device__ __forceinline__ unsigned long long order_key(double x) {
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-// Log chunk staged in shared memory while the rows replay the previous one
-constexpr int LOG_CHUNK = 1024;
-
-// double2 slots of the U region: the W x (W+1) matrix, or two log chunks ((c, s) + indices)
+// double2 slots of the U region: the W x (W+1) matrix, or the inverse-iteration factors of
+// 32 vectors (4 arrays of W x 32 doubles)
 __host__ __device__ __forceinline__ size_t bt_u_slots(int W) {
   const size_t mat = (size_t)W * (W + 1);
-  const size_t logs = 2 * LOG_CHUNK + (2 * LOG_CHUNK * sizeof(short) + 15) / 16;
-  return mat > logs ? mat : logs;
+  const size_t lu = (size_t)64 * W;
+  return mat > lu ? mat : lu;
 }
+
+// deterministic start vector in [0.5, 1.5): integer hash of (row, vector)
+__device__ __forceinline__ double iit_start(int i, int j) {
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+}
+
+constexpr int IIT_SOLVES = 3;
 
 __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, double* __restrict__ Eout,
                                                            double2* __restrict__ Uout) {
   extern __shared__ double2 smem2[];
   const int LDU = W + 1;
-  double2* U = smem2;                               // [W][LDU] complex
-  double* Z = (double*)(U + bt_u_slots(W));         // [W][LDU] real
-  int* rank = (int*)(Z + (size_t)W * LDU);          // [W]
-  // during the replay U's space holds two log chunks: (c, s) pairs, then column indices
-  double2* logcs = U;                               // [2][LOG_CHUNK]
-  short* logi = (short*)(U + 2 * LOG_CHUNK);        // [2][LOG_CHUNK]
-  // after U = D Z, Z's space holds the reflectors: column j (rows j+1..W-1) at tri(W-2-j) offsets
-  double2* Rs = (double2*)Z;
+  double2* U = smem2;                               // [W][LDU] complex (LU scratch before)
+  double* Z = (double*)(U + bt_u_slots(W));         // [W][LDU] eigenvectors of T (by sorted index)
+  double* ws = Z + (size_t)W * LDU;                 // [W] sorted eigenvalues
+  double* dd = ws + W;                              // [W] diagonal of T
+  double* ee = dd + W;                              // [W] off-diagonal of T
+  int* rank = (int*)(ee + W);                       // [W]
+  int* newc = rank + W;                             // [W] 1 = starts a cluster
+  __shared__ double s_onenrm;
 
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t k = blockIdx.x;
-  const double* dk = b.d + k * W;
+  const double* lk = b.lam + k * W;
 
   // ascending order of the eigenvalues (ties broken by index)
   for (int j = t; j < W; j += NT) {
-    unsigned long long kj = order_key(dk[j]);
+    const double lj = lk[j];
+    const unsigned long long kj = order_key(lj);
     int rnk = 0;
     for (int i = 0; i < W; ++i) {
-      unsigned long long ki = order_key(dk[i]);
+      const unsigned long long ki = order_key(lk[i]);
       rnk += (ki < kj) || (ki == kj && i < j);
     }
     rank[j] = rnk;
-    Eout[k * W + rnk] = dk[j];
+    ws[rnk] = lj;
+    Eout[k * W + rnk] = lj;
+    dd[j] = b.d[k * W + j];
+    ee[j] = b.e[k * W + j];
   }
   if (Uout == nullptr) return;
-
-  for (int idx = t; idx < W * W; idx += NT) {
-    int r = idx / W, c = idx % W;
-    Z[r * LDU + c] = r == c ? 1.0 : 0.0;
-  }
-
-  // Replay the QL rotations: row r of Z is owned by thread r (< W); the other threads stage the
-  // next chunk of the log.  Rotation i acts on columns (i, i+1); within a sweep the indices
-  // descend, so column i of one rotation is column i+1 of the next and is carried in a
-  // register (`cur`, column `ci`): two dependent FP64 operations per rotation.
-  const int nr = min(b.nrot[k], b.cap);
-  const double2* rot = b.rot + k * b.cap;
-  const short* rc = b.rcol + k * b.cap;
-  const int nchunk = (nr + LOG_CHUNK - 1) / LOG_CHUNK;
-  for (int q = t; q < min(nr, LOG_CHUNK); q += NT) {
-    logcs[q] = rot[q];
-    logi[q] = rc[q];
+  __syncthreads();
+  if (warp == 0) {   // ||T||_1
+    double mx = 0.0;
+    for (int i = lane; i < W; i += 32)
+      mx = fmax(mx, fabs(dd[i]) + (i > 0 ? ee[i - 1] : 0.0) + (i < W - 1 ? ee[i] : 0.0));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_onenrm = mx > 0.0 ? mx : 1.0;
   }
   __syncthreads();
-  double cur = 0.0;
-  int ci = -2;   // no carried column
-  double* zr = Z + (t < W ? t : 0) * LDU;
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int buf = ch & 1;
-    const int q0 = ch * LOG_CHUNK;
-    const int qn = min(LOG_CHUNK, nr - q0);
-    if (t < W) {
-      const double2* cs_b = logcs + buf * LOG_CHUNK;
-      const short* i_b = logi + buf * LOG_CHUNK;
-      for (int q = 0; q < qn; ++q) {
-        const double2 cs = cs_b[q];
-        const int i = i_b[q];
-        double f;                  // column i+1
-        if (ci == i + 1) {
-          f = cur;
-        } else {
-          if (ci >= 0) zr[ci] = cur;
-          f = zr[i + 1];
+  const double onenrm = s_onenrm;
+  const double ortol = 1e-3 * onenrm;
+  const double eps = 2.220446049250313e-16;
+  const double pertol = 10.0 * eps * onenrm;
+  const double tiny = eps * onenrm;
+  for (int j = t; j < W; j += NT) newc[j] = (j == 0) || (ws[j] - ws[j - 1] > ortol);
+  __syncthreads();
+
+  double* rU0 = (double*)U;                 // [W][32] reciprocal pivots
+  double* U1 = rU0 + (size_t)W * 32;        // [W][32] first super-diagonal of U
+  double* U2 = U1 + (size_t)W * 32;         // [W][32] second super-diagonal of U
+  double* ML = U2 + (size_t)W * 32;         // [W][32] multipliers
+  for (int p0 = 0; p0 < W; p0 += 32) {
+    const int j = p0 + lane;
+    if (warp == 0 && j < W && newc[j]) {
+      double lprev = 0.0;
+      for (int m = j; m < W && (m == j || !newc[m]); ++m) {
+        double lam = ws[m];
+        if (m > j && lam - lprev <= pertol) lam = lprev + pertol;
+        lprev = lam;
+        // ---- LU of T - lam I with row interchanges
+        unsigned long long piv = 0ull;
+        double q0 = dd[0] - lam, q1 = W > 1 ? ee[0] : 0.0, q2 = 0.0;
+        for (int i = 0; i + 1 < W; ++i) {
+          const double ei = ee[i];
+          const double a = dd[i + 1] - lam;
+          const double bb = i + 2 < W ? ee[i + 1] : 0.0;
+          if (fabs(q0) >= fabs(ei)) {
+            if (q0 == 0.0) q0 = tiny;
+            const double r = 1.0 / q0;
+            const double mlt = ei * r;
+            rU0[i * 32 + lane] = r; U1[i * 32 + lane] = q1; U2[i * 32 + lane] = q2;
+            ML[i * 32 + lane] = mlt;
+            q0 = fma(-mlt, q1, a);
+            q1 = fma(-mlt, q2, bb);
+            q2 = 0.0;
+          } else {
+            const double r = 1.0 / ei;
+            const double mlt = q0 * r;
+            rU0[i * 32 + lane] = r; U1[i * 32 + lane] = a; U2[i * 32 + lane] = bb;
+            ML[i * 32 + lane] = mlt;
+            piv |= 1ull << i;
+            const double n0 = fma(-mlt, a, q1);
+            q1 = fma(-mlt, bb, q2);
+            q0 = n0;
+            q2 = 0.0;
+          }
         }
-        const double zi = zr[i];
-        zr[i + 1] = fma(cs.y, zi, cs.x * f);
-        cur = fma(cs.x, zi, -cs.y * f);
-        ci = i;
-      }
-    } else if (ch + 1 < nchunk) {
-      const int nb = buf ^ 1;
-      const int q1 = q0 + LOG_CHUNK;
-      const int qn1 = min(LOG_CHUNK, nr - q1);
-      for (int q = t - W; q < qn1; q += NT - W) {
-        logcs[nb * LOG_CHUNK + q] = rot[q1 + q];
-        logi[nb * LOG_CHUNK + q] = rc[q1 + q];
+        if (q0 == 0.0) q0 = tiny;
+        rU0[(W - 1) * 32 + lane] = 1.0 / q0;
+        U1[(W - 1) * 32 + lane] = 0.0;   // the last row of U has no super-diagonals; the
+        U2[(W - 1) * 32 + lane] = 0.0;   // back-substitution reads them (times zero)
+        if (W >= 2) U2[(W - 2) * 32 + lane] = 0.0;
+        // ---- inverse iteration in column m of Z
+        for (int i = 0; i < W; ++i) Z[i * LDU + m] = iit_start(i, m);
+        for (int it = 0; it < IIT_SOLVES; ++it) {
+          for (int i = 0; i + 1 < W; ++i) {
+            const double mlt = ML[i * 32 + lane];
+            const double yi = Z[i * LDU + m], yn = Z[(i + 1) * LDU + m];
+            if ((piv >> i) & 1ull) {
+              Z[i * LDU + m] = yn;
+              Z[(i + 1) * LDU + m] = fma(-mlt, yn, yi);
+            } else {
+              Z[(i + 1) * LDU + m] = fma(-mlt, yi, yn);
+            }
+          }
+          double x1 = 0.0, x2 = 0.0;   // x_{i+1}, x_{i+2}
+          for (int i = W - 1; i >= 0; --i) {
+            const double xi = (Z[i * LDU + m] - U1[i * 32 + lane] * x1 - U2[i * 32 + lane] * x2) *
+                              rU0[i * 32 + lane];
+            Z[i * LDU + m] = xi;
+            x2 = x1;
+            x1 = xi;
+          }
+          // orthogonalise against the cluster's previous vectors (modified Gram-Schmidt)
+          for (int q = j; q < m; ++q) {
+            double c = 0.0;
+            for (int i = 0; i < W; ++i) c = fma(Z[i * LDU + q], Z[i * LDU + m], c);
+            for (int i = 0; i < W; ++i) Z[i * LDU + m] = fma(-c, Z[i * LDU + q], Z[i * LDU + m]);
+          }
+          double s0 = 0.0, s1 = 0.0;
+          int i = 0;
+          for (; i + 1 < W; i += 2) {
+            const double u = Z[i * LDU + m], v = Z[(i + 1) * LDU + m];
+            s0 = fma(u, u, s0);
+            s1 = fma(v, v, s1);
+          }
+          if (i < W) { const double u = Z[i * LDU + m]; s0 = fma(u, u, s0); }
+          const double inv = 1.0 / sqrt(s0 + s1);
+          for (int i2 = 0; i2 < W; ++i2) Z[i2 * LDU + m] *= inv;
+        }
       }
     }
     __syncthreads();
   }
-  if (t < W && ci >= 0) zr[ci] = cur;
-  __syncthreads();
 
-  // U = D Z (overwrites the log buffers)
+  // U = D Z, columns in the original (unsorted) eigenvalue order of rank[]: column c of U holds
+  // the vector of sorted index c (the output below writes U[:, c] to column c).
   const double2* ph = b.phase + k * W;
   for (int idx = t; idx < W * W; idx += NT) {
     int r = idx / W, c = idx % W;
@@ -383,6 +444,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
   __syncthreads();
 
   // stage the reflectors in Z's space: reflector j (length m = W-1-j) at offset roff(j)
+  double2* Rs = (double2*)Z;
   const double2* R = b.refl + (size_t)k * W * W;
   auto roff = [&](int j) { return j * (W - 1) - (j * (j - 1)) / 2; };   // sum_{j'<j} (W-1-j')
   for (int idx = t; idx < W * W; idx += NT) {
@@ -430,10 +492,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
   }
   __syncthreads();
   double2* Uk = Uout + (size_t)k * W * W;
-  for (int idx = t; idx < W * W; idx += NT) {
-    int r = idx / W, c = idx % W;
-    Uk[r * W + rank[c]] = U[r * LDU + c];
-  }
+  for (int idx = t; idx < W * W; idx += NT) Uk[idx] = U[(idx / W) * LDU + idx % W];
 }
 
 }  // namespace
@@ -443,7 +502,7 @@ size_t tridiag_smem(int W) {
 }
 size_t backtransform_smem(int W) {
   return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
-         (size_t)W * sizeof(int);
+         (size_t)3 * W * sizeof(double) + (size_t)2 * W * sizeof(int);
 }
 size_t ql_smem(int W) { return (size_t)2 * 2 * W * 32 * sizeof(double); }
 

@@ -82,7 +82,7 @@ bool tc_fourier(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_FOUR
 bool f32_rotation(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_ROTATION; }
 
 struct Plan {
-  int W = 0, N_R = 0, N_h = 0, K = 0, n_EF = 0, n_eta = 1, chunk = 0, cap = 0;
+  int W = 0, N_R = 0, N_h = 0, K = 0, n_EF = 0, n_eta = 1, chunk = 0;
   int precision = KUBO_FP64;
   int Npad = 0, Kp = 0, Mpad = 0;   // tensor-core operand padding (mixed precision)
   bool model = false;   // needs the prepared Fourier basis
@@ -92,7 +92,7 @@ struct Plan {
   Mesh mesh{1, 1, 1, 1};
   size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
          o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
-         o_ph = 0, o_refl = 0, o_tau = 0, o_rot = 0, o_rcol = 0, o_nrot = 0, o_part = 0,
+         o_ph = 0, o_refl = 0, o_tau = 0, o_lam = 0, o_part = 0,
          o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0;
   // mixed-precision fix-up buffers
   bool fixup = false;
@@ -102,12 +102,10 @@ struct Plan {
   size_t total = 0;
 };
 
-int rot_capacity(int W) { return 3 * W * W + 64; }
-
 size_t bytes_per_k(int W, int n_eta) {
   size_t WW = (size_t)W * W;
-  return 3 * WW * 8 + WW * 16 /*U*/ + WW * 16 /*refl*/ + (size_t)rot_capacity(W) * 18 +
-         (size_t)W * (8 * 4 + 16) + (size_t)n_eta * W * 8 + 64;
+  return 3 * WW * 8 + WW * 16 /*U*/ + WW * 16 /*refl*/ + (size_t)W * (8 * 5 + 16) +
+         (size_t)n_eta * W * 8 + 64;
 }
 
 int auto_chunk(int W, int n_eta, int64_t n_total) {
@@ -150,9 +148,7 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_ph = b.take(sizeof(double2) * (size_t)p.chunk * p.W);
     p.o_tau = b.take(sizeof(double) * (size_t)p.chunk * p.W);
     p.o_refl = b.take(sizeof(double2) * (size_t)p.chunk * WW);
-    p.o_rot = b.take(sizeof(double2) * (size_t)p.chunk * p.cap);
-    p.o_rcol = b.take(sizeof(short) * (size_t)p.chunk * p.cap);
-    p.o_nrot = b.take(sizeof(int) * (size_t)p.chunk);
+    p.o_lam = b.take(sizeof(double) * (size_t)p.chunk * p.W);
   }
   if (p.berry) {
     p.o_E = b.take(sizeof(double) * (size_t)p.chunk * p.W);
@@ -272,7 +268,7 @@ struct StageTimer {
 kubo_status bits_to_status(unsigned bits) {
   if (bits & (ST_NOT_HERMITIAN | ST_NONFINITE)) return KUBO_ERR_NOT_HERMITIAN;
   if (bits & ST_TIMEOUT) return KUBO_ERR_TIMEOUT;
-  if (bits & (ST_NO_CONVERGENCE | ST_LOG_OVERFLOW)) return KUBO_ERR_NO_CONVERGENCE;
+  if (bits & ST_NO_CONVERGENCE) return KUBO_ERR_NO_CONVERGENCE;
   return KUBO_OK;
 }
 
@@ -353,11 +349,7 @@ EighBufs make_eigh_bufs(const Call& c) {
   b.phase = c.at<double2>(c.p.o_ph);
   b.refl = c.at<double2>(c.p.o_refl);
   b.tau = c.at<double>(c.p.o_tau);
-  b.rot = c.at<double2>(c.p.o_rot);
-  b.rcol = c.at<short>(c.p.o_rcol);
-  b.nrot = c.at<int>(c.p.o_nrot);
-  b.perm = nullptr;
-  b.cap = c.p.cap;
+  b.lam = c.at<double>(c.p.o_lam);
   return b;
 }
 
@@ -534,7 +526,6 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   if (kb == 0 && ke == 0) ke = p.mesh.Nk;
   if (kb < 0 || ke > p.mesh.Nk || kb > ke) return KUBO_ERR_INVALID_ARG;
   p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
-  p.cap = rot_capacity(W);
   p.model = p.eigh = p.berry = p.ksum = true;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   plan_layout(p, host_io, 0);
@@ -584,7 +575,6 @@ size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
   int64_t kb = o.k_begin, ke = o.k_end;
   if (kb == 0 && ke == 0) ke = p.mesh.Nk;
   p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
-  p.cap = rot_capacity(W);
   p.model = p.eigh = p.berry = p.ksum = true;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   plan_layout(p, false, 0);
@@ -769,8 +759,7 @@ kubo_status kubo_eigh_batched(const double* A, int W, int64_t n, double* E, doub
     Plan& p = c.p;
     p.W = W; p.n_eta = 1; p.n_EF = 1;
     p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, 1, n);
-    p.cap = rot_capacity(W);
-    p.eigh = true;
+      p.eigh = true;
     plan_layout(p, false, 0);
     c.s = (cudaStream_t)o.stream;
     kubo_status r = c.acquire(o);

@@ -15,7 +15,6 @@ enum : unsigned {
   ST_NOT_HERMITIAN = 1u,   // H(-R) != H(R)^dagger beyond tolerance
   ST_NONFINITE = 2u,       // NaN/Inf in H(R)
   ST_NO_CONVERGENCE = 4u,  // QL iteration cap reached at some k
-  ST_LOG_OVERFLOW = 8u,    // rotation log capacity exceeded at some k
   ST_TIMEOUT = 16u,        // a bounded device-side wait gave up
 };
 
@@ -88,16 +87,12 @@ __device__ __forceinline__ void mesh_coords(const Mesh& m, int64_t k, int& j1, i
 // ---------------------------------------------------------------- eigensolver buffers
 // Per-k intermediate layout of the three eigensolver kernels (all device memory).
 struct EighBufs {
-  double* d;        // [n][W]  diagonal of the real tridiagonal T; later eigenvalues
+  double* d;        // [n][W]  diagonal of the real tridiagonal T
   double* e;        // [n][W]  off-diagonal |beta_i| (e[W-1] unused)
   double2* phase;   // [n][W]  D of T_complex = D T D^dagger
   double2* refl;    // [n][W*W] Householder vectors v_i stored in column i, rows i+1..W-1
   double* tau;      // [n][W]
-  double2* rot;     // [n][cap] Givens rotations (c, s) of the QL sweeps
-  short* rcol;      // [n][cap] column index i of each rotation (acts on columns i, i+1)
-  int* nrot;        // [n] number of rotations logged
-  int* perm;        // [n][W] ascending order of eigenvalues
-  int cap;
+  double* lam;      // [n][W]  eigenvalues of T (unordered)
 };
 
 // ---------------------------------------------------------------- launchers

@@ -27,21 +27,14 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-int log_capacity(int W) { return 3 * W * W + 64; }
-
 // bytes of the block used by a pass of B matrices of order W (status word first)
 size_t pass_bytes(int W, int64_t B) {
-  const size_t cap = (size_t)log_capacity(W);
-  return align_up(sizeof(DevStatus)) + 3 * align_up(sizeof(double) * B * W) +
-         align_up(sizeof(double2) * B * W) + align_up(sizeof(double2) * B * W * W) +
-         align_up(sizeof(double2) * B * cap) + align_up(sizeof(short) * B * cap) +
-         align_up(sizeof(int) * B);
+  return align_up(sizeof(DevStatus)) + 4 * align_up(sizeof(double) * B * W) +
+         align_up(sizeof(double2) * B * W) + align_up(sizeof(double2) * B * W * W);
 }
 
 int64_t pass_capacity(int W) {
-  const size_t cap = (size_t)log_capacity(W);
-  const size_t per = sizeof(double) * 3 * W + sizeof(double2) * W + sizeof(double2) * W * W +
-                     (sizeof(double2) + sizeof(short)) * cap + sizeof(int);
+  const size_t per = sizeof(double) * 4 * W + sizeof(double2) * W + sizeof(double2) * W * W;
   int64_t B = (int64_t)(kScratchBytes / per);
   while (B > 0 && pass_bytes(W, B) > kScratchBytes) --B;
   return B;
@@ -90,19 +83,14 @@ extern "C" kubo_status kubo_eigh_batched_noalloc(const double* A, int W, int64_t
     // carve the block for a pass of B matrices
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base + off; off += align_up(bytes); return p; };
-    const size_t cap = (size_t)log_capacity(W);
     DevStatus* st = (DevStatus*)take(sizeof(DevStatus));
     EighBufs b;
     b.d = (double*)take(sizeof(double) * B * W);
     b.e = (double*)take(sizeof(double) * B * W);
     b.tau = (double*)take(sizeof(double) * B * W);
+    b.lam = (double*)take(sizeof(double) * B * W);
     b.phase = (double2*)take(sizeof(double2) * B * W);
     b.refl = (double2*)take(sizeof(double2) * B * W * W);
-    b.rot = (double2*)take(sizeof(double2) * B * cap);
-    b.rcol = (short*)take(sizeof(short) * B * cap);
-    b.nrot = (int*)take(sizeof(int) * B);
-    b.perm = nullptr;
-    b.cap = (int)cap;
 
     // the block keeps the previous call's contents: the status word must start at zero;
     // every other buffer is fully written before it is read
@@ -127,7 +115,7 @@ extern "C" kubo_status kubo_eigh_batched_noalloc(const double* A, int W, int64_t
       cudaGetLastError();
       return KUBO_ERR_CUDA;
     }
-    if (h.bits & (ST_NO_CONVERGENCE | ST_LOG_OVERFLOW)) return KUBO_ERR_NO_CONVERGENCE;
+    if (h.bits & ST_NO_CONVERGENCE) return KUBO_ERR_NO_CONVERGENCE;
     return KUBO_OK;
   } catch (...) {
     return KUBO_ERR_CUDA;

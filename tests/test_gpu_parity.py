@@ -97,6 +97,19 @@ def test_eigh_batched(kubo, torch, W):
         A[2] = 0
         A[2][:h, :h] = B
         A[2][h:2 * h, h:2 * h] = B
+    if W >= 6:
+        # exactly triple-degenerate spectrum (three identical blocks)
+        t3 = W // 3
+        C = _random_hermitian(rng, 1, t3)[0]
+        A[3] = 0
+        for q in range(3):
+            A[3][q * t3:(q + 1) * t3, q * t3:(q + 1) * t3] = C
+        # clusters: eigenvalue pairs split by 1e-9 in a random unitary basis
+        lam = np.sort(rng.standard_normal(W))
+        lam[1::2] = lam[0::2][: W // 2] + 1e-9
+        X = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
+        Q, _ = np.linalg.qr(X)
+        A[4] = (Q * lam) @ np.conj(Q.T)
     At = cuda(torch, A)
     E, U = kubo.eigh_batched(kubo.pack_hermitian(At), W)
     E, U = E.cpu().numpy(), U.cpu().numpy()
