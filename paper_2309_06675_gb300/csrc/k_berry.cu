@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restric
   float2* sU = smf;
   float2* sA = sU + W * LD;
   float2* sB = sA + W * LD;
-  double* red = (double*)(sB + W * LD);   // separate region (FP32 operands are small)
+  double* red = (double*)sA;   // reused (sA and beyond) after the pair terms are formed
   __shared__ double sE[64];
   __shared__ double sEta[MAXE];
   __shared__ double s_emax;
@@ -369,7 +369,9 @@ cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const doub
 }
 
 size_t berry_mixed_smem(int W, int n_eta) {
-  return 3 * (size_t)W * (W + 1) * sizeof(float2) + (size_t)n_eta * W * 2 * 16 * sizeof(double);
+  const size_t mat = (size_t)W * (W + 1) * sizeof(float2);
+  const size_t red = (size_t)n_eta * W * 2 * 16 * sizeof(double);
+  return mat + (2 * mat > red ? 2 * mat : red);
 }
 
 template <typename TIn>

@@ -237,16 +237,21 @@ __global__ void __launch_bounds__(64) ql_kernel(int W, int n, EighBufs b, DevSta
       for (int i = m - 1; i >= l; --i) {
         double ei = E[i * 32];
         double f = s * ei, bb = c * ei;
-        r = hypot(f, g);
-        E[(i + 1) * 32] = r;
-        if (r == 0.0) {   // split: the chase stops here
+        // r = |(f, g)| and (s, c) = (f, g) / r from one reciprocal square root (the entries of
+        // T are far from the FP64 overflow/underflow range, so no scaling is needed)
+        const double r2 = fma(f, f, g * g);
+        if (r2 == 0.0) {   // split: the chase stops here
+          E[(i + 1) * 32] = 0.0;
           D[(i + 1) * 32] -= p;
           E[m * 32] = 0.0;
           early = true;
           break;
         }
-        s = f / r;
-        c = g / r;
+        const double ir = rsqrt(r2);
+        r = r2 * ir;
+        E[(i + 1) * 32] = r;
+        s = f * ir;
+        c = g * ir;
         double gi = D[(i + 1) * 32] - p;
         double rr = fma(D[i * 32] - gi, s, 2.0 * c * bb);
         p = s * rr;

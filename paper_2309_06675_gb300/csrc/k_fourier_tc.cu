@@ -49,6 +49,9 @@ constexpr int NSLICE = 4;         // slices per operand: 7 + 3 x 8 = 31 fraction
 constexpr int NLEVEL = 4;         // levels l = i + j <= 3 kept: 10 slice pairs
 constexpr int NPAIR = 10;
 constexpr int NACC = 2;           // level-accumulator sets in flight (double buffer)
+constexpr int DRAIN = 4;          // K blocks summed in TMEM before the epilogue drains a set:
+                                  // 4 blocks x 4 pairs x 64 x 2^14 = 2^24, still exact in FP32
+constexpr int GROUP_M = 8;        // M tiles rasterised together so B tiles are reused from L2
 constexpr int TILE_A_BYTES = BM * BK * 2;            // 16 KB per slice
 constexpr int TILE_B_BYTES = BN * BK * 2;            // 8 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 96 KB
@@ -268,7 +271,7 @@ __constant__ int c_pj[NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 __constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 
 // ------------------------------------------------------------------ the tcgen05 GEMM
-// grid: (Npad / BN, Mpad / BM); out: FP64 [n rows][ldc], rows >= n_rows not written.
+// grid: (Npad / BN) * (Mpad / BM) CTAs; out: FP64 [n rows][ldc], rows >= n_rows not written.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, const int* __restrict__ col_exp,
@@ -282,7 +285,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ volatile int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  // grouped rasterisation: GROUP_M consecutive M tiles per column tile, so one B tile serves
+  // several CTAs in a row and the group's A tiles stay resident in L2 across column tiles
+  const int n_mt = Mpad / BM, n_nt = Npad / BN;
+  const int id = blockIdx.x;
+  const int per_group = GROUP_M * n_nt;
+  const int grp = id / per_group;
+  const int gm0 = grp * GROUP_M;
+  const int gsz = min(GROUP_M, n_mt - gm0);
+  const int in = id - grp * per_group;
+  const int n0 = (in / gsz) * BN, m0 = (gm0 + in % gsz) * BM;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -343,8 +355,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       for (int kb = 0; kb < nkb && !abort_sh; ++kb) {
         const int s = kb % NSTAGE;
-        const int a = kb % NACC;
-        if (kb >= NACC && !mbar_wait(&acc_empty[a], (uint32_t)(kb / NACC - 1) & 1u)) {
+        const int g = kb / DRAIN;            // drain group of this K block
+        const int a = g % NACC;
+        const bool first = kb % DRAIN == 0;
+        const bool last = kb % DRAIN == DRAIN - 1 || kb == nkb - 1;
+        if (first && g >= NACC && !mbar_wait(&acc_empty[a], (uint32_t)(g / NACC - 1) & 1u)) {
           atomicOr(&st->bits, ST_TIMEOUT);
           abort_sh = 1;
           break;
@@ -356,18 +371,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         for (int kk = 0; kk < BK / 16; ++kk) {
-          int seen = 0;   // bit l set once level l has been written in this K block
+          int seen = 0;   // bit l set once level l has been written in this drain group
           for (int p = 0; p < NPAIR; ++p) {
             const int l = c_pl[p];
-            const uint32_t acc = (kk > 0 || (seen >> l) & 1) ? 1u : 0u;
+            const uint32_t acc = (!first || kk > 0 || (seen >> l) & 1) ? 1u : 0u;
             seen |= 1 << l;
             const uint64_t da = umma_desc_sw128(smem_u32(stageA(s, c_pi[p])) + kk * 32);
             const uint64_t db = umma_desc_sw128(smem_u32(stageB(s, c_pj[p])) + kk * 32);
             umma_bf16(tmem + (uint32_t)((a * NLEVEL + l) * BN), da, db, acc);
           }
         }
-        umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
-        umma_commit(&acc_full[a]);    // level sums of this K block complete
+        umma_commit(&empty_bar[s]);          // stage free once these MMAs have read it
+        if (last) umma_commit(&acc_full[a]); // level sums of this drain group complete
       }
       umma_commit(&done_bar);         // all issued MMAs complete
     }
@@ -377,15 +392,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int row = quarter * 32 + lane;
     const int grow = m0 + row;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    // One exact integer per column: sum over K blocks and levels of I_l 2^(32 - 8 l).  A block's
-    // level sum is below 2^22 in magnitude, so the total stays below 2^57 (no overflow).
+    // One exact integer per column: sum over drain groups and levels of I_l 2^(32 - 8 l).  A
+    // group's level sum is at most 2^24 in magnitude, so the total stays below 2^57.
     long long isum[BN];
 #pragma unroll
     for (int j = 0; j < BN; ++j) isum[j] = 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int a = kb % NACC;
-      ok = mbar_wait(&acc_full[a], (uint32_t)(kb / NACC) & 1u);
+    const int ngroups = (nkb + DRAIN - 1) / DRAIN;
+    for (int g = 0; g < ngroups; ++g) {
+      const int a = g % NACC;
+      ok = mbar_wait(&acc_full[a], (uint32_t)(g / NACC) & 1u);
       ok = __all_sync(0xffffffffu, ok && !abort_sh);   // tcgen05.ld is warp-collective
       if (!ok) break;
       tc_fence_after();
@@ -504,7 +520,7 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
   const size_t sm = fourier_tc_smem();
   cudaError_t e = cudaFuncSetAttribute(fourier_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid(Npad / BN, Mpad / BM);
+  dim3 grid((Npad / BN) * (Mpad / BM));
   fourier_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out,
                                                  ldc, st);
   return cudaGetLastError();
