@@ -117,7 +117,10 @@ void kubo_options_init(kubo_options* opt);
 /* Human-readable name of a status code (static storage). */
 const char* kubo_status_string(kubo_status s);
 
-/* Largest orbital count W supported by this build for the given precision. */
+/* Largest orbital count W supported by this build for the given precision (128 for every
+ * precision).  Up to W = 64 the eigenvectors and the rotations of a k-point are formed inside
+ * one thread block each; for 64 < W <= 128 they run as batched multi-pass kernels whose
+ * scratch is part of the workspace. */
 int kubo_max_orbitals(int precision);
 
 /*

@@ -509,7 +509,9 @@ size_t backtransform_smem(int W) {
   return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
          (size_t)3 * W * sizeof(double) + (size_t)2 * W * sizeof(int);
 }
-size_t ql_smem(int W) { return (size_t)2 * 2 * W * 32 * sizeof(double); }
+// threads per QL block: two warps, one beyond W = 64 (d and e of a warp take 2 W 32 doubles)
+static int ql_threads(int W) { return W > 64 ? 32 : 64; }
+size_t ql_smem(int W) { return (size_t)(ql_threads(W) / 32) * 2 * W * 32 * sizeof(double); }
 
 cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
@@ -535,7 +537,8 @@ cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s) {
   size_t sm = ql_smem(W);
   cudaError_t e = cudaFuncSetAttribute(ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  ql_kernel<<<(n + 63) / 64, 64, sm, s>>>(W, n, b, st);
+  const int nt = ql_threads(W);
+  ql_kernel<<<(n + nt - 1) / nt, nt, sm, s>>>(W, n, b, st);
   return cudaGetLastError();
 }
 

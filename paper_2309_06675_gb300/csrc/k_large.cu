@@ -1,0 +1,485 @@
+// Steps (2)-(4) for orders 64 < W <= 128, where a whole k-point no longer fits one CTA's
+// shared memory.  Same arithmetic as the fused kernels, split into batched passes:
+//   iit_large_kernel      eigenvalue sort + eigenvectors of the tridiagonal T by inverse
+//                         iteration, one thread per cluster; LU factors and iterates in global
+//                         scratch laid out [.. ][i][thread] (coalesced)
+//   reflect_large_kernel  U = Q D Z for one 32-column block of one k-point per CTA
+//   cgemm_herm_u_kernel   T = dH U   (dH from packed Hermitian rows)          } FP64 or FP32
+//   cgemm_uh_t_kernel     V = U^H T                                            } arithmetic
+//   curvature_large_kernel Omega_n = sum_{m != n} T_nm, every pair evaluated from the upper
+//                         triangle (exact antisymmetry), FP64 denominators for every eta
+#include "kubo_internal.cuh"
+
+namespace kubo {
+
+namespace {
+
+constexpr int LW_MAX = LARGE_W_MAX;
+constexpr int IIT_SOLVES = 3;
+constexpr int MAXE = 8;
+
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double iit_start(int i, int j) {
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+}
+
+// ------------------------------------------------------------------ inverse iteration
+// block = LW_MAX threads, one k-point; thread j handles the cluster starting at sorted index j.
+// Z: [n][W][W] real, column m = eigenvector of sorted eigenvalue m.
+// scratch: [n][4][W][LW_MAX] (reciprocal pivots, U1, U2, multipliers).
+__global__ void __launch_bounds__(LW_MAX) iit_large_kernel(int W, EighBufs b, double* __restrict__ Eout,
+                                                           double* __restrict__ Z,
+                                                           double* __restrict__ scratch) {
+  __shared__ double ws[LW_MAX], dd[LW_MAX], ee[LW_MAX];
+  __shared__ int newc[LW_MAX];
+  __shared__ double s_onenrm;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t k = blockIdx.x;
+  const double* lk = b.lam + k * W;
+  if (t < W) {
+    const double lj = lk[t];
+    const unsigned long long kj = order_key(lj);
+    int rnk = 0;
+    for (int i = 0; i < W; ++i) {
+      const unsigned long long ki = order_key(lk[i]);
+      rnk += (ki < kj) || (ki == kj && i < t);
+    }
+    ws[rnk] = lj;
+    Eout[k * W + rnk] = lj;
+    dd[t] = b.d[k * W + t];
+    ee[t] = b.e[k * W + t];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double mx = 0.0;
+    for (int i = lane; i < W; i += 32)
+      mx = fmax(mx, fabs(dd[i]) + (i > 0 ? ee[i - 1] : 0.0) + (i < W - 1 ? ee[i] : 0.0));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_onenrm = mx > 0.0 ? mx : 1.0;
+  }
+  __syncthreads();
+  const double onenrm = s_onenrm;
+  const double eps = 2.220446049250313e-16;
+  const double ortol = 1e-3 * onenrm, pertol = 10.0 * eps * onenrm, tiny = eps * onenrm;
+  if (t < W) newc[t] = (t == 0) || (ws[t] - ws[t - 1] > ortol);
+  __syncthreads();
+  if (Z == nullptr) return;
+
+  const size_t plane = (size_t)W * LW_MAX;
+  double* rU0 = scratch + (size_t)k * 4 * plane;
+  double* U1 = rU0 + plane;
+  double* U2 = U1 + plane;
+  double* ML = U2 + plane;
+  double* Zk = Z + (size_t)k * W * W;
+  const int j = t;
+  if (j < W && newc[j]) {
+    double lprev = 0.0;
+    for (int m = j; m < W && (m == j || !newc[m]); ++m) {
+      double lam = ws[m];
+      if (m > j && lam - lprev <= pertol) lam = lprev + pertol;
+      lprev = lam;
+      unsigned long long piv0 = 0ull, piv1 = 0ull;   // row interchanges, bits 0..127
+      double q0 = dd[0] - lam, q1 = W > 1 ? ee[0] : 0.0, q2 = 0.0;
+      for (int i = 0; i + 1 < W; ++i) {
+        const double ei = ee[i];
+        const double a = dd[i + 1] - lam;
+        const double bb = i + 2 < W ? ee[i + 1] : 0.0;
+        const size_t o = (size_t)i * LW_MAX + t;
+        if (fabs(q0) >= fabs(ei)) {
+          if (q0 == 0.0) q0 = tiny;
+          const double r = 1.0 / q0;
+          const double mlt = ei * r;
+          rU0[o] = r; U1[o] = q1; U2[o] = q2; ML[o] = mlt;
+          q0 = fma(-mlt, q1, a);
+          q1 = fma(-mlt, q2, bb);
+          q2 = 0.0;
+        } else {
+          const double r = 1.0 / ei;
+          const double mlt = q0 * r;
+          rU0[o] = r; U1[o] = a; U2[o] = bb; ML[o] = mlt;
+          if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64);
+          const double n0 = fma(-mlt, a, q1);
+          q1 = fma(-mlt, bb, q2);
+          q0 = n0;
+          q2 = 0.0;
+        }
+      }
+      if (q0 == 0.0) q0 = tiny;
+      {
+        const size_t o = (size_t)(W - 1) * LW_MAX + t;
+        rU0[o] = 1.0 / q0; U1[o] = 0.0; U2[o] = 0.0;
+      }
+      for (int i = 0; i < W; ++i) Zk[(size_t)i * W + m] = iit_start(i, m);
+      for (int it = 0; it < IIT_SOLVES; ++it) {
+        for (int i = 0; i + 1 < W; ++i) {
+          const double mlt = ML[(size_t)i * LW_MAX + t];
+          const double yi = Zk[(size_t)i * W + m], yn = Zk[(size_t)(i + 1) * W + m];
+          const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
+          if (sw) {
+            Zk[(size_t)i * W + m] = yn;
+            Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yn, yi);
+          } else {
+            Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yi, yn);
+          }
+        }
+        double x1 = 0.0, x2 = 0.0;
+        for (int i = W - 1; i >= 0; --i) {
+          const size_t o = (size_t)i * LW_MAX + t;
+          const double xi = (Zk[(size_t)i * W + m] - U1[o] * x1 - U2[o] * x2) * rU0[o];
+          Zk[(size_t)i * W + m] = xi;
+          x2 = x1;
+          x1 = xi;
+        }
+        for (int q = j; q < m; ++q) {
+          double c = 0.0;
+          for (int i = 0; i < W; ++i) c = fma(Zk[(size_t)i * W + q], Zk[(size_t)i * W + m], c);
+          for (int i = 0; i < W; ++i)
+            Zk[(size_t)i * W + m] = fma(-c, Zk[(size_t)i * W + q], Zk[(size_t)i * W + m]);
+        }
+        double s0 = 0.0, s1 = 0.0;
+        int i = 0;
+        for (; i + 1 < W; i += 2) {
+          const double u = Zk[(size_t)i * W + m], v = Zk[(size_t)(i + 1) * W + m];
+          s0 = fma(u, u, s0);
+          s1 = fma(v, v, s1);
+        }
+        if (i < W) { const double u = Zk[(size_t)i * W + m]; s0 = fma(u, u, s0); }
+        const double inv = 1.0 / sqrt(s0 + s1);
+        for (int i2 = 0; i2 < W; ++i2) Zk[(size_t)i2 * W + m] *= inv;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ U = Q D Z, column blocks
+// One CTA per (32-column block, k-point): the block of D Z in shared memory, the reflectors
+// applied from the last to the first (U <- H_j U), eight reflectors at a time staged in shared
+// memory from coalesced row segments of the reflector matrix.
+constexpr int RB_COLS = 32;
+constexpr int RB_NT = 256;   // 8 threads per column
+constexpr int RB_J = 8;      // reflectors per staged block
+
+__global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
+                                                              const double* __restrict__ Z,
+                                                              double2* __restrict__ Uout) {
+  extern __shared__ double2 ub[];   // [W][RB_COLS + 1]
+  __shared__ double2 vs[RB_J][LW_MAX + 1];
+  const int LDB = RB_COLS + 1;
+  const int t = threadIdx.x;
+  const int c0 = blockIdx.y * RB_COLS;
+  const int64_t k = blockIdx.x;
+  const int ncol = min(RB_COLS, W - c0);
+  const double* Zk = Z + (size_t)k * W * W;
+  const double2* ph = b.phase + k * W;
+  for (int idx = t; idx < W * RB_COLS; idx += RB_NT) {
+    const int r = idx / RB_COLS, c = idx % RB_COLS;
+    double2 u = make_double2(0.0, 0.0);
+    if (c < ncol) {
+      const double z = Zk[(size_t)r * W + c0 + c];
+      const double2 p = ph[r];
+      u = make_double2(p.x * z, p.y * z);
+    }
+    ub[r * LDB + c] = u;
+  }
+  const double2* R = b.refl + (size_t)k * W * W;
+  const double* tau = b.tau + k * W;
+  const int c = t >> 3, q = t & 7;
+  const bool act = c < ncol;
+  for (int jhi = W - 3; jhi >= 0; jhi -= RB_J) {
+    const int jlo = max(0, jhi - RB_J + 1);
+    __syncthreads();   // the previous block of reflectors is no longer read
+    for (int idx = t; idx < W * RB_J; idx += RB_NT) {
+      const int r = idx / RB_J, jj = idx % RB_J, j = jlo + jj;
+      if (j <= jhi) vs[jj][r] = r > j ? R[(size_t)r * W + j] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int j = jhi; j >= jlo; --j) {
+      const double tj = tau[j];
+      if (tj == 0.0) continue;
+      const int o = j + 1, m = W - 1 - j;
+      const double2* v = vs[j - jlo] + o;
+      double sx = 0.0, sy = 0.0;
+      if (act) {
+        for (int r = q; r < m; r += 8) {
+          const double2 vv = v[r];
+          const double2 u = ub[(o + r) * LDB + c];
+          sx = fma(vv.x, u.x, fma(vv.y, u.y, sx));   // conj(v) u
+          sy = fma(vv.x, u.y, fma(-vv.y, u.x, sy));
+        }
+      }
+#pragma unroll
+      for (int s = 1; s < 8; s <<= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, s);
+        sy += __shfl_xor_sync(0xffffffffu, sy, s);
+      }
+      sx *= tj; sy *= tj;
+      if (act) {
+        for (int r = q; r < m; r += 8) {
+          const double2 vv = v[r];
+          double2 u = ub[(o + r) * LDB + c];
+          u.x = fma(-sx, vv.x, fma(sy, vv.y, u.x));   // u -= s v
+          u.y = fma(-sx, vv.y, fma(-sy, vv.x, u.y));
+          ub[(o + r) * LDB + c] = u;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double2* Uk = Uout + (size_t)k * W * W;
+  for (int idx = t; idx < W * RB_COLS; idx += RB_NT) {
+    const int r = idx / RB_COLS, cc = idx % RB_COLS;
+    if (cc < ncol) Uk[(size_t)r * W + c0 + cc] = ub[r * LDB + cc];
+  }
+}
+
+// ------------------------------------------------------------------ batched complex GEMMs
+// 64 x 64 output tile per CTA, 16 x 16 threads with 4 x 4 strided micro-tiles, K tiles of 16.
+template <typename T> struct cx;
+template <> struct cx<double> { typedef double2 type; __device__ static double2 make(double a, double b) { return make_double2(a, b); } };
+template <> struct cx<float> { typedef float2 type; __device__ static float2 make(double a, double b) { return make_float2((float)a, (float)b); } };
+
+constexpr int GT = 64, GK = 16;
+
+// C[k] = H[k] U[k]; H from packed Hermitian rows P (leading dimension ldp), U complex FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) cgemm_herm_u_kernel(const double* __restrict__ P, int64_t ldp,
+                                                           const double2* __restrict__ U, int W,
+                                                           typename cx<T>::type* __restrict__ C) {
+  typedef typename cx<T>::type C2;
+  __shared__ C2 As[GT][GK + 1];
+  __shared__ C2 Bs[GK][GT + 1];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int nt = (W + GT - 1) / GT;
+  const int r0 = (blockIdx.y / nt) * GT, c0 = (blockIdx.y % nt) * GT;
+  const int64_t k = blockIdx.x;
+  const double* Pk = P + k * ldp;
+  const double2* Uk = U + (size_t)k * W * W;
+  T ax[4][4], ay[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { ax[i][j] = 0; ay[i][j] = 0; }
+  for (int q0 = 0; q0 < W; q0 += GK) {
+    for (int idx = t; idx < GT * GK; idx += 256) {
+      const int r = idx / GK, q = idx % GK;
+      const int gr = r0 + r, gq = q0 + q;
+      C2 a = cx<T>::make(0.0, 0.0);
+      if (gr < W && gq < W) {
+        if (gr < gq) a = cx<T>::make(Pk[gr * W + gq], Pk[gq * W + gr]);
+        else if (gr > gq) a = cx<T>::make(Pk[gq * W + gr], -Pk[gr * W + gq]);
+        else a = cx<T>::make(Pk[gr * W + gr], 0.0);
+      }
+      As[r][q] = a;
+    }
+    for (int idx = t; idx < GK * GT; idx += 256) {
+      const int q = idx / GT, c = idx % GT;
+      const int gq = q0 + q, gc = c0 + c;
+      C2 v = cx<T>::make(0.0, 0.0);
+      if (gq < W && gc < W) { const double2 u = Uk[(size_t)gq * W + gc]; v = cx<T>::make(u.x, u.y); }
+      Bs[q][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GK; ++q) {
+      C2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[ty + 16 * i][q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[q][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ax[i][j] = fma(a[i].x, bb[j].x, ax[i][j]);
+          ax[i][j] = fma(-a[i].y, bb[j].y, ax[i][j]);
+          ay[i][j] = fma(a[i].x, bb[j].y, ay[i][j]);
+          ay[i][j] = fma(a[i].y, bb[j].x, ay[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+  typename cx<T>::type* Ck = C + (size_t)k * W * W;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+      if (r < W && c < W) { C2 v; v.x = ax[i][j]; v.y = ay[i][j]; Ck[(size_t)r * W + c] = v; }
+    }
+}
+
+// V[k] = U[k]^H Tm[k]
+template <typename T>
+__global__ void __launch_bounds__(256) cgemm_uh_t_kernel(const double2* __restrict__ U,
+                                                         const typename cx<T>::type* __restrict__ Tm,
+                                                         int W, typename cx<T>::type* __restrict__ V) {
+  typedef typename cx<T>::type C2;
+  __shared__ C2 As[GT][GK + 1];
+  __shared__ C2 Bs[GK][GT + 1];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int nt = (W + GT - 1) / GT;
+  const int r0 = (blockIdx.y / nt) * GT, c0 = (blockIdx.y % nt) * GT;
+  const int64_t k = blockIdx.x;
+  const double2* Uk = U + (size_t)k * W * W;
+  const C2* Tk = Tm + (size_t)k * W * W;
+  if (r0 >= c0 + GT) return;   // strictly below the diagonal: V is Hermitian, never read
+  T ax[4][4], ay[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { ax[i][j] = 0; ay[i][j] = 0; }
+  for (int q0 = 0; q0 < W; q0 += GK) {
+    for (int idx = t; idx < GT * GK; idx += 256) {
+      const int q = idx / GT, r = idx % GT;   // coalesced along r (a row of U)
+      const int gr = r0 + r, gq = q0 + q;
+      C2 a = cx<T>::make(0.0, 0.0);
+      if (gr < W && gq < W) { const double2 u = Uk[(size_t)gq * W + gr]; a = cx<T>::make(u.x, -u.y); }
+      As[r][q] = a;
+    }
+    for (int idx = t; idx < GK * GT; idx += 256) {
+      const int q = idx / GT, c = idx % GT;
+      const int gq = q0 + q, gc = c0 + c;
+      Bs[q][c] = (gq < W && gc < W) ? Tk[(size_t)gq * W + gc] : cx<T>::make(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GK; ++q) {
+      C2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[ty + 16 * i][q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[q][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ax[i][j] = fma(a[i].x, bb[j].x, ax[i][j]);
+          ax[i][j] = fma(-a[i].y, bb[j].y, ax[i][j]);
+          ay[i][j] = fma(a[i].x, bb[j].y, ay[i][j]);
+          ay[i][j] = fma(a[i].y, bb[j].x, ay[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+  C2* Vk = V + (size_t)k * W * W;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+      if (r < W && c < W) { C2 v; v.x = ax[i][j]; v.y = ay[i][j]; Vk[(size_t)r * W + c] = v; }
+    }
+}
+
+// ------------------------------------------------------------------ curvature, thread per band
+template <typename T>
+__global__ void __launch_bounds__(LW_MAX) curvature_large_kernel(const double* __restrict__ E,
+                                                                 const typename cx<T>::type* __restrict__ Vx,
+                                                                 const typename cx<T>::type* __restrict__ Vy,
+                                                                 int W, const double* __restrict__ etas,
+                                                                 int n_eta, double* __restrict__ Om,
+                                                                 int64_t eta_stride) {
+  __shared__ double sE[LW_MAX];
+  __shared__ double s_emax;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t k = blockIdx.x;
+  if (t < W) sE[t] = E[k * W + t];
+  __syncthreads();
+  if (warp == 0) {
+    double mx = 0.0;
+    for (int i = lane; i < W; i += 32) mx = fmax(mx, fabs(sE[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_emax = mx;
+  }
+  __syncthreads();
+  const int n = t;
+  if (n >= W) return;
+  const double thr2 = (1e-12 * s_emax) * (1e-12 * s_emax);
+  double rp[MAXE];
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) rp[e] = 0.0;
+  const size_t base = (size_t)k * W * W;
+  for (int m = 0; m < W; ++m) {
+    if (m == n) continue;
+    const int p = n < m ? n : m, q = n < m ? m : n;
+    const typename cx<T>::type vx = Vx[base + (size_t)p * W + q];
+    const typename cx<T>::type vy = Vy[base + (size_t)p * W + q];
+    const double num = -2.0 * ((double)vx.y * (double)vy.x - (double)vx.x * (double)vy.y);
+    const double dE = sE[p] - sE[q];
+    const double d2 = dE * dE;
+    const double sgn = n < m ? 1.0 : -1.0;   // T_nm = -T_mn: evaluated from the (p < q) entry
+#pragma unroll
+    for (int e = 0; e < MAXE; ++e) {
+      if (e >= n_eta) break;
+      const double eta = etas[e];
+      if (eta == 0.0 && d2 <= thr2) continue;
+      rp[e] += sgn * (num / fma(eta, eta, d2));
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    if (e >= n_eta) break;
+    Om[e * eta_stride + k * W + n] = rp[e];
+  }
+}
+
+}  // namespace
+
+size_t large_iit_scratch_doubles(int W) { return (size_t)4 * W * LW_MAX; }
+
+cudaError_t launch_iit_large(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > LW_MAX) return cudaErrorInvalidValue;
+  iit_large_kernel<<<n, LW_MAX, 0, s>>>(W, b, E, Z, scratch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, double2* U,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t sm = (size_t)W * (RB_COLS + 1) * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(reflect_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(n, (W + RB_COLS - 1) / RB_COLS);
+  reflect_large_kernel<<<grid, RB_NT, sm, s>>>(W, b, Z, U);
+  return cudaGetLastError();
+}
+
+// steps (3)-(4) for large W: X, Y packed Hermitian rows (leading dimension ld), FP64 U.
+// f32 selects FP32 arithmetic for the products (mixed precision).  Tbuf, Vx, Vy: scratch of
+// n * W * W complex elements of the arithmetic type each.
+cudaError_t launch_berry_large(const double* E, const double2* U, const double* X, const double* Y,
+                               int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
+                               int64_t eta_stride, bool f32, void* Tbuf, void* Vx, void* Vy,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > LW_MAX || n_eta > MAXE) return cudaErrorInvalidValue;
+  const int tiles = (W + GT - 1) / GT;
+  dim3 grid(n, tiles * tiles);
+  if (f32) {
+    cgemm_herm_u_kernel<float><<<grid, 256, 0, s>>>(X, ld, U, W, (float2*)Tbuf);
+    cgemm_uh_t_kernel<float><<<grid, 256, 0, s>>>(U, (const float2*)Tbuf, W, (float2*)Vx);
+    cgemm_herm_u_kernel<float><<<grid, 256, 0, s>>>(Y, ld, U, W, (float2*)Tbuf);
+    cgemm_uh_t_kernel<float><<<grid, 256, 0, s>>>(U, (const float2*)Tbuf, W, (float2*)Vy);
+    curvature_large_kernel<float><<<n, LW_MAX, 0, s>>>(E, (const float2*)Vx, (const float2*)Vy, W,
+                                                        etas, n_eta, Om, eta_stride);
+  } else {
+    cgemm_herm_u_kernel<double><<<grid, 256, 0, s>>>(X, ld, U, W, (double2*)Tbuf);
+    cgemm_uh_t_kernel<double><<<grid, 256, 0, s>>>(U, (const double2*)Tbuf, W, (double2*)Vx);
+    cgemm_herm_u_kernel<double><<<grid, 256, 0, s>>>(Y, ld, U, W, (double2*)Tbuf);
+    cgemm_uh_t_kernel<double><<<grid, 256, 0, s>>>(U, (const double2*)Tbuf, W, (double2*)Vy);
+    curvature_large_kernel<double><<<n, LW_MAX, 0, s>>>(E, (const double2*)Vx, (const double2*)Vy,
+                                                         W, etas, n_eta, Om, eta_stride);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kubo

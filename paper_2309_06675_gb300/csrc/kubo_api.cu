@@ -14,7 +14,8 @@ using namespace kubo;
 
 namespace {
 
-constexpr int MAX_W = 64;
+constexpr int MAX_W = LARGE_W_MAX;
+constexpr int SMALL_W_MAX = 64;      // beyond: the multi-pass eigenvector / rotation kernels
 constexpr int MAX_ETA = 8;
 constexpr int KSUM_KPB = 256;        // k-points per deterministic k-sum block
 // mixed precision: share of each batch (largest ||Omega(k)||_inf) redone in FP64
@@ -89,11 +90,12 @@ struct Plan {
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
   bool ksum = false;    // needs k-sum buffers
+  bool lbuf = false;    // W > SMALL_W_MAX: scratch of the multi-pass kernels
   Mesh mesh{1, 1, 1, 1};
   size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
          o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
          o_ph = 0, o_refl = 0, o_tau = 0, o_lam = 0, o_part = 0,
-         o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0;
+         o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0, o_L = 0;
   // mixed-precision fix-up buffers
   bool fixup = false;
   int fix_cap = 0;
@@ -102,10 +104,19 @@ struct Plan {
   size_t total = 0;
 };
 
+// Per k-point scratch of the W > SMALL_W_MAX kernels, reused by stage: inverse-iteration
+// factors + Z, then the FP64 rotation products T, V^x, V^y (the largest case).
+size_t large_region_bytes(int W) {
+  const size_t WW = (size_t)W * W;
+  const size_t eig = large_iit_scratch_doubles(W) * sizeof(double) + WW * sizeof(double);
+  const size_t rot = 3 * WW * sizeof(double2);
+  return std::max(eig, rot);
+}
+
 size_t bytes_per_k(int W, int n_eta) {
   size_t WW = (size_t)W * W;
   return 3 * WW * 8 + WW * 16 /*U*/ + WW * 16 /*refl*/ + (size_t)W * (8 * 5 + 16) +
-         (size_t)n_eta * W * 8 + 64;
+         (size_t)n_eta * W * 8 + 64 + (W > SMALL_W_MAX ? large_region_bytes(W) : 0);
 }
 
 int auto_chunk(int W, int n_eta, int64_t n_total) {
@@ -168,6 +179,7 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_fE = b.take(sizeof(double) * (size_t)p.fix_cap * p.W);
     p.o_fOm = b.take(sizeof(double) * (size_t)p.fix_cap * p.W * p.n_eta);
   }
+  if (p.lbuf) p.o_L = b.take(large_region_bytes(p.W) * (size_t)std::max(1, p.chunk));
   if (p.ksum) {
     const int n_out = p.n_eta * p.n_EF;
     p.o_acc = b.take(sizeof(double2) * n_out);
@@ -353,6 +365,42 @@ EighBufs make_eigh_bufs(const Call& c) {
   return b;
 }
 
+// Eigenvalues (sorted) and eigenvectors U = Q D Z of n tridiagonalised matrices whose
+// eigenvalues QL left in eb.lam (U may be null: eigenvalues only).
+cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, double2* U) {
+  const Plan& p = c.p;
+  if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s);
+  double* scr = c.at<double>(p.o_L);
+  double* Z = U ? scr + large_iit_scratch_doubles(p.W) * (size_t)std::max(1, p.chunk) : nullptr;
+  cudaError_t e = launch_iit_large(p.W, n, eb, E, Z, scr, c.s);
+  if (e != cudaSuccess || !U) return e;
+  return launch_reflect_large(p.W, n, eb, Z, U, c.s);
+}
+
+// Steps (3)-(4) from packed Hermitian dH rows X, Y of leading dimension ld; f32 = FP32
+// products.  rows = X and Y are the W*W and 2*W*W column offsets of tensor-core output rows.
+cudaError_t berry_any(const Call& c, const double* E, const double2* U, const double* X,
+                      const double* Y, int64_t ld, bool rows, int n, bool f32, double* Om,
+                      int64_t om_stride) {
+  const Plan& p = c.p;
+  const double* etas = c.at<double>(p.o_etas);
+  if (p.W > SMALL_W_MAX) {
+    const size_t WW = (size_t)p.W * p.W;
+    const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+    char* L = c.at<char>(p.o_L);
+    const size_t cap = (size_t)std::max(1, p.chunk) * WW * es;
+    return launch_berry_large(E, U, X, Y, ld, p.W, n, etas, p.n_eta, Om, om_stride, f32, L, L + cap,
+                              L + 2 * cap, c.s);
+  }
+  if (rows) {
+    const double* C = X - (size_t)p.W * p.W;   // the row start (H | dxH | dyH)
+    return f32 ? launch_berry_mixed_rows(E, U, C, ld, p.W, n, etas, p.n_eta, Om, om_stride, c.s)
+               : launch_berry_fp64_rows(E, U, C, ld, p.W, n, etas, p.n_eta, Om, om_stride, c.s);
+  }
+  return f32 ? launch_berry_mixed_from_f64(E, U, X, Y, p.W, n, etas, p.n_eta, Om, om_stride, c.s)
+             : launch_berry_fp64(E, U, X, Y, p.W, n, etas, p.n_eta, Om, om_stride, c.s);
+}
+
 // Steps (1)-(4) for one batch [t0, t0+n) of a k-list; E and U go to the chunk buffers, Omega
 // to Om (eta stride om_stride).  Eout may redirect the sorted eigenvalues.
 // Mixed precision: step (1) on the tensor cores into rows [H | dxH | dyH], the eigensolver
@@ -379,15 +427,13 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
   }
   {
-    StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-    KCHECK(launch_backtransform(p.W, kl.n, eb, Eout, U, c.s));
+    StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
+    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U));
   }
   {
-    StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    if (f32_rotation(p.precision))
-      KCHECK(launch_berry_mixed_rows(Eout, U, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
-    else
-      KCHECK(launch_berry_fp64_rows(Eout, U, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);
+    const size_t WW = (size_t)p.W * p.W;
+    KCHECK(berry_any(c, Eout, U, C64 + WW, C64 + 2 * WW, p.Npad, true, kl.n, f32_rotation(p.precision), Om, om_stride));
   }
   return KUBO_OK;
 }
@@ -415,15 +461,12 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
     KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
   }
   {
-    StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-    KCHECK(launch_backtransform(p.W, kl.n, eb, Eout, U, c.s));
+    StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
+    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U));
   }
   {
-    StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    if (f32_rotation(p.precision))
-      KCHECK(launch_berry_mixed_from_f64(Eout, U, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
-    else
-      KCHECK(launch_berry_fp64(Eout, U, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);
+    KCHECK(berry_any(c, Eout, U, Xp, Yp, (int64_t)p.W * p.W, false, kl.n, f32_rotation(p.precision), Om, om_stride));
   }
   return KUBO_OK;
 }
@@ -464,12 +507,12 @@ kubo_status fixup_batch(Call& c, const Model& md, const KList& kl, const double*
   for (int c0 = 0; c0 < cnt; c0 += p.fix_cap) {
     const int nf = std::min(p.fix_cap, cnt - c0);
     KList fl{kid + c0, 0, nf};
-    StageTimer tm(c, KUBO_STAGE_FIXUP, 6);
+    StageTimer tm(c, KUBO_STAGE_FIXUP, p.W > SMALL_W_MAX ? 11 : 6);
     KCHECK(launch_fourier_fp64(md, p.mesh, fl, c.at<double>(p.o_fHp), c.at<double>(p.o_fXp), c.at<double>(p.o_fYp), c.s));
     KCHECK(launch_tridiag(c.at<double>(p.o_fHp), p.W, nf, eb, c.s));
     KCHECK(launch_ql(p.W, nf, eb, st, c.s));
-    KCHECK(launch_backtransform(p.W, nf, eb, fE, U, c.s));
-    KCHECK(launch_berry_fp64(fE, U, c.at<double>(p.o_fXp), c.at<double>(p.o_fYp), p.W, nf, c.at<double>(p.o_etas), p.n_eta, fOm, fstride, c.s));
+    KCHECK(eigh_vectors(c, nf, eb, fE, U));
+    KCHECK(berry_any(c, fE, U, c.at<double>(p.o_fXp), c.at<double>(p.o_fYp), (int64_t)p.W * p.W, false, nf, false, fOm, fstride));
     KCHECK(launch_fixup_scatter(pos + c0, nf, p.W, p.n_eta, fE, fOm, fstride, E, Om, (int64_t)kl.n * p.W, c.s));
   }
   return KUBO_OK;
@@ -527,6 +570,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   if (kb < 0 || ke > p.mesh.Nk || kb > ke) return KUBO_ERR_INVALID_ARG;
   p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
   p.model = p.eigh = p.berry = p.ksum = true;
+  p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   plan_layout(p, host_io, 0);
   c.s = (cudaStream_t)o.stream;
@@ -576,6 +620,7 @@ size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
   if (kb == 0 && ke == 0) ke = p.mesh.Nk;
   p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb));
   p.model = p.eigh = p.berry = p.ksum = true;
+  p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   plan_layout(p, false, 0);
   return p.total;
@@ -759,7 +804,8 @@ kubo_status kubo_eigh_batched(const double* A, int W, int64_t n, double* E, doub
     Plan& p = c.p;
     p.W = W; p.n_eta = 1; p.n_EF = 1;
     p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, 1, n);
-      p.eigh = true;
+    p.eigh = true;
+    p.lbuf = W > SMALL_W_MAX;
     plan_layout(p, false, 0);
     c.s = (cudaStream_t)o.stream;
     kubo_status r = c.acquire(o);
@@ -772,7 +818,7 @@ kubo_status kubo_eigh_batched(const double* A, int W, int64_t n, double* E, doub
       int nn = (int)std::min<int64_t>(p.chunk, n - t0);
       if (launch_tridiag(A + t0 * WW, W, nn, eb, c.s) != cudaSuccess ||
           launch_ql(W, nn, eb, st, c.s) != cudaSuccess ||
-          launch_backtransform(W, nn, eb, E + t0 * W, U ? (double2*)U + t0 * WW : nullptr, c.s) != cudaSuccess) {
+          eigh_vectors(c, nn, eb, E + t0 * W, U ? (double2*)U + t0 * WW : nullptr) != cudaSuccess) {
         cudaGetLastError();
         r = KUBO_ERR_CUDA;
       }
@@ -800,17 +846,19 @@ kubo_status kubo_berry_batched(const double* E, const double* U, const double* d
     Call c;
     Plan& p = c.p;
     p.W = W; p.n_eta = o.n_eta > 0 ? o.n_eta : 1; p.n_EF = 1;
+    p.lbuf = W > SMALL_W_MAX;   // the GEMM products of large orders go through the workspace
+    p.chunk = p.lbuf ? (o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, p.n_eta, n)) : 0;
     plan_layout(p, false, 0);
     c.s = (cudaStream_t)o.stream;
     kubo_status r = c.acquire(o);
     if (r != KUBO_OK) return r;
     r = upload_etas(c, o, eta);
     const size_t WW = (size_t)W * W;
-    const int64_t step = 1 << 30;
+    const int64_t step = p.lbuf ? p.chunk : 1 << 30;
     for (int64_t t0 = 0; t0 < n && r == KUBO_OK; t0 += step) {
       int nn = (int)std::min<int64_t>(step, n - t0);
-      if (launch_berry_fp64(E + t0 * W, (const double2*)U + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, W, nn,
-                            c.at<double>(p.o_etas), p.n_eta, Omega + t0 * W, n * W, c.s) != cudaSuccess) {
+      if (berry_any(c, E + t0 * W, (const double2*)U + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, (int64_t)WW,
+                    false, nn, false, Omega + t0 * W, n * W) != cudaSuccess) {
         cudaGetLastError();
         r = KUBO_ERR_CUDA;
       }

@@ -169,6 +169,22 @@ cudaError_t launch_fixup_scatter(const int* pos, int cnt, int W, int n_eta, cons
                                  const double* Omfix, int64_t fix_eta_stride, double* E, double* Om,
                                  int64_t eta_stride, cudaStream_t s);
 
+// orders 64 < W <= 128 (k_large.cu): eigenvectors of T by inverse iteration into Z
+// ([n][W][W] real, column m for sorted eigenvalue m) with LU scratch of
+// large_iit_scratch_doubles(W) doubles per k-point, then U = Q D Z by column blocks
+constexpr int LARGE_W_MAX = 128;
+size_t large_iit_scratch_doubles(int W);
+cudaError_t launch_iit_large(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
+                             cudaStream_t s);
+cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, double2* U,
+                                 cudaStream_t s);
+// steps (3)-(4) as batched complex GEMMs: X, Y packed Hermitian rows of leading dimension ld;
+// f32 = FP32 products.  Tbuf, Vx, Vy: n * W * W complex elements (of the product type) each.
+cudaError_t launch_berry_large(const double* E, const double2* U, const double* X, const double* Y,
+                               int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
+                               int64_t eta_stride, bool f32, void* Tbuf, void* Vx, void* Vy,
+                               cudaStream_t s);
+
 size_t tridiag_smem(int W);
 size_t backtransform_smem(int W);
 size_t ql_smem(int W);

@@ -1,0 +1,184 @@
+"""Orders 64 < W <= 128 (batched multi-pass eigenvector and rotation kernels) against the
+FP64 oracle: the W = 96 end of the uneven-model batch and the W = 128, N_R = 1331 sweep model.
+
+Same bars as the W <= 64 path: eigenvalues 1e-12 ||H||, residual / orthogonality at FP64
+grade, per-k curvatures 1e-9 ||Omega(k)||_inf and S(E_F) 1e-10 in FP64; the mixed path is held
+to the per-k error profile of the W = 64 mixed test and to 1e-5 on S(E_F).
+"""
+import numpy as np
+import pytest
+
+import tbgen
+from oracle import kubo_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+REL_OM = 1e-9
+
+
+@pytest.fixture(scope="module")
+def kubo():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_06675_gb300 import _build
+    _build.build()
+    import paper_2309_06675_gb300 as k
+    k.lib()
+    return k
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def cuda(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def assert_omega_close(Om_gpu, Om_ref, rel=REL_OM):
+    scale = np.max(np.abs(Om_ref), axis=-1, keepdims=True)
+    err = np.abs(Om_gpu - Om_ref) / np.maximum(scale, 1e-300)
+    assert np.all(err <= rel), np.max(err)
+
+
+def _random_hermitian(rng, n, W):
+    X = rng.standard_normal((n, W, W)) + 1j * rng.standard_normal((n, W, W))
+    return X + np.conj(np.swapaxes(X, -1, -2))
+
+
+@pytest.fixture(scope="module")
+def m128():
+    return tbgen.random_tb(128, 5, 1.5, 0)
+
+
+def test_max_orbitals(kubo):
+    assert kubo.max_orbitals("fp64") == 128
+    assert kubo.max_orbitals("mixed") == 128
+
+
+@pytest.mark.parametrize("W", [65, 96, 128])
+def test_eigh_batched_large(kubo, torch, W):
+    rng = np.random.default_rng(W)
+    n = 41
+    A = _random_hermitian(rng, n, W)
+    A[0] = np.diag(rng.standard_normal(W))
+    T = np.diag(rng.standard_normal(W)) + np.diag(rng.standard_normal(W - 1), 1)
+    A[1] = T + T.T
+    h = W // 2
+    B = _random_hermitian(rng, 1, h)[0]
+    A[2] = 0
+    A[2][:h, :h] = B
+    A[2][h:2 * h, h:2 * h] = B
+    t3 = W // 3
+    C = _random_hermitian(rng, 1, t3)[0]
+    A[3] = 0
+    for q in range(3):
+        A[3][q * t3:(q + 1) * t3, q * t3:(q + 1) * t3] = C
+    lam = np.sort(rng.standard_normal(W))
+    lam[1::2] = lam[0::2][: W // 2] + 1e-9
+    X = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
+    Q, _ = np.linalg.qr(X)
+    A[4] = (Q * lam) @ np.conj(Q.T)
+    E, U = kubo.eigh_batched(kubo.pack_hermitian(cuda(torch, A)), W)
+    E, U = E.cpu().numpy(), U.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    nrm = np.max(np.abs(ref), axis=-1)[:, None]
+    assert np.all(np.abs(E - ref) <= 1e-12 * np.maximum(nrm, 1))
+    res = np.abs(A @ U - U * E[:, None, :]).max(axis=(1, 2))
+    assert np.all(res <= 1e-12 * np.maximum(nrm[:, 0], 1)), res.max()
+    orth = np.abs(np.conj(np.swapaxes(U, -1, -2)) @ U - np.eye(W)).max(axis=(1, 2))
+    assert np.all(orth <= 1e-13 * W), orth.max()
+
+
+def test_eigh_values_only_large(kubo, torch):
+    rng = np.random.default_rng(3)
+    A = _random_hermitian(rng, 7, 100)
+    E, U = kubo.eigh_batched(kubo.pack_hermitian(cuda(torch, A)), 100, vectors=False)
+    assert U is None
+    ref = np.linalg.eigvalsh(A)
+    assert np.max(np.abs(E.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_berry_batched_large(kubo, torch):
+    m = tbgen.random_tb(96, 1, 1.0, 4)
+    kmesh = (8, 8, 8)
+    kidx = tbgen.k_sample(kmesh, 19, seed=1)
+    Hk, dHx, dHy = O.bloch(m.H_R, m.R, kmesh, kidx)
+    E, U = np.linalg.eigh(Hk)
+    etas = [0.0, 1e-3, 5e-2]
+    Om = kubo.berry_batched(cuda(torch, E), cuda(torch, U), kubo.pack_hermitian(cuda(torch, dHx)),
+                            kubo.pack_hermitian(cuda(torch, dHy)), etas=etas).cpu().numpy()
+    vx, vy = O.velocity(U, dHx), O.velocity(U, dHy)
+    for e, eta in enumerate(etas):
+        assert_omega_close(Om[e], O.berry_curvature(E, vx, vy, eta))
+
+
+@pytest.mark.parametrize("W,hw,chunk", [(72, 2, 0), (96, 3, 13)])
+def test_ahc_k_large_fp64(kubo, torch, W, hw, chunk):
+    m = tbgen.random_tb(W, hw, 1.5, 100 + W)
+    kmesh = (32, 32, 32)
+    kidx = tbgen.k_sample(kmesh, 40, seed=W)
+    etas = [1e-4, 1e-2]
+    E, Om = kubo.ahc_k(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, kidx), etas=etas, chunk_k=chunk)
+    E_ref, Om_ref = O.kubo_per_k(m.H_R, m.R, kmesh, kidx, etas)
+    assert rel_err(E.cpu().numpy(), E_ref) < 1e-12
+    for e in range(2):
+        assert_omega_close(Om.cpu().numpy()[e], Om_ref[e])
+
+
+def test_ahc_k_w128_full_size_model_fp64(kubo, torch, m128):
+    """W=128, N_R=1331, 96^3 mesh, the sweep's four broadenings: sampled k-points."""
+    kmesh = (96, 96, 96)
+    kidx = tbgen.k_sample(kmesh, 24, seed=7)
+    etas = [1e-4, 1e-3, 5e-3, 1e-2]
+    E, Om = kubo.ahc_k(cuda(torch, m128.H_R), m128.R, kmesh, cuda(torch, kidx), etas=etas)
+    E_ref, Om_ref = O.kubo_per_k(m128.H_R, m128.R, kmesh, kidx, etas)
+    assert rel_err(E.cpu().numpy(), E_ref) < 1e-12
+    for e in range(4):
+        assert_omega_close(Om.cpu().numpy()[e], Om_ref[e])
+
+
+def test_ahc_k_w128_mixed(kubo, torch, m128):
+    kmesh = (96, 96, 96)
+    kidx = tbgen.k_sample(kmesh, 24, seed=8)
+    E, Om = kubo.ahc_k(cuda(torch, m128.H_R), m128.R, kmesh, cuda(torch, kidx), eta=1e-3,
+                       precision="mixed")
+    E_ref, Om_ref = O.kubo_per_k(m128.H_R, m128.R, kmesh, kidx, [1e-3])
+    E, Om = E.cpu().numpy(), Om.cpu().numpy()[0]
+    assert np.max(np.abs(E - E_ref)) <= 1e-6 * np.max(np.abs(E_ref))
+    scale = np.max(np.abs(Om_ref[0]), axis=-1)
+    err = np.max(np.abs(Om - Om_ref[0]), axis=-1) / scale
+    assert np.max(err) < 1e-3, np.max(err)
+    assert np.median(err) < 1e-5, np.median(err)
+
+
+def test_ahc_large_w_full_small_mesh_vs_oracle(kubo, torch):
+    """k-summed S(E_F) at W = 96 on a whole 6^3 mesh in ragged batches (FP64, 1e-10)."""
+    m = tbgen.random_tb(96, 1, 1.0, 11)
+    kmesh = (6, 6, 6)
+    EF = np.linspace(-3.0, 3.0, 9)
+    etas = [1e-3, 1e-2]
+    S = kubo.ahc(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, EF), etas=etas, chunk_k=50).cpu().numpy()
+    S_ref = O.ahc(m.H_R, m.R, kmesh, EF, etas=etas)
+    assert rel_err(S, S_ref) < 1e-10, rel_err(S, S_ref)
+
+
+def test_ahc_w128_mixed_vs_fp64_sweep_slab(kubo, torch, m128):
+    """A slab of the W = 128 sweep (96^3 mesh, 512 Fermi levels, 4 broadenings): mixed vs FP64."""
+    kmesh = (96, 96, 96)
+    EF = np.linspace(-2.0, 2.0, 512)
+    etas = [1e-4, 1e-3, 5e-3, 1e-2]
+    H = cuda(torch, m128.H_R)
+    EFt = cuda(torch, EF)
+    rng = (41 * 9216, 41 * 9216 + 4608)
+    S64 = kubo.ahc(H, m128.R, kmesh, EFt, etas=etas, k_range=rng).cpu().numpy()
+    Smx = kubo.ahc(H, m128.R, kmesh, EFt, etas=etas, k_range=rng, precision="mixed").cpu().numpy()
+    for e in range(4):
+        assert rel_err(Smx[e], S64[e]) < 1e-5, (e, rel_err(Smx[e], S64[e]))
