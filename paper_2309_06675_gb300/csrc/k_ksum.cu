@@ -1,6 +1,12 @@
 // k-sum of Eq. 2 (with Eq. 4's batching): S(E_F) = (1/N_k) sum_k sum_n occ(E_n(k)) Omega_n(k)
 // for every (eta, E_F) pair.  Deterministic: every block sums a fixed k-range in order with
 // Neumaier compensation, blocks are folded in index order, batches in call order.
+//
+// Step occupation (kT = 0): the levels of a k-point are ascending, so the occupied ones are a
+// prefix of the bands and the per-k term is an inclusive prefix sum of Omega over the bands,
+// looked up at the count of levels below E_F (binary search): O(log W) per (k, E_F) instead of
+// O(W).  The prefix is accumulated in band order, so the per-k term is bit-identical to the
+// direct sum over occupied bands.
 #include <algorithm>
 
 #include "kubo_internal.cuh"
@@ -43,6 +49,58 @@ __global__ void ksum_partial_kernel(const double* __restrict__ E, const double* 
       neumaier_add(s, c, v);
     }
     part[(size_t)b * n_out + o] = make_double2(s, c);
+  }
+}
+
+// Omega_n(k) <- sum_{m <= n} Omega_m(k), in place, for every eta (thread per (eta, k))
+__global__ void band_prefix_kernel(double* __restrict__ Om, int W, int n, int n_eta,
+                                   int64_t eta_stride) {
+  const int64_t total = (int64_t)n_eta * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(t / n);
+    const int64_t k = t % n;
+    double* o = Om + e * eta_stride + k * W;
+    double s = 0.0;
+    for (int q = 0; q < W; ++q) {
+      s += o[q];
+      o[q] = s;
+    }
+  }
+}
+
+constexpr int KS_MAXE = 8;
+
+// kT = 0: thread per E_F (all etas), k-range of the block in order
+__global__ void ksum_step_kernel(const double* __restrict__ E, const double* __restrict__ P,
+                                 int W, int n, int n_eta, int64_t eta_stride,
+                                 const double* __restrict__ E_F, int n_EF,
+                                 double2* __restrict__ part, int kpb) {
+  const int b = blockIdx.x;
+  const int kb = b * kpb, ke = min(n, kb + kpb);
+  const int n_out = n_eta * n_EF;
+  for (int j = threadIdx.x; j < n_EF; j += blockDim.x) {
+    const double ef = E_F[j];
+    double s[KS_MAXE], c[KS_MAXE];
+#pragma unroll
+    for (int e = 0; e < KS_MAXE; ++e) { s[e] = 0.0; c[e] = 0.0; }
+    for (int k = kb; k < ke; ++k) {
+      const double* Ek = E + (size_t)k * W;
+      int lo = 0, hi = W;   // number of levels strictly below E_F
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Ek[mid] < ef) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo == 0) continue;
+      const double* Pk = P + (size_t)k * W + (lo - 1);
+#pragma unroll
+      for (int e = 0; e < KS_MAXE; ++e)
+        if (e < n_eta) neumaier_add(s[e], c[e], Pk[e * eta_stride]);
+    }
+#pragma unroll
+    for (int e = 0; e < KS_MAXE; ++e)
+      if (e < n_eta) part[(size_t)b * n_out + e * n_EF + j] = make_double2(s[e], c[e]);
   }
 }
 
@@ -173,12 +231,20 @@ __global__ void fixup_scatter_kernel(const int* __restrict__ pos, int cnt, int W
 
 }  // namespace
 
-cudaError_t launch_ksum_partial(const double* E, const double* Om, int W, int n, int n_eta,
+cudaError_t launch_ksum_partial(const double* E, double* Om, int W, int n, int n_eta,
                                 int64_t eta_stride, const double* E_F, int n_EF, double kT,
                                 double2* part, int kpb, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  int nb = (n + kpb - 1) / kpb;
-  ksum_partial_kernel<<<nb, 128, 0, s>>>(E, Om, W, n, n_eta, eta_stride, E_F, n_EF, kT, part, kpb);
+  const int nb = (n + kpb - 1) / kpb;
+  if (kT == 0.0 && n_eta <= KS_MAXE) {
+    const int64_t rows = (int64_t)n_eta * n;
+    const int pb = (int)std::min<int64_t>((rows + 127) / 128, 152 * 16);
+    band_prefix_kernel<<<pb, 128, 0, s>>>(Om, W, n, n_eta, eta_stride);
+    const int nt = std::min(256, (n_EF + 31) / 32 * 32);
+    ksum_step_kernel<<<nb, nt, 0, s>>>(E, Om, W, n, n_eta, eta_stride, E_F, n_EF, part, kpb);
+  } else {
+    ksum_partial_kernel<<<nb, 128, 0, s>>>(E, Om, W, n, n_eta, eta_stride, E_F, n_EF, kT, part, kpb);
+  }
   return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@ namespace {
 constexpr int MAX_W = LARGE_W_MAX;
 constexpr int SMALL_W_MAX = 64;      // beyond: the multi-pass eigenvector / rotation kernels
 constexpr int MAX_ETA = 8;
-constexpr int KSUM_KPB = 256;        // k-points per deterministic k-sum block
+constexpr int KSUM_KPB = 32;         // k-points per deterministic k-sum block (at least)
+constexpr size_t KSUM_PART_BYTES = (size_t)256 << 20;   // cap on the per-block partials
 // mixed precision: share of each batch (largest ||Omega(k)||_inf) redone in FP64
 constexpr double kFixupSpikyFraction = 0.005;
 constexpr size_t ALIGN = 256;
@@ -86,6 +87,7 @@ struct Plan {
   int W = 0, N_R = 0, N_h = 0, K = 0, n_EF = 0, n_eta = 1, chunk = 0;
   int precision = KUBO_FP64;
   int Npad = 0, Kp = 0, Mpad = 0;   // tensor-core operand padding (mixed precision)
+  int kpb = KSUM_KPB;               // k-points per k-sum block
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -183,7 +185,10 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
   if (p.ksum) {
     const int n_out = p.n_eta * p.n_EF;
     p.o_acc = b.take(sizeof(double2) * n_out);
-    p.o_part = b.take(sizeof(double2) * (size_t)n_out * ((p.chunk + KSUM_KPB - 1) / KSUM_KPB));
+    const int64_t max_blocks = std::max<int64_t>(1, (int64_t)(KSUM_PART_BYTES / (sizeof(double2) * n_out)));
+    const int64_t ch = std::max(1, p.chunk);
+    p.kpb = (int)std::max<int64_t>(KSUM_KPB, (ch + max_blocks - 1) / max_blocks);
+    p.o_part = b.take(sizeof(double2) * (size_t)n_out * ((ch + p.kpb - 1) / p.kpb));
   }
   if (host_io) {
     p.o_HR = b.take(sizeof(double2) * (size_t)p.N_R * WW);
@@ -541,9 +546,9 @@ kubo_status ahc_device(Call& c, const kubo_options& o, const double* H_R, const 
       r = fixup_batch(c, md, kl, E_F, o.mixed_fixup_rel, kFixupSpikyFraction, E, Om);
       if (r != KUBO_OK) return r;
     }
-    StageTimer tm(c, KUBO_STAGE_KSUM, 2);
-    KCHECK(launch_ksum_partial(E, Om, p.W, kl.n, p.n_eta, (int64_t)kl.n * p.W, E_F, p.n_EF, o.kT, part, KSUM_KPB, c.s));
-    KCHECK(launch_ksum_fold(part, (kl.n + KSUM_KPB - 1) / KSUM_KPB, n_out, acc, c.s));
+    StageTimer tm(c, KUBO_STAGE_KSUM, o.kT == 0.0 ? 3 : 2);
+    KCHECK(launch_ksum_partial(E, Om, p.W, kl.n, p.n_eta, (int64_t)kl.n * p.W, E_F, p.n_EF, o.kT, part, p.kpb, c.s));
+    KCHECK(launch_ksum_fold(part, (kl.n + p.kpb - 1) / p.kpb, n_out, acc, c.s));
   }
   {
     StageTimer tm(c, KUBO_STAGE_KSUM, 1);

@@ -150,7 +150,9 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
 cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,
                                double* Y, cudaStream_t s);
 
-cudaError_t launch_ksum_partial(const double* E, const double* Om, int W, int n, int n_eta,
+// per-block partial sums; with kT = 0 Om is overwritten by its prefix sums over the bands
+// (E must be ascending per k-point)
+cudaError_t launch_ksum_partial(const double* E, double* Om, int W, int n, int n_eta,
                                 int64_t eta_stride, const double* E_F, int n_EF, double kT,
                                 double2* part, int k_per_block, cudaStream_t s);
 cudaError_t launch_ksum_fold(const double2* part, int n_blocks, int n_out, double2* acc,
