@@ -77,7 +77,8 @@ enum {
   KUBO_STAGE_BERRY = 5,         /* steps (3)-(4) */
   KUBO_STAGE_KSUM = 6,          /* k-sum of Eq. 2 */
   KUBO_STAGE_FIXUP = 7,         /* mixed precision: FP64 redo of k-points with a level near E_F */
-  KUBO_N_STAGES = 8
+  KUBO_STAGE_ADJOINT = 8,       /* kubo_ahc_grad: reverse mode of steps (1)-(4) */
+  KUBO_N_STAGES = 9
 };
 
 /* Per-stage kernel launch counts and summed device time (CUDA events recorded on the call's
@@ -108,6 +109,9 @@ typedef struct kubo_options {
                                precision energy could flip) and of the 0.5 % of each batch with
                                the largest ||Omega(k)||_inf (near-degenerate pairs).  <= 0 (the
                                default) = no fix-up. */
+  double grad_eps;          /* kubo_ahc_grad: broadening eps of the eigenvector-derivative
+                               kernel (E_j - E_i) / ((E_j - E_i)^2 + eps^2) (energy units);
+                               <= 0 (the default) = 1e-12 max_n |E_n(k)| at each k. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,
@@ -215,9 +219,38 @@ kubo_status kubo_berry_batched(const double* E, const double* U, const double* d
 kubo_status kubo_eigh_batched_noalloc(const double* A, int W, int64_t n, double* E, double* U,
                                       void* stream);
 
+/*
+ * Gradient of the anomalous Hall sum with respect to H(R) (reverse mode of Eq. 2-3 and of
+ * steps (1)-(4); the paper evaluates sigma only, this is its adjoint).  FP64 only: any other
+ * opt->precision returns KUBO_ERR_UNSUPPORTED.
+ *   dL_dout   device, double [n_eta][n_EF]: weights g of L = sum g[e][j] S_e(E_F_j) (the
+ *             incoming gradient of the outputs of kubo_ahc)
+ *   grad_H_R  device, complex128 [N_R][W][W]: G(R) = dL/dRe H(R) + i dL/dIm H(R), the
+ *             Hermitian part of H(k), d_x H(k), d_y H(k) being what L depends on; hence
+ *             G(-R) = G(R)^dagger.  A Hermitian-paired real step d of H(R)_ij and H(-R)_ji
+ *             changes L by 2 d Re G(R)_ij (d Re G(0)_ii for a diagonal entry of H(0)); an
+ *             imaginary step i d by 2 d Im G(R)_ij.  This is also PyTorch's convention for the
+ *             gradient of a real loss with respect to a complex tensor.
+ *   out       device, double [n_eta][n_EF] or NULL: S(E_F) of the same call (as kubo_ahc)
+ * Other arguments and options as kubo_ahc (etas, kT: Fermi-Dirac occupation derivative
+ * included; kT = 0 differentiates the step almost everywhere, i.e. without the Fermi-surface
+ * term; k_begin/k_end; opt->grad_eps).  The eigenvectors are recomputed batch by batch inside
+ * the call (never stored for the whole mesh).  Deterministic.  grad_H_R and out are written
+ * only on KUBO_OK.
+ */
+kubo_status kubo_ahc_grad(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                          const int32_t* kmesh, const double* E_F, int n_EF, double eta,
+                          const double* dL_dout, double* grad_H_R, double* out,
+                          const kubo_options* opt);
+
 /* Device bytes of scratch a kubo_ahc / kubo_ahc_k call with these sizes needs. */
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
                            const kubo_options* opt);
+
+/* Device bytes of scratch a kubo_ahc_grad call with these sizes needs (0 for invalid sizes
+ * or a precision other than KUBO_FP64). */
+size_t kubo_grad_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
+                                const kubo_options* opt);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,8 @@ Entry points (same names as the C ABI, without the ``kubo_`` prefix):
   bloch(H_R, R, kmesh, kidx)                                    -> packed H, dHx, dHy
   eigh_batched(A_packed, W)                                     -> (E, U)
   berry_batched(E, U, dHx_packed, dHy_packed, eta | etas)       -> Omega
+  ahc_grad(H_R, R, kmesh, E_F, dL_dout, ...)                    -> G = dL/dH(R) (and S)
+  AHC.apply(H_R, R, kmesh, E_F, eta, etas, kT)                  -> S, differentiable in H_R
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ import numpy as np
 __all__ = [
     "KuboError", "lib", "ahc", "ahc_host", "ahc_k", "bloch", "eigh_batched", "berry_batched",
     "workspace_size", "max_orbitals", "pack_hermitian", "unpack_hermitian", "FP64", "MIXED",
-    "LIB_PATH", "Profile", "Options", "STAGES",
+    "LIB_PATH", "Profile", "Options", "STAGES", "ahc_grad", "grad_workspace_size", "AHC",
 ]
 
 FP64 = 0
@@ -51,7 +53,7 @@ class KuboError(RuntimeError):
         self.name = _STATUS.get(code, str(code))
 
 
-STAGES = ("prep", "fourier", "tridiag", "ql", "backtransform", "berry", "ksum", "fixup")
+STAGES = ("prep", "fourier", "tridiag", "ql", "backtransform", "berry", "ksum", "fixup", "adjoint")
 
 
 class Profile(ctypes.Structure):
@@ -78,6 +80,7 @@ class Options(ctypes.Structure):
         ("chunk_k", ctypes.c_int),
         ("profile", ctypes.POINTER(Profile)),
         ("mixed_fixup_rel", ctypes.c_double),
+        ("grad_eps", ctypes.c_double),
     ]
 
 
@@ -101,6 +104,8 @@ def lib():
             "kubo_status_string": (ctypes.c_char_p, [I]),
             "kubo_max_orbitals": (I, [I]),
             "kubo_workspace_size": (ctypes.c_size_t, [I, I, P, I, OPT]),
+            "kubo_grad_workspace_size": (ctypes.c_size_t, [I, I, P, I, OPT]),
+            "kubo_ahc_grad": (I, [P, P, I, I, P, P, I, D, P, P, P, OPT]),
             "kubo_ahc": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_host": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_k": (I, [P, P, I, I, P, P, I64, D, P, P, OPT]),
@@ -222,6 +227,94 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
                           _dev(out, torch.float64, "out"), ctypes.byref(o))
     _check(code, "kubo_ahc")
     return out
+
+
+def ahc_grad(H_R, R, kmesh, E_F, dL_dout, eta=1e-3, etas=None, kT=0.0, k_range=None,
+             stream=None, chunk_k=0, workspace=None, profile=None, grad_eps=0.0,
+             with_value=False):
+    """Gradient G(R) = dL/dRe H(R) + i dL/dIm H(R) of L = sum dL_dout[e, j] S_e(E_F_j).
+
+    dL_dout: float64 CUDA [n_eta, n_EF].  Returns a complex128 CUDA tensor [N_R, W, W]
+    (and S [n_eta, n_EF] of the same call when with_value).  FP64.
+    """
+    torch = _torch()
+    Rh = _host_int32(R, 3)
+    km = _host_int32(kmesh)
+    N_R, W = int(H_R.shape[0]), int(H_R.shape[1])
+    n_EF = int(E_F.numel())
+    n_eta = 1 if etas is None else int(np.asarray(etas).size)
+    g = dL_dout.to(torch.float64).contiguous().reshape(n_eta, n_EF)
+    G = torch.empty((N_R, W, W), dtype=torch.complex128, device=H_R.device)
+    S = torch.empty((n_eta, n_EF), dtype=torch.float64, device=H_R.device) if with_value else None
+    keep = []
+    o = _options(FP64, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
+    o.grad_eps = float(grad_eps)
+    code = lib().kubo_ahc_grad(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
+                               W, N_R, km.ctypes.data_as(ctypes.c_void_p),
+                               _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),
+                               _dev(g, torch.float64, "dL_dout"), _dev(G, torch.complex128, "G"),
+                               _dev(S, torch.float64, "out") if with_value else None,
+                               ctypes.byref(o))
+    _check(code, "kubo_ahc_grad")
+    return (G, S) if with_value else G
+
+
+def grad_workspace_size(W, N_R, kmesh, n_EF, n_eta=1, kT=0.0, k_range=None, chunk_k=0) -> int:
+    km = _host_int32(kmesh)
+    keep = []
+    o = Options()
+    lib().kubo_options_init(ctypes.byref(o))
+    if n_eta > 1:
+        e = np.full(n_eta, 1e-3)
+        keep.append(e)
+        o.n_eta = n_eta
+        o.etas = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o.kT = kT
+    if k_range is not None:
+        o.k_begin, o.k_end = k_range
+    o.chunk_k = chunk_k
+    return int(lib().kubo_grad_workspace_size(int(W), int(N_R), km.ctypes.data_as(ctypes.c_void_p),
+                                              int(n_EF), ctypes.byref(o)))
+
+
+def _make_autograd_function():
+    torch = _torch()
+
+    class _AHC(torch.autograd.Function):
+        """S(E_F) = kubo_ahc(H_R, ...) with backward = kubo_ahc_grad (FP64).
+
+        H_R must be Hermitian-paired (H(-R) = H(R)^dagger); its gradient is
+        dL/dRe H(R) + i dL/dIm H(R), PyTorch's convention for complex inputs.
+        """
+
+        @staticmethod
+        def forward(ctx, H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, k_range=None):
+            ctx.save_for_backward(H_R, E_F)
+            ctx.args = (R, kmesh, eta, etas, kT, k_range)
+            return ahc(H_R.detach(), R, kmesh, E_F, eta=eta, etas=etas, kT=kT, k_range=k_range)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            H_R, E_F = ctx.saved_tensors
+            R, kmesh, eta, etas, kT, k_range = ctx.args
+            G = ahc_grad(H_R.detach(), R, kmesh, E_F, grad_out.contiguous(), eta=eta, etas=etas,
+                         kT=kT, k_range=k_range)
+            return G, None, None, None, None, None, None, None
+
+    return _AHC
+
+
+class _LazyAHC:
+    """Deferred torch.autograd.Function (torch is imported on first use)."""
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyAHC._fn is None:
+            _LazyAHC._fn = _make_autograd_function()
+        return _LazyAHC._fn.apply(*args)
+
+
+AHC = _LazyAHC()
 
 
 def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,

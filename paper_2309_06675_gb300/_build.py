@@ -19,6 +19,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libkubo.so")
 
 SOURCES = ["k_prep.cu", "k_fourier.cu", "k_fourier_tc.cu", "k_eigh.cu", "k_berry.cu", "k_ksum.cu",
+           "k_grad.cu",
            "k_large.cu", "kubo_api.cu",
            "kubo_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -453,6 +453,17 @@ cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, doub
   return cudaGetLastError();
 }
 
+// T[k] = X[k] U[k], X packed Hermitian rows of leading dimension ld, FP64 (any W <= 128)
+cudaError_t launch_herm_u(const double* X, int64_t ld, const double2* U, double2* T, int W, int n,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > LW_MAX) return cudaErrorInvalidValue;
+  const int tiles = (W + GT - 1) / GT;
+  dim3 grid(n, tiles * tiles);
+  cgemm_herm_u_kernel<double><<<grid, 256, 0, s>>>(X, ld, U, W, T);
+  return cudaGetLastError();
+}
+
 // steps (3)-(4) for large W: X, Y packed Hermitian rows (leading dimension ld), FP64 U.
 // f32 selects FP32 arithmetic for the products (mixed precision).  Tbuf, Vx, Vy: scratch of
 // n * W * W complex elements of the arithmetic type each.

@@ -93,11 +93,15 @@ struct Plan {
   bool berry = false;   // needs velocity / curvature buffers
   bool ksum = false;    // needs k-sum buffers
   bool lbuf = false;    // W > SMALL_W_MAX: scratch of the multi-pass kernels
+  bool grad = false;    // reverse-mode buffers (kubo_ahc_grad)
   Mesh mesh{1, 1, 1, 1};
   size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
          o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
          o_ph = 0, o_refl = 0, o_tau = 0, o_lam = 0, o_part = 0,
          o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0, o_L = 0;
+  // reverse mode: six complex W x W work matrices per k, Ebar, packed [Hbar|dxHbar|dyHbar],
+  // the Fourier coefficient rows of the batch and the accumulated G rows
+  size_t o_gw = 0, o_Ebar = 0, o_Mbar = 0, o_Coef = 0, o_Gacc = 0;
   // mixed-precision fix-up buffers
   bool fixup = false;
   int fix_cap = 0;
@@ -121,9 +125,9 @@ size_t bytes_per_k(int W, int n_eta) {
          (size_t)n_eta * W * 8 + 64 + (W > SMALL_W_MAX ? large_region_bytes(W) : 0);
 }
 
-int auto_chunk(int W, int n_eta, int64_t n_total) {
+int auto_chunk(int W, int n_eta, int64_t n_total, size_t extra_per_k = 0) {
   const size_t budget = (size_t)12 << 30;
-  int64_t c = (int64_t)(budget / bytes_per_k(W, n_eta));
+  int64_t c = (int64_t)(budget / (bytes_per_k(W, n_eta) + extra_per_k));
   c = std::max<int64_t>(1024, std::min<int64_t>(c, 65536));
   c = c / 1024 * 1024;
   return (int)std::max<int64_t>(1, std::min<int64_t>(c, n_total));
@@ -182,6 +186,14 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_fOm = b.take(sizeof(double) * (size_t)p.fix_cap * p.W * p.n_eta);
   }
   if (p.lbuf) p.o_L = b.take(large_region_bytes(p.W) * (size_t)std::max(1, p.chunk));
+  if (p.grad) {
+    const size_t ch = (size_t)std::max(1, p.chunk);
+    p.o_gw = b.take(6 * sizeof(double2) * ch * WW);
+    p.o_Ebar = b.take(sizeof(double) * ch * p.W);
+    p.o_Mbar = b.take(3 * sizeof(double) * ch * WW);
+    p.o_Coef = b.take(sizeof(double) * (size_t)(2 * p.N_h + 1) * ch);
+    p.o_Gacc = b.take(3 * sizeof(double) * (size_t)(2 * p.N_h + 1) * WW);
+  }
   if (p.ksum) {
     const int n_out = p.n_eta * p.n_EF;
     p.o_acc = b.take(sizeof(double2) * n_out);
@@ -583,6 +595,112 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   return KUBO_OK;
 }
 
+// per-k bytes of the reverse-mode buffers (for the automatic batch size)
+size_t grad_bytes_per_k(int W, int N_R) {
+  const size_t WW = (size_t)W * W;
+  return 6 * 16 * WW + 8 * (size_t)W + 3 * 8 * WW + 8 * (size_t)N_R;
+}
+
+// Body of kubo_ahc_grad (device pointers): per batch the forward steps (1)-(3) in FP64, the
+// optional forward k-sum, then the reverse pass and the transposed Fourier accumulation.
+kubo_status ahc_grad_device(Call& c, const kubo_options& o, const double* H_R, const RInfo& ri,
+                            const double* E_F, double eta, const double* g, double2* G,
+                            double* out, int64_t kb, int64_t ke) {
+  Plan& p = c.p;
+  kubo_status r = upload_etas(c, o, eta);
+  if (r != KUBO_OK) return r;
+  r = prepare_model(c, H_R, ri);
+  if (r != KUBO_OK) return r;
+  const int n_out = p.n_eta * p.n_EF;
+  const size_t WW = (size_t)p.W * p.W;
+  const int M = 2 * p.N_h + 1;
+  KCHECK(cudaMemsetAsync(c.at<char>(p.o_acc), 0, sizeof(double2) * n_out, c.s));
+  KCHECK(cudaMemsetAsync(c.at<char>(p.o_Gacc), 0, 3 * sizeof(double) * (size_t)M * WW, c.s));
+  const Model md = make_model(c);
+  EighBufs eb = make_eigh_bufs(c);
+  DevStatus* st = c.at<DevStatus>(p.o_status);
+  double* Hp = c.at<double>(p.o_Hp);
+  double* Xp = c.at<double>(p.o_Xp);
+  double* Yp = c.at<double>(p.o_Yp);
+  double* E = c.at<double>(p.o_E);
+  double* Om = c.at<double>(p.o_Om);
+  double2* U = c.at<double2>(p.o_U);
+  double2* part = c.at<double2>(p.o_part);
+  double2* acc = c.at<double2>(p.o_acc);
+  const size_t cap = (size_t)std::max(1, p.chunk) * WW;
+  double2* bw[6];
+  for (int q = 0; q < 6; ++q) bw[q] = c.at<double2>(p.o_gw) + q * cap;
+  double* Ebar = c.at<double>(p.o_Ebar);
+  double* Mbar = c.at<double>(p.o_Mbar);
+  double* Coef = c.at<double>(p.o_Coef);
+  double* Gacc = c.at<double>(p.o_Gacc);
+  const double* etas = c.at<double>(p.o_etas);
+  const double inv_Nk = 1.0 / (double)p.mesh.Nk;
+  for (int64_t base = kb; base < ke; base += p.chunk) {
+    KList kl{nullptr, base, (int)std::min<int64_t>(p.chunk, ke - base)};
+    const int n = kl.n;
+    {
+      StageTimer tm(c, KUBO_STAGE_FOURIER, 1);
+      KCHECK(launch_fourier_fp64(md, p.mesh, kl, Hp, Xp, Yp, c.s));
+    }
+    {
+      StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
+      KCHECK(launch_tridiag(Hp, p.W, n, eb, c.s));
+    }
+    {
+      StageTimer tm(c, KUBO_STAGE_QL, 1);
+      KCHECK(launch_ql(p.W, n, eb, st, c.s));
+    }
+    {
+      StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
+      KCHECK(eigh_vectors(c, n, eb, E, U));
+    }
+    if (out) {
+      {
+        StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);
+        KCHECK(berry_any(c, E, U, Xp, Yp, (int64_t)WW, false, n, false, Om, (int64_t)n * p.W));
+      }
+      StageTimer tm(c, KUBO_STAGE_KSUM, o.kT == 0.0 ? 3 : 2);
+      KCHECK(launch_ksum_partial(E, Om, p.W, n, p.n_eta, (int64_t)n * p.W, E_F, p.n_EF, o.kT, part, p.kpb, c.s));
+      KCHECK(launch_ksum_fold(part, (n + p.kpb - 1) / p.kpb, n_out, acc, c.s));
+    }
+    StageTimer tm(c, KUBO_STAGE_ADJOINT, 17);
+    // v^x, v^y (full): b0 = U^H (X U), b1 = U^H (Y U)
+    KCHECK(launch_herm_u(Xp, (int64_t)WW, U, bw[5], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(true, false, false, U, bw[5], bw[0], p.W, n, c.s));
+    KCHECK(launch_herm_u(Yp, (int64_t)WW, U, bw[5], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(true, false, false, U, bw[5], bw[1], p.W, n, c.s));
+    // vbar^x -> b2, vbar^y -> b3, Ebar
+    KCHECK(launch_grad_pairs(E, bw[0], bw[1], p.W, n, g, E_F, p.n_EF, etas, p.n_eta, o.kT, inv_Nk, bw[2], bw[3], Ebar, c.s));
+    // N = vbar^x v^x + vbar^y v^y -> b4; Gp -> b0
+    KCHECK(launch_zgemm_batched(false, false, false, bw[2], bw[0], bw[4], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(false, false, true, bw[3], bw[1], bw[4], p.W, n, c.s));
+    KCHECK(launch_grad_gp(E, Ebar, bw[4], p.W, n, o.grad_eps, bw[0], c.s));
+    // Hbar = U Gp U^H -> b1, dxHbar = U vbar^x U^H -> b0, dyHbar = U vbar^y U^H -> b4
+    KCHECK(launch_zgemm_batched(false, false, false, U, bw[0], bw[5], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(false, true, false, bw[5], U, bw[1], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(false, false, false, U, bw[2], bw[5], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(false, true, false, bw[5], U, bw[0], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(false, false, false, U, bw[3], bw[5], p.W, n, c.s));
+    KCHECK(launch_zgemm_batched(false, true, false, bw[5], U, bw[4], p.W, n, c.s));
+    KCHECK(launch_pack3(bw[1], bw[0], bw[4], p.W, n, Mbar, c.s));
+    // transposed Fourier sum of the batch into the G rows
+    KCHECK(launch_grad_coef(md, p.mesh, kl, n, Coef, c.s));
+    KCHECK(launch_grad_fourier_t(Coef, n, Mbar, M, (int)(3 * WW), n, Gacc, c.s));
+  }
+  r = read_status(c);
+  if (r != KUBO_OK) return r;
+  {
+    StageTimer tm(c, KUBO_STAGE_ADJOINT, 1);
+    KCHECK(launch_grad_finalize(Gacc, c.at<int>(p.o_pairs), c.at<int>(p.o_Rh), ri.idx0, p.N_h, p.W, G, c.s));
+  }
+  if (out) {
+    StageTimer tm(c, KUBO_STAGE_KSUM, 1);
+    KCHECK(launch_ksum_final(acc, n_out, inv_Nk, st, out, c.s));
+  }
+  return read_status(c);
+}
+
 }  // namespace
 
 // ====================================================================== public ABI
@@ -627,6 +745,26 @@ size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
   p.model = p.eigh = p.berry = p.ksum = true;
   p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
+  plan_layout(p, false, 0);
+  return p.total;
+}
+
+size_t kubo_grad_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
+                                const kubo_options* opt) {
+  kubo_options o = opt ? *opt : defaults();
+  int n_eta = 1;
+  if (validate_common(W, N_R, kmesh, o, n_eta) != KUBO_OK || n_EF < 1) return 0;
+  if (o.precision != KUBO_FP64) return 0;
+  Plan p;
+  p.W = W; p.N_R = N_R; p.N_h = (N_R - 1) / 2; p.K = N_R; p.n_EF = n_EF; p.n_eta = n_eta;
+  p.precision = o.precision;
+  p.mesh = Mesh{kmesh[0], kmesh[1], kmesh[2], (int64_t)kmesh[0] * kmesh[1] * kmesh[2]};
+  int64_t kb = o.k_begin, ke = o.k_end;
+  if (kb == 0 && ke == 0) ke = p.mesh.Nk;
+  p.chunk = o.chunk_k > 0 ? o.chunk_k
+                          : auto_chunk(W, n_eta, std::max<int64_t>(1, ke - kb), grad_bytes_per_k(W, N_R));
+  p.model = p.eigh = p.berry = p.ksum = p.grad = true;
+  p.lbuf = W > SMALL_W_MAX;
   plan_layout(p, false, 0);
   return p.total;
 }
@@ -686,6 +824,40 @@ kubo_status kubo_ahc_host(const double* H_R, const int32_t* R_vecs, int W, int N
         r = KUBO_ERR_CUDA;
       }
     }
+    c.release();
+    if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    return r;
+  } catch (const std::bad_alloc&) {
+    return KUBO_ERR_OOM;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_ahc_grad(const double* H_R, const int32_t* R_vecs, int W, int N_R,
+                          const int32_t* kmesh, const double* E_F, int n_EF, double eta,
+                          const double* dL_dout, double* grad_H_R, double* out,
+                          const kubo_options* opt) {
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!H_R || !E_F || !dL_dout || !grad_H_R) return KUBO_ERR_INVALID_ARG;
+    if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
+    if (!std::isfinite(o.grad_eps)) return KUBO_ERR_INVALID_ARG;
+    Call c;
+    RInfo ri;
+    int64_t kb, ke;
+    kubo_status r = setup_ahc(c, o, R_vecs, W, N_R, kmesh, n_EF, ri, kb, ke, false);
+    if (r != KUBO_OK) return r;
+    if (o.precision != KUBO_FP64) return KUBO_ERR_UNSUPPORTED;
+    Plan& p = c.p;
+    p.grad = true;
+    p.fixup = false;
+    p.chunk = o.chunk_k > 0 ? o.chunk_k
+                            : auto_chunk(W, p.n_eta, std::max<int64_t>(1, ke - kb), grad_bytes_per_k(W, N_R));
+    plan_layout(p, false, 0);
+    r = c.acquire(o);
+    if (r != KUBO_OK) return r;
+    r = ahc_grad_device(c, o, H_R, ri, E_F, eta, dL_dout, (double2*)grad_H_R, out, kb, ke);
     c.release();
     if (cudaStreamSynchronize(c.s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
     return r;

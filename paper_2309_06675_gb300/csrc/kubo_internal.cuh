@@ -187,6 +187,28 @@ cudaError_t launch_berry_large(const double* E, const double2* U, const double* 
                                int64_t eta_stride, bool f32, void* Tbuf, void* Vx, void* Vy,
                                cudaStream_t s);
 
+// T = X U with X packed Hermitian rows (leading dimension ld), FP64
+cudaError_t launch_herm_u(const double* X, int64_t ld, const double2* U, double2* T, int W, int n,
+                          cudaStream_t s);
+
+// reverse mode (k_grad.cu)
+cudaError_t launch_zgemm_batched(bool hA, bool hB, bool acc, const double2* A, const double2* B,
+                                 double2* C, int W, int n, cudaStream_t s);
+cudaError_t launch_grad_pairs(const double* E, const double2* vx, const double2* vy, int W, int n,
+                              const double* g, const double* E_F, int n_EF, const double* etas,
+                              int n_eta, double kT, double inv_Nk, double2* vbx, double2* vby,
+                              double* Ebar, cudaStream_t s);
+cudaError_t launch_grad_gp(const double* E, const double* Ebar, const double2* N, int W, int n,
+                           double grad_eps, double2* Gp, cudaStream_t s);
+cudaError_t launch_pack3(const double2* A0, const double2* A1, const double2* A2, int W, int n,
+                         double* out, cudaStream_t s);
+cudaError_t launch_grad_coef(const Model& md, const Mesh& mesh, const KList& kl, int ldc,
+                             double* Coef, cudaStream_t s);
+cudaError_t launch_grad_fourier_t(const double* Coef, int ldc, const double* Mbar, int M, int N,
+                                  int K, double* Gacc, cudaStream_t s);
+cudaError_t launch_grad_finalize(const double* Gacc, const int* pairs, const int* Rh, int idx0,
+                                 int N_h, int W, double2* G, cudaStream_t s);
+
 size_t tridiag_smem(int W);
 size_t backtransform_smem(int W);
 size_t ql_smem(int W);
