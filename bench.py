@@ -35,16 +35,25 @@ METRIC = "k-points/sec for σ_xy (W=64, N_R=1331), mixed vs FP64 GPU at rel err 
 WORKLOAD = "w64_r1331_k128"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
 # algorithmic flops per k-point by stage (W = 64, N_R = 1331), see the design doc
-def stage_flops(W, N_R):
+def stage_flops(W, N_R, prec="fp64"):
+    """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
+
+    In the mixed path the eigenvector stage stops at the eigenvectors Z of the tridiagonal
+    (inverse iteration) and U = Q D Z is assembled in FP32 inside the rotation kernel.
+    """
+    mixed = prec != "fp64"
     return {
         "fourier": 6.0 * N_R * W * W,     # real contraction [3 x N_R] . [N_R x W^2]
         "tridiag": 16.0 / 3.0 * W ** 3,   # complex Householder reduction
         "ql": 25.0 * 1.2 * W * W,         # ~1.2 W^2 Givens steps of ~25 flops
-        "backtransform": 8.0 * W ** 3 + 42.0 * W * W,   # reflectors U = Q D Z + inverse iteration
-        "berry": 24.0 * W ** 3,           # two Hermitian rotations U^H dH U
+        # inverse iteration (+ reflectors U = Q D Z in the FP64 path)
+        "backtransform": 42.0 * W * W + (0.0 if mixed else 8.0 * W ** 3),
+        # two Hermitian rotations U^H dH U (+ FP32 assembly of U in the mixed path)
+        "berry": 24.0 * W ** 3 + (8.0 * W ** 3 if mixed else 0.0),
         "ksum": 2.0 * W * 64,
         "prep": 0.0,
         "fixup": 0.0,
+        "adjoint": 0.0,
     }
 
 
@@ -269,15 +278,15 @@ def main():
             dist.destroy_process_group()
         return
 
-    fl = stage_flops(model.W, model.N_R)
     k_total = args.steps * k_per_step
     paths = {}
     fixup_k = {p: r[1].pop("_fixup_k") for p, r in res.items()}
     for p, (ms, st, clk, outs) in res.items():
         paths[p] = {"value": world * k_total / (ms / 1e3), "ms_per_step": ms / args.steps,
-                    "stages": stage_table(st, fl, k_total),
+                    "stages": stage_table(st, stage_flops(model.W, model.N_R, p), k_total),
                     "gpu_launches": int(sum(v["launches"] for v in st.values())), "clocks": clk}
     ms, st, clk, outs = res[head]
+    fl = stage_flops(model.W, model.N_R, head)
     dom = max((s for s in st if st[s]["launches"] > 0), key=lambda s: st[s]["ms"])
     launches = st[dom]["launches"]
     k_per_launch = k_total / launches

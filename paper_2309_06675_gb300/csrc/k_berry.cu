@@ -262,10 +262,73 @@ __device__ __forceinline__ void unpack_hermitian_f32(const TIn* __restrict__ P, 
   }
 }
 
-// X and Y: packed Hermitian rows of leading dimension ld.
-template <typename TIn>
+// U = Q D Z in FP32, in shared memory, from the FP64 factors of the eigensolver: Z (eigenvectors
+// of the real tridiagonal, [W][W]), the phases D and the Householder reflectors (staged in
+// `stage`, W (W - 1) / 2 complex).  Each column is transformed by its own 4 threads, so the
+// reflectors are applied without block barriers.  The only consumer of this U is the FP32
+// rotation, so it is formed at that precision.
+__device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
+                                               const double2* __restrict__ ph,
+                                               const double2* __restrict__ R,
+                                               const double* __restrict__ tau, int W, int LD,
+                                               int t, float2* sU, float2* stage) {
+  for (int idx = t; idx < W * W; idx += NT) {
+    const int r = idx / W, c = idx % W;
+    const double z = Zk[idx];
+    const double2 p = ph[r];
+    sU[r * LD + c] = make_float2((float)(p.x * z), (float)(p.y * z));
+  }
+  auto roff = [&](int j) { return j * (W - 1) - (j * (j - 1)) / 2; };   // sum_{j'<j} (W-1-j')
+  for (int idx = t; idx < W * W; idx += NT) {
+    const int r = idx / W, c = idx % W;
+    if (r > c && c < W - 2) {
+      const double2 v = R[idx];
+      stage[roff(c) + (r - c - 1)] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+  __syncthreads();
+  const int q = t & 3, c = t >> 2;   // NT / 4 = 64 >= W columns
+  const bool act = c < W;
+  for (int j = W - 3; j >= 0; --j) {
+    const float tj = (float)tau[j];
+    if (tj == 0.f) continue;
+    const int o = j + 1, m = W - 1 - j;
+    const float2* v = stage + roff(j);
+    float sx = 0.f, sy = 0.f;
+    if (act) {
+      for (int r = q; r < m; r += 4) {
+        const float2 vv = v[r];
+        const float2 u = sU[(o + r) * LD + c];
+        sx = fmaf(vv.x, u.x, fmaf(vv.y, u.y, sx));   // conj(v) u
+        sy = fmaf(vv.x, u.y, fmaf(-vv.y, u.x, sy));
+      }
+    }
+    sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+    sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+    sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+    sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+    sx *= tj; sy *= tj;
+    if (act) {
+      for (int r = q; r < m; r += 4) {
+        const float2 vv = v[r];
+        float2 u = sU[(o + r) * LD + c];
+        u.x = fmaf(-sx, vv.x, fmaf(sy, vv.y, u.x));   // u -= s v
+        u.y = fmaf(-sx, vv.y, fmaf(-sy, vv.x, u.y));
+        sU[(o + r) * LD + c] = u;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// X and Y: packed Hermitian rows of leading dimension ld.  FROMZ: U is assembled in FP32 from
+// the eigensolver's factors (Z, eb.phase, eb.refl, eb.tau) instead of being read.
+template <typename TIn, bool FROMZ>
 __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restrict__ E,
                                                          const double2* __restrict__ U,
+                                                         const double* __restrict__ Z,
+                                                         EighBufs eb,
                                                          const TIn* __restrict__ Xp,
                                                          const TIn* __restrict__ Yp, int64_t ld,
                                                          int W, const double* __restrict__ etas,
@@ -285,9 +348,13 @@ __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restric
   const int64_t k = blockIdx.x;
   const size_t WW = (size_t)W * W;
 
-  for (int idx = t; idx < W * W; idx += NT) {
-    double2 u = U[k * WW + idx];
-    sU[(idx / W) * LD + idx % W] = make_float2((float)u.x, (float)u.y);
+  if (FROMZ) {
+    assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, LD, t, sU, sA);
+  } else {
+    for (int idx = t; idx < W * W; idx += NT) {
+      double2 u = U[k * WW + idx];
+      sU[(idx / W) * LD + idx % W] = make_float2((float)u.x, (float)u.y);
+    }
   }
   unpack_hermitian_f32(Xp + k * ld, sA, W, LD, t);
   for (int j = t; j < W; j += NT) sE[j] = E[k * W + j];
@@ -374,15 +441,17 @@ size_t berry_mixed_smem(int W, int n_eta) {
   return mat + (2 * mat > red ? 2 * mat : red);
 }
 
-template <typename TIn>
-cudaError_t launch_berry_mixed_t(const double* E, const double2* U, const TIn* Xp, const TIn* Yp,
+template <typename TIn, bool FROMZ>
+cudaError_t launch_berry_mixed_t(const double* E, const double2* U, const double* Z,
+                                 const EighBufs& eb, const TIn* Xp, const TIn* Yp,
                                  int64_t ld, int W, int n, const double* etas, int n_eta,
                                  double* Om, int64_t eta_stride, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   size_t sm = berry_mixed_smem(W, n_eta);
-  cudaError_t e = cudaFuncSetAttribute(berry_mixed_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(berry_mixed_kernel<TIn, FROMZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  berry_mixed_kernel<TIn><<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride);
+  berry_mixed_kernel<TIn, FROMZ><<<n, NT, sm, s>>>(E, U, Z, eb, Xp, Yp, ld, W, etas, n_eta, Om,
+                                                   eta_stride);
   return cudaGetLastError();
 }
 
@@ -390,16 +459,33 @@ cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const dou
                                     int64_t ld, int W, int n, const double* etas, int n_eta,
                                     double* Om, int64_t eta_stride, cudaStream_t s) {
   const int64_t WW = (int64_t)W * W;
-  return launch_berry_mixed_t<double>(E, U, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
-                                      eta_stride, s);
+  return launch_berry_mixed_t<double, false>(E, U, nullptr, EighBufs{}, C + WW, C + 2 * WW, ld, W,
+                                             n, etas, n_eta, Om, eta_stride, s);
+}
+
+cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const EighBufs& eb,
+                                      const double* C, int64_t ld, int W, int n,
+                                      const double* etas, int n_eta, double* Om,
+                                      int64_t eta_stride, cudaStream_t s) {
+  const int64_t WW = (int64_t)W * W;
+  return launch_berry_mixed_t<double, true>(E, nullptr, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas,
+                                            n_eta, Om, eta_stride, s);
+}
+
+cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,
+                                          const double* Xp, const double* Yp, int W, int n,
+                                          const double* etas, int n_eta, double* Om,
+                                          int64_t eta_stride, cudaStream_t s) {
+  return launch_berry_mixed_t<double, true>(E, nullptr, Z, eb, Xp, Yp, (int64_t)W * W, W, n, etas,
+                                            n_eta, Om, eta_stride, s);
 }
 
 cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
                                         const double* Yp, int W, int n, const double* etas,
                                         int n_eta, double* Om, int64_t eta_stride,
                                         cudaStream_t s) {
-  return launch_berry_mixed_t<double>(E, U, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
-                                      eta_stride, s);
+  return launch_berry_mixed_t<double, false>(E, U, nullptr, EighBufs{}, Xp, Yp, (int64_t)W * W, W,
+                                             n, etas, n_eta, Om, eta_stride, s);
 }
 
 cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,

@@ -443,13 +443,25 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     StageTimer tm(c, KUBO_STAGE_QL, 1);
     KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
   }
+  const size_t WW = (size_t)p.W * p.W;
+  if (f32_rotation(p.precision) && p.W <= SMALL_W_MAX) {
+    // FP32 rotations: U = Q D Z is assembled in FP32 inside the rotation kernel from the FP64
+    // eigenvectors Z of the tridiagonal (kept in the U buffer) and the reflectors
+    double* Z = reinterpret_cast<double*>(U);
+    {
+      StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
+      KCHECK(launch_eigvec_z(p.W, kl.n, eb, Eout, Z, c.s));
+    }
+    StageTimer tm(c, KUBO_STAGE_BERRY, 1);
+    KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    return KUBO_OK;
+  }
   {
     StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
     KCHECK(eigh_vectors(c, kl.n, eb, Eout, U));
   }
   {
     StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);
-    const size_t WW = (size_t)p.W * p.W;
     KCHECK(berry_any(c, Eout, U, C64 + WW, C64 + 2 * WW, p.Npad, true, kl.n, f32_rotation(p.precision), Om, om_stride));
   }
   return KUBO_OK;
@@ -476,6 +488,16 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
   {
     StageTimer tm(c, KUBO_STAGE_QL, 1);
     KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
+  }
+  if (f32_rotation(p.precision) && p.W <= SMALL_W_MAX) {
+    double* Z = reinterpret_cast<double*>(U);
+    {
+      StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
+      KCHECK(launch_eigvec_z(p.W, kl.n, eb, Eout, Z, c.s));
+    }
+    StageTimer tm(c, KUBO_STAGE_BERRY, 1);
+    KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    return KUBO_OK;
   }
   {
     StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);

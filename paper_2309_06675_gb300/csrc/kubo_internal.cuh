@@ -114,6 +114,8 @@ cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, Eigh
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
                                  cudaStream_t s);
+// same solver stopped at the eigenvectors Z of T ([n][W][W] real), W <= 64
+cudaError_t launch_eigvec_z(int W, int n, EighBufs b, double* E, double* Z, cudaStream_t s);
 
 cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
                               const double* Yp, int W, int n, const double* etas, int n_eta,
@@ -127,6 +129,17 @@ cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const dou
 cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const double* C,
                                    int64_t ld, int W, int n, const double* etas, int n_eta,
                                    double* Om, int64_t eta_stride, cudaStream_t s);
+
+// FP32 rotations with U = Q D Z assembled in FP32 inside the kernel from Z and the eigensolver
+// factors in eb (phase, refl, tau), W <= 64
+cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const EighBufs& eb,
+                                      const double* C, int64_t ld, int W, int n,
+                                      const double* etas, int n_eta, double* Om,
+                                      int64_t eta_stride, cudaStream_t s);
+cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,
+                                          const double* Xp, const double* Yp, int W, int n,
+                                          const double* etas, int n_eta, double* Om,
+                                          int64_t eta_stride, cudaStream_t s);
 
 // FP32 rotation from FP64 packed arrays (error-budget mode)
 cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
