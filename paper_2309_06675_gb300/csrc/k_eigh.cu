@@ -299,12 +299,8 @@ __device__ __forceinline__ double iit_start(int i, int j) {
 
 constexpr int IIT_SOLVES = 3;
 
-// ZONLY: stop after the eigenvectors Z of T and write them ([k][W][W] real, column c = sorted
-// eigenvalue c) to Zout; the product U = Q D Z is then formed by the consumer.
-template <bool ZONLY>
 __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, double* __restrict__ Eout,
-                                                           double2* __restrict__ Uout,
-                                                           double* __restrict__ Zout) {
+                                                           double2* __restrict__ Uout) {
   extern __shared__ double2 smem2[];
   const int LDU = W + 1;
   double2* U = smem2;                               // [W][LDU] complex (LU scratch before)
@@ -335,7 +331,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
     dd[j] = b.d[k * W + j];
     ee[j] = b.e[k * W + j];
   }
-  if (ZONLY ? Zout == nullptr : Uout == nullptr) return;
+  if (Uout == nullptr) return;
   __syncthreads();
   if (warp == 0) {   // ||T||_1
     double mx = 0.0;
@@ -439,12 +435,6 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
       }
     }
     __syncthreads();
-  }
-
-  if (ZONLY) {
-    double* Zk = Zout + (size_t)k * W * W;
-    for (int idx = t; idx < W * W; idx += NT) Zk[idx] = Z[(idx / W) * LDU + idx % W];
-    return;
   }
 
   // U = D Z, columns in the original (unsorted) eigenvalue order of rank[]: column c of U holds
@@ -555,18 +545,9 @@ cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s) {
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   size_t sm = backtransform_smem(W);
-  cudaError_t e = cudaFuncSetAttribute(backtransform_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  backtransform_kernel<false><<<n, NT, sm, s>>>(W, b, E, U, nullptr);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_eigvec_z(int W, int n, EighBufs b, double* E, double* Z, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  size_t sm = backtransform_smem(W);
-  cudaError_t e = cudaFuncSetAttribute(backtransform_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  backtransform_kernel<true><<<n, NT, sm, s>>>(W, b, E, nullptr, Z);
+  backtransform_kernel<<<n, NT, sm, s>>>(W, b, E, U);
   return cudaGetLastError();
 }
 

@@ -1,13 +1,16 @@
 // Steps (2)-(4) for orders 64 < W <= 128, where a whole k-point no longer fits one CTA's
 // shared memory.  Same arithmetic as the fused kernels, split into batched passes:
-//   iit_large_kernel      eigenvalue sort + eigenvectors of the tridiagonal T by inverse
-//                         iteration, one thread per cluster; LU factors and iterates in global
-//                         scratch laid out [.. ][i][thread] (coalesced)
+//   iit_kernel            eigenvalue sort + eigenvectors of the tridiagonal T by inverse
+//                         iteration, one thread per cluster, persistent CTAs; LU factors in
+//                         per-CTA global scratch laid out [i][thread] (coalesced), iterates in
+//                         their column of Z (also used for W <= 64 when U is formed in FP32)
 //   reflect_large_kernel  U = Q D Z for one 32-column block of one k-point per CTA
 //   cgemm_herm_u_kernel   T = dH U   (dH from packed Hermitian rows)          } FP64 or FP32
 //   cgemm_uh_t_kernel     V = U^H T                                            } arithmetic
 //   curvature_large_kernel Omega_n = sum_{m != n} T_nm, every pair evaluated from the upper
 //                         triangle (exact antisymmetry), FP64 denominators for every eta
+#include <algorithm>
+
 #include "kubo_internal.cuh"
 
 namespace kubo {
@@ -17,6 +20,7 @@ namespace {
 constexpr int LW_MAX = LARGE_W_MAX;
 constexpr int IIT_SOLVES = 3;
 constexpr int MAXE = 8;
+constexpr int IIT_SMS = 152;   // GB300 SM count: persistent inverse-iteration grid
 
 __device__ __forceinline__ unsigned long long order_key(double x) {
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -30,128 +34,133 @@ __device__ __forceinline__ double iit_start(int i, int j) {
 }
 
 // ------------------------------------------------------------------ inverse iteration
-// block = LW_MAX threads, one k-point; thread j handles the cluster starting at sorted index j.
-// Z: [n][W][W] real, column m = eigenvector of sorted eigenvalue m.
-// scratch: [n][4][W][LW_MAX] (reciprocal pivots, U1, U2, multipliers).
-__global__ void __launch_bounds__(LW_MAX) iit_large_kernel(int W, EighBufs b, double* __restrict__ Eout,
-                                                           double* __restrict__ Z,
-                                                           double* __restrict__ scratch) {
+// Persistent: CTA b handles k = b, b + gridDim.x, ...; block = ldt = W rounded up to a warp;
+// thread j handles the cluster starting at sorted index j.  Z: [n][W][W] real, column m =
+// eigenvector of sorted eigenvalue m.  scratch: per CTA [4][W][ldt] (reciprocal pivots, U1,
+// U2, multipliers), lane-interleaved so every access of a warp is one coalesced row segment.
+__global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
+                                                     double* __restrict__ Eout,
+                                                     double* __restrict__ Z,
+                                                     double* __restrict__ scratch) {
   __shared__ double ws[LW_MAX], dd[LW_MAX], ee[LW_MAX];
   __shared__ int newc[LW_MAX];
   __shared__ double s_onenrm;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t k = blockIdx.x;
-  const double* lk = b.lam + k * W;
-  if (t < W) {
-    const double lj = lk[t];
-    const unsigned long long kj = order_key(lj);
-    int rnk = 0;
-    for (int i = 0; i < W; ++i) {
-      const unsigned long long ki = order_key(lk[i]);
-      rnk += (ki < kj) || (ki == kj && i < t);
-    }
-    ws[rnk] = lj;
-    Eout[k * W + rnk] = lj;
-    dd[t] = b.d[k * W + t];
-    ee[t] = b.e[k * W + t];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    double mx = 0.0;
-    for (int i = lane; i < W; i += 32)
-      mx = fmax(mx, fabs(dd[i]) + (i > 0 ? ee[i - 1] : 0.0) + (i < W - 1 ? ee[i] : 0.0));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) s_onenrm = mx > 0.0 ? mx : 1.0;
-  }
-  __syncthreads();
-  const double onenrm = s_onenrm;
-  const double eps = 2.220446049250313e-16;
-  const double ortol = 1e-3 * onenrm, pertol = 10.0 * eps * onenrm, tiny = eps * onenrm;
-  if (t < W) newc[t] = (t == 0) || (ws[t] - ws[t - 1] > ortol);
-  __syncthreads();
-  if (Z == nullptr) return;
-
-  const size_t plane = (size_t)W * LW_MAX;
-  double* rU0 = scratch + (size_t)k * 4 * plane;
+  const int ldt = blockDim.x;
+  const size_t plane = (size_t)W * ldt;
+  double* rU0 = scratch + (size_t)blockIdx.x * 4 * plane;
   double* U1 = rU0 + plane;
   double* U2 = U1 + plane;
   double* ML = U2 + plane;
-  double* Zk = Z + (size_t)k * W * W;
-  const int j = t;
-  if (j < W && newc[j]) {
-    double lprev = 0.0;
-    for (int m = j; m < W && (m == j || !newc[m]); ++m) {
-      double lam = ws[m];
-      if (m > j && lam - lprev <= pertol) lam = lprev + pertol;
-      lprev = lam;
-      unsigned long long piv0 = 0ull, piv1 = 0ull;   // row interchanges, bits 0..127
-      double q0 = dd[0] - lam, q1 = W > 1 ? ee[0] : 0.0, q2 = 0.0;
-      for (int i = 0; i + 1 < W; ++i) {
-        const double ei = ee[i];
-        const double a = dd[i + 1] - lam;
-        const double bb = i + 2 < W ? ee[i + 1] : 0.0;
-        const size_t o = (size_t)i * LW_MAX + t;
-        if (fabs(q0) >= fabs(ei)) {
-          if (q0 == 0.0) q0 = tiny;
-          const double r = 1.0 / q0;
-          const double mlt = ei * r;
-          rU0[o] = r; U1[o] = q1; U2[o] = q2; ML[o] = mlt;
-          q0 = fma(-mlt, q1, a);
-          q1 = fma(-mlt, q2, bb);
-          q2 = 0.0;
-        } else {
-          const double r = 1.0 / ei;
-          const double mlt = q0 * r;
-          rU0[o] = r; U1[o] = a; U2[o] = bb; ML[o] = mlt;
-          if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64);
-          const double n0 = fma(-mlt, a, q1);
-          q1 = fma(-mlt, bb, q2);
-          q0 = n0;
-          q2 = 0.0;
-        }
+  const double eps = 2.220446049250313e-16;
+  for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+    __syncthreads();   // the previous k-point's shared arrays are no longer read
+    const double* lk = b.lam + k * W;
+    if (t < W) {
+      const double lj = lk[t];
+      const unsigned long long kj = order_key(lj);
+      int rnk = 0;
+      for (int i = 0; i < W; ++i) {
+        const unsigned long long ki = order_key(lk[i]);
+        rnk += (ki < kj) || (ki == kj && i < t);
       }
-      if (q0 == 0.0) q0 = tiny;
-      {
-        const size_t o = (size_t)(W - 1) * LW_MAX + t;
-        rU0[o] = 1.0 / q0; U1[o] = 0.0; U2[o] = 0.0;
-      }
-      for (int i = 0; i < W; ++i) Zk[(size_t)i * W + m] = iit_start(i, m);
-      for (int it = 0; it < IIT_SOLVES; ++it) {
+      ws[rnk] = lj;
+      Eout[k * W + rnk] = lj;
+      dd[t] = b.d[k * W + t];
+      ee[t] = b.e[k * W + t];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double mx = 0.0;
+      for (int i = lane; i < W; i += 32)
+        mx = fmax(mx, fabs(dd[i]) + (i > 0 ? ee[i - 1] : 0.0) + (i < W - 1 ? ee[i] : 0.0));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) s_onenrm = mx > 0.0 ? mx : 1.0;
+    }
+    __syncthreads();
+    const double onenrm = s_onenrm;
+    const double ortol = 1e-3 * onenrm, pertol = 10.0 * eps * onenrm, tiny = eps * onenrm;
+    if (t < W) newc[t] = (t == 0) || (ws[t] - ws[t - 1] > ortol);
+    __syncthreads();
+    if (Z == nullptr) continue;
+
+    double* Zk = Z + (size_t)k * W * W;
+    const int j = t;
+    if (j < W && newc[j]) {
+      double lprev = 0.0;
+      for (int m = j; m < W && (m == j || !newc[m]); ++m) {
+        double lam = ws[m];
+        if (m > j && lam - lprev <= pertol) lam = lprev + pertol;
+        lprev = lam;
+        unsigned long long piv0 = 0ull, piv1 = 0ull;   // row interchanges, bits 0..127
+        double q0 = dd[0] - lam, q1 = W > 1 ? ee[0] : 0.0, q2 = 0.0;
         for (int i = 0; i + 1 < W; ++i) {
-          const double mlt = ML[(size_t)i * LW_MAX + t];
-          const double yi = Zk[(size_t)i * W + m], yn = Zk[(size_t)(i + 1) * W + m];
-          const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
-          if (sw) {
-            Zk[(size_t)i * W + m] = yn;
-            Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yn, yi);
+          const double ei = ee[i];
+          const double a = dd[i + 1] - lam;
+          const double bb = i + 2 < W ? ee[i + 1] : 0.0;
+          const size_t o = (size_t)i * ldt + t;
+          if (fabs(q0) >= fabs(ei)) {
+            if (q0 == 0.0) q0 = tiny;
+            const double r = 1.0 / q0;
+            const double mlt = ei * r;
+            rU0[o] = r; U1[o] = q1; U2[o] = q2; ML[o] = mlt;
+            q0 = fma(-mlt, q1, a);
+            q1 = fma(-mlt, q2, bb);
+            q2 = 0.0;
           } else {
-            Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yi, yn);
+            const double r = 1.0 / ei;
+            const double mlt = q0 * r;
+            rU0[o] = r; U1[o] = a; U2[o] = bb; ML[o] = mlt;
+            if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64);
+            const double n0 = fma(-mlt, a, q1);
+            q1 = fma(-mlt, bb, q2);
+            q0 = n0;
+            q2 = 0.0;
           }
         }
-        double x1 = 0.0, x2 = 0.0;
-        for (int i = W - 1; i >= 0; --i) {
-          const size_t o = (size_t)i * LW_MAX + t;
-          const double xi = (Zk[(size_t)i * W + m] - U1[o] * x1 - U2[o] * x2) * rU0[o];
-          Zk[(size_t)i * W + m] = xi;
-          x2 = x1;
-          x1 = xi;
+        if (q0 == 0.0) q0 = tiny;
+        {
+          const size_t o = (size_t)(W - 1) * ldt + t;
+          rU0[o] = 1.0 / q0; U1[o] = 0.0; U2[o] = 0.0;
         }
-        for (int q = j; q < m; ++q) {
-          double c = 0.0;
-          for (int i = 0; i < W; ++i) c = fma(Zk[(size_t)i * W + q], Zk[(size_t)i * W + m], c);
-          for (int i = 0; i < W; ++i)
-            Zk[(size_t)i * W + m] = fma(-c, Zk[(size_t)i * W + q], Zk[(size_t)i * W + m]);
+        for (int i = 0; i < W; ++i) Zk[(size_t)i * W + m] = iit_start(i, m);
+        for (int it = 0; it < IIT_SOLVES; ++it) {
+          for (int i = 0; i + 1 < W; ++i) {
+            const double mlt = ML[(size_t)i * ldt + t];
+            const double yi = Zk[(size_t)i * W + m], yn = Zk[(size_t)(i + 1) * W + m];
+            const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
+            if (sw) {
+              Zk[(size_t)i * W + m] = yn;
+              Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yn, yi);
+            } else {
+              Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yi, yn);
+            }
+          }
+          double x1 = 0.0, x2 = 0.0;
+          for (int i = W - 1; i >= 0; --i) {
+            const size_t o = (size_t)i * ldt + t;
+            const double xi = (Zk[(size_t)i * W + m] - U1[o] * x1 - U2[o] * x2) * rU0[o];
+            Zk[(size_t)i * W + m] = xi;
+            x2 = x1;
+            x1 = xi;
+          }
+          for (int q = j; q < m; ++q) {
+            double c = 0.0;
+            for (int i = 0; i < W; ++i) c = fma(Zk[(size_t)i * W + q], Zk[(size_t)i * W + m], c);
+            for (int i = 0; i < W; ++i)
+              Zk[(size_t)i * W + m] = fma(-c, Zk[(size_t)i * W + q], Zk[(size_t)i * W + m]);
+          }
+          double s0 = 0.0, s1 = 0.0;
+          int i = 0;
+          for (; i + 1 < W; i += 2) {
+            const double u = Zk[(size_t)i * W + m], v = Zk[(size_t)(i + 1) * W + m];
+            s0 = fma(u, u, s0);
+            s1 = fma(v, v, s1);
+          }
+          if (i < W) { const double u = Zk[(size_t)i * W + m]; s0 = fma(u, u, s0); }
+          const double inv = 1.0 / sqrt(s0 + s1);
+          for (int i2 = 0; i2 < W; ++i2) Zk[(size_t)i2 * W + m] *= inv;
         }
-        double s0 = 0.0, s1 = 0.0;
-        int i = 0;
-        for (; i + 1 < W; i += 2) {
-          const double u = Zk[(size_t)i * W + m], v = Zk[(size_t)(i + 1) * W + m];
-          s0 = fma(u, u, s0);
-          s1 = fma(v, v, s1);
-        }
-        if (i < W) { const double u = Zk[(size_t)i * W + m]; s0 = fma(u, u, s0); }
-        const double inv = 1.0 / sqrt(s0 + s1);
-        for (int i2 = 0; i2 < W; ++i2) Zk[(size_t)i2 * W + m] *= inv;
       }
     }
   }
@@ -432,13 +441,20 @@ __global__ void __launch_bounds__(LW_MAX) curvature_large_kernel(const double* _
 
 }  // namespace
 
-size_t large_iit_scratch_doubles(int W) { return (size_t)4 * W * LW_MAX; }
+// threads per inverse-iteration CTA and number of persistent CTAs (scratch slots): one warp
+// per 32 orders; CTAs per SM so that about 1024 threads of each SM run inverse iteration
+static int iit_threads(int W) { return (W + 31) / 32 * 32; }
 
-cudaError_t launch_iit_large(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
-                             cudaStream_t s) {
+int iit_max_slots(int W) { return IIT_SMS * std::min(32, 1024 / iit_threads(W)); }
+
+size_t iit_scratch_doubles(int W, int slots) { return (size_t)slots * 4 * W * iit_threads(W); }
+
+cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* scratch, int slots,
+                       cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (W > LW_MAX) return cudaErrorInvalidValue;
-  iit_large_kernel<<<n, LW_MAX, 0, s>>>(W, b, E, Z, scratch);
+  if (W > LW_MAX || slots < 1) return cudaErrorInvalidValue;
+  const int grid = std::min(n, slots);
+  iit_kernel<<<grid, iit_threads(W), 0, s>>>(W, n, b, E, Z, scratch);
   return cudaGetLastError();
 }
 

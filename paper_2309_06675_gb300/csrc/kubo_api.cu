@@ -94,11 +94,14 @@ struct Plan {
   bool ksum = false;    // needs k-sum buffers
   bool lbuf = false;    // W > SMALL_W_MAX: scratch of the multi-pass kernels
   bool grad = false;    // reverse-mode buffers (kubo_ahc_grad)
+  bool iit = false;     // inverse-iteration scratch (separate eigenvector kernel)
+  int iit_slots = 0;
   Mesh mesh{1, 1, 1, 1};
   size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
          o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
          o_ph = 0, o_refl = 0, o_tau = 0, o_lam = 0, o_part = 0,
-         o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0, o_L = 0;
+         o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0, o_L = 0,
+         o_iit = 0;
   // reverse mode: six complex W x W work matrices per k, Ebar, packed [Hbar|dxHbar|dyHbar],
   // the Fourier coefficient rows of the batch and the accumulated G rows
   size_t o_gw = 0, o_Ebar = 0, o_Mbar = 0, o_Coef = 0, o_Gacc = 0;
@@ -110,14 +113,15 @@ struct Plan {
   size_t total = 0;
 };
 
-// Per k-point scratch of the W > SMALL_W_MAX kernels, reused by stage: inverse-iteration
-// factors + Z, then the FP64 rotation products T, V^x, V^y (the largest case).
+// Per k-point scratch of the W > SMALL_W_MAX kernels, reused by stage: the eigenvectors Z of
+// the tridiagonal, then the FP64 rotation products T, V^x, V^y (the larger of the two).
 size_t large_region_bytes(int W) {
   const size_t WW = (size_t)W * W;
-  const size_t eig = large_iit_scratch_doubles(W) * sizeof(double) + WW * sizeof(double);
-  const size_t rot = 3 * WW * sizeof(double2);
-  return std::max(eig, rot);
+  return std::max(WW * sizeof(double), 3 * WW * sizeof(double2));
 }
+
+// persistent inverse-iteration CTAs of a plan (their LU scratch is per CTA)
+int iit_slots_for(int W, int chunk) { return std::max(1, std::min(chunk, iit_max_slots(W))); }
 
 size_t bytes_per_k(int W, int n_eta) {
   size_t WW = (size_t)W * W;
@@ -186,6 +190,11 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_fOm = b.take(sizeof(double) * (size_t)p.fix_cap * p.W * p.n_eta);
   }
   if (p.lbuf) p.o_L = b.take(large_region_bytes(p.W) * (size_t)std::max(1, p.chunk));
+  p.iit = p.eigh && (p.W > SMALL_W_MAX || f32_rotation(p.precision));
+  if (p.iit) {
+    p.iit_slots = iit_slots_for(p.W, std::max(1, p.chunk));
+    p.o_iit = b.take(sizeof(double) * iit_scratch_doubles(p.W, p.iit_slots));
+  }
   if (p.grad) {
     const size_t ch = (size_t)std::max(1, p.chunk);
     p.o_gw = b.take(6 * sizeof(double2) * ch * WW);
@@ -387,9 +396,8 @@ EighBufs make_eigh_bufs(const Call& c) {
 cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, double2* U) {
   const Plan& p = c.p;
   if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s);
-  double* scr = c.at<double>(p.o_L);
-  double* Z = U ? scr + large_iit_scratch_doubles(p.W) * (size_t)std::max(1, p.chunk) : nullptr;
-  cudaError_t e = launch_iit_large(p.W, n, eb, E, Z, scr, c.s);
+  double* Z = U ? c.at<double>(p.o_L) : nullptr;
+  cudaError_t e = launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
   if (e != cudaSuccess || !U) return e;
   return launch_reflect_large(p.W, n, eb, Z, U, c.s);
 }
@@ -450,7 +458,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     double* Z = reinterpret_cast<double*>(U);
     {
       StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-      KCHECK(launch_eigvec_z(p.W, kl.n, eb, Eout, Z, c.s));
+      KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
     KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
@@ -493,7 +501,7 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
     double* Z = reinterpret_cast<double*>(U);
     {
       StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-      KCHECK(launch_eigvec_z(p.W, kl.n, eb, Eout, Z, c.s));
+      KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
     KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));

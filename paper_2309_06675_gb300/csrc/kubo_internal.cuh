@@ -114,8 +114,6 @@ cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, Eigh
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
                                  cudaStream_t s);
-// same solver stopped at the eigenvectors Z of T ([n][W][W] real), W <= 64
-cudaError_t launch_eigvec_z(int W, int n, EighBufs b, double* E, double* Z, cudaStream_t s);
 
 cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
                               const double* Yp, int W, int n, const double* etas, int n_eta,
@@ -184,13 +182,16 @@ cudaError_t launch_fixup_scatter(const int* pos, int cnt, int W, int n_eta, cons
                                  const double* Omfix, int64_t fix_eta_stride, double* E, double* Om,
                                  int64_t eta_stride, cudaStream_t s);
 
-// orders 64 < W <= 128 (k_large.cu): eigenvectors of T by inverse iteration into Z
-// ([n][W][W] real, column m for sorted eigenvalue m) with LU scratch of
-// large_iit_scratch_doubles(W) doubles per k-point, then U = Q D Z by column blocks
+// k_large.cu: sorted eigenvalues E and eigenvectors Z of T by inverse iteration ([n][W][W]
+// real, column m for sorted eigenvalue m; Z may be null: eigenvalues only), any W <= 128,
+// at most `slots` persistent CTAs (iit_max_slots(W) fill the GPU) with
+// iit_scratch_doubles(W, slots) doubles of scratch in total; then, for 64 < W <= 128,
+// U = Q D Z by column blocks
 constexpr int LARGE_W_MAX = 128;
-size_t large_iit_scratch_doubles(int W);
-cudaError_t launch_iit_large(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
-                             cudaStream_t s);
+int iit_max_slots(int W);
+size_t iit_scratch_doubles(int W, int slots);
+cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* scratch, int slots,
+                       cudaStream_t s);
 cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, double2* U,
                                  cudaStream_t s);
 // steps (3)-(4) as batched complex GEMMs: X, Y packed Hermitian rows of leading dimension ld;
