@@ -243,6 +243,49 @@ kubo_status kubo_ahc_grad(const double* H_R, const int32_t* R_vecs, int W, int N
                           const double* dL_dout, double* grad_H_R, double* out,
                           const kubo_options* opt);
 
+/*
+ * Many models in one call (the paper's high-throughput setting: one sigma per material, many
+ * materials).  Each problem carries the arguments kubo_ahc takes for one model; every model
+ * is summed over its whole mesh.
+ */
+typedef struct kubo_problem {
+  const double* H_R;        /* device, complex128 [N_R][W][W] */
+  const int32_t* R_vecs;    /* host, int32 [N_R][3] */
+  int W, N_R;
+  int32_t kmesh[3];
+  const double* E_F;        /* device, double [n_EF] */
+  int n_EF;
+  double eta;               /* broadening when opt->n_eta == 0 */
+  double* out;              /* device, double [n_eta][n_EF]; written only if status == KUBO_OK */
+  kubo_status status;       /* written by the call: this model's result */
+} kubo_problem;
+
+/* Schedule of a kubo_ahc_batched call.  In: 0 fields are chosen by the library; tune = 1 runs
+ * the autotuner (candidate schedules timed on a probe of every model's first k-points; the
+ * winner is cached per batch signature).  Out: the schedule that ran. */
+typedef struct kubo_batch_schedule {
+  int tune;                 /* in: 1 = autotune the fields below that are 0 */
+  int streams;              /* concurrent CUDA streams the models are spread over */
+  int chunk_k;              /* upper bound on the k-points per internal batch of a model */
+  int graph;                /* in: 0 = capture the batch in a CUDA graph (default), -1 = no */
+  double probe_ms;          /* out: the tuner's time for the chosen schedule (0 if not tuned) */
+  int tuned_candidates;     /* out: schedules the tuner timed (0 if cached or not tuned) */
+} kubo_batch_schedule;
+
+/*
+ * sigma for n_probs models of uneven W, N_R and k-mesh in one call.  Models are ordered by
+ * estimated cost (longest first) and spread over `streams` concurrent streams; the whole batch
+ * (basis preparation, every k-batch of every model, the k-sums) is captured in one CUDA
+ * graph and launched once.  Shared settings come from opt (precision, etas, kT, stream);
+ * opt->k_begin/k_end must be 0, opt->workspace NULL (the library allocates), and the mixed-
+ * precision fix-up and per-stage profile are not available in this entry point.  Hermitian
+ * pairing of every model is checked before any model runs.  Returns KUBO_OK when every model
+ * succeeded, else the first failing model's status (every problem's status field is set).
+ * sched may be NULL (library defaults).  Deterministic for a given schedule.
+ */
+kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_options* opt,
+                             kubo_batch_schedule* sched);
+
 /* Device bytes of scratch a kubo_ahc / kubo_ahc_k call with these sizes needs. */
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
                            const kubo_options* opt);

@@ -15,6 +15,7 @@ Entry points (same names as the C ABI, without the ``kubo_`` prefix):
   berry_batched(E, U, dHx_packed, dHy_packed, eta | etas)       -> Omega
   ahc_grad(H_R, R, kmesh, E_F, dL_dout, ...)                    -> G = dL/dH(R) (and S)
   AHC.apply(H_R, R, kmesh, E_F, eta, etas, kT)                  -> S, differentiable in H_R
+  ahc_batched([(H_R, R, kmesh, E_F[, eta]), ...], ...)          -> [S per model], schedule
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ __all__ = [
     "KuboError", "lib", "ahc", "ahc_host", "ahc_k", "bloch", "eigh_batched", "berry_batched",
     "workspace_size", "max_orbitals", "pack_hermitian", "unpack_hermitian", "FP64", "MIXED",
     "LIB_PATH", "Profile", "Options", "STAGES", "ahc_grad", "grad_workspace_size", "AHC",
+    "ahc_batched", "Problem", "BatchSchedule",
 ]
 
 FP64 = 0
@@ -84,6 +86,27 @@ class Options(ctypes.Structure):
     ]
 
 
+class Problem(ctypes.Structure):
+    """kubo_problem of include/kubo.h (one model of a batched call)."""
+    _fields_ = [
+        ("H_R", ctypes.c_void_p), ("R_vecs", ctypes.c_void_p), ("W", ctypes.c_int),
+        ("N_R", ctypes.c_int), ("kmesh", ctypes.c_int32 * 3), ("E_F", ctypes.c_void_p),
+        ("n_EF", ctypes.c_int), ("eta", ctypes.c_double), ("out", ctypes.c_void_p),
+        ("status", ctypes.c_int),
+    ]
+
+
+class BatchSchedule(ctypes.Structure):
+    """kubo_batch_schedule of include/kubo.h."""
+    _fields_ = [
+        ("tune", ctypes.c_int), ("streams", ctypes.c_int), ("chunk_k", ctypes.c_int),
+        ("graph", ctypes.c_int), ("probe_ms", ctypes.c_double), ("tuned_candidates", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -106,6 +129,7 @@ def lib():
             "kubo_workspace_size": (ctypes.c_size_t, [I, I, P, I, OPT]),
             "kubo_grad_workspace_size": (ctypes.c_size_t, [I, I, P, I, OPT]),
             "kubo_ahc_grad": (I, [P, P, I, I, P, P, I, D, P, P, P, OPT]),
+            "kubo_ahc_batched": (I, [ctypes.POINTER(Problem), I, OPT, ctypes.POINTER(BatchSchedule)]),
             "kubo_ahc": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_host": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_k": (I, [P, P, I, I, P, P, I64, D, P, P, OPT]),
@@ -257,6 +281,49 @@ def ahc_grad(H_R, R, kmesh, E_F, dL_dout, eta=1e-3, etas=None, kT=0.0, k_range=N
                                ctypes.byref(o))
     _check(code, "kubo_ahc_grad")
     return (G, S) if with_value else G
+
+
+def ahc_batched(problems, etas=None, kT=0.0, precision=FP64, stream=None, tune=False, streams=0,
+                chunk_k=0, graph=True):
+    """S(E_F) of many models in one call (kubo_ahc_batched).
+
+    problems: sequence of (H_R complex128 CUDA [N_R, W, W], R host [N_R, 3], kmesh,
+    E_F float64 CUDA [n_EF][, eta]).  Returns (list of float64 CUDA [n_eta, n_EF], schedule
+    dict, list of per-model status names).  Raises KuboError if any model failed.
+    """
+    torch = _torch()
+    n = len(problems)
+    arr = (Problem * n)()
+    keep, outs = [], []
+    n_eta = 1 if etas is None else int(np.asarray(etas).size)
+    for i, pr in enumerate(problems):
+        H_R, R, kmesh, E_F = pr[:4]
+        eta = float(pr[4]) if len(pr) > 4 else 1e-3
+        Rh = _host_int32(R, 3)
+        keep.append(Rh)
+        out = torch.empty((n_eta, int(E_F.numel())), dtype=torch.float64, device=H_R.device)
+        outs.append(out)
+        a = arr[i]
+        a.H_R = _dev(H_R, torch.complex128, "H_R")
+        a.R_vecs = Rh.ctypes.data_as(ctypes.c_void_p)
+        a.W, a.N_R = int(H_R.shape[1]), int(H_R.shape[0])
+        for q in range(3):
+            a.kmesh[q] = int(kmesh[q])
+        a.E_F = _dev(E_F, torch.float64, "E_F")
+        a.n_EF = int(E_F.numel())
+        a.eta = eta
+        a.out = _dev(out, torch.float64, "out")
+        a.status = -1
+    o = _options(precision, etas, kT, None, stream, 0, None, keep)
+    sc = BatchSchedule()
+    sc.tune = 1 if tune else 0
+    sc.streams = int(streams)
+    sc.chunk_k = int(chunk_k)
+    sc.graph = 0 if graph else -1
+    code = lib().kubo_ahc_batched(arr, n, ctypes.byref(o), ctypes.byref(sc))
+    status = [_STATUS.get(arr[i].status, str(arr[i].status)) for i in range(n)]
+    _check(code, f"kubo_ahc_batched (per-model status: {status})")
+    return outs, sc.as_dict(), status
 
 
 def grad_workspace_size(W, N_R, kmesh, n_EF, n_eta=1, kT=0.0, k_range=None, chunk_k=0) -> int:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -731,6 +732,229 @@ kubo_status ahc_grad_device(Call& c, const kubo_options& o, const double* H_R, c
   return read_status(c);
 }
 
+// ------------------------------------------------------------------ batched models
+// One model of a kubo_ahc_batched call: its validated plan (laid out inside the buffer of the
+// stream it runs on), its R analysis and its device tables.
+struct Job {
+  int idx = 0;          // index in the caller's problem array
+  RInfo ri;
+  Plan p;
+  double cost = 0.0;    // estimated device work (LPT order)
+  int stream = 0;
+  size_t o_tables = 0;  // offset of neg / pairs / Rh / status in the tables region
+};
+
+// Estimated device time of a model in units of FP64 flops: the FP64 pipe runs the eigensolver
+// (and, in FP64 mode, everything else); tensor-core and FP32 work is discounted by its rate.
+double job_cost(const Plan& p) {
+  const double W = p.W, NR = p.N_R, Nk = (double)p.mesh.Nk;
+  const double fourier = 6.0 * NR * W * W * (tc_fourier(p.precision) ? 10.0 / 1500.0 : 1.0);
+  const double eig = 16.0 / 3.0 * W * W * W + 72.0 * W * W;
+  const double rot = 24.0 * W * W * W * (f32_rotation(p.precision) ? 1.0 / 48.0 : 1.0);
+  return Nk * (fourier + eig + rot + 1e4);   // + per-k fixed cost (launch/latency share)
+}
+
+struct BatchRun {
+  std::vector<Job> jobs;
+  int streams = 1;
+  std::vector<size_t> stream_off, stream_bytes;   // stream buffers inside the workspace
+  size_t tables_bytes = 0, total = 0;
+};
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+// Tables region at the start of the workspace: neg, pairs, Rh and a status word per model
+// (laid out once per call; independent of the schedule).
+void layout_tables(BatchRun& br) {
+  Bump t;
+  for (auto& j : br.jobs)
+    j.o_tables = t.take(sizeof(DevStatus) + sizeof(double) * MAX_ETA +
+                        sizeof(int) * (j.p.N_R + 2 * std::max(1, j.p.N_h) + 3 * std::max(1, j.p.N_h)));
+  br.tables_bytes = align_up(t.off);
+}
+
+// Lay out a batch for S streams with batches of at most chunk_cap k-points: LPT assignment of
+// the models (longest first, to the least loaded stream), one buffer per stream sized for its
+// largest model.
+void layout_batch(BatchRun& br, int S, int chunk_cap, int n_eta) {
+  br.streams = S;
+  std::vector<Job*> order;
+  for (auto& j : br.jobs) order.push_back(&j);
+  std::stable_sort(order.begin(), order.end(), [](const Job* a, const Job* b) { return a->cost > b->cost; });
+  std::vector<double> load(S, 0.0);
+  for (Job* j : order) {
+    int best = 0;
+    for (int q = 1; q < S; ++q) if (load[q] < load[best]) best = q;
+    j->stream = best;
+    load[best] += j->cost;
+  }
+  const size_t stream_budget = ((size_t)12 << 30) / (size_t)S;
+  br.stream_bytes.assign(S, 0);
+  for (auto& j : br.jobs) {
+    Plan& p = j.p;
+    const int64_t nk = p.mesh.Nk;
+    int64_t c = (int64_t)(stream_budget / bytes_per_k(p.W, n_eta));
+    c = std::max<int64_t>(1, std::min<int64_t>(c, chunk_cap));
+    p.chunk = (int)std::min<int64_t>(c, nk);
+    plan_layout(p, false, 0);
+    br.stream_bytes[j.stream] = std::max(br.stream_bytes[j.stream], align_up(p.total));
+  }
+  br.stream_off.assign(S, 0);
+  size_t off = br.tables_bytes;
+  for (int q = 0; q < S; ++q) { br.stream_off[q] = off; off += br.stream_bytes[q]; }
+  br.total = off;
+}
+
+struct JobTables {
+  DevStatus* st;
+  double* etas;   // [MAX_ETA] this model's broadenings
+  int *neg, *pairs, *Rh;
+};
+
+JobTables job_tables(char* base, const Job& j) {
+  char* t = base + j.o_tables;
+  JobTables jt;
+  jt.st = (DevStatus*)t;
+  jt.etas = (double*)(t + sizeof(DevStatus));
+  jt.neg = (int*)(t + sizeof(DevStatus) + sizeof(double) * MAX_ETA);
+  jt.pairs = jt.neg + j.p.N_R;
+  jt.Rh = jt.pairs + 2 * std::max(1, j.p.N_h);
+  return jt;
+}
+
+// Everything of one model after its Hermitian check, stream-ordered on c.s without host
+// synchronisation (capturable): twiddles, packed basis (and its tensor-core split), every
+// k-batch, the k-sum, and a copy of the model's status word into its table slot.
+kubo_status run_job(Call& c, const Job& j, const kubo_problem& pr, const kubo_options& o,
+                    const JobTables& jt, double* out, int64_t nk) {
+  const Plan& p = c.p;
+  DevStatus* st = c.at<DevStatus>(p.o_status);
+  KCHECK(cudaMemsetAsync(st, 0, sizeof(DevStatus), c.s));
+  KCHECK(cudaMemcpyAsync(c.at<double>(p.o_etas), jt.etas, sizeof(double) * MAX_ETA, cudaMemcpyDeviceToDevice, c.s));
+  KCHECK(launch_twiddles(c.at<double2>(p.o_tab), p.mesh.N1, p.mesh.N2, p.mesh.N3, c.s));
+  KCHECK(launch_pack_basis((const double2*)pr.H_R, jt.pairs, j.ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s));
+  if (tc_fourier(p.precision))
+    KCHECK(launch_basis_split(c.at<double>(p.o_Bp), jt.Rh, p.N_h, p.W, p.Npad, p.Kp, c.at<int>(p.o_cexp), c.at<char>(p.o_Bt), c.s));
+  const int n_out = p.n_eta * p.n_EF;
+  KCHECK(cudaMemsetAsync(c.at<char>(p.o_acc), 0, sizeof(double2) * n_out, c.s));
+  Model md = make_model(c);
+  md.Rh = jt.Rh;
+  double* E = c.at<double>(p.o_E);
+  double* Om = c.at<double>(p.o_Om);
+  double2* part = c.at<double2>(p.o_part);
+  double2* acc = c.at<double2>(p.o_acc);
+  for (int64_t base = 0; base < nk; base += p.chunk) {
+    KList kl{nullptr, base, (int)std::min<int64_t>(p.chunk, nk - base)};
+    kubo_status r = run_batch(c, md, kl, E, Om, (int64_t)kl.n * p.W);
+    if (r != KUBO_OK) return r;
+    KCHECK(launch_ksum_partial(E, Om, p.W, kl.n, p.n_eta, (int64_t)kl.n * p.W, pr.E_F, p.n_EF, o.kT, part, p.kpb, c.s));
+    KCHECK(launch_ksum_fold(part, (kl.n + p.kpb - 1) / p.kpb, n_out, acc, c.s));
+  }
+  KCHECK(launch_ksum_final(acc, n_out, 1.0 / (double)p.mesh.Nk, st, out, c.s));
+  KCHECK(cudaMemcpyAsync(jt.st, st, sizeof(DevStatus), cudaMemcpyDeviceToDevice, c.s));
+  return KUBO_OK;
+}
+
+// Issue the whole batch: fork the origin stream into S streams, run every model on its
+// stream, join.  With graph != nullptr the work is captured and instantiated into *graph
+// (one CUDA graph, launched by the caller); otherwise it is issued directly.  probe_out:
+// per-model scratch outputs and k-limits for autotuner probes (empty = real run).
+kubo_status issue_batch(const BatchRun& br, const std::vector<kubo_problem>& probs,
+                        const kubo_options& o, char* ws, cudaStream_t origin,
+                        const std::vector<cudaStream_t>& streams, cudaGraphExec_t* graph,
+                        double* probe_out, const std::vector<int64_t>& probe_nk) {
+  std::vector<cudaEvent_t> evs(br.streams + 1, nullptr);
+  for (auto& e : evs)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& x : evs) if (x) cudaEventDestroy(x);
+      return KUBO_ERR_CUDA;
+    }
+  if (graph && cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    for (auto& x : evs) cudaEventDestroy(x);
+    return KUBO_ERR_CUDA;
+  }
+  kubo_status r = KUBO_OK;
+  if (cudaEventRecord(evs[0], origin) != cudaSuccess) r = KUBO_ERR_CUDA;
+  for (int q = 0; q < br.streams && r == KUBO_OK; ++q)
+    if (cudaStreamWaitEvent(streams[q], evs[0], 0) != cudaSuccess) r = KUBO_ERR_CUDA;
+  for (size_t i = 0; i < br.jobs.size() && r == KUBO_OK; ++i) {
+    const Job& j = br.jobs[i];
+    Call c;
+    c.p = j.p;
+    c.s = streams[j.stream];
+    c.ws = ws + br.stream_off[j.stream];
+    const kubo_problem& pr = probs[j.idx];
+    double* out = probe_out ? probe_out + i * (size_t)(j.p.n_eta * j.p.n_EF) : pr.out;
+    const int64_t nk = probe_out ? probe_nk[i] : j.p.mesh.Nk;
+    r = run_job(c, j, pr, o, job_tables(ws, j), out, nk);
+    c.ws = nullptr;
+  }
+  for (int q = 0; q < br.streams && r == KUBO_OK; ++q) {
+    if (cudaEventRecord(evs[q + 1], streams[q]) != cudaSuccess ||
+        cudaStreamWaitEvent(origin, evs[q + 1], 0) != cudaSuccess)
+      r = KUBO_ERR_CUDA;
+  }
+  if (graph) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(origin, &g) != cudaSuccess) r = KUBO_ERR_CUDA;
+    if (r == KUBO_OK && cudaGraphInstantiate(graph, g, 0) != cudaSuccess) {
+      *graph = nullptr;
+      r = KUBO_ERR_CUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  if (r != KUBO_OK) cudaGetLastError();
+  for (auto& x : evs) cudaEventDestroy(x);
+  return r;
+}
+
+// Run a laid-out batch once (graph or direct) and return the device time of the launch.
+kubo_status run_batch_once(const BatchRun& br, const std::vector<kubo_problem>& probs,
+                           const kubo_options& o, char* ws, cudaStream_t origin,
+                           const std::vector<cudaStream_t>& streams, bool graph,
+                           double* probe_out, const std::vector<int64_t>& probe_nk, float* ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    return KUBO_ERR_CUDA;
+  }
+  kubo_status r = KUBO_OK;
+  cudaGraphExec_t ge = nullptr;
+  if (graph) r = issue_batch(br, probs, o, ws, origin, streams, &ge, probe_out, probe_nk);
+  if (r == KUBO_OK && cudaEventRecord(a, origin) != cudaSuccess) r = KUBO_ERR_CUDA;
+  if (r == KUBO_OK) {
+    if (graph) {
+      if (cudaGraphLaunch(ge, origin) != cudaSuccess) r = KUBO_ERR_CUDA;
+    } else {
+      r = issue_batch(br, probs, o, ws, origin, streams, nullptr, probe_out, probe_nk);
+    }
+  }
+  if (r == KUBO_OK && cudaEventRecord(b, origin) != cudaSuccess) r = KUBO_ERR_CUDA;
+  if (cudaStreamSynchronize(origin) != cudaSuccess) r = KUBO_ERR_CUDA;
+  if (r == KUBO_OK && ms && cudaEventElapsedTime(ms, a, b) != cudaSuccess) r = KUBO_ERR_CUDA;
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (r != KUBO_OK) cudaGetLastError();
+  return r;
+}
+
+// process-wide cache of tuned schedules, keyed by the batch signature
+std::mutex g_tune_mutex;
+std::map<std::vector<int64_t>, std::array<int, 2>> g_tune_cache;
+
+std::vector<int64_t> batch_signature(const std::vector<Job>& jobs, const kubo_options& o) {
+  std::vector<int64_t> sig{o.precision, o.kT > 0.0 ? 1 : 0, o.n_eta};
+  std::vector<std::array<int64_t, 3>> m;
+  for (const auto& j : jobs) m.push_back({j.p.W, j.p.N_R, j.p.mesh.Nk});
+  std::sort(m.begin(), m.end());
+  for (auto& x : m) sig.insert(sig.end(), x.begin(), x.end());
+  return sig;
+}
+
 }  // namespace
 
 // ====================================================================== public ABI
@@ -895,6 +1119,225 @@ kubo_status kubo_ahc_grad(const double* H_R, const int32_t* R_vecs, int W, int N
     return KUBO_ERR_OOM;
   } catch (...) {
     return KUBO_ERR_CUDA;
+  }
+}
+
+kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_options* opt,
+                             kubo_batch_schedule* sched) {
+  std::vector<cudaStream_t> streams;
+  char* ws = nullptr;
+  cudaStream_t user = nullptr, origin = nullptr;   // origin: the library's own capture stream
+  auto finish = [&](kubo_status r) {
+    for (auto& q : streams)
+      if (q && cudaStreamSynchronize(q) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    if (origin) {
+      if (ws) cudaFreeAsync(ws, origin);
+      if (cudaStreamSynchronize(origin) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+      cudaStreamDestroy(origin);
+    }
+    for (auto& q : streams) if (q) cudaStreamDestroy(q);
+    cudaGetLastError();
+    return r;
+  };
+  try {
+    kubo_options o = opt ? *opt : defaults();
+    if (!probs || n_probs < 1) return KUBO_ERR_INVALID_ARG;
+    if (o.k_begin != 0 || o.k_end != 0 || o.workspace) return KUBO_ERR_INVALID_ARG;
+    kubo_batch_schedule sc{};
+    if (sched) sc = *sched;
+    if (sc.streams < 0 || sc.chunk_k < 0) return KUBO_ERR_INVALID_ARG;
+    user = (cudaStream_t)o.stream;
+    // ---- validate every model; invalid ones are skipped (their status says why)
+    std::vector<kubo_problem> P(probs, probs + n_probs);
+    BatchRun br;
+    kubo_status first = KUBO_OK;
+    int n_eta = 1;
+    for (int i = 0; i < n_probs; ++i) {
+      kubo_problem& q = probs[i];
+      kubo_status r = KUBO_OK;
+      if (!q.H_R || !q.E_F || !q.out || !q.R_vecs || q.n_EF < 1) r = KUBO_ERR_INVALID_ARG;
+      else if (o.n_eta == 0 && !finite_nonneg(q.eta)) r = KUBO_ERR_INVALID_ARG;
+      if (r == KUBO_OK) r = validate_common(q.W, q.N_R, q.kmesh, o, n_eta);
+      Job j;
+      if (r == KUBO_OK) r = analyze_R(q.R_vecs, q.N_R, j.ri);
+      q.status = r;
+      if (r != KUBO_OK) {
+        if (first == KUBO_OK) first = r;
+        continue;
+      }
+      j.idx = i;
+      Plan& p = j.p;
+      p.W = q.W; p.N_R = q.N_R; p.N_h = j.ri.N_h; p.K = q.N_R; p.n_EF = q.n_EF; p.n_eta = n_eta;
+      p.precision = o.precision;
+      p.mesh = Mesh{q.kmesh[0], q.kmesh[1], q.kmesh[2], (int64_t)q.kmesh[0] * q.kmesh[1] * q.kmesh[2]};
+      p.model = p.eigh = p.berry = p.ksum = true;
+      p.lbuf = q.W > SMALL_W_MAX;
+      p.fixup = false;
+      j.cost = job_cost(p);
+      br.jobs.push_back(std::move(j));
+    }
+    if (br.jobs.empty()) return first;
+    const int n_jobs = (int)br.jobs.size();
+    // ---- schedule: given, cached, tuned or default
+    const int kStreamsMax = 16;
+    int S = sc.streams > 0 ? std::min({sc.streams, n_jobs, kStreamsMax}) : 0;
+    int chunk = sc.chunk_k > 0 ? sc.chunk_k : 0;
+    const bool graph = sc.graph >= 0;
+    sc.probe_ms = 0.0;
+    sc.tuned_candidates = 0;
+    std::vector<int64_t> sig;
+    bool need_tune = sc.tune && (S == 0 || chunk == 0);
+    if (need_tune) {
+      sig = batch_signature(br.jobs, o);
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(sig);
+      if (it != g_tune_cache.end()) {
+        if (S == 0) S = std::min(it->second[0], n_jobs);
+        if (chunk == 0) chunk = it->second[1];
+        need_tune = false;
+      }
+    }
+    // ---- one allocation for the largest layout any candidate can need, plus probe outputs
+    std::vector<int> cand_S, cand_C;
+    if (need_tune) {
+      for (int v : {1, 2, 4, 8}) if ((S == 0 || v == S) && v <= n_jobs) cand_S.push_back(v);
+      if (S != 0 && cand_S.empty()) cand_S.push_back(S);
+      for (int v : {8192, 65536}) if (chunk == 0 || v == chunk) cand_C.push_back(v);
+      if (chunk != 0 && cand_C.empty()) cand_C.push_back(chunk);
+    } else {
+      cand_S.push_back(S > 0 ? S : std::min(4, n_jobs));
+      cand_C.push_back(chunk > 0 ? chunk : 65536);
+    }
+    layout_tables(br);
+    size_t need = 0;
+    for (int cs : cand_S)
+      for (int cc : cand_C) {
+        layout_batch(br, cs, cc, n_eta);
+        need = std::max(need, br.total);
+      }
+    size_t probe_doubles = 0;
+    for (const auto& j : br.jobs) probe_doubles += (size_t)j.p.n_eta * j.p.n_EF;
+    const size_t probe_off = align_up(need);
+    // the batch runs behind the caller's stream on a stream of its own (the legacy default
+    // stream cannot be captured), and the call returns when it is done
+    {
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        origin = nullptr;
+        return finish(KUBO_ERR_CUDA);
+      }
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(origin, ev, 0) != cudaSuccess) {
+        if (ev) cudaEventDestroy(ev);
+        return finish(KUBO_ERR_CUDA);
+      }
+      cudaEventDestroy(ev);
+    }
+    if (cudaMallocAsync((void**)&ws, probe_off + sizeof(double) * probe_doubles, origin) != cudaSuccess) {
+      cudaGetLastError();
+      ws = nullptr;
+      return finish(KUBO_ERR_OOM);
+    }
+    const int max_S = *std::max_element(cand_S.begin(), cand_S.end());
+    streams.assign(max_S, nullptr);
+    for (auto& q : streams)
+      if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        q = nullptr;
+        return finish(KUBO_ERR_CUDA);
+      }
+    // ---- tables and the Hermitian check of every model (one host synchronisation)
+#define BCHECK(expr)                                  \
+  do {                                                \
+    if ((expr) != cudaSuccess) return finish(KUBO_ERR_CUDA); \
+  } while (0)
+    std::vector<std::array<double, MAX_ETA>> eta_h(br.jobs.size());
+    for (size_t i = 0; i < br.jobs.size(); ++i) {
+      eta_h[i].fill(0.0);
+      if (o.n_eta > 0) for (int e = 0; e < o.n_eta; ++e) eta_h[i][e] = o.etas[e];
+      else eta_h[i][0] = probs[br.jobs[i].idx].eta;
+    }
+    for (size_t i = 0; i < br.jobs.size(); ++i) {
+      const Job& j = br.jobs[i];
+      const JobTables jt = job_tables(ws, j);
+      BCHECK(cudaMemsetAsync(jt.st, 0, sizeof(DevStatus), origin));
+      BCHECK(cudaMemcpyAsync(jt.etas, eta_h[i].data(), sizeof(double) * MAX_ETA, cudaMemcpyHostToDevice, origin));
+      BCHECK(cudaMemcpyAsync(jt.neg, j.ri.neg.data(), sizeof(int) * j.p.N_R, cudaMemcpyHostToDevice, origin));
+      if (j.p.N_h > 0) {
+        BCHECK(cudaMemcpyAsync(jt.pairs, j.ri.pairs.data(), sizeof(int) * 2 * j.p.N_h, cudaMemcpyHostToDevice, origin));
+        BCHECK(cudaMemcpyAsync(jt.Rh, j.ri.Rh.data(), sizeof(int) * 3 * j.p.N_h, cudaMemcpyHostToDevice, origin));
+      }
+      BCHECK(launch_check_hermitian((const double2*)probs[j.idx].H_R, jt.neg, j.p.N_R, j.p.W, jt.st, origin));
+      BCHECK(launch_hermitian_verdict(jt.st, origin));
+    }
+    std::vector<DevStatus> hs(br.jobs.size());
+    for (size_t i = 0; i < br.jobs.size(); ++i)
+      BCHECK(cudaMemcpyAsync(&hs[i], job_tables(ws, br.jobs[i]).st, sizeof(DevStatus), cudaMemcpyDeviceToHost, origin));
+    BCHECK(cudaStreamSynchronize(origin));
+    {
+      std::vector<Job> ok;
+      for (size_t i = 0; i < br.jobs.size(); ++i) {
+        const kubo_status r = bits_to_status(hs[i].bits);
+        if (r != KUBO_OK) {
+          probs[br.jobs[i].idx].status = r;
+          if (first == KUBO_OK) first = r;
+        } else {
+          ok.push_back(std::move(br.jobs[i]));
+        }
+      }
+      br.jobs.swap(ok);
+    }
+    if (br.jobs.empty()) return finish(first);
+    std::vector<kubo_problem> PP(probs, probs + n_probs);
+    double* probe_out = (double*)(ws + probe_off);
+    // ---- autotune: time every candidate schedule on a probe of each model's first k-points
+    if (need_tune) {
+      std::vector<int64_t> probe_nk;
+      for (const auto& j : br.jobs)
+        probe_nk.push_back(std::min<int64_t>(j.p.mesh.Nk, std::max<int64_t>(4096, j.p.mesh.Nk / 16)));
+      float best = -1.f;
+      int bS = cand_S[0], bC = cand_C[0];
+      for (int cs : cand_S)
+        for (int cc : cand_C) {
+          layout_batch(br, std::min(cs, (int)br.jobs.size()), cc, n_eta);
+          float ms = 0.f;
+          kubo_status r = run_batch_once(br, PP, o, ws, origin, streams, graph, probe_out, probe_nk, &ms);
+          if (r != KUBO_OK) return finish(r);
+          ++sc.tuned_candidates;
+          if (best < 0.f || ms < best) { best = ms; bS = cs; bC = cc; }
+        }
+      S = bS;
+      chunk = bC;
+      sc.probe_ms = best;
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_cache[sig] = {S, chunk};
+    } else {
+      S = cand_S[0];
+      chunk = cand_C[0];
+    }
+    // ---- the real run
+    layout_batch(br, std::min(S, (int)br.jobs.size()), chunk, n_eta);
+    kubo_status r = run_batch_once(br, PP, o, ws, origin, streams, graph, nullptr, {}, nullptr);
+    if (r != KUBO_OK) return finish(r);
+    for (size_t i = 0; i < br.jobs.size(); ++i)
+      BCHECK(cudaMemcpyAsync(&hs[i], job_tables(ws, br.jobs[i]).st, sizeof(DevStatus), cudaMemcpyDeviceToHost, origin));
+    BCHECK(cudaStreamSynchronize(origin));
+    for (size_t i = 0; i < br.jobs.size(); ++i) {
+      const kubo_status rj = bits_to_status(hs[i].bits);
+      probs[br.jobs[i].idx].status = rj;
+      if (rj != KUBO_OK && first == KUBO_OK) first = rj;
+    }
+    sc.streams = br.streams;
+    sc.chunk_k = chunk;
+    sc.graph = graph ? 1 : -1;
+    if (sched) *sched = sc;
+    return finish(first);
+#undef BCHECK
+  } catch (const std::bad_alloc&) {
+    return finish(KUBO_ERR_OOM);
+  } catch (...) {
+    return finish(KUBO_ERR_CUDA);
   }
 }
 

@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "TBModel", "r_box", "random_tb", "qwz", "haldane", "stack_layers",
-    "k_sample", "config", "CONFIGS",
+    "k_sample", "config", "CONFIGS", "batch_recipe",
 ]
 
 
@@ -204,6 +204,25 @@ CONFIGS = {
                            E_F=list(np.linspace(-2.0, 2.0, 512)),
                            etas=[1e-4, 1e-3, 5e-3, 1e-2], kT=0.0),
 }
+
+
+def batch_recipe(n_models: int = 64, seed: int = 7, w_range=(8, 96), hw_range=(3, 5),
+                 mesh_range=(32, 64), decay: float = 1.5, model_seed0: int = 1000):
+    """Shapes of the uneven-model batch: per model (W, half_width, mesh N, model seed).
+
+    W uniform in w_range, cubic R box of half-width uniform in hw_range ((2h+1)^3 vectors),
+    k-mesh N^3 with N uniform in mesh_range, hoppings as ``random_tb`` with the given decay
+    and seed model_seed0 + i.  Draw with ``random_tb(W, h, decay, seed)``; the Fermi level
+    of each model (its median band energy at k = 0) is for the caller to compute.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(int(n_models)):
+        W = int(rng.integers(w_range[0], w_range[1] + 1))
+        h = int(rng.integers(hw_range[0], hw_range[1] + 1))
+        N = int(rng.integers(mesh_range[0], mesh_range[1] + 1))
+        out.append(dict(W=W, half_width=h, mesh=N, decay=decay, seed=model_seed0 + i))
+    return out
 
 
 def config(name: str):
