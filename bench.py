@@ -12,6 +12,12 @@ collective.  Timed: exactly K steps after W warm-up steps, CUDA events on the li
 stream (torch's current stream), barrier + synchronize on both sides, max over ranks.
 
 ``--impl reference`` times the FP64 CPU oracle (tests' reference) on the host cores instead.
+
+Other workloads (``--workload``, one JSON line each, not the headline):
+  batched  64 uneven models (W 8..96, R boxes 7^3..11^3, meshes 32^3..64^3), one
+           kubo_ahc_batched call over every model's whole mesh
+  grad     W = 32, N_R = 729, 48^3 mesh, kT = 25 meV, eta = 5e-3: kubo_ahc_grad (FP64)
+  sweep    W = 128, N_R = 1331, 96^3 mesh, 512 Fermi levels x 4 etas (slabs of the mesh)
 """
 from __future__ import annotations
 
@@ -69,6 +75,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="k-points per internal batch (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep"])
     return ap.parse_args()
 
 
@@ -180,6 +187,95 @@ def stage_table(st, fl, k_total):
             for s, v in st.items()}
 
 
+# ------------------------------------------------------------------ other workloads
+def _timed(fn, steps, warmup, local):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps, clocks.stop()
+
+
+def run_extra(args, local):
+    """Informational lines for the other workloads (see the module docstring)."""
+    import torch
+    import paper_2309_06675_gb300 as kubo
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic (tbgen)", "unit": "k-points/s"}
+    if args.workload == "batched":
+        rec = tbgen.batch_recipe()
+        prec = "mixed" if args.precision == "both" else args.precision
+        P, nk = [], 0
+        for r in rec:
+            m = tbgen.random_tb(r["W"], r["half_width"], r["decay"], r["seed"])
+            H = torch.from_numpy(m.H_R).to(dev)
+            # Fermi level: midpoint of the two middle levels of H(k=0), from the library itself
+            Hp, _, _ = kubo.bloch(H, m.R, (1, 1, 1), torch.zeros(1, dtype=torch.int64, device=dev))
+            E, _ = kubo.eigh_batched(Hp, m.W, vectors=False)
+            E = E[0].cpu().numpy()
+            h = (m.W + 1) // 2
+            ef = 0.5 * (E[h - 1] + E[h])
+            P.append((H, m.R, (r["mesh"],) * 3, torch.tensor([ef], dtype=torch.float64, device=dev)))
+            nk += r["mesh"] ** 3
+        sched = {}
+        def step():
+            _, sc, _ = kubo.ahc_batched(P, precision=prec, tune=True)
+            sched.update(sc)
+        ms, clk = _timed(step, args.steps, args.warmup, local)
+        line.update(metric="k-points/sec over a batch of 64 uneven models (one kubo_ahc_batched call)",
+                    value=nk / (ms / 1e3), ms_per_step=ms, dtype="f64" if prec == "fp64" else prec,
+                    config={"workload": "batch64_w8-96_r343-1331_k32-64", "models": len(P),
+                            "k_points": nk, "precision": prec, "schedule": sched}, clocks=clk)
+    elif args.workload == "grad":
+        model, kmesh, E_F, etas, kT = tbgen.config("w32_r729_k48_fd")
+        H = torch.from_numpy(model.H_R).to(dev)
+        EF = torch.from_numpy(E_F).to(dev)
+        g = torch.ones((1, E_F.size), dtype=torch.float64, device=dev)
+        prof = kubo.Profile()
+        def step():
+            kubo.ahc_grad(H, model.R, kmesh, EF, g, eta=float(etas[0]), kT=kT, with_value=True,
+                          profile=prof)
+        ms, clk = _timed(step, args.steps, args.warmup, local)
+        nk = int(np.prod(kmesh))
+        fwd = kubo.ahc  # forward alone on the same workload, for the adjoint/forward ratio
+        ms_f, _ = _timed(lambda: fwd(H, model.R, kmesh, EF, eta=float(etas[0]), kT=kT), args.steps, 1, local)
+        line.update(metric="k-points/sec for dσ_xy/dH(R) (value and gradient, FP64)",
+                    value=nk / (ms / 1e3), ms_per_step=ms, dtype="f64",
+                    config={"workload": "w32_r729_k48_fd", "W": model.W, "N_R": model.N_R,
+                            "kmesh": list(kmesh), "kT": kT, "eta": float(etas[0])},
+                    forward_only={"value": nk / (ms_f / 1e3), "ms_per_step": ms_f},
+                    stages={k: v for k, v in prof.as_dict().items() if v["launches"]}, clocks=clk)
+    else:  # sweep
+        model, kmesh, E_F, etas, kT = tbgen.config("w128_r1331_k96")
+        H = torch.from_numpy(model.H_R).to(dev)
+        EF = torch.from_numpy(E_F).to(dev)
+        plane = kmesh[1] * kmesh[2]
+        prec = "mixed" if args.precision == "both" else args.precision
+        k_step = args.planes * plane
+        state = {"s": 0}
+        def step():
+            s = state["s"] % (kmesh[0] // args.planes)
+            state["s"] += 1
+            kubo.ahc(H, model.R, kmesh, EF, etas=list(etas), kT=kT, precision=prec,
+                     k_range=(s * k_step, (s + 1) * k_step))
+        ms, clk = _timed(step, args.steps, args.warmup, local)
+        line.update(metric="k-points/sec for σ_xy (W=128, N_R=1331, 512 E_F x 4 eta)",
+                    value=k_step / (ms / 1e3), ms_per_step=ms, dtype=prec,
+                    config={"workload": "w128_r1331_k96", "k_per_step": k_step, "precision": prec},
+                    clocks=clk)
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -187,6 +283,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "w64":
+        return run_extra(args, local)
 
     import torch
     import paper_2309_06675_gb300 as kubo
