@@ -18,6 +18,8 @@ Other workloads (``--workload``, one JSON line each, not the headline):
            kubo_ahc_batched call over every model's whole mesh
   grad     W = 32, N_R = 729, 48^3 mesh, kT = 25 meV, eta = 5e-3: kubo_ahc_grad (FP64)
   sweep    W = 128, N_R = 1331, 96^3 mesh, 512 Fermi levels x 4 etas (slabs of the mesh)
+  pad      the W = 64 workload with padded (W + 1) and unpadded (W) shared-memory matrices in
+           the eigenvector and rotation kernels: the padding ablation
 """
 from __future__ import annotations
 
@@ -75,7 +77,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="k-points per internal batch (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep"])
+    ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep", "pad"])
     return ap.parse_args()
 
 
@@ -255,6 +257,27 @@ def run_extra(args, local):
                             "kmesh": list(kmesh), "kT": kT, "eta": float(etas[0])},
                     forward_only={"value": nk / (ms_f / 1e3), "ms_per_step": ms_f},
                     stages={k: v for k, v in prof.as_dict().items() if v["launches"]}, clocks=clk)
+    elif args.workload == "pad":
+        model, kmesh, E_F, etas, kT = tbgen.config(WORKLOAD)
+        H = torch.from_numpy(model.H_R).to(dev)
+        EF = torch.from_numpy(E_F).to(dev)
+        plane = kmesh[1] * kmesh[2]
+        k_step = args.planes * plane
+        res = {}
+        for prec in ("fp64", "mixed"):
+            for unp in (False, True):
+                prof = kubo.Profile()
+                ms, _ = _timed(lambda: kubo.ahc(H, model.R, kmesh, EF, eta=float(etas[0]), precision=prec,
+                                                k_range=(0, k_step), profile=prof, unpadded=unp),
+                               args.steps, args.warmup, local)
+                st = prof.as_dict()
+                n = args.steps + args.warmup
+                res[f"{prec}_{'unpadded' if unp else 'padded'}"] = {
+                    "k_per_s": k_step / (ms / 1e3),
+                    "backtransform_ms": st["backtransform"]["ms"] / n, "berry_ms": st["berry"]["ms"] / n}
+        line.update(metric="padding ablation: k-points/s with padded vs unpadded shared-memory matrices",
+                    value=res["fp64_padded"]["k_per_s"], ms_per_step=None, dtype="f64",
+                    config={"workload": WORKLOAD, "k_per_step": k_step}, ablation=res)
     else:  # sweep
         model, kmesh, E_F, etas, kT = tbgen.config("w128_r1331_k96")
         H = torch.from_numpy(model.H_R).to(dev)

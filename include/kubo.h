@@ -112,6 +112,10 @@ typedef struct kubo_options {
   double grad_eps;          /* kubo_ahc_grad: broadening eps of the eigenvector-derivative
                                kernel (E_j - E_i) / ((E_j - E_i)^2 + eps^2) (energy units);
                                <= 0 (the default) = 1e-12 max_n |E_n(k)| at each k. */
+  int layout_unpadded;      /* 1: shared-memory matrices of the eigenvector and rotation
+                               kernels with leading dimension W instead of W + 1 -- the
+                               padding ablation (Sec. 2.3 pads against memory-bank
+                               conflicts); slower, same results.  0 (default): padded. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,

@@ -83,6 +83,7 @@ class Options(ctypes.Structure):
         ("profile", ctypes.POINTER(Profile)),
         ("mixed_fixup_rel", ctypes.c_double),
         ("grad_eps", ctypes.c_double),
+        ("layout_unpadded", ctypes.c_int),
     ]
 
 
@@ -229,7 +230,8 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
-        stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0):
+        stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
+        unpadded=False):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
@@ -245,6 +247,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     keep = []
     o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
     o.mixed_fixup_rel = float(fixup_rel)
+    o.layout_unpadded = 1 if unpadded else 0
     code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                           W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                           _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),

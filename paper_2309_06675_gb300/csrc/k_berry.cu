@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
                                                         int W,
                                                         const double* __restrict__ etas,
                                                         int n_eta, double* __restrict__ Om,
-                                                        int64_t eta_stride) {
+                                                        int64_t eta_stride, int pad) {
   extern __shared__ double2 sm[];
-  const int LD = W + 1;
+  const int LD = W + pad;   // pad = 1: conflict-free column walks; 0: the padding ablation
   double2* sU = sm;
   double2* sA = sU + W * LD;
   double2* sB = sA + W * LD;
@@ -322,6 +322,14 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
   __syncthreads();
 }
 
+// Leading dimension (in float2) of the FP32 shared-memory matrices.  Padded: W + P with
+// W + P = 4 (mod 16), so that a row step moves 8 banks: the 4 rows x 2 columns of float2 that
+// a quarter of a warp touches in the reflector application, and the 16 consecutive columns of
+// a half warp elsewhere, fall on distinct banks.  Unpadded (the ablation): W.
+__host__ __device__ __forceinline__ int mixed_ld(int W, int pad) {
+  return pad ? W + ((4 - W) & 15) : W;
+}
+
 // X and Y: packed Hermitian rows of leading dimension ld.  FROMZ: U is assembled in FP32 from
 // the eigensolver's factors (Z, eb.phase, eb.refl, eb.tau) instead of being read.
 template <typename TIn, bool FROMZ>
@@ -333,9 +341,9 @@ __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restric
                                                          const TIn* __restrict__ Yp, int64_t ld,
                                                          int W, const double* __restrict__ etas,
                                                          int n_eta, double* __restrict__ Om,
-                                                         int64_t eta_stride) {
+                                                         int64_t eta_stride, int pad) {
   extern __shared__ float2 smf[];
-  const int LD = W + 1;
+  const int LD = mixed_ld(W, pad);
   float2* sU = smf;
   float2* sA = sU + W * LD;
   float2* sB = sA + W * LD;
@@ -411,32 +419,33 @@ size_t berry_fp64_smem(int W, int n_eta) {
 template <typename TIn>
 cudaError_t launch_berry_fp64_t(const double* E, const double2* U, const TIn* Xp, const TIn* Yp,
                                 int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
-                                int64_t eta_stride, cudaStream_t s) {
+                                int64_t eta_stride, cudaStream_t s, int pad) {
   if (n <= 0) return cudaSuccess;
   size_t sm = berry_fp64_smem(W, n_eta);
   cudaError_t e = cudaFuncSetAttribute(berry_fp64_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  berry_fp64_kernel<TIn><<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride);
+  berry_fp64_kernel<TIn><<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride,
+                                           pad ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
                               const double* Yp, int W, int n, const double* etas, int n_eta,
-                              double* Om, int64_t eta_stride, cudaStream_t s) {
+                              double* Om, int64_t eta_stride, cudaStream_t s, int pad) {
   return launch_berry_fp64_t<double>(E, U, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
-                                     eta_stride, s);
+                                     eta_stride, s, pad);
 }
 
 cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const double* C,
                                    int64_t ld, int W, int n, const double* etas, int n_eta,
-                                   double* Om, int64_t eta_stride, cudaStream_t s) {
+                                   double* Om, int64_t eta_stride, cudaStream_t s, int pad) {
   const int64_t WW = (int64_t)W * W;
   return launch_berry_fp64_t<double>(E, U, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
-                                     eta_stride, s);
+                                     eta_stride, s, pad);
 }
 
 size_t berry_mixed_smem(int W, int n_eta) {
-  const size_t mat = (size_t)W * (W + 1) * sizeof(float2);
+  const size_t mat = (size_t)W * mixed_ld(W, 1) * sizeof(float2);
   const size_t red = (size_t)n_eta * W * 2 * 16 * sizeof(double);
   return mat + (2 * mat > red ? 2 * mat : red);
 }
@@ -445,47 +454,47 @@ template <typename TIn, bool FROMZ>
 cudaError_t launch_berry_mixed_t(const double* E, const double2* U, const double* Z,
                                  const EighBufs& eb, const TIn* Xp, const TIn* Yp,
                                  int64_t ld, int W, int n, const double* etas, int n_eta,
-                                 double* Om, int64_t eta_stride, cudaStream_t s) {
+                                 double* Om, int64_t eta_stride, cudaStream_t s, int pad) {
   if (n <= 0) return cudaSuccess;
   size_t sm = berry_mixed_smem(W, n_eta);
   cudaError_t e = cudaFuncSetAttribute(berry_mixed_kernel<TIn, FROMZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   berry_mixed_kernel<TIn, FROMZ><<<n, NT, sm, s>>>(E, U, Z, eb, Xp, Yp, ld, W, etas, n_eta, Om,
-                                                   eta_stride);
+                                                   eta_stride, pad ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const double* C,
                                     int64_t ld, int W, int n, const double* etas, int n_eta,
-                                    double* Om, int64_t eta_stride, cudaStream_t s) {
+                                    double* Om, int64_t eta_stride, cudaStream_t s, int pad) {
   const int64_t WW = (int64_t)W * W;
   return launch_berry_mixed_t<double, false>(E, U, nullptr, EighBufs{}, C + WW, C + 2 * WW, ld, W,
-                                             n, etas, n_eta, Om, eta_stride, s);
+                                             n, etas, n_eta, Om, eta_stride, s, pad);
 }
 
 cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const EighBufs& eb,
                                       const double* C, int64_t ld, int W, int n,
                                       const double* etas, int n_eta, double* Om,
-                                      int64_t eta_stride, cudaStream_t s) {
+                                      int64_t eta_stride, cudaStream_t s, int pad) {
   const int64_t WW = (int64_t)W * W;
   return launch_berry_mixed_t<double, true>(E, nullptr, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas,
-                                            n_eta, Om, eta_stride, s);
+                                            n_eta, Om, eta_stride, s, pad);
 }
 
 cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,
                                           const double* Xp, const double* Yp, int W, int n,
                                           const double* etas, int n_eta, double* Om,
-                                          int64_t eta_stride, cudaStream_t s) {
+                                          int64_t eta_stride, cudaStream_t s, int pad) {
   return launch_berry_mixed_t<double, true>(E, nullptr, Z, eb, Xp, Yp, (int64_t)W * W, W, n, etas,
-                                            n_eta, Om, eta_stride, s);
+                                            n_eta, Om, eta_stride, s, pad);
 }
 
 cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
                                         const double* Yp, int W, int n, const double* etas,
                                         int n_eta, double* Om, int64_t eta_stride,
-                                        cudaStream_t s) {
+                                        cudaStream_t s, int pad) {
   return launch_berry_mixed_t<double, false>(E, U, nullptr, EighBufs{}, Xp, Yp, (int64_t)W * W, W,
-                                             n, etas, n_eta, Om, eta_stride, s);
+                                             n, etas, n_eta, Om, eta_stride, s, pad);
 }
 
 cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,

@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
   double2* vb = A + (size_t)W * (W + 1) / 2;       // [W] reflector (contiguous copy)
   double2* pb = vb + W;                            // [W] p, then w
   double2* be = pb + W;                            // [W] complex sub-diagonal beta_i
-  double* tb = (double*)(be + W);                  // [W] tau_i
+  double2* sp = be + W;                            // [NT] partial sums of the symv
+  double* tb = (double*)(sp + NT);                 // [W] tau_i
   __shared__ double s_tau, s_K;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -103,32 +104,39 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
     if (tau != 0.0) {
       for (int r = t; r < m; r += NT) vb[r] = A[tri(o + r, i)];
       __syncthreads();
-      // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r)
-      for (int r = t; r < m; r += NT) {
-        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
-        const int rowb = tri(o + r, o);
-        int c = 0;
-        for (; c + 1 < m; c += 2) {
-          const int i0 = c <= r ? rowb + c : tri(o + c, o + r);
-          const int i1 = c + 1 <= r ? rowb + c + 1 : tri(o + c + 1, o + r);
-          double2 a0 = A[i0], a1 = A[i1];
-          if (c > r) a0.y = -a0.y;
-          if (c + 1 > r) a1.y = -a1.y;
-          const double2 v0 = vb[c], v1 = vb[c + 1];
-          ax = fma(a0.x, v0.x, ax); ax = fma(-a0.y, v0.y, ax);
-          ay = fma(a0.x, v0.y, ay); ay = fma(a0.y, v0.x, ay);
-          bx = fma(a1.x, v1.x, bx); bx = fma(-a1.y, v1.y, bx);
-          by = fma(a1.x, v1.y, by); by = fma(a1.y, v1.x, by);
+      // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r).  The m x m
+      // product is spread densely over the block: thread t takes row r = t mod m and the
+      // columns c = part, part + P, ... (part = t / m, P = NT / m parts per row), so every warp
+      // issues full (the m rows of one thread each would leave lanes idle for m < 64 and
+      // partial warps); the P partial sums of a row are added in part order.  The conjugate of
+      // the mirrored element flips a sign bit on the integer side (no FP64 instruction).
+      {
+        const int P = NT / m;
+        const int r = t % m, part = t / m;
+        if (part < P) {
+          double ax = 0.0, ay = 0.0;
+          const int rowb = tri(o + r, o);
+          for (int c = part; c < m; c += P) {
+            const int idx = c <= r ? rowb + c : tri(o + c, o + r);
+            double2 a = A[idx];
+            const unsigned long long flip = c > r ? 0x8000000000000000ull : 0ull;
+            a.y = __longlong_as_double(__double_as_longlong(a.y) ^ flip);
+            const double2 v = vb[c];
+            ax = fma(a.x, v.x, ax); ax = fma(-a.y, v.y, ax);
+            ay = fma(a.x, v.y, ay); ay = fma(a.y, v.x, ay);
+          }
+          sp[part * m + r] = make_double2(ax, ay);
         }
-        if (c < m) {
-          const int i0 = c <= r ? rowb + c : tri(o + c, o + r);
-          double2 a0 = A[i0];
-          if (c > r) a0.y = -a0.y;
-          const double2 v0 = vb[c];
-          ax = fma(a0.x, v0.x, ax); ax = fma(-a0.y, v0.y, ax);
-          ay = fma(a0.x, v0.y, ay); ay = fma(a0.y, v0.x, ay);
+        __syncthreads();
+        for (int rr = t; rr < m; rr += NT) {
+          double sx = 0.0, sy = 0.0;
+          for (int q = 0; q < P; ++q) {
+            const double2 v = sp[q * m + rr];
+            sx += v.x;
+            sy += v.y;
+          }
+          pb[rr] = make_double2(tau * sx, tau * sy);
         }
-        pb[r] = make_double2(tau * (ax + bx), tau * (ay + by));
       }
       __syncthreads();
       if (warp == 0) {
@@ -300,9 +308,9 @@ __device__ __forceinline__ double iit_start(int i, int j) {
 constexpr int IIT_SOLVES = 3;
 
 __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, double* __restrict__ Eout,
-                                                           double2* __restrict__ Uout) {
+                                                           double2* __restrict__ Uout, int pad) {
   extern __shared__ double2 smem2[];
-  const int LDU = W + 1;
+  const int LDU = W + pad;   // pad = 1: conflict-free column walks; 0: the padding ablation
   double2* U = smem2;                               // [W][LDU] complex (LU scratch before)
   double* Z = (double*)(U + bt_u_slots(W));         // [W][LDU] eigenvectors of T (by sorted index)
   double* ws = Z + (size_t)W * LDU;                 // [W] sorted eigenvalues
@@ -503,7 +511,8 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
 }  // namespace
 
 size_t tridiag_smem(int W) {
-  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W) * sizeof(double2) + (size_t)W * sizeof(double);
+  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W + NT) * sizeof(double2) +
+         (size_t)W * sizeof(double);
 }
 size_t backtransform_smem(int W) {
   return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
@@ -542,12 +551,13 @@ cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U, cudaStream_t s) {
+cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U, cudaStream_t s,
+                                 int pad) {
   if (n <= 0) return cudaSuccess;
   size_t sm = backtransform_smem(W);
   cudaError_t e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  backtransform_kernel<<<n, NT, sm, s>>>(W, b, E, U);
+  backtransform_kernel<<<n, NT, sm, s>>>(W, b, E, U, pad ? 1 : 0);
   return cudaGetLastError();
 }
 

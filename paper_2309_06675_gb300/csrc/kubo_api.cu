@@ -89,6 +89,7 @@ struct Plan {
   int precision = KUBO_FP64;
   int Npad = 0, Kp = 0, Mpad = 0;   // tensor-core operand padding (mixed precision)
   int kpb = KSUM_KPB;               // k-points per k-sum block
+  int pad = 1;                      // leading dimension W + pad in the fused kernels' smem
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -396,7 +397,7 @@ EighBufs make_eigh_bufs(const Call& c) {
 // eigenvalues QL left in eb.lam (U may be null: eigenvalues only).
 cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, double2* U) {
   const Plan& p = c.p;
-  if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s);
+  if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s, p.pad);
   double* Z = U ? c.at<double>(p.o_L) : nullptr;
   cudaError_t e = launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
   if (e != cudaSuccess || !U) return e;
@@ -420,11 +421,11 @@ cudaError_t berry_any(const Call& c, const double* E, const double2* U, const do
   }
   if (rows) {
     const double* C = X - (size_t)p.W * p.W;   // the row start (H | dxH | dyH)
-    return f32 ? launch_berry_mixed_rows(E, U, C, ld, p.W, n, etas, p.n_eta, Om, om_stride, c.s)
-               : launch_berry_fp64_rows(E, U, C, ld, p.W, n, etas, p.n_eta, Om, om_stride, c.s);
+    return f32 ? launch_berry_mixed_rows(E, U, C, ld, p.W, n, etas, p.n_eta, Om, om_stride, c.s, p.pad)
+               : launch_berry_fp64_rows(E, U, C, ld, p.W, n, etas, p.n_eta, Om, om_stride, c.s, p.pad);
   }
-  return f32 ? launch_berry_mixed_from_f64(E, U, X, Y, p.W, n, etas, p.n_eta, Om, om_stride, c.s)
-             : launch_berry_fp64(E, U, X, Y, p.W, n, etas, p.n_eta, Om, om_stride, c.s);
+  return f32 ? launch_berry_mixed_from_f64(E, U, X, Y, p.W, n, etas, p.n_eta, Om, om_stride, c.s, p.pad)
+             : launch_berry_fp64(E, U, X, Y, p.W, n, etas, p.n_eta, Om, om_stride, c.s, p.pad);
 }
 
 // Steps (1)-(4) for one batch [t0, t0+n) of a k-list; E and U go to the chunk buffers, Omega
@@ -462,7 +463,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
       KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
     return KUBO_OK;
   }
   {
@@ -505,7 +506,7 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
       KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s));
+    KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
     return KUBO_OK;
   }
   {
@@ -620,6 +621,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.model = p.eigh = p.berry = p.ksum = true;
   p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
+  p.pad = o.layout_unpadded ? 0 : 1;
   plan_layout(p, host_io, 0);
   c.s = (cudaStream_t)o.stream;
   c.prof = o.profile;

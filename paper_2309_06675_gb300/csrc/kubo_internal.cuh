@@ -107,43 +107,45 @@ cudaError_t launch_twiddles(double2* tab, int N1, int N2, int N3, cudaStream_t s
 cudaError_t launch_fourier_fp64(const Model& md, const Mesh& mesh, const KList& kl, double* Hp,
                                 double* Xp, double* Yp, cudaStream_t s);
 
+// pad (fused back-transform and rotation kernels): leading dimension W + pad of the shared-
+// memory matrices; 1 (default) keeps column walks conflict-free, 0 is the padding ablation
 cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s);
 // same reduction reading packed H from rows of leading dimension ld (tensor-core output)
 cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
                                 cudaStream_t s);
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int pad = 1);
 
 cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
                               const double* Yp, int W, int n, const double* etas, int n_eta,
-                              double* Om, int64_t eta_stride, cudaStream_t s);
+                              double* Om, int64_t eta_stride, cudaStream_t s, int pad = 1);
 
 // rotations from packed dH rows of leading dimension ld (d_x H at column offset W*W, d_y H at
 // 2*W*W, as written by the tensor-core Fourier kernel): in FP32 (mixed) or in FP64
 cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const double* C,
                                     int64_t ld, int W, int n, const double* etas, int n_eta,
-                                    double* Om, int64_t eta_stride, cudaStream_t s);
+                                    double* Om, int64_t eta_stride, cudaStream_t s, int pad = 1);
 cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const double* C,
                                    int64_t ld, int W, int n, const double* etas, int n_eta,
-                                   double* Om, int64_t eta_stride, cudaStream_t s);
+                                   double* Om, int64_t eta_stride, cudaStream_t s, int pad = 1);
 
 // FP32 rotations with U = Q D Z assembled in FP32 inside the kernel from Z and the eigensolver
 // factors in eb (phase, refl, tau), W <= 64
 cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const EighBufs& eb,
                                       const double* C, int64_t ld, int W, int n,
                                       const double* etas, int n_eta, double* Om,
-                                      int64_t eta_stride, cudaStream_t s);
+                                      int64_t eta_stride, cudaStream_t s, int pad = 1);
 cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,
                                           const double* Xp, const double* Yp, int W, int n,
                                           const double* etas, int n_eta, double* Om,
-                                          int64_t eta_stride, cudaStream_t s);
+                                          int64_t eta_stride, cudaStream_t s, int pad = 1);
 
 // FP32 rotation from FP64 packed arrays (error-budget mode)
 cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
                                         const double* Yp, int W, int n, const double* etas,
                                         int n_eta, double* Om, int64_t eta_stride,
-                                        cudaStream_t s);
+                                        cudaStream_t s, int pad = 1);
 
 // tensor-core Fourier sum (k_fourier_tc.cu)
 int tc_pad_m(int n);

@@ -274,3 +274,15 @@ def test_caller_workspace(kubo, torch, m16):
     with pytest.raises(kubo.KuboError) as ei:
         kubo.ahc(cuda(torch, m16.H_R), m16.R, kmesh, cuda(torch, np.array([0.0])), workspace=small)
     assert ei.value.name == "KUBO_ERR_WORKSPACE"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_padding_ablation_gives_identical_sums(kubo, torch, m64, precision):
+    """The unpadded shared-memory layout (padding ablation) changes addresses only."""
+    kmesh = (128, 128, 128)
+    EF = cuda(torch, np.linspace(-1.0, 1.0, 64))
+    H = cuda(torch, m64.H_R)
+    rng = (9 * 16384, 9 * 16384 + 4096)
+    a = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision=precision).cpu().numpy()
+    b = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision=precision, unpadded=True).cpu().numpy()
+    assert np.array_equal(a, b)
