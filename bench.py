@@ -20,6 +20,8 @@ Other workloads (``--workload``, one JSON line each, not the headline):
   sweep    W = 128, N_R = 1331, 96^3 mesh, 512 Fermi levels x 4 etas (slabs of the mesh)
   pad      the W = 64 workload with padded (W + 1) and unpadded (W) shared-memory matrices in
            the eigenvector and rotation kernels: the padding ablation
+  separable the W = 64 workload with the separable Fourier sum (FP64, and with FP32 rotations)
+           next to the dense contraction
 """
 from __future__ import annotations
 
@@ -77,7 +79,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="k-points per internal batch (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep", "pad"])
+    ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep", "pad", "separable"])
     return ap.parse_args()
 
 
@@ -278,6 +280,28 @@ def run_extra(args, local):
         line.update(metric="padding ablation: k-points/s with padded vs unpadded shared-memory matrices",
                     value=res["fp64_padded"]["k_per_s"], ms_per_step=None, dtype="f64",
                     config={"workload": WORKLOAD, "k_per_step": k_step}, ablation=res)
+    elif args.workload == "separable":
+        model, kmesh, E_F, etas, kT = tbgen.config(WORKLOAD)
+        H = torch.from_numpy(model.H_R).to(dev)
+        EF = torch.from_numpy(E_F).to(dev)
+        k_step = args.planes * kmesh[1] * kmesh[2]
+        res, outs = {}, {}
+        for name, kw in (("fp64_dense", {}), ("fp64_separable", {"separable": True}),
+                         ("mixed_rotation_separable", {"separable": True, "precision": "mixed_rotation"})):
+            prof = kubo.Profile()
+            ms, _ = _timed(lambda: outs.__setitem__(name, kubo.ahc(H, model.R, kmesh, EF, eta=float(etas[0]),
+                                                                   k_range=(0, k_step), profile=prof, **kw)),
+                           args.steps, args.warmup, local)
+            n = args.steps + args.warmup
+            res[name] = {"k_per_s": k_step / (ms / 1e3),
+                         "stages_ms": {k: v["ms"] / n for k, v in prof.as_dict().items() if v["launches"]}}
+        ref = outs["fp64_dense"].cpu().numpy()
+        for name in ("fp64_separable", "mixed_rotation_separable"):
+            o = outs[name].cpu().numpy()
+            res[name]["rel_err_vs_dense"] = float(np.max(np.abs(o - ref)) / np.max(np.abs(ref)))
+        line.update(metric="k-points/sec with the separable Fourier sum vs the dense contraction (W=64)",
+                    value=res["fp64_separable"]["k_per_s"], ms_per_step=None, dtype="f64",
+                    config={"workload": WORKLOAD, "k_per_step": k_step}, separable=res)
     else:  # sweep
         model, kmesh, E_F, etas, kT = tbgen.config("w128_r1331_k96")
         H = torch.from_numpy(model.H_R).to(dev)

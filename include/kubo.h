@@ -116,6 +116,12 @@ typedef struct kubo_options {
                                kernels with leading dimension W instead of W + 1 -- the
                                padding ablation (Sec. 2.3 pads against memory-bank
                                conflicts); slower, same results.  0 (default): padded. */
+  int fourier_separable;    /* 1: step (1) as three one-axis sums over the bounding box of the
+                               R set instead of the dense contraction (FP64; precision
+                               KUBO_FP64 or KUBO_MIXED_ROTATION; kubo_ahc / kubo_ahc_host with a
+                               k-range of whole k1-planes; bounding box at most 8 N_R vectors;
+                               otherwise KUBO_ERR_UNSUPPORTED).  Same result up to rounding
+                               order.  0 (default): dense contraction. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,

@@ -84,6 +84,7 @@ class Options(ctypes.Structure):
         ("mixed_fixup_rel", ctypes.c_double),
         ("grad_eps", ctypes.c_double),
         ("layout_unpadded", ctypes.c_int),
+        ("fourier_separable", ctypes.c_int),
     ]
 
 
@@ -231,7 +232,7 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
         stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
-        unpadded=False):
+        unpadded=False, separable=False):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
@@ -248,6 +249,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
     o.mixed_fixup_rel = float(fixup_rel)
     o.layout_unpadded = 1 if unpadded else 0
+    o.fourier_separable = 1 if separable else 0
     code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                           W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                           _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),
@@ -388,7 +390,7 @@ AHC = _LazyAHC()
 
 
 def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
-             stream=None, chunk_k=0, workspace=None, profile=None):
+             stream=None, chunk_k=0, workspace=None, profile=None, separable=False):
     """Host-buffer variant: H_R complex128 numpy [N_R, W, W], E_F float64 numpy -> numpy S."""
     H = np.ascontiguousarray(H_R, dtype=np.complex128)
     EF = np.ascontiguousarray(E_F, dtype=np.float64).ravel()
@@ -399,6 +401,7 @@ def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_
     out = np.empty((n_eta, EF.size), dtype=np.float64)
     keep = []
     o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
+    o.fourier_separable = 1 if separable else 0
     code = lib().kubo_ahc_host(H.ctypes.data_as(ctypes.c_void_p), Rh.ctypes.data_as(ctypes.c_void_p),
                                W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                                EF.ctypes.data_as(ctypes.c_void_p), int(EF.size), float(eta),

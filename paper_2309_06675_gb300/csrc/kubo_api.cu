@@ -39,6 +39,7 @@ struct RInfo {
   std::vector<int> Rh;      // [N_h][3]
   int idx0 = -1;
   int N_h = 0;
+  std::vector<int> box;     // separable Fourier sum: bounding-box index table (or empty)
 };
 
 kubo_status analyze_R(const int32_t* R, int N_R, RInfo& info) {
@@ -98,12 +99,16 @@ struct Plan {
   bool grad = false;    // reverse-mode buffers (kubo_ahc_grad)
   bool iit = false;     // inverse-iteration scratch (separate eigenvector kernel)
   int iit_slots = 0;
+  // separable Fourier sum: bounding box, pairs per batch, planes of the range
+  bool sep = false;
+  SepBox sb{0, 0, 0};
+  int sep_np = 0, sep_np1 = 0, sep_j1a = 0;
   Mesh mesh{1, 1, 1, 1};
   size_t o_status = 0, o_neg = 0, o_pairs = 0, o_Rh = 0, o_tab = 0, o_Bp = 0, o_etas = 0,
          o_acc = 0, o_Hp = 0, o_Xp = 0, o_Yp = 0, o_E = 0, o_U = 0, o_Om = 0, o_d = 0, o_e = 0,
          o_ph = 0, o_refl = 0, o_tau = 0, o_lam = 0, o_part = 0,
          o_HR = 0, o_EF = 0, o_out = 0, o_Bt = 0, o_A = 0, o_C64 = 0, o_cexp = 0, o_L = 0,
-         o_iit = 0;
+         o_iit = 0, o_box = 0, o_sepA = 0, o_sepB = 0, o_sepBy = 0;
   // reverse mode: six complex W x W work matrices per k, Ebar, packed [Hbar|dxHbar|dyHbar],
   // the Fourier coefficient rows of the batch and the accumulated G rows
   size_t o_gw = 0, o_Ebar = 0, o_Mbar = 0, o_Coef = 0, o_Gacc = 0;
@@ -151,6 +156,12 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_Rh = b.take(sizeof(int) * 3 * std::max(1, p.N_h));
     p.o_tab = b.take(sizeof(double2) * (p.mesh.N1 + p.mesh.N2 + p.mesh.N3));
     p.o_Bp = b.take(sizeof(double) * (size_t)p.K * WW);
+    if (p.sep) {
+      p.o_box = b.take(sizeof(int) * (size_t)(2 * p.sb.h1 + 1) * (2 * p.sb.h2 + 1) * (2 * p.sb.h3 + 1));
+      p.o_sepA = b.take(sizeof(double2) * sep_a_elems(p.sb, p.W, p.mesh.N3));
+      p.o_sepB = b.take(sizeof(double2) * sep_b_elems_per_pair(p.sb, p.W) * (size_t)std::max(1, p.sep_np));
+      p.o_sepBy = b.take(sizeof(double2) * sep_b_elems_per_pair(p.sb, p.W) * (size_t)std::max(1, p.sep_np));
+    }
     if (tc_fourier(p.precision)) {
       p.Npad = tc_pad_n(p.W);
       p.Kp = tc_pad_k(p.N_R);
@@ -360,6 +371,11 @@ kubo_status prepare_model(Call& c, const double* H_R, const RInfo& ri) {
     KCHECK(launch_twiddles(c.at<double2>(p.o_tab), p.mesh.N1, p.mesh.N2, p.mesh.N3, c.s));
     KCHECK(launch_pack_basis((const double2*)H_R, c.at<int>(p.o_pairs), ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s));
   }
+  if (p.sep) {
+    StageTimer tm(c, KUBO_STAGE_PREP, 1);
+    KCHECK(cudaMemcpyAsync(c.at<int>(p.o_box), ri.box.data(), sizeof(int) * ri.box.size(), cudaMemcpyHostToDevice, c.s));
+    KCHECK(launch_sep_stage_a((const double2*)H_R, c.at<int>(p.o_box), p.sb, p.W, p.mesh, c.at<double2>(p.o_tab), p.mesh.N1 + p.mesh.N2, c.at<double2>(p.o_sepA), c.s));
+  }
   if (tc_fourier(p.precision)) {
     StageTimer tm(c, KUBO_STAGE_PREP, 1);
     KCHECK(launch_basis_split(c.at<double>(p.o_Bp), c.at<int>(p.o_Rh), p.N_h, p.W, p.Npad, p.Kp, c.at<int>(p.o_cexp), c.at<char>(p.o_Bt), c.s));
@@ -477,8 +493,9 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   return KUBO_OK;
 }
 
+// fourier_done: step (1) already wrote Hp / Xp / Yp (separable Fourier sum)
 kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
-                      int64_t om_stride) {
+                      int64_t om_stride, bool fourier_done = false) {
   Plan& p = c.p;
   if (tc_fourier(p.precision)) return run_batch_mixed(c, md, kl, Eout, Om, om_stride);
   double* Hp = c.at<double>(p.o_Hp);
@@ -487,7 +504,7 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
   EighBufs eb = make_eigh_bufs(c);
   DevStatus* st = c.at<DevStatus>(p.o_status);
   double2* U = c.at<double2>(p.o_U);
-  {
+  if (!fourier_done) {
     StageTimer tm(c, KUBO_STAGE_FOURIER, 1);
     KCHECK(launch_fourier_fp64(md, p.mesh, kl, Hp, Xp, Yp, c.s));
   }
@@ -582,9 +599,23 @@ kubo_status ahc_device(Call& c, const kubo_options& o, const double* H_R, const 
   double* Om = c.at<double>(p.o_Om);
   double2* part = c.at<double2>(p.o_part);
   double2* acc = c.at<double2>(p.o_acc);
+  const int64_t plane = (int64_t)p.mesh.N2 * p.mesh.N3;
   for (int64_t base = kb; base < ke; base += p.chunk) {
     KList kl{nullptr, base, (int)std::min<int64_t>(p.chunk, ke - base)};
-    r = run_batch(c, md, kl, E, Om, (int64_t)kl.n * p.W);
+    bool done = false;
+    if (p.sep) {
+      // batch = pairs [p0, p0 + np) x every plane of the range (pair-major); the loop index
+      // base counts k-points of the range, so p0 = (base - kb) / np1
+      const int64_t p0 = (base - kb) / p.sep_np1;
+      const int np = (int)std::min<int64_t>(p.sep_np, plane - p0);
+      kl = KList{nullptr, 0, np * p.sep_np1};
+      StageTimer tm(c, KUBO_STAGE_FOURIER, 2);
+      KCHECK(launch_sep_batch(c.at<double2>(p.o_sepA), p.sb, p.W, p.mesh, md.tab, md.tab_off, p0, np,
+                              p.sep_j1a, p.sep_np1, c.at<double2>(p.o_sepB), c.at<double2>(p.o_sepBy),
+                              c.at<double>(p.o_Hp), c.at<double>(p.o_Xp), c.at<double>(p.o_Yp), c.s));
+      done = true;
+    }
+    r = run_batch(c, md, kl, E, Om, (int64_t)kl.n * p.W, done);
     if (r != KUBO_OK) return r;
     if (p.fixup) {
       r = fixup_batch(c, md, kl, E_F, o.mixed_fixup_rel, kFixupSpikyFraction, E, Om);
@@ -599,6 +630,37 @@ kubo_status ahc_device(Call& c, const kubo_options& o, const double* H_R, const 
     KCHECK(launch_ksum_final(acc, n_out, 1.0 / (double)p.mesh.Nk, c.at<DevStatus>(p.o_status), out, c.s));
   }
   return read_status(c);
+}
+
+// Separable Fourier sum: the bounding box of the R set, its index table, and the batch shape
+// (pairs of (k2, k3) per batch x the k1-planes of the range; the batch k-count becomes the
+// chunk).  Requires whole k1-planes and a box of at most 8 N_R vectors.
+kubo_status setup_separable(Plan& p, const int32_t* R, int N_R, int64_t kb, int64_t ke, RInfo& ri) {
+  if (p.precision != KUBO_FP64 && p.precision != KUBO_MIXED_ROTATION) return KUBO_ERR_UNSUPPORTED;
+  const int64_t plane = (int64_t)p.mesh.N2 * p.mesh.N3;
+  if (kb % plane != 0 || ke % plane != 0 || ke <= kb) return KUBO_ERR_UNSUPPORTED;
+  int h[3] = {0, 0, 0};
+  for (int i = 0; i < N_R; ++i)
+    for (int a = 0; a < 3; ++a) h[a] = std::max(h[a], std::abs(R[3 * i + a]));
+  const int64_t n1 = 2 * h[0] + 1, n2 = 2 * h[1] + 1, n3 = 2 * h[2] + 1;
+  if (n1 * n2 * n3 > 8 * (int64_t)N_R) return KUBO_ERR_UNSUPPORTED;
+  ri.box.assign((size_t)(n1 * n2 * n3), -1);
+  for (int i = 0; i < N_R; ++i)
+    ri.box[((size_t)(R[3 * i] + h[0]) * n2 + (R[3 * i + 1] + h[1])) * n3 + (R[3 * i + 2] + h[2])] = i;
+  p.sep = true;
+  p.sb = SepBox{h[0], h[1], h[2]};
+  const int64_t np1 = (ke - kb) / plane;
+  if (np1 > 65536) return KUBO_ERR_UNSUPPORTED;
+  p.sep_np1 = (int)np1;
+  p.sep_j1a = (int)(kb / plane);
+  // pairs per batch: about the automatic batch size, B and By within 4 GiB
+  const size_t per_pair = 2 * sizeof(double2) * sep_b_elems_per_pair(p.sb, p.W);
+  int64_t np = std::max<int64_t>(1, (int64_t)p.chunk / np1);
+  np = std::min<int64_t>(np, std::max<int64_t>(1, (int64_t)(((size_t)4 << 30) / per_pair)));
+  np = std::min<int64_t>(np, plane);
+  p.sep_np = (int)np;
+  p.chunk = (int)(np * np1);
+  return KUBO_OK;
 }
 
 kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int W, int N_R,
@@ -622,6 +684,11 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   p.pad = o.layout_unpadded ? 0 : 1;
+  if (o.fourier_separable) {
+    if (o.workspace) return KUBO_ERR_UNSUPPORTED;   // its size depends on the R set
+    r = setup_separable(p, R_vecs, N_R, kb, ke, ri);
+    if (r != KUBO_OK) return r;
+  }
   plan_layout(p, host_io, 0);
   c.s = (cudaStream_t)o.stream;
   c.prof = o.profile;
@@ -989,6 +1056,7 @@ int kubo_max_orbitals(int precision) {
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
                            const kubo_options* opt) {
   kubo_options o = opt ? *opt : defaults();
+  if (o.fourier_separable) return 0;   // depends on the R set: library allocation only
   int n_eta = 1;
   if (validate_common(W, N_R, kmesh, o, n_eta) != KUBO_OK || n_EF < 1) return 0;
   Plan p;
@@ -1097,6 +1165,7 @@ kubo_status kubo_ahc_grad(const double* H_R, const int32_t* R_vecs, int W, int N
   try {
     kubo_options o = opt ? *opt : defaults();
     if (!H_R || !E_F || !dL_dout || !grad_H_R) return KUBO_ERR_INVALID_ARG;
+    if (o.fourier_separable) return KUBO_ERR_UNSUPPORTED;
     if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
     if (!std::isfinite(o.grad_eps)) return KUBO_ERR_INVALID_ARG;
     Call c;
@@ -1145,6 +1214,7 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
     kubo_options o = opt ? *opt : defaults();
     if (!probs || n_probs < 1) return KUBO_ERR_INVALID_ARG;
     if (o.k_begin != 0 || o.k_end != 0 || o.workspace) return KUBO_ERR_INVALID_ARG;
+    if (o.fourier_separable) return KUBO_ERR_UNSUPPORTED;
     kubo_batch_schedule sc{};
     if (sched) sc = *sched;
     if (sc.streams < 0 || sc.chunk_k < 0) return KUBO_ERR_INVALID_ARG;
@@ -1349,6 +1419,7 @@ kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
   try {
     kubo_options o = opt ? *opt : defaults();
     if (!H_R || !kidx || !E || !Omega || n_k < 1) return KUBO_ERR_INVALID_ARG;
+    if (o.fourier_separable) return KUBO_ERR_UNSUPPORTED;
     if (o.n_eta == 0 && !finite_nonneg(eta)) return KUBO_ERR_INVALID_ARG;
     o.k_begin = o.k_end = 0;
     Call c;

@@ -57,6 +57,12 @@ struct Model {
   int tab_off[3];
 };
 
+// ---------------------------------------------------------------- separable Fourier sum
+// Bounding box |R_a| <= h_a of the R set (k_fourier_sep.cu).
+struct SepBox {
+  int h1, h2, h3;
+};
+
 // ---------------------------------------------------------------- small helpers
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -202,6 +208,21 @@ cudaError_t launch_berry_large(const double* E, const double2* U, const double* 
                                int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
                                int64_t eta_stride, bool f32, void* Tbuf, void* Vx, void* Vy,
                                cudaStream_t s);
+
+// separable Fourier sum (k_fourier_sep.cu).  box: [2h1+1][2h2+1][2h3+1] index of (R1, R2, R3)
+// in the R list or -1.  Stage A once per call into A (sep_a_elems complex); per batch the
+// pairs p0 .. p0+np-1 (pair = j2 N3 + j3) times the planes j1a .. j1a+np1-1: B and By hold
+// np * sep_b_elems_per_pair complex each, Hp / Xp / Yp receive the packed FP64 matrices of the
+// batch's k-points in pair-major order (local t -> pair p0 + t / np1, plane j1a + t % np1).
+size_t sep_a_elems(const SepBox& sb, int W, int N3);
+size_t sep_b_elems_per_pair(const SepBox& sb, int W);
+cudaError_t launch_sep_stage_a(const double2* H_R, const int* box, const SepBox& sb, int W,
+                               const Mesh& mesh, const double2* tab, int off3, double2* A,
+                               cudaStream_t s);
+cudaError_t launch_sep_batch(const double2* A, const SepBox& sb, int W, const Mesh& mesh,
+                             const double2* tab, const int tab_off[3], int64_t p0, int np,
+                             int j1a, int np1, double2* B, double2* By, double* Hp, double* Xp,
+                             double* Yp, cudaStream_t s);
 
 // T = X U with X packed Hermitian rows (leading dimension ld), FP64
 cudaError_t launch_herm_u(const double* X, int64_t ld, const double2* U, double2* T, int W, int n,
