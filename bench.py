@@ -44,6 +44,10 @@ import tbgen  # noqa: E402
 METRIC = "k-points/sec for σ_xy (W=64, N_R=1331), mixed vs FP64 GPU at rel err ≤1e-5; % roofline"
 WORKLOAD = "w64_r1331_k128"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
+# DRAM bytes (read + write) per k-point of the kernels that can dominate a step, from one ncu
+# capture of the current kernel (profiles/mixed_path_w64_r1331_k128.md, W = 64); a kernel
+# that changes after its capture leaves this table.
+DRAM_BYTES_PER_K = {"tridiag": 98.9e3}
 # algorithmic flops per k-point by stage (W = 64, N_R = 1331), see the design doc
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
@@ -436,8 +440,11 @@ def main():
     launches = st[dom]["launches"]
     k_per_launch = k_total / launches
     achieved = fl[dom] * k_per_launch / (st[dom]["ms"] / launches / 1e3) / 1e12
+    traffic = DRAM_BYTES_PER_K[dom] * k_per_launch if dom in DRAM_BYTES_PER_K and model.W == 64 else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + write.sum, scaled "
+                                "by k-points per launch)",
                 "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk/SM (one DFMA warp instruction per 16 "
                              "cycles, measured) x 2.07 GHz (derived; measured DFMA loop 1.199 TFLOP/s)"}
     line = {
