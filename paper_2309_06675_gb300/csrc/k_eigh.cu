@@ -85,11 +85,18 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
         if (s2 != 0.0) {
           // H = I - tau v v^H with v = x - beta e1, beta = -e^{i arg alpha} |x|:
           // v0 = alpha + e^{i arg alpha} |x|, tau = 2 / v^H v = 1 / (|x| (|x| + |alpha|))
+          // (square roots as x * rsqrt(x): one lane runs this, so every FP64 instruction of it
+          // costs a whole warp slot of the pipe)
           const double aa2 = fma(al.x, al.x, al.y * al.y);
-          const double aa = sqrt(aa2);
-          const double nrm = sqrt(aa2 + s2);
-          double pr = 1.0, pi = 0.0;
-          if (aa > 0.0) { const double ia = 1.0 / aa; pr = al.x * ia; pi = al.y * ia; }
+          const double n2 = aa2 + s2;
+          const double nrm = n2 * rsqrt(n2);
+          double pr = 1.0, pi = 0.0, aa = 0.0;
+          if (aa2 > 0.0) {
+            const double ra = rsqrt(aa2);
+            aa = aa2 * ra;
+            pr = al.x * ra;
+            pi = al.y * ra;
+          }
           beta = make_double2(-pr * nrm, -pi * nrm);
           A[tri(o, i)] = make_double2(fma(pr, nrm, al.x), fma(pi, nrm, al.y));
           tau = 1.0 / (nrm * (nrm + aa));
@@ -184,15 +191,29 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
   double* eout = b.e + k * W;
   double2* phout = b.phase + k * W;
   double* tout = b.tau + k * W;
+  // |beta_j| and the unit phases beta_j / |beta_j| in parallel, then their running product
+  // D_{j+1} = D_j beta_j / |beta_j| by one thread (4 FP64 operations per step)
+  if (t == 0 && W >= 2) be[W - 2] = A[tri(W - 1, W - 2)];
+  __syncthreads();
+  for (int j = t; j + 1 < W; j += NT) {
+    const double2 bj = be[j];
+    const double a2 = fma(bj.x, bj.x, bj.y * bj.y);
+    double a = 0.0;
+    double2 u = make_double2(1.0, 0.0);
+    if (a2 > 0.0) {
+      const double ra = rsqrt(a2);
+      a = a2 * ra;
+      u = make_double2(bj.x * ra, bj.y * ra);
+    }
+    eout[j] = a;
+    vb[j] = u;
+  }
+  __syncthreads();
   if (t == 0) {
-    if (W >= 2) be[W - 2] = A[tri(W - 1, W - 2)];
     double2 D = make_double2(1.0, 0.0);
     phout[0] = D;
     for (int j = 0; j + 1 < W; ++j) {
-      double2 bj = be[j];
-      double a = hypot(bj.x, bj.y);
-      eout[j] = a;
-      if (a > 0.0) D = cmul(D, make_double2(bj.x / a, bj.y / a));
+      D = cmul(D, vb[j]);
       phout[j + 1] = D;
     }
     eout[W - 1] = 0.0;
@@ -212,7 +233,7 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
 // Eigenvalues of the real symmetric tridiagonal T by implicit QL with Wilkinson shifts, one
 // k-point per lane.  Smem per warp: d and e as [W][32] (lane-interleaved: conflict-free for
 // any mix of indices across lanes).  Iterations per eigenvalue are capped (-> ST_NO_CONVERGENCE).
-__global__ void __launch_bounds__(64) ql_kernel(int W, int n, EighBufs b, DevStatus* st) {
+__global__ void __launch_bounds__(32) ql_kernel(int W, int n, EighBufs b, DevStatus* st) {
   extern __shared__ double qsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -518,8 +539,9 @@ size_t backtransform_smem(int W) {
   return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
          (size_t)3 * W * sizeof(double) + (size_t)2 * W * sizeof(int);
 }
-// threads per QL block: two warps, one beyond W = 64 (d and e of a warp take 2 W 32 doubles)
-static int ql_threads(int W) { return W > 64 ? 32 : 64; }
+// threads per QL block: one warp (d and e of a warp take 2 W 32 doubles of shared memory, so
+// single-warp blocks pack the most warps onto an SM: 7 at W = 64)
+static int ql_threads(int W) { (void)W; return 32; }
 size_t ql_smem(int W) { return (size_t)(ql_threads(W) / 32) * 2 * W * 32 * sizeof(double); }
 
 cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s) {
