@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.
 # DRAM bytes (read + write) per k-point of the kernels that can dominate a step, from one ncu
 # capture of the current kernel (profiles/mixed_path_w64_r1331_k128.md, W = 64); a kernel
 # that changes after its capture leaves this table.
-DRAM_BYTES_PER_K = {}
+DRAM_BYTES_PER_K = {"tridiag": 97.3e3}
 # algorithmic flops per k-point by stage (W = 64, N_R = 1331), see the design doc
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).

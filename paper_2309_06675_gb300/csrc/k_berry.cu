@@ -12,10 +12,11 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int MAXE = 8;
-constexpr int TM = 4;   // 16 x 16 threads, 4 x 4 tile each: W <= 64
+// 16 x 16 threads, each a TM x TM tile of the W x W products: TM = 1, 2, 4 for W up to 16,
+// 32, 64 (the smallest tile that covers W, so no thread multiplies padding)
 
 // acc[i][j] = sum_q op(A)[r_i][q] * B[q][c_j],  r_i = ty + 16 i, c_j = tx + 16 j
-template <bool ADJ>
+template <int TM, bool ADJ>
 __device__ __forceinline__ void cgemm_tile(const double2* __restrict__ A,
                                            const double2* __restrict__ B, int W, int LD,
                                            int ty, int tx, double2 (&acc)[TM][TM]) {
@@ -52,6 +53,7 @@ __device__ __forceinline__ void cgemm_tile(const double2* __restrict__ A,
   }
 }
 
+template <int TM>
 __device__ __forceinline__ void store_tile(double2* C, int W, int LD, int ty, int tx,
                                            const double2 (&acc)[TM][TM]) {
 #pragma unroll
@@ -82,7 +84,7 @@ __device__ __forceinline__ void unpack_hermitian(const TIn* __restrict__ P, doub
 // rounding.  Per-thread row / column partials go to `red` (2 * n_eta * W * 16 doubles, may
 // alias sVx: a barrier separates the last read of sVx from the first write of red) and are
 // summed in a fixed order (deterministic).
-template <typename V>
+template <int TM, typename V>
 __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[TM][TM],
                                                    const double* sE, const double* sEta,
                                                    int n_eta, double emax, int W, int LD, int ty,
@@ -144,7 +146,7 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
 
 // X and Y: packed Hermitian rows of leading dimension ld (FP64 rows of the FP64 Fourier
 // kernel, or FP32 rows of the tensor-core one).
-template <typename TIn>
+template <typename TIn, int TM>
 __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict__ E,
                                                         const double2* __restrict__ U,
                                                         const TIn* __restrict__ Xp,
@@ -179,21 +181,21 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
   }
 
   double2 acc[TM][TM];
-  cgemm_tile<false>(sA, sU, W, LD, ty, tx, acc);        // T = X U
+  cgemm_tile<TM, false>(sA, sU, W, LD, ty, tx, acc);        // T = X U
   __syncthreads();
-  store_tile(sA, W, LD, ty, tx, acc);
+  store_tile<TM>(sA, W, LD, ty, tx, acc);
   __syncthreads();
-  cgemm_tile<true>(sU, sA, W, LD, ty, tx, acc);         // v^x = U^H T
+  cgemm_tile<TM, true>(sU, sA, W, LD, ty, tx, acc);         // v^x = U^H T
   __syncthreads();
-  store_tile(sA, W, LD, ty, tx, acc);
+  store_tile<TM>(sA, W, LD, ty, tx, acc);
   unpack_hermitian(Yp + k * ld, sB, W, LD, t);
   __syncthreads();
-  cgemm_tile<false>(sB, sU, W, LD, ty, tx, acc);        // T = Y U
+  cgemm_tile<TM, false>(sB, sU, W, LD, ty, tx, acc);        // T = Y U
   __syncthreads();
-  store_tile(sB, W, LD, ty, tx, acc);
+  store_tile<TM>(sB, W, LD, ty, tx, acc);
   __syncthreads();
-  cgemm_tile<true>(sU, sB, W, LD, ty, tx, acc);         // v^y = U^H T
-  curvature_epilogue<double2>(sA, acc, sE, sEta, n_eta, s_emax, W, LD, ty, tx, t, red, Om,
+  cgemm_tile<TM, true>(sU, sB, W, LD, ty, tx, acc);         // v^y = U^H T
+  curvature_epilogue<TM, double2>(sA, acc, sE, sEta, n_eta, s_emax, W, LD, ty, tx, t, red, Om,
                               eta_stride, k);
 }
 
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
 // The two rotations in FP32 on the FP32 pipe (64x the FP64 rate on GB300): operands U
 // (rounded from FP64) and the FP32 tensor-core Fourier output; the energy denominators,
 // the pair terms and the band sums stay FP64.
-template <bool ADJ>
+template <int TM, bool ADJ>
 __device__ __forceinline__ void cgemm_tile_f32(const float2* __restrict__ A,
                                                const float2* __restrict__ B, int W, int LD,
                                                int ty, int tx, float2 (&acc)[TM][TM]) {
@@ -238,6 +240,7 @@ __device__ __forceinline__ void cgemm_tile_f32(const float2* __restrict__ A,
   }
 }
 
+template <int TM>
 __device__ __forceinline__ void store_tile_f32(float2* C, int W, int LD, int ty, int tx,
                                                const float2 (&acc)[TM][TM]) {
 #pragma unroll
@@ -332,7 +335,7 @@ __host__ __device__ __forceinline__ int mixed_ld(int W, int pad) {
 
 // X and Y: packed Hermitian rows of leading dimension ld.  FROMZ: U is assembled in FP32 from
 // the eigensolver's factors (Z, eb.phase, eb.refl, eb.tau) instead of being read.
-template <typename TIn, bool FROMZ>
+template <typename TIn, bool FROMZ, int TM>
 __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restrict__ E,
                                                          const double2* __restrict__ U,
                                                          const double* __restrict__ Z,
@@ -375,21 +378,21 @@ __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restric
   }
 
   float2 acc[TM][TM];
-  cgemm_tile_f32<false>(sA, sU, W, LD, ty, tx, acc);   // T = X U
+  cgemm_tile_f32<TM, false>(sA, sU, W, LD, ty, tx, acc);   // T = X U
   __syncthreads();
-  store_tile_f32(sA, W, LD, ty, tx, acc);
+  store_tile_f32<TM>(sA, W, LD, ty, tx, acc);
   __syncthreads();
-  cgemm_tile_f32<true>(sU, sA, W, LD, ty, tx, acc);    // v^x = U^H T
+  cgemm_tile_f32<TM, true>(sU, sA, W, LD, ty, tx, acc);    // v^x = U^H T
   __syncthreads();
-  store_tile_f32(sA, W, LD, ty, tx, acc);
+  store_tile_f32<TM>(sA, W, LD, ty, tx, acc);
   unpack_hermitian_f32(Yp + k * ld, sB, W, LD, t);
   __syncthreads();
-  cgemm_tile_f32<false>(sB, sU, W, LD, ty, tx, acc);   // T = Y U
+  cgemm_tile_f32<TM, false>(sB, sU, W, LD, ty, tx, acc);   // T = Y U
   __syncthreads();
-  store_tile_f32(sB, W, LD, ty, tx, acc);
+  store_tile_f32<TM>(sB, W, LD, ty, tx, acc);
   __syncthreads();
-  cgemm_tile_f32<true>(sU, sB, W, LD, ty, tx, acc);    // v^y = U^H T
-  curvature_epilogue<float2>(sA, acc, sE, sEta, n_eta, s_emax, W, LD, ty, tx, t, red, Om,
+  cgemm_tile_f32<TM, true>(sU, sB, W, LD, ty, tx, acc);    // v^y = U^H T
+  curvature_epilogue<TM, float2>(sA, acc, sE, sEta, n_eta, s_emax, W, LD, ty, tx, t, red, Om,
                              eta_stride, k);
 }
 
@@ -422,11 +425,15 @@ cudaError_t launch_berry_fp64_t(const double* E, const double2* U, const TIn* Xp
                                 int64_t eta_stride, cudaStream_t s, int pad) {
   if (n <= 0) return cudaSuccess;
   size_t sm = berry_fp64_smem(W, n_eta);
-  cudaError_t e = cudaFuncSetAttribute(berry_fp64_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  berry_fp64_kernel<TIn><<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride,
-                                           pad ? 1 : 0);
-  return cudaGetLastError();
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<n, NT, sm, s>>>(E, U, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride, pad ? 1 : 0);
+    return cudaGetLastError();
+  };
+  if (W <= 16) return go(berry_fp64_kernel<TIn, 1>);
+  if (W <= 32) return go(berry_fp64_kernel<TIn, 2>);
+  return go(berry_fp64_kernel<TIn, 4>);
 }
 
 cudaError_t launch_berry_fp64(const double* E, const double2* U, const double* Xp,
@@ -457,11 +464,15 @@ cudaError_t launch_berry_mixed_t(const double* E, const double2* U, const double
                                  double* Om, int64_t eta_stride, cudaStream_t s, int pad) {
   if (n <= 0) return cudaSuccess;
   size_t sm = berry_mixed_smem(W, n_eta);
-  cudaError_t e = cudaFuncSetAttribute(berry_mixed_kernel<TIn, FROMZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  berry_mixed_kernel<TIn, FROMZ><<<n, NT, sm, s>>>(E, U, Z, eb, Xp, Yp, ld, W, etas, n_eta, Om,
-                                                   eta_stride, pad ? 1 : 0);
-  return cudaGetLastError();
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<n, NT, sm, s>>>(E, U, Z, eb, Xp, Yp, ld, W, etas, n_eta, Om, eta_stride, pad ? 1 : 0);
+    return cudaGetLastError();
+  };
+  if (W <= 16) return go(berry_mixed_kernel<TIn, FROMZ, 1>);
+  if (W <= 32) return go(berry_mixed_kernel<TIn, FROMZ, 2>);
+  return go(berry_mixed_kernel<TIn, FROMZ, 4>);
 }
 
 cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const double* C,

@@ -24,33 +24,35 @@ namespace kubo {
 
 namespace {
 
-constexpr int GT = 64, GK = 16;   // GEMM tiles: 64 x 64 outputs, K steps of 16
+constexpr int GT = 64, GK = 16;   // GEMM tiles: up to 64 x 64 outputs, K steps of 16
 constexpr int MAXE = 8;
 constexpr int PW = 128;            // threads of the per-k kernels (W <= 128)
 
 // ------------------------------------------------------------------ batched complex GEMM
 // C[k] = op(A[k]) op(B[k]) (+ C[k]), W x W complex FP64, op = identity or conjugate transpose.
-template <bool HA, bool HB, bool ACC>
+// Output tile T = 16 TM (TM x TM per thread); TM = 2 for W <= 32 so no thread multiplies padding.
+template <bool HA, bool HB, bool ACC, int TM>
 __global__ void __launch_bounds__(256) zgemm_kernel(const double2* __restrict__ A,
                                                     const double2* __restrict__ B,
                                                     double2* __restrict__ C, int W) {
-  __shared__ double2 As[GT][GK + 1];
-  __shared__ double2 Bs[GK][GT + 1];
+  constexpr int T = 16 * TM;
+  __shared__ double2 As[T][GK + 1];
+  __shared__ double2 Bs[GK][T + 1];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int nt = (W + GT - 1) / GT;
-  const int r0 = (blockIdx.y / nt) * GT, c0 = (blockIdx.y % nt) * GT;
+  const int nt = (W + T - 1) / T;
+  const int r0 = (blockIdx.y / nt) * T, c0 = (blockIdx.y % nt) * T;
   const size_t base = (size_t)blockIdx.x * W * W;
   const double2* Ak = A + base;
   const double2* Bk = B + base;
-  double ax[4][4], ay[4][4];
+  double ax[TM][TM], ay[TM][TM];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { ax[i][j] = 0.0; ay[i][j] = 0.0; }
+    for (int j = 0; j < TM; ++j) { ax[i][j] = 0.0; ay[i][j] = 0.0; }
   for (int q0 = 0; q0 < W; q0 += GK) {
-    for (int idx = t; idx < GT * GK; idx += 256) {
+    for (int idx = t; idx < T * GK; idx += 256) {
       int r, q;
-      if (HA) { q = idx / GT; r = idx % GT; } else { r = idx / GK; q = idx % GK; }
+      if (HA) { q = idx / T; r = idx % T; } else { r = idx / GK; q = idx % GK; }
       const int gr = r0 + r, gq = q0 + q;
       double2 a = make_double2(0.0, 0.0);
       if (gr < W && gq < W) {
@@ -59,9 +61,9 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const double2* __restrict__ 
       }
       As[r][q] = a;
     }
-    for (int idx = t; idx < GK * GT; idx += 256) {
+    for (int idx = t; idx < GK * T; idx += 256) {
       int q, c;
-      if (HB) { c = idx / GK; q = idx % GK; } else { q = idx / GT; c = idx % GT; }
+      if (HB) { c = idx / GK; q = idx % GK; } else { q = idx / T; c = idx % T; }
       const int gq = q0 + q, gc = c0 + c;
       double2 b = make_double2(0.0, 0.0);
       if (gq < W && gc < W) {
@@ -73,15 +75,15 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const double2* __restrict__ 
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < GK; ++q) {
-      double2 a[4], b[4];
+      double2 a[TM], b[TM];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[ty + 16 * i][q];
+      for (int i = 0; i < TM; ++i) a[i] = As[ty + 16 * i][q];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[q][tx + 16 * j];
+      for (int j = 0; j < TM; ++j) b[j] = Bs[q][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TM; ++j) {
           ax[i][j] = fma(a[i].x, b[j].x, ax[i][j]);
           ax[i][j] = fma(-a[i].y, b[j].y, ax[i][j]);
           ay[i][j] = fma(a[i].x, b[j].y, ay[i][j]);
@@ -92,9 +94,9 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const double2* __restrict__ 
   }
   double2* Ck = C + base;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TM; ++j) {
       const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
       if (r < W && c < W) {
         double2 v = make_double2(ax[i][j], ay[i][j]);
@@ -369,9 +371,14 @@ __global__ void grad_finalize_kernel(const double* __restrict__ Gacc, const int*
 cudaError_t launch_zgemm_batched(bool hA, bool hB, bool acc, const double2* A, const double2* B,
                                  double2* C, int W, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int tiles = (W + GT - 1) / GT;
+  const int T = W <= 32 ? 32 : GT;
+  const int tiles = (W + T - 1) / T;
   dim3 grid(n, tiles * tiles);
-#define ZG(a, b, c) zgemm_kernel<a, b, c><<<grid, 256, 0, s>>>(A, B, C, W)
+#define ZG(a, b, c)                                                          \
+  do {                                                                       \
+    if (T == 32) zgemm_kernel<a, b, c, 2><<<grid, 256, 0, s>>>(A, B, C, W);  \
+    else zgemm_kernel<a, b, c, 4><<<grid, 256, 0, s>>>(A, B, C, W);          \
+  } while (0)
   if (!hA && !hB && !acc) ZG(false, false, false);
   else if (!hA && !hB && acc) ZG(false, false, true);
   else if (hA && !hB && !acc) ZG(true, false, false);
