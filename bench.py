@@ -87,6 +87,24 @@ def parse():
     return ap.parse_args()
 
 
+# ------------------------------------------------------------------ sharding (N > 1 ranks)
+def slab_of(rank, world, step, n_slabs):
+    """k1-slab a rank evaluates at a step: within a step the ranks take consecutive slabs, so
+    ranks never share work while world <= n_slabs (the k-points are independent: weak scaling,
+    no data-path collective)."""
+    return (step * world + rank) % n_slabs
+
+
+def max_over_ranks(x, dist, device):
+    """The step time of the slowest rank (every rank gets it)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload():
     model, kmesh, E_F, etas, kT = tbgen.config(WORKLOAD)
     return model, kmesh, E_F, float(etas[0]), kT
@@ -356,7 +374,7 @@ def main():
     precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
 
     def slab(step):
-        s = (rank * (args.warmup + args.steps) + step) % n_slabs
+        s = slab_of(rank, world, step, n_slabs)
         return (s * k_per_step, (s + 1) * k_per_step)
 
     def timed(prec):
@@ -383,11 +401,8 @@ def main():
         ev1.record()
         torch.cuda.synchronize()
         clk = clocks.stop()
-        ms = ev0.elapsed_time(ev1)
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
         if dist:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         d = prof.as_dict()
         d["_fixup_k"] = int(prof.fixup_k)
@@ -414,11 +429,7 @@ def main():
             kubo.ahc_host(H_pin.numpy(), model.R, kmesh, EF_pin.numpy(), eta=eta, kT=kT,
                           precision=head, k_range=slab(args.warmup + s))
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": world * args.steps * k_per_step / dt, "unit": "k-points/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "precision": head}
 
