@@ -170,15 +170,24 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
 // One CTA per (32-column block, k-point): the block of D Z in shared memory, the reflectors
 // applied from the last to the first (U <- H_j U), eight reflectors at a time staged in shared
 // memory from coalesced row segments of the reflector matrix.
+template <typename T> struct cx;
+template <> struct cx<double> { typedef double2 type; __device__ static double2 make(double a, double b) { return make_double2(a, b); } };
+template <> struct cx<float> { typedef float2 type; __device__ static float2 make(double a, double b) { return make_float2((float)a, (float)b); } };
+
 constexpr int RB_COLS = 32;
 constexpr int RB_NT = 256;   // 8 threads per column
 constexpr int RB_J = 8;      // reflectors per staged block
 
+// T = float: U is formed in FP32 from the FP64 factors, for the FP32 rotations (its only
+// consumer in that mode); T = double: the FP64 eigenvectors.
+template <typename T>
 __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
                                                               const double* __restrict__ Z,
-                                                              double2* __restrict__ Uout) {
-  extern __shared__ double2 ub[];   // [W][RB_COLS + 1]
-  __shared__ double2 vs[RB_J][LW_MAX + 1];
+                                                              typename cx<T>::type* __restrict__ Uout) {
+  typedef typename cx<T>::type C2;
+  extern __shared__ __align__(16) unsigned char rb_smem[];
+  C2* ub = reinterpret_cast<C2*>(rb_smem);   // [W][RB_COLS + 1]
+  __shared__ C2 vs[RB_J][LW_MAX + 1];
   const int LDB = RB_COLS + 1;
   const int t = threadIdx.x;
   const int c0 = blockIdx.y * RB_COLS;
@@ -188,11 +197,11 @@ __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
   const double2* ph = b.phase + k * W;
   for (int idx = t; idx < W * RB_COLS; idx += RB_NT) {
     const int r = idx / RB_COLS, c = idx % RB_COLS;
-    double2 u = make_double2(0.0, 0.0);
+    C2 u = cx<T>::make(0.0, 0.0);
     if (c < ncol) {
       const double z = Zk[(size_t)r * W + c0 + c];
       const double2 p = ph[r];
-      u = make_double2(p.x * z, p.y * z);
+      u = cx<T>::make(p.x * z, p.y * z);
     }
     ub[r * LDB + c] = u;
   }
@@ -205,19 +214,22 @@ __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
     __syncthreads();   // the previous block of reflectors is no longer read
     for (int idx = t; idx < W * RB_J; idx += RB_NT) {
       const int r = idx / RB_J, jj = idx % RB_J, j = jlo + jj;
-      if (j <= jhi) vs[jj][r] = r > j ? R[(size_t)r * W + j] : make_double2(0.0, 0.0);
+      if (j <= jhi) {
+        const double2 v = r > j ? R[(size_t)r * W + j] : make_double2(0.0, 0.0);
+        vs[jj][r] = cx<T>::make(v.x, v.y);
+      }
     }
     __syncthreads();
     for (int j = jhi; j >= jlo; --j) {
-      const double tj = tau[j];
-      if (tj == 0.0) continue;
+      const T tj = (T)tau[j];
+      if (tj == (T)0) continue;
       const int o = j + 1, m = W - 1 - j;
-      const double2* v = vs[j - jlo] + o;
-      double sx = 0.0, sy = 0.0;
+      const C2* v = vs[j - jlo] + o;
+      T sx = 0, sy = 0;
       if (act) {
         for (int r = q; r < m; r += 8) {
-          const double2 vv = v[r];
-          const double2 u = ub[(o + r) * LDB + c];
+          const C2 vv = v[r];
+          const C2 u = ub[(o + r) * LDB + c];
           sx = fma(vv.x, u.x, fma(vv.y, u.y, sx));   // conj(v) u
           sy = fma(vv.x, u.y, fma(-vv.y, u.x, sy));
         }
@@ -230,8 +242,8 @@ __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
       sx *= tj; sy *= tj;
       if (act) {
         for (int r = q; r < m; r += 8) {
-          const double2 vv = v[r];
-          double2 u = ub[(o + r) * LDB + c];
+          const C2 vv = v[r];
+          C2 u = ub[(o + r) * LDB + c];
           u.x = fma(-sx, vv.x, fma(sy, vv.y, u.x));   // u -= s v
           u.y = fma(-sx, vv.y, fma(-sy, vv.x, u.y));
           ub[(o + r) * LDB + c] = u;
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
     }
   }
   __syncthreads();
-  double2* Uk = Uout + (size_t)k * W * W;
+  C2* Uk = Uout + (size_t)k * W * W;
   for (int idx = t; idx < W * RB_COLS; idx += RB_NT) {
     const int r = idx / RB_COLS, cc = idx % RB_COLS;
     if (cc < ncol) Uk[(size_t)r * W + c0 + cc] = ub[r * LDB + cc];
@@ -250,16 +262,15 @@ __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
 
 // ------------------------------------------------------------------ batched complex GEMMs
 // 64 x 64 output tile per CTA, 16 x 16 threads with 4 x 4 strided micro-tiles, K tiles of 16.
-template <typename T> struct cx;
-template <> struct cx<double> { typedef double2 type; __device__ static double2 make(double a, double b) { return make_double2(a, b); } };
-template <> struct cx<float> { typedef float2 type; __device__ static float2 make(double a, double b) { return make_float2((float)a, (float)b); } };
 
 constexpr int GT = 64, GK = 16;
 
-// C[k] = H[k] U[k]; H from packed Hermitian rows P (leading dimension ldp), U complex FP64.
+// C[k] = H[k] U[k]; H from packed Hermitian rows P (leading dimension ldp), U complex in the
+// compute type.
 template <typename T>
 __global__ void __launch_bounds__(256) cgemm_herm_u_kernel(const double* __restrict__ P, int64_t ldp,
-                                                           const double2* __restrict__ U, int W,
+                                                           const typename cx<T>::type* __restrict__ U,
+                                                           int W,
                                                            typename cx<T>::type* __restrict__ C) {
   typedef typename cx<T>::type C2;
   __shared__ C2 As[GT][GK + 1];
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(256) cgemm_herm_u_kernel(const double* __restr
   const int r0 = (blockIdx.y / nt) * GT, c0 = (blockIdx.y % nt) * GT;
   const int64_t k = blockIdx.x;
   const double* Pk = P + k * ldp;
-  const double2* Uk = U + (size_t)k * W * W;
+  const C2* Uk = U + (size_t)k * W * W;
   T ax[4][4], ay[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(256) cgemm_herm_u_kernel(const double* __restr
       const int q = idx / GT, c = idx % GT;
       const int gq = q0 + q, gc = c0 + c;
       C2 v = cx<T>::make(0.0, 0.0);
-      if (gq < W && gc < W) { const double2 u = Uk[(size_t)gq * W + gc]; v = cx<T>::make(u.x, u.y); }
+      if (gq < W && gc < W) v = Uk[(size_t)gq * W + gc];
       Bs[q][c] = v;
     }
     __syncthreads();
@@ -326,7 +337,7 @@ __global__ void __launch_bounds__(256) cgemm_herm_u_kernel(const double* __restr
 
 // V[k] = U[k]^H Tm[k]
 template <typename T>
-__global__ void __launch_bounds__(256) cgemm_uh_t_kernel(const double2* __restrict__ U,
+__global__ void __launch_bounds__(256) cgemm_uh_t_kernel(const typename cx<T>::type* __restrict__ U,
                                                          const typename cx<T>::type* __restrict__ Tm,
                                                          int W, typename cx<T>::type* __restrict__ V) {
   typedef typename cx<T>::type C2;
@@ -336,7 +347,7 @@ __global__ void __launch_bounds__(256) cgemm_uh_t_kernel(const double2* __restri
   const int nt = (W + GT - 1) / GT;
   const int r0 = (blockIdx.y / nt) * GT, c0 = (blockIdx.y % nt) * GT;
   const int64_t k = blockIdx.x;
-  const double2* Uk = U + (size_t)k * W * W;
+  const C2* Uk = U + (size_t)k * W * W;
   const C2* Tk = Tm + (size_t)k * W * W;
   if (r0 >= c0 + GT) return;   // strictly below the diagonal: V is Hermitian, never read
   T ax[4][4], ay[4][4];
@@ -349,7 +360,7 @@ __global__ void __launch_bounds__(256) cgemm_uh_t_kernel(const double2* __restri
       const int q = idx / GT, r = idx % GT;   // coalesced along r (a row of U)
       const int gr = r0 + r, gq = q0 + q;
       C2 a = cx<T>::make(0.0, 0.0);
-      if (gr < W && gq < W) { const double2 u = Uk[(size_t)gq * W + gr]; a = cx<T>::make(u.x, -u.y); }
+      if (gr < W && gq < W) { a = Uk[(size_t)gq * W + gr]; a.y = -a.y; }
       As[r][q] = a;
     }
     for (int idx = t; idx < GK * GT; idx += 256) {
@@ -458,14 +469,21 @@ cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* s
   return cudaGetLastError();
 }
 
-cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, double2* U,
+cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, void* U, bool f32,
                                  cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const size_t sm = (size_t)W * (RB_COLS + 1) * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(reflect_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   dim3 grid(n, (W + RB_COLS - 1) / RB_COLS);
-  reflect_large_kernel<<<grid, RB_NT, sm, s>>>(W, b, Z, U);
+  if (f32) {
+    const size_t sm = (size_t)W * (RB_COLS + 1) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(reflect_large_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    reflect_large_kernel<float><<<grid, RB_NT, sm, s>>>(W, b, Z, (float2*)U);
+  } else {
+    const size_t sm = (size_t)W * (RB_COLS + 1) * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(reflect_large_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    reflect_large_kernel<double><<<grid, RB_NT, sm, s>>>(W, b, Z, (double2*)U);
+  }
   return cudaGetLastError();
 }
 
@@ -480,10 +498,11 @@ cudaError_t launch_herm_u(const double* X, int64_t ld, const double2* U, double2
   return cudaGetLastError();
 }
 
-// steps (3)-(4) for large W: X, Y packed Hermitian rows (leading dimension ld), FP64 U.
+// steps (3)-(4) for large W: X, Y packed Hermitian rows (leading dimension ld); U is float2
+// when f32 (formed in FP32 by launch_reflect_large), double2 otherwise.
 // f32 selects FP32 arithmetic for the products (mixed precision).  Tbuf, Vx, Vy: scratch of
 // n * W * W complex elements of the arithmetic type each.
-cudaError_t launch_berry_large(const double* E, const double2* U, const double* X, const double* Y,
+cudaError_t launch_berry_large(const double* E, const void* Uv, const double* X, const double* Y,
                                int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
                                int64_t eta_stride, bool f32, void* Tbuf, void* Vx, void* Vy,
                                cudaStream_t s) {
@@ -492,6 +511,7 @@ cudaError_t launch_berry_large(const double* E, const double2* U, const double* 
   const int tiles = (W + GT - 1) / GT;
   dim3 grid(n, tiles * tiles);
   if (f32) {
+    const float2* U = (const float2*)Uv;
     cgemm_herm_u_kernel<float><<<grid, 256, 0, s>>>(X, ld, U, W, (float2*)Tbuf);
     cgemm_uh_t_kernel<float><<<grid, 256, 0, s>>>(U, (const float2*)Tbuf, W, (float2*)Vx);
     cgemm_herm_u_kernel<float><<<grid, 256, 0, s>>>(Y, ld, U, W, (float2*)Tbuf);
@@ -499,6 +519,7 @@ cudaError_t launch_berry_large(const double* E, const double2* U, const double* 
     curvature_large_kernel<float><<<n, LW_MAX, 0, s>>>(E, (const float2*)Vx, (const float2*)Vy, W,
                                                         etas, n_eta, Om, eta_stride);
   } else {
+    const double2* U = (const double2*)Uv;
     cgemm_herm_u_kernel<double><<<grid, 256, 0, s>>>(X, ld, U, W, (double2*)Tbuf);
     cgemm_uh_t_kernel<double><<<grid, 256, 0, s>>>(U, (const double2*)Tbuf, W, (double2*)Vx);
     cgemm_herm_u_kernel<double><<<grid, 256, 0, s>>>(Y, ld, U, W, (double2*)Tbuf);

@@ -410,14 +410,16 @@ EighBufs make_eigh_bufs(const Call& c) {
 }
 
 // Eigenvalues (sorted) and eigenvectors U = Q D Z of n tridiagonalised matrices whose
-// eigenvalues QL left in eb.lam (U may be null: eigenvalues only).
-cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, double2* U) {
+// eigenvalues QL left in eb.lam (U may be null: eigenvalues only).  f32u (W > 64 only): U is
+// formed in FP32 (float2) for the FP32 rotations, its only consumer in that mode.
+cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, double2* U,
+                         bool f32u = false) {
   const Plan& p = c.p;
   if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s, p.pad);
   double* Z = U ? c.at<double>(p.o_L) : nullptr;
   cudaError_t e = launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
   if (e != cudaSuccess || !U) return e;
-  return launch_reflect_large(p.W, n, eb, Z, U, c.s);
+  return launch_reflect_large(p.W, n, eb, Z, U, f32u, c.s);
 }
 
 // Steps (3)-(4) from packed Hermitian dH rows X, Y of leading dimension ld; f32 = FP32
@@ -484,7 +486,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   }
   {
     StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
-    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U));
+    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U, f32_rotation(p.precision)));
   }
   {
     StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);
@@ -528,7 +530,7 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
   }
   {
     StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
-    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U));
+    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U, f32_rotation(p.precision)));
   }
   {
     StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);

@@ -200,11 +200,12 @@ int iit_max_slots(int W);
 size_t iit_scratch_doubles(int W, int slots);
 cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* scratch, int slots,
                        cudaStream_t s);
-cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, double2* U,
+// U: float2 [n][W][W] when f32 (formed in FP32 for the FP32 rotations), else double2
+cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, void* U, bool f32,
                                  cudaStream_t s);
 // steps (3)-(4) as batched complex GEMMs: X, Y packed Hermitian rows of leading dimension ld;
 // f32 = FP32 products.  Tbuf, Vx, Vy: n * W * W complex elements (of the product type) each.
-cudaError_t launch_berry_large(const double* E, const double2* U, const double* X, const double* Y,
+cudaError_t launch_berry_large(const double* E, const void* U, const double* X, const double* Y,
                                int64_t ld, int W, int n, const double* etas, int n_eta, double* Om,
                                int64_t eta_stride, bool f32, void* Tbuf, void* Vx, void* Vy,
                                cudaStream_t s);
