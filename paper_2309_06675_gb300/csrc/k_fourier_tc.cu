@@ -31,6 +31,8 @@
 //
 // Every mbarrier wait is bounded; on timeout the CTA records ST_TIMEOUT, drains its own
 // copies (bounded), frees its TMEM and returns.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -272,11 +274,18 @@ __constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 
 // ------------------------------------------------------------------ the tcgen05 GEMM
 // grid: (Npad / BN) * (Mpad / BM) CTAs; out: FP64 [n rows][ldc], rows >= n_rows not written.
+// NS = slices per operand kept: 4 (levels i + j <= 3, 10 slice pairs, ~31 fractional bits) or
+// 3 (levels <= 2, 6 pairs, ~23 bits: for the velocity columns when their only consumer is the
+// FP32 rotation, whose own input rounding is 2^-24).  The grid covers the column tiles
+// nt0 .. nt0 + ntc - 1.
+template <int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, const int* __restrict__ col_exp,
                       int Mpad, int Npad, int nkb, int n_rows, double* __restrict__ out, int ldc,
-                      DevStatus* st) {
+                      DevStatus* st, int nt0, int ntc) {
+  constexpr int NLEV = NS;
+  constexpr int NPR = NS * (NS + 1) / 2;   // pairs with i + j < NS (listed first in c_p*)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
@@ -287,14 +296,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // grouped rasterisation: GROUP_M consecutive M tiles per column tile, so one B tile serves
   // several CTAs in a row and the group's A tiles stay resident in L2 across column tiles
-  const int n_mt = Mpad / BM, n_nt = Npad / BN;
+  const int n_mt = Mpad / BM, n_nt = ntc;
   const int id = blockIdx.x;
   const int per_group = GROUP_M * n_nt;
   const int grp = id / per_group;
   const int gm0 = grp * GROUP_M;
   const int gsz = min(GROUP_M, n_mt - gm0);
   const int in = id - grp * per_group;
-  const int n0 = (in / gsz) * BN, m0 = (gm0 + in % gsz) * BM;
+  const int n0 = (nt0 + in / gsz) * BN, m0 = (gm0 + in % gsz) * BM;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -339,10 +348,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           abort_sh = 1;
           break;
         }
-        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-        for (int sl = 0; sl < NSLICE; ++sl)
+        mbar_expect_tx(&full_bar[s], (uint32_t)NS * (TILE_A_BYTES + TILE_B_BYTES));
+        for (int sl = 0; sl < NS; ++sl)
           tma_load_2d(stageA(s, sl), &mapA, &full_bar[s], kb * BK, sl * Mpad + m0);
-        for (int sl = 0; sl < NSLICE; ++sl)
+        for (int sl = 0; sl < NS; ++sl)
           tma_load_2d(stageB(s, sl), &mapB, &full_bar[s], kb * BK, sl * Npad + n0);
         ++issued;
       }
@@ -372,7 +381,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         for (int kk = 0; kk < BK / 16; ++kk) {
           int seen = 0;   // bit l set once level l has been written in this drain group
-          for (int p = 0; p < NPAIR; ++p) {
+          for (int p = 0; p < NPR; ++p) {
             const int l = c_pl[p];
             const uint32_t acc = (!first || kk > 0 || (seen >> l) & 1) ? 1u : 0u;
             seen |= 1 << l;
@@ -406,7 +415,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       tc_fence_after();
 #pragma unroll
-      for (int l = 0; l < NLEVEL; ++l) {
+      for (int l = 0; l < NLEV; ++l) {
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 16) {
           uint32_t r[16];
@@ -511,19 +520,27 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s) {
+                              cudaStream_t s, int red_n0) {
   if (n_rows <= 0) return cudaSuccess;
   if (Mpad % BM || Npad % BN || Kp % BK || ldc % 2) return cudaErrorInvalidValue;
   CUtensorMap mA, mB;
   if (!encode_2d(&mA, A, (uint64_t)Kp, (uint64_t)NSLICE * Mpad, BK, BM)) return cudaErrorInvalidValue;
   if (!encode_2d(&mB, Bt, (uint64_t)Kp, (uint64_t)NSLICE * Npad, BK, BN)) return cudaErrorInvalidValue;
   const size_t sm = fourier_tc_smem();
-  cudaError_t e = cudaFuncSetAttribute(fourier_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int nt = Npad / BN;
+  // first column tile that lies entirely at or after red_n0
+  const int rt = std::min(nt, (std::max(red_n0, 0) + BN - 1) / BN);
+  auto go = [&](auto kern, int t0, int tc) -> cudaError_t {
+    if (tc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<tc * (Mpad / BM), TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out,
+                                                 ldc, st, t0, tc);
+    return cudaGetLastError();
+  };
+  cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt);
   if (e != cudaSuccess) return e;
-  dim3 grid((Npad / BN) * (Mpad / BM));
-  fourier_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out,
-                                                 ldc, st);
-  return cudaGetLastError();
+  return go(fourier_tc_kernel<NSLICE - 1>, rt, nt - rt);
 }
 
 }  // namespace kubo

@@ -459,9 +459,12 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   double* C64 = c.at<double>(p.o_C64);
   const int Mb = tc_pad_m(kl.n);
   {
-    StageTimer tm(c, KUBO_STAGE_FOURIER, 2);
+    // the velocity columns feed only the FP32 rotation in the MIXED mode: FP32-grade slices
+    // (a second tensor-core launch over those column tiles)
+    const int red_n0 = f32_rotation(p.precision) ? p.W * p.W : p.Npad;
+    StageTimer tm(c, KUBO_STAGE_FOURIER, red_n0 < p.Npad ? 3 : 2);
     KCHECK(launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s));
-    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s));
+    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0));
   }
   {
     StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
@@ -1493,7 +1496,7 @@ kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
           KList kl{kidx + t0, 0, (int)std::min<int64_t>(p.chunk, n_k - t0)};
           const int Mb = tc_pad_m(kl.n);
           if (launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s) != cudaSuccess ||
-              launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s) != cudaSuccess ||
+              launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, p.Npad) != cudaSuccess ||
               launch_unpack_rows(C64, p.Npad, W, kl.n, Hk + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, c.s) != cudaSuccess) {
             cudaGetLastError();
             r = KUBO_ERR_CUDA;

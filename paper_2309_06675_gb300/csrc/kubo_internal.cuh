@@ -162,9 +162,10 @@ cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, 
                                int* col_exp, void* Bt, cudaStream_t s);
 cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl, int Mpad, int Kp,
                               void* A, cudaStream_t s);
+// red_n0: first output column whose tile may keep three slices (FP32-grade; Npad = none)
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s);
+                              cudaStream_t s, int red_n0);
 // rows [n][ld] (H | dxH | dyH packed) -> three packed arrays [n][W*W]
 cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,
                                double* Y, cudaStream_t s);
