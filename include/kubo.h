@@ -161,7 +161,9 @@ kubo_status kubo_ahc_host(const double* H_R, const int32_t* R_vecs, int W, int N
 
 /*
  * Per-k results for a list of mesh points (steps (1)-(4) of List 1 without the k-sum):
- *   kidx   device, int64 [n_k] linear mesh indices (each in [0, N_k))
+ *   kidx   device, int64 [n_k] linear mesh indices (each in [0, N_k), checked on the device
+ *          before anything is computed: KUBO_ERR_INVALID_ARG otherwise; any order, repeats
+ *          allowed)
  *   E      device, double [n_k][W]            eigenvalues, ascending
  *   Omega  device, double [n_eta][n_k][W]     band Berry curvatures
  * opt->k_begin/k_end are ignored.
@@ -295,6 +297,15 @@ typedef struct kubo_batch_schedule {
  */
 kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_options* opt,
                              kubo_batch_schedule* sched);
+
+/*
+ * Failure-detection check (no counterpart in the paper): runs, on one thread, the bounded
+ * mbarrier wait that every pipeline wait of the tensor-core kernel uses, on a barrier that
+ * nothing completes, giving up after `spins` tries.  Returns KUBO_ERR_TIMEOUT -- the status a
+ * stalled tensor-core pipeline reports -- and leaves the context usable; no fault, trap or
+ * hang is involved.  spins < 1: KUBO_ERR_INVALID_ARG.  stream: cudaStream_t (NULL = legacy).
+ */
+kubo_status kubo_check_bounded_wait(uint32_t spins, void* stream);
 
 /* Device bytes of scratch a kubo_ahc / kubo_ahc_k call with these sizes needs. */
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,

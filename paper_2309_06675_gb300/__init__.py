@@ -132,6 +132,7 @@ def lib():
             "kubo_grad_workspace_size": (ctypes.c_size_t, [I, I, P, I, OPT]),
             "kubo_ahc_grad": (I, [P, P, I, I, P, P, I, D, P, P, P, OPT]),
             "kubo_ahc_batched": (I, [ctypes.POINTER(Problem), I, OPT, ctypes.POINTER(BatchSchedule)]),
+            "kubo_check_bounded_wait": (I, [ctypes.c_uint32, P]),
             "kubo_ahc": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_host": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_k": (I, [P, P, I, I, P, P, I64, D, P, P, OPT]),

@@ -92,11 +92,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+// bounded wait for the phase with the given parity to complete (false: gave up)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Failure-detection check: the same bounded wait on a barrier that nothing ever completes.
+// Thread 0 gives up after `limit` tries and records ST_TIMEOUT; the kernel then returns, so
+// the context stays usable.
+__global__ void bounded_wait_check_kernel(uint32_t limit, DevStatus* st) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) atomicOr(&st->bits, ST_TIMEOUT);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -499,6 +513,11 @@ int tc_pad_m(int n) { return (n + BM - 1) / BM * BM; }
 int tc_pad_n(int W) { return (3 * W * W + BN - 1) / BN * BN; }
 int tc_pad_k(int N_R) { return (N_R + BK - 1) / BK * BK; }
 int tc_slices() { return NSLICE; }
+
+cudaError_t launch_bounded_wait_check(uint32_t limit, DevStatus* st, cudaStream_t s) {
+  bounded_wait_check_kernel<<<1, 32, 0, s>>>(limit, st);
+  return cudaGetLastError();
+}
 size_t fourier_tc_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
 
 cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, int Npad, int Kp,

@@ -42,6 +42,18 @@ __global__ void check_hermitian_kernel(const double2* __restrict__ H, const int*
   }
 }
 
+// every listed mesh index in [0, Nk)
+__global__ void check_kidx_kernel(const int64_t* __restrict__ kidx, int64_t n, int64_t Nk,
+                                  DevStatus* st) {
+  bool bad = false;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = kidx[t];
+    bad |= k < 0 || k >= Nk;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->bits, ST_BAD_INDEX);
+}
+
 __global__ void hermitian_verdict_kernel(DevStatus* st) {
   double dev = __longlong_as_double((long long)st->herm_dev_bits);
   double mx = __longlong_as_double((long long)st->herm_max_bits);
@@ -125,6 +137,13 @@ cudaError_t launch_pack_basis(const double2* H_R, const int* pairs, int idx0, in
                               double* Bp, cudaStream_t s) {
   int64_t total = (int64_t)(1 + 2 * N_h) * W * W;
   pack_basis_kernel<<<grid_for(total, 256), 256, 0, s>>>(H_R, pairs, idx0, N_h, W, Bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_kidx(const int64_t* kidx, int64_t n, int64_t Nk, DevStatus* st,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_kidx_kernel<<<grid_for(n, 256), 256, 0, s>>>(kidx, n, Nk, st);
   return cudaGetLastError();
 }
 

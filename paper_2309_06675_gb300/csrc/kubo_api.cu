@@ -317,6 +317,7 @@ struct StageTimer {
   } while (0)
 
 kubo_status bits_to_status(unsigned bits) {
+  if (bits & ST_BAD_INDEX) return KUBO_ERR_INVALID_ARG;
   if (bits & (ST_NOT_HERMITIAN | ST_NONFINITE)) return KUBO_ERR_NOT_HERMITIAN;
   if (bits & ST_TIMEOUT) return KUBO_ERR_TIMEOUT;
   if (bits & ST_NO_CONVERGENCE) return KUBO_ERR_NO_CONVERGENCE;
@@ -351,6 +352,13 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
   if (!std::isfinite(o.mixed_fixup_rel)) return KUBO_ERR_INVALID_ARG;
   n_eta = o.n_eta > 0 ? o.n_eta : 1;
   return KUBO_OK;
+}
+
+// Device k-list check before any output is written: every index in [0, N_k) (one host sync).
+kubo_status check_klist(Call& c, const int64_t* kidx, int64_t n) {
+  KCHECK(cudaMemsetAsync(c.at<char>(c.p.o_status), 0, sizeof(DevStatus), c.s));
+  KCHECK(launch_check_kidx(kidx, n, c.p.mesh.Nk, c.at<DevStatus>(c.p.o_status), c.s));
+  return read_status(c);
 }
 
 // Prepare the model (status reset, Hermitian check, twiddles, packed basis) and return the
@@ -1418,6 +1426,33 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
   }
 }
 
+kubo_status kubo_check_bounded_wait(uint32_t spins, void* stream) {
+  try {
+    if (spins < 1) return KUBO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStatus* st = nullptr;
+    if (cudaMallocAsync((void**)&st, sizeof(DevStatus), s) != cudaSuccess) {
+      cudaGetLastError();
+      return KUBO_ERR_OOM;
+    }
+    kubo_status r = KUBO_OK;
+    DevStatus h;
+    if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess ||
+        launch_bounded_wait_check(spins, st, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      r = KUBO_ERR_CUDA;
+    else
+      r = bits_to_status(h.bits);
+    cudaFreeAsync(st, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && r == KUBO_OK) r = KUBO_ERR_CUDA;
+    cudaGetLastError();
+    return r;
+  } catch (...) {
+    return KUBO_ERR_CUDA;
+  }
+}
+
 kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
                        const int32_t* kmesh, const int64_t* kidx, int64_t n_k, double eta,
                        double* E, double* Omega, const kubo_options* opt) {
@@ -1440,7 +1475,8 @@ kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
     plan_layout(p, false, 0);
     r = c.acquire(o);
     if (r != KUBO_OK) return r;
-    r = upload_etas(c, o, eta);
+    r = check_klist(c, kidx, n_k);
+    if (r == KUBO_OK) r = upload_etas(c, o, eta);
     if (r == KUBO_OK) r = prepare_model(c, H_R, ri);
     if (r == KUBO_OK) {
       const Model md = make_model(c);
@@ -1485,7 +1521,8 @@ kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
     c.prof = o.profile;
     r = c.acquire(o);
     if (r != KUBO_OK) return r;
-    r = prepare_model(c, H_R, ri);
+    r = check_klist(c, kidx, n_k);
+    if (r == KUBO_OK) r = prepare_model(c, H_R, ri);
     if (r == KUBO_OK) {
       const Model md = make_model(c);
       const size_t WW = (size_t)W * W;

@@ -16,6 +16,7 @@ enum : unsigned {
   ST_NONFINITE = 2u,       // NaN/Inf in H(R)
   ST_NO_CONVERGENCE = 4u,  // QL iteration cap reached at some k
   ST_TIMEOUT = 16u,        // a bounded device-side wait gave up
+  ST_BAD_INDEX = 32u,      // a listed mesh index outside [0, N_k)
 };
 
 struct DevStatus {
@@ -106,6 +107,8 @@ struct EighBufs {
 cudaError_t launch_check_hermitian(const double2* H_R, const int* neg, int N_R, int W,
                                    DevStatus* st, cudaStream_t s);
 cudaError_t launch_hermitian_verdict(DevStatus* st, cudaStream_t s);
+cudaError_t launch_check_kidx(const int64_t* kidx, int64_t n, int64_t Nk, DevStatus* st,
+                              cudaStream_t s);
 cudaError_t launch_pack_basis(const double2* H_R, const int* pairs, int idx0, int N_h, int W,
                               double* Bp, cudaStream_t s);
 cudaError_t launch_twiddles(double2* tab, int N1, int N2, int N3, cudaStream_t s);
@@ -166,6 +169,8 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
                               cudaStream_t s, int red_n0);
+// the tensor-core kernel's bounded mbarrier wait on a barrier that never completes
+cudaError_t launch_bounded_wait_check(uint32_t limit, DevStatus* st, cudaStream_t s);
 // rows [n][ld] (H | dxH | dyH packed) -> three packed arrays [n][W*W]
 cudaError_t launch_unpack_rows(const double* C, int64_t ld, int W, int n, double* H, double* X,
                                double* Y, cudaStream_t s);

@@ -286,3 +286,13 @@ def test_padding_ablation_gives_identical_sums(kubo, torch, m64, precision):
     a = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision=precision).cpu().numpy()
     b = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision=precision, unpadded=True).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(kubo, torch, m16):
+    """The tensor-core pipeline's bounded wait, on a barrier nothing completes, returns
+    KUBO_ERR_TIMEOUT (9) instead of hanging; the context stays usable."""
+    stream = torch.cuda.current_stream().cuda_stream
+    assert kubo.lib().kubo_check_bounded_wait(2000, stream) == 9
+    assert kubo.lib().kubo_check_bounded_wait(0, stream) == 1
+    S = kubo.ahc(cuda(torch, m16.H_R), m16.R, (4, 4, 4), cuda(torch, np.array([0.0])))
+    assert np.all(np.isfinite(S.cpu().numpy()))
