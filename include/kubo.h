@@ -122,6 +122,10 @@ typedef struct kubo_options {
                                k-range of whole k1-planes; bounding box at most 8 N_R vectors;
                                otherwise KUBO_ERR_UNSUPPORTED).  Same result up to rounding
                                order.  0 (default): dense contraction. */
+  int rotation_tc;          /* KUBO_MIXED / KUBO_MIXED_ROTATION, W <= 64: 1 = step (3) on the
+                               tensor cores (exact fixed-point BF16-slice products, FP32-grade)
+                               instead of FP32 on the FMA pipe.  Same accuracy class; currently
+                               slower at W = 64, so 0 (FMA pipe) is the default. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,

@@ -85,6 +85,7 @@ class Options(ctypes.Structure):
         ("grad_eps", ctypes.c_double),
         ("layout_unpadded", ctypes.c_int),
         ("fourier_separable", ctypes.c_int),
+        ("rotation_tc", ctypes.c_int),
     ]
 
 
@@ -233,7 +234,7 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
         stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
-        unpadded=False, separable=False):
+        unpadded=False, separable=False, rotation_tc=False):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
@@ -251,6 +252,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     o.mixed_fixup_rel = float(fixup_rel)
     o.layout_unpadded = 1 if unpadded else 0
     o.fourier_separable = 1 if separable else 0
+    o.rotation_tc = 1 if rotation_tc else 0
     code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                           W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                           _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),
@@ -411,7 +413,8 @@ def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_
     return out
 
 
-def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None, chunk_k=0):
+def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None, chunk_k=0,
+          rotation_tc=False):
     """Per-k eigenvalues and band curvatures for the listed mesh points."""
     torch = _torch()
     Rh = _host_int32(R, 3)
@@ -423,6 +426,7 @@ def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None,
     Om = torch.empty((n_eta, n_k, W), dtype=torch.float64, device=H_R.device)
     keep = []
     o = _options(precision, etas, 0.0, None, stream, chunk_k, None, keep)
+    o.rotation_tc = 1 if rotation_tc else 0
     code = lib().kubo_ahc_k(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                             W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                             _dev(kidx, torch.int64, "kidx"), n_k, float(eta),

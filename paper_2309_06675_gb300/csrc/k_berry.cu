@@ -4,7 +4,12 @@
 // (v^y_mn = conj(v^y_nm) because v^y is Hermitian.)  Both rotations are register-tiled
 // complex products over shared-memory operands; the curvature is reduced per band in a
 // fixed order (deterministic), for every requested broadening eta at once.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
 #include "kubo_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace kubo {
 
@@ -411,6 +416,368 @@ __global__ void unpack_rows_kernel(const double* __restrict__ C, int64_t ld, int
   }
 }
 
+
+// ------------------------------------------------------------------ rotations on the tensor cores
+// Step (3) as exact fixed-point products on tcgen05 (the scheme of the tensor-core Fourier sum):
+// every operand is scaled by a power of two to |x| <= 1 and cut into four 8-bit integer slices
+// held exactly in BF16 (x = sum_i s_i 2^(-7-8i) + O(2^-32)); the ten slice pairs with i + j <= 3
+// are multiplied into one FP32 TMEM accumulator per level l = i + j, where every partial sum
+// is an integer below 2^24 (exact), and the levels are folded in int64.  The complex products
+// are block-real GEMMs with M = 128, N = 64, K = 128 (W padded to 64):
+//   T = X U:    [T_r; T_i] = [[X_r, -X_i], [X_i, X_r]] [U_r; U_i]
+//   V = U^H T:  [V_r; V_i] = [[U_r^T, U_i^T], [-U_i^T, U_r^T]] [T_r; T_i]
+// U = Q D Z is assembled in FP32 in shared memory first (its FP32 rounding is the dominant
+// error, ~1e-7); T is re-sliced with its own exponent for the second product.  V^x waits in
+// TMEM while V^y is formed; the curvature uses FP64 denominators as in the SIMT kernels.
+// One persistent CTA per SM (226 KB of shared memory), k-points in turn.
+constexpr int RT_NT = 256;
+constexpr int RT_WP = 64;                                 // padded order
+constexpr int RT_NS = 4;                                  // slices per operand
+constexpr int RT_NPAIR = 10;
+constexpr int RT_A_BLOCK = 128 * 128;                     // bytes: 128 rows x 64 K (BF16)
+constexpr int RT_B_BLOCK = 64 * 128;                      // bytes: 64 rows x 64 K
+constexpr int RT_A_BYTES = RT_NS * 2 * RT_A_BLOCK;        // 128 KB (4 slices x 2 K halves)
+constexpr int RT_B_BYTES = RT_NS * 2 * RT_B_BLOCK;        // 64 KB
+constexpr int RT_U_BYTES = RT_WP * RT_WP * 8;             // float2 [64][64]
+constexpr int RT_TMEM_COLS = 512;                         // 4 levels x 64 + V^x (64)
+constexpr int RT_VX_COL = 256;
+constexpr uint32_t RT_WAIT_LIMIT = 1u << 20;              // a product takes microseconds
+constexpr uint32_t RT_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+__constant__ int c_rpi[RT_NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+__constant__ int c_rpj[RT_NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+__constant__ int c_rpl[RT_NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+
+// byte offset of element (row, k in 0..63) in a K-major 128-byte-swizzled block of 2-byte elements
+__device__ __forceinline__ uint32_t sw128_off(int row, int k) {
+  const uint32_t b = (uint32_t)k * 2u;
+  return (uint32_t)row * 128u + ((((b >> 4) ^ (uint32_t)(row & 7)) & 7u) << 4) + (b & 15u);
+}
+
+// The operands are 31-bit fixed-point integers q (value q 2^-31, |q| <= 2^31 - 1) cut into
+// four signed 8-bit slices with round-to-nearest carries in 32-bit integer arithmetic (no FP64
+// and no 64-bit conversions, which share the slow FP64 pipe):
+// q = s0 2^24 + s1 2^16 + s2 2^8 + s3, |s_i| <= 128, each exact in BF16.  round(q / 2^24) is
+// formed as (floor(q / 2^23) + 1) >> 1, which cannot overflow; the remainder q - s0 2^24 lies
+// in [-2^23, 2^23] and is formed modulo 2^32.
+__device__ __forceinline__ void slice4(int q, uint16_t (&o)[RT_NS]) {
+  const int s0 = ((q >> 23) + 1) >> 1;
+  int r = (int)((uint32_t)q - ((uint32_t)s0 << 24));
+  const int s1 = ((r >> 15) + 1) >> 1;
+  r -= s1 * 65536;
+  const int s2 = ((r >> 7) + 1) >> 1;
+  const int s3 = r - s2 * 256;
+  o[0] = __bfloat16_as_ushort(__int2bfloat16_rn(s0));
+  o[1] = __bfloat16_as_ushort(__int2bfloat16_rn(s1));
+  o[2] = __bfloat16_as_ushort(__int2bfloat16_rn(s2));
+  o[3] = __bfloat16_as_ushort(__int2bfloat16_rn(s3));
+}
+
+constexpr int RT_QMAX = 2147483647;
+
+// round(x 2^(31 - e)) for |x| <= 2^e (clamped to 2^31 - 1), from the bit pattern
+__device__ __forceinline__ int fixed31(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int sh = 1044 + e - ex;   // x 2^(31-e) = m 2^(ex - 1075 + 31 - e) = m 2^-sh
+  if (ex == 0 || sh >= 63) return 0;   // zero, subnormal, or below half a unit
+  const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const unsigned long long q = sh <= 21 ? (1ull << 31) : (m + (1ull << (sh - 1))) >> sh;
+  const int qi = q > (unsigned long long)RT_QMAX ? RT_QMAX : (int)q;
+  return (b >> 63) ? -qi : qi;
+}
+// round(u 2^31) for an FP32 value |u| <= 1 (the conversion saturates at 2^31 - 1)
+__device__ __forceinline__ int fixed31f(float u) { return __float2int_rn(u * 2147483648.0f); }
+
+// |x| as an ordered unsigned integer (FP64 bit pattern), and the smallest e with |x| <= 2^e
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ int pow2_exponent_bits(unsigned long long ab) {
+  if (ab == 0) return 0;
+  const int ex = (int)(ab >> 52) - 1023;
+  return (ab & ((1ull << 52) - 1)) ? ex + 1 : ex;
+}
+
+// store a pair of adjacent-K elements (k even) of all slices into the operand region
+__device__ __forceinline__ void put2(unsigned char* region, int block_bytes, int row, int k,
+                                     int v0, int v1) {
+  uint16_t a[RT_NS], b[RT_NS];
+  slice4(v0, a);
+  slice4(v1, b);
+  const int kc = k >> 6, kin = k & 63;
+#pragma unroll
+  for (int i = 0; i < RT_NS; ++i) {
+    unsigned char* blk = region + (size_t)(i * 2 + kc) * block_bytes;
+    *reinterpret_cast<uint32_t*>(blk + sw128_off(row, kin)) = (uint32_t)a[i] | ((uint32_t)b[i] << 16);
+  }
+}
+
+// issue the 80 MMAs of one block-real product (10 slice pairs x 2 K halves x 4 K16 steps)
+__device__ __forceinline__ void rot_issue(uint32_t tmem, uint32_t a_base, uint32_t b_base) {
+  int seen = 0;
+  for (int p = 0; p < RT_NPAIR; ++p) {
+    const int i = c_rpi[p], j = c_rpj[p], l = c_rpl[p];
+    for (int kc = 0; kc < 2; ++kc)
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t acc = ((seen >> l) & 1) ? 1u : 0u;
+        seen |= 1 << l;
+        const uint64_t da = tc::umma_desc_sw128(a_base + (uint32_t)((i * 2 + kc) * RT_A_BLOCK + kk * 32));
+        const uint64_t db = tc::umma_desc_sw128(b_base + (uint32_t)((j * 2 + kc) * RT_B_BLOCK + kk * 32));
+        tc::umma_bf16(tmem + (uint32_t)(l * 64), da, db, RT_IDESC, acc);
+      }
+  }
+}
+
+// the 32 columns c0 .. c0 + 31 of this thread's TMEM lane, folded over the four levels:
+// value = isum 2^(-46) in units of the operands' scales (exact integers)
+__device__ __forceinline__ void rot_fold(uint32_t lane_addr, int c0, long long (&isum)[32]) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) isum[j] = 0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t r[16];
+      tc::tmem_ld16(lane_addr + (uint32_t)(l * 64 + c0 + 16 * h), r);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        isum[16 * h + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
+    }
+  }
+}
+
+// block-wide maximum of 64-bit unsigned integers (256 threads)
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
+                                                            unsigned long long* red8) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red8[w] = v;
+  __syncthreads();
+  unsigned long long m = 0;
+  for (int i = 0; i < RT_NT / 32; ++i) m = max(m, red8[i]);
+  return m;
+}
+
+// an exact integer |v| < 2^62 to FP32 with 32-bit conversions only (two parts; the sum is
+// rounded twice, an error below 2^-23 relative)
+__device__ __forceinline__ float ll_to_float(long long v) {
+  const int hi = (int)(v >> 31);
+  const int lo = (int)(v & 0x7FFFFFFF);
+  return fmaf((float)hi, 2147483648.0f, (float)lo);
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
+    const double* __restrict__ E, const double* __restrict__ Z, EighBufs eb,
+    const TIn* __restrict__ Xp, const TIn* __restrict__ Yp, int64_t ld, int W, int n,
+    const double* __restrict__ etas, int n_eta, double* __restrict__ Om, int64_t eta_stride,
+    DevStatus* st) {
+  extern __shared__ unsigned char rt_smem[];
+  __shared__ double sE[64];
+  __shared__ double sEta[MAXE];
+  __shared__ double s_emax;
+  __shared__ unsigned long long redl[RT_NT / 32];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int s_ok;
+  // [U float2 64 x 64][pad to 1024][A operand 128 KB][B operand 64 KB]
+  float2* sU = reinterpret_cast<float2*>(rt_smem);
+  unsigned char* opA = reinterpret_cast<unsigned char*>(
+      ((uintptr_t)(rt_smem + RT_U_BYTES) + 1023) & ~(uintptr_t)1023);
+  unsigned char* opB = opA + RT_A_BYTES;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int LDV = mixed_ld(RT_WP, 1);   // 68: the curvature matrices live in opB / opA
+  const size_t WW = (size_t)W * W;
+
+  if (t == 0) {
+    tc::mbar_init(&mma_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc::smem_u32(&tmem_sh)), "r"(RT_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  const uint32_t a_base = tc::smem_u32(opA), b_base = tc::smem_u32(opB);
+  // TMEM lane quarter and column half of this warp in the epilogues
+  const int quarter = warp & 3, chalf = warp >> 2;
+  const int mrow = quarter * 32 + lane;                   // row of [.._r; .._i]
+  const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  // run the MMAs of one product and wait (bounded) for them; false on timeout
+  auto product = [&]() -> bool {
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+      rot_issue(tmem, a_base, b_base);
+      tc::umma_commit(&mma_bar);
+      s_ok = tc::mbar_wait(&mma_bar, phase, RT_WAIT_LIMIT) ? 1 : 0;
+    }
+    __syncthreads();
+    phase ^= 1u;
+    tc::tc_fence_after();
+    return s_ok != 0;
+  };
+
+  for (int64_t k = blockIdx.x; k < n && ok; k += gridDim.x) {
+    __syncthreads();
+    if (t < W) sE[t] = E[k * W + t];
+    if (t < n_eta) sEta[t] = etas[t];
+    // ---- U = Q D Z in FP32 (reflectors staged in the A operand region)
+    for (int idx = t; idx < RT_WP * RT_WP; idx += RT_NT) sU[idx] = make_float2(0.f, 0.f);
+    __syncthreads();
+    assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, RT_WP, t, sU,
+                   reinterpret_cast<float2*>(opA));
+    if (t == 0) {
+      double mx = 0.0;
+      for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
+      s_emax = mx;
+    }
+    for (int a = 0; a < 2 && ok; ++a) {
+      const TIn* P = (a == 0 ? Xp : Yp) + k * ld;
+      // ---- A1 = [[X_r, -X_i], [X_i, X_r]] 2^-eX (W padded to 64)
+      unsigned long long mx = 0;
+      for (int idx = t; idx < W * W; idx += RT_NT) mx = max(mx, abs_bits(P[idx]));
+      const int eX = pow2_exponent_bits(block_max_u64(mx, redl));
+      for (int idx = t; idx < RT_WP * RT_WP / 2; idx += RT_NT) {
+        const int r = idx / (RT_WP / 2), c = 2 * (idx % (RT_WP / 2));
+        int qr[2] = {0, 0}, qi[2] = {0, 0};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int cc = c + q;
+          if (r < W && cc < W) {
+            if (r < cc) { qr[q] = fixed31(P[r * W + cc], eX); qi[q] = fixed31(P[cc * W + r], eX); }
+            else if (r > cc) { qr[q] = fixed31(P[cc * W + r], eX); qi[q] = -fixed31(P[r * W + cc], eX); }
+            else qr[q] = fixed31(P[r * W + r], eX);
+          }
+        }
+        const int qr0 = qr[0], qr1 = qr[1], qi0 = qi[0], qi1 = qi[1];
+        put2(opA, RT_A_BLOCK, r, c, qr0, qr1);
+        put2(opA, RT_A_BLOCK, r, 64 + c, -qi0, -qi1);
+        put2(opA, RT_A_BLOCK, 64 + r, c, qi0, qi1);
+        put2(opA, RT_A_BLOCK, 64 + r, 64 + c, qr0, qr1);
+      }
+      // ---- B1[n][k] = U_r[k][n] (k < 64), U_i[k-64][n] (|U| <= 1: no scale)
+      for (int idx = t; idx < RT_WP * RT_WP / 2; idx += RT_NT) {
+        const int nn = idx / (RT_WP / 2), kk = 2 * (idx % (RT_WP / 2));
+        const float2 u0 = sU[kk * RT_WP + nn], u1 = sU[(kk + 1) * RT_WP + nn];
+        put2(opB, RT_B_BLOCK, nn, kk, fixed31f(u0.x), fixed31f(u1.x));
+        put2(opB, RT_B_BLOCK, nn, 64 + kk, fixed31f(u0.y), fixed31f(u1.y));
+      }
+      if (!product()) { ok = false; break; }
+      // ---- T' = [T_r; T_i] 2^-eX = isum 2^-46 from TMEM; re-cut as 31-bit fixed point
+      // q = round(isum 2^-sh) with the smallest sh >= 0 that keeps |q| <= 2^31
+      long long tv[32];
+      rot_fold(lane_addr, chalf * 32, tv);
+      unsigned long long tm = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tm = max(tm, (unsigned long long)(tv[j] < 0 ? -tv[j] : tv[j]));
+      tc::tc_fence_before();
+      const unsigned long long tmax = block_max_u64(tm, redl);
+      const int bits = tmax > 0 ? 64 - __clzll((long long)tmax) : 0;
+      const int sh = bits > 31 ? bits - 31 : 0;
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        // B2 row = output column n of T, K index = mrow; a pair of adjacent K needs the
+        // neighbouring lane's value (rounding can reach 2^31: clamp)
+        const int v0 = (int)min((sh ? (tv[j] + (1ll << (sh - 1))) >> sh : tv[j]), (long long)RT_QMAX);
+        const int v1 = (int)min((sh ? (tv[j + 1] + (1ll << (sh - 1))) >> sh : tv[j + 1]), (long long)RT_QMAX);
+        const int w0 = __shfl_down_sync(0xffffffffu, v0, 1);
+        const int w1 = __shfl_down_sync(0xffffffffu, v1, 1);
+        if ((lane & 1) == 0) {
+          put2(opB, RT_B_BLOCK, chalf * 32 + j, mrow, v0, w0);
+          put2(opB, RT_B_BLOCK, chalf * 32 + j + 1, mrow, v1, w1);
+        }
+      }
+      // ---- A2 = [[U_r^T, U_i^T], [-U_i^T, U_r^T]]
+      for (int idx = t; idx < RT_WP * RT_WP / 2; idx += RT_NT) {
+        const int r = idx / (RT_WP / 2), c = 2 * (idx % (RT_WP / 2));
+        const float2 u0 = sU[c * RT_WP + r], u1 = sU[(c + 1) * RT_WP + r];   // U[c][r], U[c+1][r]
+        const int ar0 = fixed31f(u0.x), ar1 = fixed31f(u1.x);
+        const int ai0 = fixed31f(u0.y), ai1 = fixed31f(u1.y);
+        put2(opA, RT_A_BLOCK, r, c, ar0, ar1);
+        put2(opA, RT_A_BLOCK, r, 64 + c, ai0, ai1);
+        put2(opA, RT_A_BLOCK, 64 + r, c, -ai0, -ai1);
+        put2(opA, RT_A_BLOCK, 64 + r, 64 + c, ar0, ar1);
+      }
+      if (!product()) { ok = false; break; }
+      // ---- V = [V_r; V_i]: the B2 slices stood for T' 2^(sh - 15) (q 2^-31 = isum 2^(sh-46)),
+      // so V = isum2 2^-46 2^(sh - 15) 2^eX
+      long long vi[32];
+      rot_fold(lane_addr, chalf * 32, vi);
+      const float sV = ldexpf(1.0f, eX + sh - 61);
+      float vv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) vv[j] = ll_to_float(vi[j]) * sV;
+      if (a == 0) {
+        // park V^x in TMEM columns RT_VX_COL.. (FP32) while V^y is formed
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t r[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(vv[16 * h + j]);
+          tc::tmem_st16(lane_addr + (uint32_t)(RT_VX_COL + chalf * 32 + 16 * h), r);
+        }
+        tc::tc_fence_before();
+      } else {
+        // V^y -> opA (float2 [64][LDV]), V^x (TMEM) -> opB
+        float2* sVy = reinterpret_cast<float2*>(opA);
+        float2* sVx = reinterpret_cast<float2*>(opB);
+        __syncthreads();   // the product's operands are no longer read (it completed)
+        const int rr = mrow & 63;
+        const bool im = mrow >= 64;
+        uint32_t px[32];
+        tc::tmem_ld16(lane_addr + (uint32_t)(RT_VX_COL + chalf * 32), *reinterpret_cast<uint32_t(*)[16]>(px));
+        tc::tmem_ld16(lane_addr + (uint32_t)(RT_VX_COL + chalf * 32 + 16), *reinterpret_cast<uint32_t(*)[16]>(px + 16));
+        tc::tc_fence_before();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int cn = chalf * 32 + j;
+          float* vy = reinterpret_cast<float*>(&sVy[rr * LDV + cn]);
+          float* vx = reinterpret_cast<float*>(&sVx[rr * LDV + cn]);
+          vy[im ? 1 : 0] = vv[j];
+          vx[im ? 1 : 0] = __uint_as_float(px[j]);
+        }
+      }
+    }
+    if (!ok) break;
+    __syncthreads();
+    // ---- curvature (FP64 denominators), as the SIMT kernels
+    {
+      const int tx = t & 15, ty = t >> 4;
+      const float2* sVx = reinterpret_cast<const float2*>(opB);
+      const float2* sVy = reinterpret_cast<const float2*>(opA);
+      float2 vy[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vy[i][j] = sVy[(ty + 16 * i) * LDV + tx + 16 * j];
+      curvature_epilogue<4, float2>(sVx, vy, sE, sEta, n_eta, s_emax, W, LDV, ty, tx, t,
+                                    reinterpret_cast<double*>(opA), Om, eta_stride, k);
+    }
+  }
+  if (!ok && t == 0) atomicOr(&st->bits, ST_TIMEOUT);
+  // no MMA may still write TMEM when it is released
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0 && !ok) tc::mbar_wait(&mma_bar, phase, RT_WAIT_LIMIT);
+    __syncwarp();
+    tc::tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(RT_TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 size_t berry_fp64_smem(int W, int n_eta) {
@@ -490,6 +857,44 @@ cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const Ei
   const int64_t WW = (int64_t)W * W;
   return launch_berry_mixed_t<double, true>(E, nullptr, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas,
                                             n_eta, Om, eta_stride, s, pad);
+}
+
+size_t berry_tc_smem() { return (size_t)RT_U_BYTES + 1024 + RT_A_BYTES + RT_B_BYTES; }
+
+template <typename TIn>
+static cudaError_t launch_berry_tc_t(const double* E, const double* Z, const EighBufs& eb,
+                                     const TIn* Xp, const TIn* Yp, int64_t ld, int W, int n,
+                                     const double* etas, int n_eta, double* Om, int64_t eta_stride,
+                                     DevStatus* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > RT_WP || n_eta > MAXE) return cudaErrorInvalidValue;
+  const size_t sm = berry_tc_smem();
+  cudaError_t e = cudaFuncSetAttribute(berry_tc_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  const int grid = std::min(n, std::max(1, sms));
+  berry_tc_kernel<TIn><<<grid, RT_NT, sm, s>>>(E, Z, eb, Xp, Yp, ld, W, n, etas, n_eta, Om,
+                                               eta_stride, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_berry_tc_rows(const double* E, const double* Z, const EighBufs& eb,
+                                 const double* C, int64_t ld, int W, int n, const double* etas,
+                                 int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
+                                 cudaStream_t s) {
+  const int64_t WW = (int64_t)W * W;
+  return launch_berry_tc_t<double>(E, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
+                                   eta_stride, st, s);
+}
+
+cudaError_t launch_berry_tc_from_f64(const double* E, const double* Z, const EighBufs& eb,
+                                     const double* Xp, const double* Yp, int W, int n,
+                                     const double* etas, int n_eta, double* Om,
+                                     int64_t eta_stride, DevStatus* st, cudaStream_t s) {
+  return launch_berry_tc_t<double>(E, Z, eb, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
+                                   eta_stride, st, s);
 }
 
 cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,

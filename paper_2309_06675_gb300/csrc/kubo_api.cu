@@ -91,6 +91,7 @@ struct Plan {
   int Npad = 0, Kp = 0, Mpad = 0;   // tensor-core operand padding (mixed precision)
   int kpb = KSUM_KPB;               // k-points per k-sum block
   int pad = 1;                      // leading dimension W + pad in the fused kernels' smem
+  bool rot_tc = false;              // FP32-grade rotations on the tensor cores (W <= 64)
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -492,7 +493,10 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
       KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
+    if (p.rot_tc)
+      KCHECK(launch_berry_tc_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
+    else
+      KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
     return KUBO_OK;
   }
   {
@@ -536,7 +540,10 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
       KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
+    if (p.rot_tc)
+      KCHECK(launch_berry_tc_from_f64(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
+    else
+      KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
     return KUBO_OK;
   }
   {
@@ -697,6 +704,8 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   p.pad = o.layout_unpadded ? 0 : 1;
+  // the padding ablation concerns the SIMT rotation kernel's shared-memory layout
+  p.rot_tc = o.rotation_tc && !o.layout_unpadded;
   if (o.fourier_separable) {
     if (o.workspace) return KUBO_ERR_UNSUPPORTED;   // its size depends on the R set
     r = setup_separable(p, R_vecs, N_R, kb, ke, ri);

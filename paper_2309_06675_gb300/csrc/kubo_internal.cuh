@@ -150,6 +150,17 @@ cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, cons
                                           const double* etas, int n_eta, double* Om,
                                           int64_t eta_stride, cudaStream_t s, int pad = 1);
 
+// the same rotations as exact fixed-point BF16-slice products on the tensor cores (U assembled
+// in FP32 from Z and eb), W <= 64; a stalled MMA completion sets ST_TIMEOUT in st
+cudaError_t launch_berry_tc_rows(const double* E, const double* Z, const EighBufs& eb,
+                                 const double* C, int64_t ld, int W, int n, const double* etas,
+                                 int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
+                                 cudaStream_t s);
+cudaError_t launch_berry_tc_from_f64(const double* E, const double* Z, const EighBufs& eb,
+                                     const double* Xp, const double* Yp, int W, int n,
+                                     const double* etas, int n_eta, double* Om,
+                                     int64_t eta_stride, DevStatus* st, cudaStream_t s);
+
 // FP32 rotation from FP64 packed arrays (error-budget mode)
 cudaError_t launch_berry_mixed_from_f64(const double* E, const double2* U, const double* Xp,
                                         const double* Yp, int W, int n, const double* etas,

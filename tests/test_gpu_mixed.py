@@ -141,3 +141,35 @@ def test_mixed_haldane_chern(kubo, torch):
                  precision="mixed")
     C = 2 * np.pi * S.cpu().numpy()[0, 0]
     assert abs(abs(C) - 1) < 1e-5
+
+
+def test_tensor_core_rotation_vs_simt_and_fp64(kubo, torch, m64):
+    """Step (3) on the tensor cores (exact fixed-point BF16-slice products) against the FP32
+    SIMT rotation and the FP64 path on a slab of the W = 64 workload: both mixed variants
+    within 1e-5 of FP64, the tensor-core one at least as close as the SIMT one."""
+    kmesh = (128, 128, 128)
+    EF = cuda(torch, np.linspace(-1.0, 1.0, 64))
+    H = cuda(torch, m64.H_R)
+    rng = (77 * 16384, 77 * 16384 + 8192)
+    S64 = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng).cpu().numpy()
+    Stc = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision="mixed_rotation",
+                   rotation_tc=True).cpu().numpy()
+    Ssi = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision="mixed_rotation").cpu().numpy()
+    e_tc, e_si = rel_err(Stc, S64), rel_err(Ssi, S64)
+    assert e_tc < 1e-5 and e_si < 1e-5, (e_tc, e_si)
+    assert e_tc <= 1.5 * e_si, (e_tc, e_si)
+
+
+@pytest.mark.parametrize("W", [5, 16, 33])
+def test_tensor_core_rotation_small_orders_per_k(kubo, torch, W):
+    m = tbgen.random_tb(W, 2, 1.2, 300 + W)
+    kmesh = (16, 16, 16)
+    kidx = tbgen.k_sample(kmesh, 150, seed=W)
+    E, Om = kubo.ahc_k(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, kidx), etas=[1e-3, 0.05],
+                       precision="mixed_rotation", rotation_tc=True)
+    E_ref, Om_ref = O.kubo_per_k(m.H_R, m.R, kmesh, kidx, [1e-3, 0.05])
+    assert np.max(np.abs(E.cpu().numpy() - E_ref)) <= 1e-12 * np.max(np.abs(E_ref))
+    for e in range(2):
+        scale = np.max(np.abs(Om_ref[e]), axis=-1)
+        err = np.max(np.abs(Om.cpu().numpy()[e] - Om_ref[e]), axis=-1) / scale
+        assert np.median(err) < 1e-5, np.median(err)
