@@ -5,6 +5,7 @@
 // complex products over shared-memory operands; the curvature is reduced per band in a
 // fixed order (deterministic), for every requested broadening eta at once.
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -83,12 +84,40 @@ __device__ __forceinline__ void unpack_hermitian(const TIn* __restrict__ P, doub
   }
 }
 
+// a b - c d within 2 ulp (Kahan: the rounding error of c d is recovered exactly by an FMA)
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = fmaf(-c, d, w);     // w - c d, exact
+  const float f = fmaf(a, b, -w);
+  return __fadd_rn(f, e);
+}
+
+// (hi, lo) += x with the rounding error of hi + x carried exactly into lo (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float ap = __fsub_rn(s, bp);
+  const float err = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
 // Curvature epilogue shared by both precisions.  Every pair is evaluated once (n < m) and
 // enters Omega_n with +T_nm and Omega_m with -T_nm, so the antisymmetry T_mn = -T_nm that
 // makes occupied-occupied pairs cancel holds exactly even when v is only Hermitian to FP32
 // rounding.  Per-thread row / column partials go to `red` (2 * n_eta * W * 16 doubles, may
 // alias sVx: a barrier separates the last read of sVx from the first write of red) and are
 // summed in a fixed order (deterministic).
+//
+// FP32 velocities (V = float2): the numerator carries FP32 rounding already, so the quotient
+// T = num / (dE^2 + eta^2) is formed in FP32 too; only dE = E_n - E_m (a difference of close
+// FP64 eigenvalues), its square and the eta = 0 cut-off stay in FP64.  The numerator is
+// Kahan's difference of products (within 2 ulp of the exact Im part), and the partial sums are
+// exact FP32 pairs (Knuth's TwoSum): a large term of a near-degenerate pair enters Omega_n and
+// Omega_m with the same rounded value and no accumulation error, so it still cancels when
+// both bands are occupied.  Every term is bounded (|num| <= 2 |v^x| |v^y|) while the FP32
+// denominator is at least 2^-86; a thread whose tile holds a smaller one (eta and a gap below
+// ~1e-13) takes the FP64 quotient for that eta.
 template <int TM, typename V>
 __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[TM][TM],
                                                    const double* sE, const double* sEta,
@@ -96,46 +125,90 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
                                                    int tx, int t, double* red,
                                                    double* __restrict__ Om, int64_t eta_stride,
                                                    int64_t k) {
-  double num[TM][TM], d2[TM][TM];
+  constexpr bool F32 = std::is_same<V, float2>::value;
+  using R = typename std::conditional<F32, float, double>::type;
+  const double thr2 = (1e-12 * emax) * (1e-12 * emax);
+  R num[TM][TM];
+  double d2[TM][TM];
+  unsigned small0 = 0;   // bit (i TM + j): d2 <= thr2 (dropped when eta = 0)
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int n = ty + 16 * i;
 #pragma unroll
     for (int j = 0; j < TM; ++j) {
       const int m = tx + 16 * j;
-      num[i][j] = 0.0;
+      num[i][j] = 0;
       d2[i][j] = -1.0;   // marks "no pair"
       if (n < W && m < W && n < m) {
         const V vx = sVx[n * LD + m];
-        num[i][j] = -2.0 * ((double)vx.y * (double)vy[i][j].x - (double)vx.x * (double)vy[i][j].y);
+        if constexpr (F32)
+          num[i][j] = -2.0f * diff_of_products(vx.y, vy[i][j].x, vx.x, vy[i][j].y);
+        else
+          num[i][j] = -2.0 * (vx.y * vy[i][j].x - vx.x * vy[i][j].y);
         const double dE = sE[n] - sE[m];
         d2[i][j] = dE * dE;
+        if (d2[i][j] <= thr2) small0 |= 1u << (i * TM + j);
       }
     }
   }
-  __syncthreads();
-  const double thr2 = (1e-12 * emax) * (1e-12 * emax);
-  for (int e = 0; e < n_eta; ++e) {
-    const double eta = sEta[e];
-    double rp[TM], cp[TM];
-#pragma unroll
-    for (int i = 0; i < TM; ++i) { rp[i] = 0.0; cp[i] = 0.0; }
+  float d2f[TM][TM];
+  if constexpr (F32) {
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TM; ++j) {
-        if (d2[i][j] < 0.0) continue;
-        if (eta == 0.0 && d2[i][j] <= thr2) continue;
-        const double T = num[i][j] / fma(eta, eta, d2[i][j]);
-        rp[i] += T;
-        cp[j] -= T;
-      }
+      for (int j = 0; j < TM; ++j) d2f[i][j] = (float)d2[i][j];
+  }
+  __syncthreads();
+  for (int e = 0; e < n_eta; ++e) {
+    const double eta = sEta[e];
+    R rp[TM], cp[TM], rl[TM], cl[TM];   // (rl, cl: the FP32 pairs' low parts)
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int n = ty + 16 * i;
-      if (n < W) red[((size_t)(e * W + n) * 2) * 16 + tx] = rp[i];
-      const int m = tx + 16 * i;
-      if (m < W) red[((size_t)(e * W + m) * 2 + 1) * 16 + ty] = cp[i];
+    for (int i = 0; i < TM; ++i) { rp[i] = 0; cp[i] = 0; rl[i] = 0; cl[i] = 0; }
+    bool fp64 = !F32;
+    if constexpr (F32) {
+      const float eta2 = (float)(eta * eta);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+          if (d2[i][j] < 0.0) continue;
+          if (eta == 0.0 && ((small0 >> (i * TM + j)) & 1u)) continue;
+          const float den = d2f[i][j] + eta2;
+          if (den < 0x1p-86f) fp64 = true;
+          const float T = num[i][j] / den;
+          two_sum_acc(rp[i], rl[i], T);
+          two_sum_acc(cp[j], cl[j], -T);
+        }
+    }
+    if (fp64) {
+      double rq[TM], cq[TM];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) { rq[i] = 0.0; cq[i] = 0.0; }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+          if (d2[i][j] < 0.0) continue;
+          if (eta == 0.0 && ((small0 >> (i * TM + j)) & 1u)) continue;
+          const double T = (double)num[i][j] / fma(eta, eta, d2[i][j]);
+          rq[i] += T;
+          cq[j] -= T;
+        }
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int n = ty + 16 * i;
+        if (n < W) red[((size_t)(e * W + n) * 2) * 16 + tx] = rq[i];
+        const int m = tx + 16 * i;
+        if (m < W) red[((size_t)(e * W + m) * 2 + 1) * 16 + ty] = cq[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int n = ty + 16 * i;
+        if (n < W) red[((size_t)(e * W + n) * 2) * 16 + tx] = (double)rp[i] + (double)rl[i];
+        const int m = tx + 16 * i;
+        if (m < W) red[((size_t)(e * W + m) * 2 + 1) * 16 + ty] = (double)cp[i] + (double)cl[i];
+      }
     }
   }
   __syncthreads();
@@ -282,9 +355,9 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
                                                int t, float2* sU, float2* stage) {
   for (int idx = t; idx < W * W; idx += NT) {
     const int r = idx / W, c = idx % W;
-    const double z = Zk[idx];
+    const float z = (float)Zk[idx];
     const double2 p = ph[r];
-    sU[r * LD + c] = make_float2((float)(p.x * z), (float)(p.y * z));
+    sU[r * LD + c] = make_float2((float)p.x * z, (float)p.y * z);
   }
   auto roff = [&](int j) { return j * (W - 1) - (j * (j - 1)) / 2; };   // sum_{j'<j} (W-1-j')
   for (int idx = t; idx < W * W; idx += NT) {
