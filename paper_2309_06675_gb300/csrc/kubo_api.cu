@@ -476,8 +476,12 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0));
   }
   {
+    // MIXED: the reduction in double-float on the FP32 pipe (FP64-pipe-bound otherwise)
     StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
-    KCHECK(launch_tridiag_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
+    if (p.precision == KUBO_MIXED)
+      KCHECK(launch_tridiag_df_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
+    else
+      KCHECK(launch_tridiag_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
   }
   {
     StageTimer tm(c, KUBO_STAGE_QL, 1);

@@ -122,6 +122,10 @@ cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStrea
 // same reduction reading packed H from rows of leading dimension ld (tensor-core output)
 cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
                                 cudaStream_t s);
+// the same reduction with its symv and rank-2 updates in double-float (FP32 pairs, ~2^-46
+// per operation) on the FP32 pipe; FP64 outputs (MIXED mode)
+cudaError_t launch_tridiag_df_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
+                                   cudaStream_t s);
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
                                  cudaStream_t s, int pad = 1);
@@ -265,6 +269,7 @@ cudaError_t launch_grad_finalize(const double* Gacc, const int* pairs, const int
                                  int N_h, int W, double2* G, cudaStream_t s);
 
 size_t tridiag_smem(int W);
+size_t tridiag_df_smem(int W);
 size_t backtransform_smem(int W);
 size_t ql_smem(int W);
 size_t berry_fp64_smem(int W, int n_eta);

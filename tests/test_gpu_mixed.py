@@ -173,3 +173,32 @@ def test_tensor_core_rotation_small_orders_per_k(kubo, torch, W):
         scale = np.max(np.abs(Om_ref[e]), axis=-1)
         err = np.max(np.abs(Om.cpu().numpy()[e] - Om_ref[e]), axis=-1) / scale
         assert np.median(err) < 1e-5, np.median(err)
+
+
+@pytest.mark.parametrize("W,hw", [(2, 1), (5, 2), (33, 1), (64, 5), (100, 1)])
+def test_double_float_reduction_eigenvalues(kubo, torch, W, hw):
+    """The MIXED mode's double-float Householder reduction against the FP64 one: MIXED and
+    MIXED_FOURIER read the same tensor-core rows of H and differ only in the reduction, so
+    their eigenvalues agree to the reduction's backward error (~W 2^-46 max|E|)."""
+    m = tbgen.random_tb(W, hw, 1.5, 500 + W)
+    kmesh = (16, 16, 16)
+    kidx = tbgen.k_sample(kmesh, 97, seed=W)
+    H, K = cuda(torch, m.H_R), cuda(torch, kidx)
+    Emx, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed")
+    Efx, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed_fourier")
+    Emx, Efx = Emx.cpu().numpy(), Efx.cpu().numpy()
+    scale = np.max(np.abs(Efx))
+    assert np.max(np.abs(Emx - Efx)) <= max(W, 8) * 2.0 ** -46 * scale, \
+        np.max(np.abs(Emx - Efx)) / scale
+
+
+def test_double_float_reduction_degenerate_bands(kubo, torch):
+    """Exactly degenerate bands (two identical layers): the double-float reduction keeps the
+    pairs degenerate to its precision and the curvature sums match the FP64 path."""
+    m = tbgen.stack_layers(tbgen.qwz(-1.2, tz=0.3, c0=0.2), 2)
+    kmesh = (24, 24, 4)
+    EF = cuda(torch, np.array([-0.5, 0.1, 0.7]))
+    H = cuda(torch, m.H_R)
+    S64 = kubo.ahc(H, m.R, kmesh, EF, eta=0.05).cpu().numpy()
+    Smx = kubo.ahc(H, m.R, kmesh, EF, eta=0.05, precision="mixed").cpu().numpy()
+    assert rel_err(Smx, S64) < REL_MIXED, rel_err(Smx, S64)
