@@ -18,7 +18,7 @@ OBJDIR = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libkubo.so")
 
-SOURCES = ["k_prep.cu", "k_fourier.cu", "k_fourier_tc.cu", "k_fourier_sep.cu", "k_eigh.cu", "k_tridiag_df.cu", "k_berry.cu", "k_ksum.cu",
+SOURCES = ["k_prep.cu", "k_fourier.cu", "k_fourier_tc.cu", "k_fourier_sep.cu", "k_eigh.cu", "k_eigh_df.cu", "k_berry.cu", "k_ksum.cu",
            "k_grad.cu",
            "k_large.cu", "kubo_api.cu",
            "kubo_noalloc.cu"]

@@ -1,0 +1,552 @@
+// Step (2) for the MIXED mode: the Householder tridiagonalisation H = Q T_c Q^dagger and the
+// implicit QL eigenvalue iteration of the FP64 eigensolver in double-float arithmetic.
+//
+// On GB300 a warp FP64 instruction holds the SM's FP64 pipe for 16 cycles, 64 times the cost
+// of an FP32 one, and the FP64 reduction is bound by that pipe.  Here every element of the
+// packed lower triangle, the reflector v, p = tau A v and w are unevaluated pairs (hi, lo) of
+// FP32 numbers with hi + lo the value and |lo| <= ulp(hi) / 2: products by FMA-exact
+// TwoProd, sums by Knuth's TwoSum, so each operation keeps about 46 bits (relative error
+// ~2^-46, against 2^-53 for FP64).  The symv and the rank-2 update (16/3 W^3 of the
+// reduction's flops) run on the FP32 pipe; the scalar Householder step of each column
+// (norm, square roots, tau) and the outputs stay FP64.  The reduction's backward error is
+// then ~W 2^-46 ||H|| (1e-12 ||H|| at W = 64): the eigenvalues move by that much, four orders
+// below what the FP32 rotations and eta ~ 1e-3 of the MIXED mode resolve.  Same algorithm,
+// same outputs (FP64 d, |e|, phases, tau, reflectors) as the FP64 kernel in k_eigh.cu.
+#include "kubo_internal.cuh"
+
+namespace kubo {
+
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ int tri(int r, int c) { return (r * (r + 1) >> 1) + c; }
+
+// exact s + e = a + b (Knuth's TwoSum; no ordering of |a|, |b| needed)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// (h, l) normalised from s + e with |s| >= |e| (Dekker's Fast2Sum)
+__device__ __forceinline__ void fast_two_sum(float s, float e, float& h, float& l) {
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// accumulator (sh, sl) += (xh + xl)(yh + yl); sl stays unnormalised until the end.  The
+// dropped xl yl is below 2^-48 of the product.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float xh, float xl, float yh,
+                                       float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float q = fmaf(xh, yh, -p);   // the rounding error of p, exactly
+  q = fmaf(xh, yl, q);
+  q = fmaf(xl, yh, q);
+  float s, e;
+  two_sum(sh, p, s, e);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, q));
+}
+
+__device__ __forceinline__ void df_norm(float& h, float& l) { fast_two_sum(h, l, h, l); }
+
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// The conversions between FP64 and FP32 pairs run on the FP64 pipe; for the bulk input and
+// output they are done on the bit patterns instead (integer pipe), with the FP64 conversion
+// only for exponents outside a safe range (zero included on the input side).
+// x = hi + lo with hi = x truncated to 24 significant bits and lo the remaining 29 bits
+// rounded to FP32 (|x - hi - lo| <= 2^-48 |x|).
+__device__ __forceinline__ float2 df_split_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex < 1023 - 70 || ex > 1023 + 70) return df_split(x);
+  const uint32_t sgn = (uint32_t)(b >> 63) << 31;
+  const uint32_t hb = sgn | ((uint32_t)(ex - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
+  // the low 29 bits are worth low29 2^(ex - 1075); 2^(ex - 1075) = 2^(ex - 1023 - 52) is a
+  // normal FP32 for the exponents admitted above
+  const float scale = __uint_as_float((uint32_t)(ex - 1023 - 52 + 127) << 23);
+  const float lo = __uint2float_rn((uint32_t)(b & 0x1FFFFFFFu)) * scale;
+  return make_float2(__uint_as_float(hb), sgn ? -lo : lo);
+}
+
+// exact FP32 -> FP64 widening on the bit pattern (zero exactly; subnormals, inf and NaN by
+// the FP64 conversion)
+__device__ __forceinline__ double widen_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  if (ex == 0 || ex == 0xFFu) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                          ((unsigned long long)(ex + 896) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double df_val(float h, float l) { return widen_bits(h) + widen_bits(l); }
+
+// complex element as float4 (re_h, re_l, im_h, im_l)
+__device__ __forceinline__ float4 cdf_split(double re, double im) {
+  const float2 a = df_split_bits(re), b = df_split_bits(im);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// a += x * y (complex double-float; conjugate x when CX)
+template <bool CX>
+__device__ __forceinline__ void cdf_mac(float4& a, const float4& x, const float4& y) {
+  // re += x.re y.re -/+ x.im y.im ; im += x.re y.im +/- x.im y.re
+  df_mac(a.x, a.y, x.x, x.y, y.x, y.y);
+  if (CX) df_mac(a.x, a.y, x.z, x.w, y.z, y.w);
+  else df_mac(a.x, a.y, -x.z, -x.w, y.z, y.w);
+  df_mac(a.z, a.w, x.x, x.y, y.z, y.w);
+  if (CX) df_mac(a.z, a.w, -x.z, -x.w, y.x, y.y);
+  else df_mac(a.z, a.w, x.z, x.w, y.x, y.y);
+}
+
+__device__ __forceinline__ float4 cdf_norm(float4 a) {
+  df_norm(a.x, a.y);
+  df_norm(a.z, a.w);
+  return a;
+}
+
+// double-float warp sum: exact TwoSum of the high parts, low parts added
+__device__ __forceinline__ void warp_sum_df(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, oh, s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(ol, e));
+  }
+}
+
+// Householder step j's scalar part on warp 0: the norm of column j below the sub-diagonal,
+// the reflector H = I - tau v v^H with v = x - beta e1, beta = -e^{i arg alpha} |x|,
+// v0 = alpha + e^{i arg alpha} |x|, tau = 1 / (|x| (|x| + |alpha|)) (FP64 on lane 0), and the
+// copy of v into vdst.  Column j must be final (its last update done by this warp).
+__device__ __forceinline__ void householder_warp0(float4* A, int W, int j, float4* vdst,
+                                                  double2* be, double* tb, float2* s_tdf,
+                                                  int* s_act, int lane) {
+  const int o = j + 1, m = W - 1 - j;
+  float sh = 0.f, sl = 0.f;
+  for (int r = o + 1 + lane; r < W; r += 32) {
+    const float4 x = A[tri(r, j)];
+    df_mac(sh, sl, x.x, x.y, x.x, x.y);
+    df_mac(sh, sl, x.z, x.w, x.z, x.w);
+  }
+  warp_sum_df(sh, sl);
+  if (lane == 0) {
+    const double s2 = df_val(sh, sl);
+    const float4 a4 = A[tri(o, j)];
+    const double alx = df_val(a4.x, a4.y), aly = df_val(a4.z, a4.w);
+    double tau = 0.0;
+    double2 beta = make_double2(alx, aly);
+    if (s2 > 0.0) {
+      const double aa2 = fma(alx, alx, aly * aly);
+      const double n2 = aa2 + s2;
+      const double nrm = n2 * rsqrt(n2);
+      double pr = 1.0, pi = 0.0, aa = 0.0;
+      if (aa2 > 0.0) {
+        const double ra = rsqrt(aa2);
+        aa = aa2 * ra;
+        pr = alx * ra;
+        pi = aly * ra;
+      }
+      beta = make_double2(-pr * nrm, -pi * nrm);
+      A[tri(o, j)] = cdf_split(fma(pr, nrm, alx), fma(pi, nrm, aly));
+      tau = 1.0 / (nrm * (nrm + aa));
+    }
+    *s_tdf = df_split(tau);
+    *s_act = tau != 0.0;
+    be[j] = beta;
+    tb[j] = tau;
+  }
+  __syncwarp();
+  for (int r = lane; r < m; r += 32) vdst[r] = A[tri(o + r, j)];
+}
+
+// a -= vr conj(wc) + wr conj(vc) (the rank-2 update of one lower element; diag: real)
+__device__ __forceinline__ void rank2_elem(float4& a, const float4& vr, const float4& wr,
+                                           const float4& vc, const float4& wc, bool diag) {
+  df_mac(a.x, a.y, -vr.x, -vr.y, wc.x, wc.y);
+  df_mac(a.x, a.y, -vr.z, -vr.w, wc.z, wc.w);
+  df_mac(a.x, a.y, -wr.x, -wr.y, vc.x, vc.y);
+  df_mac(a.x, a.y, -wr.z, -wr.w, vc.z, vc.w);
+  df_norm(a.x, a.y);
+  if (diag) {
+    a.z = 0.f;
+    a.w = 0.f;
+  } else {
+    // im -= vr.im wc.re - vr.re wc.im + wr.im vc.re - wr.re vc.im
+    df_mac(a.z, a.w, -vr.z, -vr.w, wc.x, wc.y);
+    df_mac(a.z, a.w, vr.x, vr.y, wc.z, wc.w);
+    df_mac(a.z, a.w, -wr.z, -wr.w, vc.x, vc.y);
+    df_mac(a.z, a.w, wr.x, wr.y, vc.z, vc.w);
+    df_norm(a.z, a.w);
+  }
+}
+
+// Packed rows of leading dimension ld (the [H | dxH | dyH] rows of the tensor-core Fourier
+// sum).  Shared memory: the lower triangle packed by rows (element (r, c <= r) at
+// r (r + 1) / 2 + c) as complex double-float, two reflector buffers, p / w, the symv
+// partials.  Per column step three block barriers: after the symv partials, after w, and
+// after the rank-2 update, during which warp 0 first finishes the next column and prepares
+// the next reflector (so the serial Householder step overlaps the other warps' update).
+__global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restrict__ Hp,
+                                                           int64_t ld, int W, EighBufs b) {
+  extern __shared__ float4 sm4[];
+  float4* A = sm4;                                  // W (W + 1) / 2
+  float4* vbuf = A + (size_t)W * (W + 1) / 2;       // [2][W] reflectors of even / odd steps
+  float4* pb = vbuf + 2 * W;                        // [W] p, then w
+  float4* sp = pb + W;                              // [NT] symv partial sums
+  double2* be = reinterpret_cast<double2*>(sp + NT);   // [W] complex sub-diagonal beta_i
+  double* tb = reinterpret_cast<double*>(be + W);      // [W] tau_i
+  // tau as an FP32 pair and tau != 0, by step parity (warp 0 writes step i + 1's while the
+  // other warps may still read step i's)
+  __shared__ float2 s_tdf[2];
+  __shared__ int s_act[2];
+  __shared__ float2 s_vp[4];  // per-warp parts of Re(v^H p) (warps 0..3)
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t k = blockIdx.x;
+  const double* P = Hp + (size_t)k * ld;
+
+  for (int idx = t; idx < W * (W + 1) / 2; idx += NT) {
+    int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while (tri(r, 0) > idx) --r;
+    while (tri(r + 1, 0) <= idx) ++r;
+    const int c = idx - tri(r, 0);
+    A[idx] = r == c ? cdf_split(P[r * W + r], 0.0)
+                    : cdf_split(P[c * W + r], -P[r * W + c]);   // conj(A_cr)
+  }
+  __syncthreads();
+  if (W > 2 && warp == 0) householder_warp0(A, W, 0, vbuf, be, tb, &s_tdf[0], &s_act[0], lane);
+  __syncthreads();
+
+  for (int i = 0; i < W - 2; ++i) {
+    const int o = i + 1;       // first row of the trailing block
+    const int m = W - 1 - i;   // its size
+    const float4* vb = vbuf + (i & 1) * W;
+    float4* vnext = vbuf + ((i + 1) & 1) * W;
+    const bool next = i + 1 < W - 2;
+    const int ph = i & 1, nph = ph ^ 1;
+    if (!s_act[ph]) {
+      // no reflection: the trailing block is unchanged; prepare the next step
+      if (next && warp == 0) householder_warp0(A, W, o, vnext, be, tb, &s_tdf[nph], &s_act[nph], lane);
+      __syncthreads();
+      continue;
+    }
+    // p = tau A22 v, spread densely: thread t takes row r = t mod m and the columns
+    // c = part, part + P, ... (part = t / m, P = NT / m); the P partials of a row are added
+    // in part order.  Mirrored elements (c > r) are conjugated by flipping the sign bits of
+    // both imaginary halves.
+    {
+      const int Pp = NT / m;
+      const int r = t % m, part = t / m;
+      if (part < Pp) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int rowb = tri(o + r, o);
+        for (int c = part; c < m; c += Pp) {
+          const bool up = c > r;
+          float4 a = A[up ? tri(o + c, o + r) : rowb + c];
+          if (up) {
+            a.z = -a.z;
+            a.w = -a.w;
+          }
+          cdf_mac<false>(acc, a, vb[c]);
+        }
+        sp[part * m + r] = acc;
+      }
+    }
+    __syncthreads();
+    // warps 0..3 (m <= 127 rows): p_t = tau sum of the partials, K = tau Re(v^H p) / 2,
+    // w_t = p_t - K v_t
+    if (t < 128) {
+      const int Pp = NT / m;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = make_float4(0.f, 0.f, 0.f, 0.f);
+      float dh = 0.f, dl = 0.f;
+      if (t < m) {
+        float4 s = sp[t];
+        for (int q = 1; q < Pp; ++q) {
+          const float4 u = sp[q * m + t];
+          float e;
+          two_sum(s.x, u.x, s.x, e);
+          s.y = __fadd_rn(s.y, __fadd_rn(u.y, e));
+          two_sum(s.z, u.z, s.z, e);
+          s.w = __fadd_rn(s.w, __fadd_rn(u.w, e));
+        }
+        s = cdf_norm(s);
+        const float2 tdf = s_tdf[ph];
+        df_mac(p.x, p.y, tdf.x, tdf.y, s.x, s.y);
+        df_mac(p.z, p.w, tdf.x, tdf.y, s.z, s.w);
+        p = cdf_norm(p);
+        v = vb[t];
+        df_mac(dh, dl, v.x, v.y, p.x, p.y);
+        df_mac(dh, dl, v.z, v.w, p.z, p.w);
+      }
+      warp_sum_df(dh, dl);
+      if (lane == 0) s_vp[warp] = make_float2(dh, dl);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (t < m) {
+        float vh = s_vp[0].x, vl = s_vp[0].y;
+        for (int q = 1; q < 4; ++q) {
+          float e;
+          two_sum(vh, s_vp[q].x, vh, e);
+          vl = __fadd_rn(vl, __fadd_rn(s_vp[q].y, e));
+        }
+        // K = tau (vh + vl) / 2 as an FP32 pair (the factor 1/2 is exact)
+        const float2 tdf = s_tdf[ph];
+        float Kh = 0.f, Kl = 0.f;
+        df_mac(Kh, Kl, 0.5f * tdf.x, 0.5f * tdf.y, vh, vl);
+        df_norm(Kh, Kl);
+        const float2 Kd = make_float2(Kh, Kl);
+        df_mac(p.x, p.y, -Kd.x, -Kd.y, v.x, v.y);
+        df_mac(p.z, p.w, -Kd.x, -Kd.y, v.z, v.w);
+        pb[t] = cdf_norm(p);
+      }
+    }
+    __syncthreads();
+    // A22 <- A22 - v w^H - w v^H on the lower triangle (c <= r).  Warp 0: column 0 of the
+    // block (it becomes column o of A, the next step's), then the next Householder step;
+    // warps 1..: the columns 1 .. m-1 (a triangle of order m - 1).
+    if (warp == 0) {
+      const float4 v0 = vb[0], w0 = pb[0];
+      for (int r = lane; r < m; r += 32) {
+        float4 a = A[tri(o + r, o)];
+        rank2_elem(a, vb[r], pb[r], v0, w0, r == 0);
+        A[tri(o + r, o)] = a;
+      }
+      __syncwarp();
+      if (next) householder_warp0(A, W, o, vnext, be, tb, &s_tdf[nph], &s_act[nph], lane);
+    } else {
+      const int n1 = m - 1;
+      const int ntri = n1 * (n1 + 1) / 2;
+      for (int idx = t - 32; idx < ntri; idx += NT - 32) {
+        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+        while (r * (r + 1) / 2 > idx) --r;
+        while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+        const int c = idx - r * (r + 1) / 2;
+        // element (r + 1, c + 1) of the trailing block
+        float4 a = A[tri(o + r + 1, o + c + 1)];
+        rank2_elem(a, vb[r + 1], pb[r + 1], vb[c + 1], pb[c + 1], r == c);
+        A[tri(o + r + 1, o + c + 1)] = a;
+      }
+    }
+    __syncthreads();
+  }
+
+  // outputs (FP64): d, |e|, phases D, tau, reflectors
+  double* dout = b.d + k * W;
+  double* eout = b.e + k * W;
+  double2* phout = b.phase + k * W;
+  double* tout = b.tau + k * W;
+  if (t == 0 && W >= 2) {
+    const float4 a = A[tri(W - 1, W - 2)];
+    be[W - 2] = make_double2(df_val(a.x, a.y), df_val(a.z, a.w));
+  }
+  __syncthreads();
+  double2* ub = reinterpret_cast<double2*>(vbuf);   // unit phases (the reflector buffers are free)
+  for (int j = t; j + 1 < W; j += NT) {
+    const double2 bj = be[j];
+    const double a2 = fma(bj.x, bj.x, bj.y * bj.y);
+    double a = 0.0;
+    double2 u = make_double2(1.0, 0.0);
+    if (a2 > 0.0) {
+      const double ra = rsqrt(a2);
+      a = a2 * ra;
+      u = make_double2(bj.x * ra, bj.y * ra);
+    }
+    eout[j] = a;
+    ub[j] = u;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double2 D = make_double2(1.0, 0.0);
+    phout[0] = D;
+    for (int j = 0; j + 1 < W; ++j) {
+      D = cmul(D, ub[j]);
+      phout[j + 1] = D;
+    }
+    eout[W - 1] = 0.0;
+  }
+  for (int j = t; j < W; j += NT) {
+    const float4 a = A[tri(j, j)];
+    dout[j] = df_val(a.x, a.y);
+    tout[j] = j < W - 2 ? tb[j] : 0.0;
+  }
+  double2* rout = b.refl + (size_t)k * W * W;
+  for (int idx = t; idx < W * W; idx += NT) {
+    const int r = idx / W, c = idx % W;
+    double2 v = make_double2(0.0, 0.0);
+    if (r > c) {
+      const float4 a = A[tri(r, c)];
+      v = make_double2(df_val(a.x, a.y), df_val(a.z, a.w));
+    }
+    rout[idx] = v;
+  }
+}
+
+// ------------------------------------------------------------------ QL in double-float
+// Scalar double-float operations (value h + l): results normalised, ~2^-46 relative.
+struct Df {
+  float h, l;
+};
+__device__ __forceinline__ Df dfv(float h, float l = 0.f) { return Df{h, l}; }
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  Df r;
+  fast_two_sum(s, e, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ Df df_neg(Df a) { return Df{-a.h, -a.l}; }
+__device__ __forceinline__ Df df_sub(Df a, Df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ Df df_mul(Df a, Df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  Df r;
+  fast_two_sum(p, e, r.h, r.l);
+  return r;
+}
+// a * b + c
+__device__ __forceinline__ Df df_fma(Df a, Df b, Df c) { return df_add(df_mul(a, b), c); }
+// 1 / sqrt(a), a > 0: the FP32 estimate and one Newton step, y + y (1 - a y^2) / 2, whose
+// correction is ~2^-22 of y and needs FP32 precision only
+__device__ __forceinline__ Df df_rsqrt(Df a) {
+  const float y = rsqrtf(a.h);
+  const float y2 = __fmul_rn(y, y);
+  const Df t = df_mul(a, Df{y2, fmaf(y, y, -y2)});
+  const float r = __fadd_rn(__fsub_rn(1.0f, t.h), -t.l);
+  Df out;
+  fast_two_sum(y, 0.5f * y * r, out.h, out.l);
+  return out;
+}
+// sqrt(a), a >= 0: y + (a - y^2) / (2 y)
+__device__ __forceinline__ Df df_sqrt(Df a) {
+  if (!(a.h > 0.f)) return Df{0.f, 0.f};
+  const float y = sqrtf(a.h);
+  const float y2 = __fmul_rn(y, y);
+  const Df d = df_sub(a, Df{y2, fmaf(y, y, -y2)});
+  Df out;
+  fast_two_sum(y, d.h / (2.0f * y), out.h, out.l);
+  return out;
+}
+// a / b: q1 = a / b in FP32, then the remainder's quotient
+__device__ __forceinline__ Df df_div(Df a, Df b) {
+  const float q1 = a.h / b.h;
+  const Df r = df_sub(a, df_mul(b, Df{q1, 0.f}));
+  Df out;
+  fast_two_sum(q1, r.h / b.h, out.h, out.l);
+  return out;
+}
+
+// Eigenvalues of the real symmetric tridiagonal T (FP64 d, |e|) by implicit QL with Wilkinson
+// shifts, one k-point per lane, in double-float: the same chase as the FP64 kernel, with the
+// deflation test |e_m| <= 2^-44 (|d_m| + |d_m+1|) matched to the pair precision.  d and e live
+// lane-interleaved in shared memory as [W][32] pairs.
+__global__ void __launch_bounds__(32) ql_df_kernel(int W, int n, EighBufs b, DevStatus* st) {
+  extern __shared__ float2 qsm2[];
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  float2* D = qsm2 + lane;
+  float2* E = D + (size_t)W * 32;
+  if (k >= n) return;
+  for (int i = 0; i < W; ++i) {
+    D[i * 32] = df_split_bits(b.d[(size_t)k * W + i]);
+    E[i * 32] = df_split_bits(b.e[(size_t)k * W + i]);
+  }
+  auto ld = [&](const float2* a, int i) { const float2 v = a[i * 32]; return Df{v.x, v.y}; };
+  auto st2 = [&](float2* a, int i, Df v) { a[i * 32] = make_float2(v.h, v.l); };
+  bool fail = false;
+  const float eps = 0x1p-44f;
+  for (int l = 0; l < W && !fail; ++l) {
+    int iter = 0;
+    while (true) {
+      int m = l;
+      for (; m < W - 1; ++m) {
+        const float dd = fabsf(D[m * 32].x) + fabsf(D[(m + 1) * 32].x);
+        if (fabsf(E[m * 32].x) <= eps * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 60) { fail = true; break; }
+      // Wilkinson shift from the leading 2x2 of the block, then chase up from the bottom
+      const Df dl = ld(D, l), el = ld(E, l);
+      Df g = df_div(df_sub(ld(D, l + 1), dl), Df{2.0f * el.h, 2.0f * el.l});
+      const Df r0 = df_sqrt(df_fma(g, g, dfv(1.0f)));
+      g = df_add(df_sub(ld(D, m), dl), df_div(el, df_add(g, g.h >= 0.f ? r0 : df_neg(r0))));
+      Df s = dfv(1.0f), c = dfv(1.0f), p = dfv(0.0f);
+      bool early = false;
+      for (int i = m - 1; i >= l; --i) {
+        const Df ei = ld(E, i);
+        const Df f = df_mul(s, ei), bb = df_mul(c, ei);
+        const Df r2 = df_fma(f, f, df_mul(g, g));
+        if (r2.h == 0.f) {   // split: the chase stops here
+          st2(E, i + 1, dfv(0.f));
+          st2(D, i + 1, df_sub(ld(D, i + 1), p));
+          st2(E, m, dfv(0.f));
+          early = true;
+          break;
+        }
+        const Df ir = df_rsqrt(r2);
+        st2(E, i + 1, df_mul(r2, ir));
+        s = df_mul(f, ir);
+        c = df_mul(g, ir);
+        const Df gi = df_sub(ld(D, i + 1), p);
+        const Df cb = df_mul(c, bb);
+        const Df rr = df_fma(df_sub(ld(D, i), gi), s, df_add(cb, cb));
+        p = df_mul(s, rr);
+        st2(D, i + 1, df_add(gi, p));
+        g = df_sub(df_mul(c, rr), bb);
+      }
+      if (early) continue;
+      st2(D, l, df_sub(ld(D, l), p));
+      st2(E, l, g);
+      st2(E, m, dfv(0.f));
+    }
+  }
+  for (int i = 0; i < W; ++i) {
+    const float2 v = D[i * 32];
+    b.lam[(size_t)k * W + i] = df_val(v.x, v.y);
+  }
+  if (fail) atomicOr(&st->bits, ST_NO_CONVERGENCE);
+}
+
+}  // namespace
+
+size_t tridiag_df_smem(int W) {
+  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W + NT) * sizeof(float4) +
+         (size_t)W * (sizeof(double2) + sizeof(double));
+}
+
+cudaError_t launch_tridiag_df_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
+                                   cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t sm = tridiag_df_smem(W);
+  cudaError_t e = cudaFuncSetAttribute(tridiag_df_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  tridiag_df_kernel<<<n, NT, sm, s>>>(Hp, ld, W, b);
+  return cudaGetLastError();
+}
+
+size_t ql_df_smem(int W) { return (size_t)2 * W * 32 * sizeof(float2); }
+
+cudaError_t launch_ql_df(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t sm = ql_df_smem(W);
+  cudaError_t e = cudaFuncSetAttribute(ql_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  ql_df_kernel<<<(n + 31) / 32, 32, sm, s>>>(W, n, b, st);
+  return cudaGetLastError();
+}
+
+}  // namespace kubo

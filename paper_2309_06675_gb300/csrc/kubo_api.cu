@@ -476,7 +476,8 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0));
   }
   {
-    // MIXED: the reduction in double-float on the FP32 pipe (FP64-pipe-bound otherwise)
+    // MIXED: the reduction and the QL iteration in double-float on the FP32 pipe (both are
+    // FP64-pipe-bound otherwise)
     StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
     if (p.precision == KUBO_MIXED)
       KCHECK(launch_tridiag_df_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
@@ -485,7 +486,10 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   }
   {
     StageTimer tm(c, KUBO_STAGE_QL, 1);
-    KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
+    if (p.precision == KUBO_MIXED)
+      KCHECK(launch_ql_df(p.W, kl.n, eb, st, c.s));
+    else
+      KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
   }
   const size_t WW = (size_t)p.W * p.W;
   if (f32_rotation(p.precision) && p.W <= SMALL_W_MAX) {
