@@ -12,6 +12,8 @@
 // then ~W 2^-46 ||H|| (1e-12 ||H|| at W = 64): the eigenvalues move by that much, four orders
 // below what the FP32 rotations and eta ~ 1e-3 of the MIXED mode resolve.  Same algorithm,
 // same outputs (FP64 d, |e|, phases, tau, reflectors) as the FP64 kernel in k_eigh.cu.
+#include <algorithm>
+
 #include "kubo_internal.cuh"
 
 namespace kubo {
@@ -429,22 +431,32 @@ __device__ __forceinline__ Df df_rsqrt(Df a) {
   fast_two_sum(y, 0.5f * y * r, out.h, out.l);
   return out;
 }
-// sqrt(a), a >= 0: y + (a - y^2) / (2 y)
+// sqrt(a), a >= 0: y + (a - y^2) / (2 y) from an approximate FP32 root (the correction
+// absorbs its few-ulp error)
 __device__ __forceinline__ Df df_sqrt(Df a) {
   if (!(a.h > 0.f)) return Df{0.f, 0.f};
-  const float y = sqrtf(a.h);
+  const float ry = rsqrtf(a.h);
+  const float y = a.h * ry;
   const float y2 = __fmul_rn(y, y);
   const Df d = df_sub(a, Df{y2, fmaf(y, y, -y2)});
   Df out;
-  fast_two_sum(y, d.h / (2.0f * y), out.h, out.l);
+  fast_two_sum(y, d.h * (0.5f * ry), out.h, out.l);
   return out;
 }
-// a / b: q1 = a / b in FP32, then the remainder's quotient
+// FP32 reciprocal estimate (one MUFU instruction, ~1 ulp)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// a / b: an approximate FP32 quotient q1 = a rcp(b), then the quotient of the remainder
+// a - q1 b (exact to 2^-46): ~2^-45 relative in all
 __device__ __forceinline__ Df df_div(Df a, Df b) {
-  const float q1 = a.h / b.h;
+  const float rb = rcp_approx(b.h);
+  const float q1 = a.h * rb;
   const Df r = df_sub(a, df_mul(b, Df{q1, 0.f}));
   Df out;
-  fast_two_sum(q1, r.h / b.h, out.h, out.l);
+  fast_two_sum(q1, r.h * rb, out.h, out.l);
   return out;
 }
 
@@ -519,6 +531,186 @@ __global__ void __launch_bounds__(32) ql_df_kernel(int W, int n, EighBufs b, Dev
   if (fail) atomicOr(&st->bits, ST_NO_CONVERGENCE);
 }
 
+// ------------------------------------------------------------------ inverse iteration in double-float
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// deterministic start vector in [0.5, 1.5) from an integer hash of (row, vector)
+__device__ __forceinline__ float iit_start_f(int i, int j) {
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return 0.5f + (float)(h >> 8) * (1.0f / 16777216.0f);
+}
+
+constexpr int IIT_DF_SOLVES = 3;
+
+// Eigenvectors of the tridiagonal T by inverse iteration, as the FP64 kernel (sort, clusters
+// closer than 1e-3 ||T||_1 on one thread, LU of T - lambda I with row interchanges, three
+// solves from a fixed pseudo-random start, modified Gram-Schmidt inside a cluster,
+// normalisation), in FP32 pairs: the solves' backward error ~2^-46 ||T|| sets the residual,
+// and the eigenvectors are accurate to ~2^-46 ||T|| / gap.  Coincident eigenvalues are
+// separated by 10 2^-46 ||T||_1.
+// Memory: each thread's iterate lives in shared memory ([W][ldt], lane-interleaved); the LU
+// factors go to the per-CTA global scratch (L2-resident) as three planes: reciprocal pivots,
+// multipliers and the first super-diagonal of U (the second, nonzero only on swapped rows, is
+// the next e of T).  Finished vectors are written to Z in FP64; Gram-Schmidt reads a
+// cluster's earlier vectors from there.
+__global__ void __launch_bounds__(128) iit_df_kernel(int W, int n, EighBufs b,
+                                                     double* __restrict__ Eout,
+                                                     double* __restrict__ Z,
+                                                     double* __restrict__ scratch) {
+  extern __shared__ float2 zsm[];               // [W][ldt] iterates
+  __shared__ float2 ws[128], dd[128], ee[128];
+  __shared__ int newc[128];
+  __shared__ float s_onenrm;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ldt = blockDim.x;
+  const size_t plane = (size_t)W * ldt;
+  float2* __restrict__ RP = reinterpret_cast<float2*>(scratch) + (size_t)blockIdx.x * 3 * plane;
+  float2* __restrict__ ML = RP + plane;   // multipliers
+  float2* __restrict__ U1 = ML + plane;   // first super-diagonal of U
+  float2* Zs = zsm + t;
+  auto ldf = [](const float2* a, size_t i) { const float2 v = a[i]; return Df{v.x, v.y}; };
+  auto sdf = [](float2* a, size_t i, Df v) { a[i] = make_float2(v.h, v.l); };
+  for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+    __syncthreads();   // the previous k-point's shared arrays are no longer read
+    const double* lk = b.lam + k * W;
+    if (t < W) {
+      const double lj = lk[t];
+      const unsigned long long kj = order_key(lj);
+      int rnk = 0;
+      for (int i = 0; i < W; ++i) {
+        const unsigned long long ki = order_key(lk[i]);
+        rnk += (ki < kj) || (ki == kj && i < t);
+      }
+      ws[rnk] = df_split_bits(lj);
+      Eout[k * W + rnk] = lj;
+      dd[t] = df_split_bits(b.d[k * W + t]);
+      ee[t] = df_split_bits(b.e[k * W + t]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float mx = 0.f;
+      for (int i = lane; i < W; i += 32)
+        mx = fmaxf(mx, fabsf(dd[i].x) + (i > 0 ? ee[i - 1].x : 0.f) + (i < W - 1 ? ee[i].x : 0.f));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) s_onenrm = mx > 0.f ? mx : 1.f;
+    }
+    __syncthreads();
+    const float onenrm = s_onenrm;
+    const float ortol = 1e-3f * onenrm, pertol = 10.0f * 0x1p-46f * onenrm;
+    const float tiny = 0x1p-46f * onenrm;
+    if (t < W) {
+      const Df gap = t > 0 ? df_sub(ldf(ws, t), ldf(ws, t - 1)) : Df{0.f, 0.f};
+      newc[t] = (t == 0) || (gap.h > ortol);
+    }
+    __syncthreads();
+
+    double* __restrict__ Zd = Z + (size_t)k * W * W;
+    const int j = t;
+    if (j < W && newc[j]) {
+      Df lprev = Df{0.f, 0.f};
+      for (int m = j; m < W && (m == j || !newc[m]); ++m) {
+        Df lam = ldf(ws, m);
+        if (m > j && df_sub(lam, lprev).h <= pertol) lam = df_add(lprev, Df{pertol, 0.f});
+        lprev = lam;
+        // ---- LU of T - lam I with row interchanges (the carried third entry of a row is
+        // always 0 after a step, so a row of U is (q0, q1, 0) or swapped (e_i, a, e_i+1))
+        unsigned long long piv0 = 0ull, piv1 = 0ull;   // row interchanges, bits 0..127
+        Df q0 = df_sub(ldf(dd, 0), lam), q1 = W > 1 ? ldf(ee, 0) : Df{0.f, 0.f};
+        for (int i = 0; i + 1 < W; ++i) {
+          const Df ei = ldf(ee, i);
+          const Df a = df_sub(ldf(dd, i + 1), lam);
+          const Df bb = i + 2 < W ? ldf(ee, i + 1) : Df{0.f, 0.f};
+          const size_t o = (size_t)i * ldt + t;
+          if (fabsf(q0.h) >= fabsf(ei.h)) {
+            if (q0.h == 0.f) q0 = Df{tiny, 0.f};
+            const Df r = df_div(Df{1.f, 0.f}, q0);
+            const Df mlt = df_mul(ei, r);
+            sdf(RP, o, r); sdf(ML, o, mlt); sdf(U1, o, q1);
+            q0 = df_sub(a, df_mul(mlt, q1));
+            q1 = bb;
+          } else {
+            const Df r = df_div(Df{1.f, 0.f}, ei);
+            const Df mlt = df_mul(q0, r);
+            sdf(RP, o, r); sdf(ML, o, mlt); sdf(U1, o, a);
+            if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64);
+            const Df n0 = df_sub(q1, df_mul(mlt, a));
+            q1 = df_neg(df_mul(mlt, bb));
+            q0 = n0;
+          }
+        }
+        if (q0.h == 0.f) q0 = Df{tiny, 0.f};
+        sdf(RP, (size_t)(W - 1) * ldt + t, df_div(Df{1.f, 0.f}, q0));
+        sdf(U1, (size_t)(W - 1) * ldt + t, Df{0.f, 0.f});
+        for (int i = 0; i < W; ++i) Zs[(size_t)i * ldt] = make_float2(iit_start_f(i, m), 0.f);
+        for (int it = 0; it < IIT_DF_SOLVES; ++it) {
+          // forward elimination L y = P b; the running row value is carried in registers
+          Df cur = ldf(Zs, 0);
+#pragma unroll 4
+          for (int i = 0; i + 1 < W; ++i) {
+            const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
+            const Df mlt = ldf(ML, (size_t)i * ldt + t);
+            const Df yn = ldf(Zs, (size_t)(i + 1) * ldt);
+            if (sw) {
+              sdf(Zs, (size_t)i * ldt, yn);
+              cur = df_sub(cur, df_mul(mlt, yn));
+            } else {
+              sdf(Zs, (size_t)i * ldt, cur);
+              cur = df_sub(yn, df_mul(mlt, cur));
+            }
+          }
+          sdf(Zs, (size_t)(W - 1) * ldt, cur);
+          // back substitution U x = y (U2 of row i: e_i+1 on swapped rows, else 0)
+          Df x1 = Df{0.f, 0.f}, x2 = Df{0.f, 0.f};
+#pragma unroll 4
+          for (int i = W - 1; i >= 0; --i) {
+            const bool sw = i + 1 < W && (i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull));
+            const size_t o = (size_t)i * ldt + t;
+            const Df y = ldf(Zs, (size_t)i * ldt);
+            Df num = df_sub(y, df_mul(ldf(U1, o), x1));
+            if (sw && i + 2 < W) num = df_sub(num, df_mul(ldf(ee, i + 1), x2));
+            const Df xi = df_mul(num, ldf(RP, o));
+            sdf(Zs, (size_t)i * ldt, xi);
+            x2 = x1;
+            x1 = xi;
+          }
+          for (int q = j; q < m; ++q) {   // earlier vectors of the cluster (FP64 in Z)
+            float ch = 0.f, cl = 0.f;
+            for (int i = 0; i < W; ++i) {
+              const float2 zq = df_split_bits(Zd[(size_t)i * W + q]);
+              const Df zm = ldf(Zs, (size_t)i * ldt);
+              df_mac(ch, cl, zq.x, zq.y, zm.h, zm.l);
+            }
+            Df c;
+            fast_two_sum(ch, cl, c.h, c.l);
+            for (int i = 0; i < W; ++i) {
+              const float2 zq = df_split_bits(Zd[(size_t)i * W + q]);
+              sdf(Zs, (size_t)i * ldt, df_sub(ldf(Zs, (size_t)i * ldt), df_mul(c, Df{zq.x, zq.y})));
+            }
+          }
+          float sh = 0.f, sl = 0.f;
+          for (int i = 0; i < W; ++i) {
+            const Df u = ldf(Zs, (size_t)i * ldt);
+            df_mac(sh, sl, u.h, u.l, u.h, u.l);
+          }
+          Df s2;
+          fast_two_sum(sh, sl, s2.h, s2.l);
+          const Df inv = df_rsqrt(s2);
+          for (int i = 0; i < W; ++i)
+            sdf(Zs, (size_t)i * ldt, df_mul(ldf(Zs, (size_t)i * ldt), inv));
+        }
+        for (int i = 0; i < W; ++i) {
+          const float2 v = Zs[(size_t)i * ldt];
+          Zd[(size_t)i * W + m] = df_val(v.x, v.y);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t tridiag_df_smem(int W) {
@@ -546,6 +738,29 @@ cudaError_t launch_ql_df(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s
                                        (int)sm);
   if (e != cudaSuccess) return e;
   ql_df_kernel<<<(n + 31) / 32, 32, sm, s>>>(W, n, b, st);
+  return cudaGetLastError();
+}
+
+// persistent CTAs of the double-float inverse iteration: as many per SM as the iterate
+// arrays (W x ldt pairs of shared memory per CTA) allow; each uses 3 W ldt pairs of the scratch
+int iit_df_ctas(int W) {
+  const int ldt = (W + 31) / 32 * 32;
+  const size_t sm = (size_t)W * ldt * sizeof(float2) + 4 * 1024;
+  return 152 * (int)std::max<size_t>(1, std::min<size_t>(16, (200 * 1024) / sm));
+}
+
+cudaError_t launch_iit_df(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
+                          int slots, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > 128 || slots < 1 || Z == nullptr) return cudaErrorInvalidValue;
+  const int ldt = (W + 31) / 32 * 32;
+  const size_t sm = (size_t)W * ldt * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(iit_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  // the FP64 scratch of `slots` CTAs (4 planes each) holds at least as many of these (3)
+  const int grid = std::min(std::min(n, slots), iit_df_ctas(W));
+  iit_df_kernel<<<grid, ldt, sm, s>>>(W, n, b, E, Z, scratch);
   return cudaGetLastError();
 }
 

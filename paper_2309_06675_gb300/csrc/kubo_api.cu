@@ -426,7 +426,9 @@ cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, do
   const Plan& p = c.p;
   if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s, p.pad);
   double* Z = U ? c.at<double>(p.o_L) : nullptr;
-  cudaError_t e = launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
+  cudaError_t e = Z && p.precision == KUBO_MIXED
+                      ? launch_iit_df(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s)
+                      : launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
   if (e != cudaSuccess || !U) return e;
   return launch_reflect_large(p.W, n, eb, Z, U, f32u, c.s);
 }
@@ -498,7 +500,10 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     double* Z = reinterpret_cast<double*>(U);
     {
       StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-      KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
+      if (p.precision == KUBO_MIXED)
+        KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
+      else
+        KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
     if (p.rot_tc)
@@ -545,7 +550,10 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
     double* Z = reinterpret_cast<double*>(U);
     {
       StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-      KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
+      if (p.precision == KUBO_MIXED)
+        KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
+      else
+        KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
     if (p.rot_tc)

@@ -129,6 +129,10 @@ cudaError_t launch_tridiag_df_rows(const double* Hp, int64_t ld, int W, int n, E
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
 // the same QL iteration in double-float (MIXED mode; FP64 eigenvalues out)
 cudaError_t launch_ql_df(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s);
+// eigenvectors of T by inverse iteration in double-float (MIXED mode; same layout, scratch and
+// outputs as launch_iit, Z required)
+cudaError_t launch_iit_df(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
+                          int slots, cudaStream_t s);
 cudaError_t launch_backtransform(int W, int n, EighBufs b, double* E, double2* U,
                                  cudaStream_t s, int pad = 1);
 
