@@ -127,6 +127,72 @@ __device__ __forceinline__ void warp_sum_df(float& h, float& l) {
   }
 }
 
+// Scalar double-float operations (value h + l): results normalised, ~2^-46 relative.
+struct Df {
+  float h, l;
+};
+__device__ __forceinline__ Df dfv(float h, float l = 0.f) { return Df{h, l}; }
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  Df r;
+  fast_two_sum(s, e, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ Df df_neg(Df a) { return Df{-a.h, -a.l}; }
+__device__ __forceinline__ Df df_sub(Df a, Df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ Df df_mul(Df a, Df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  Df r;
+  fast_two_sum(p, e, r.h, r.l);
+  return r;
+}
+// a * b + c
+__device__ __forceinline__ Df df_fma(Df a, Df b, Df c) { return df_add(df_mul(a, b), c); }
+// 1 / sqrt(a), a > 0: the FP32 estimate and one Newton step, y + y (1 - a y^2) / 2, whose
+// correction is ~2^-22 of y and needs FP32 precision only
+__device__ __forceinline__ Df df_rsqrt(Df a) {
+  const float y = rsqrtf(a.h);
+  const float y2 = __fmul_rn(y, y);
+  const Df t = df_mul(a, Df{y2, fmaf(y, y, -y2)});
+  const float r = __fadd_rn(__fsub_rn(1.0f, t.h), -t.l);
+  Df out;
+  fast_two_sum(y, 0.5f * y * r, out.h, out.l);
+  return out;
+}
+// sqrt(a), a >= 0: y + (a - y^2) / (2 y) from an approximate FP32 root (the correction
+// absorbs its few-ulp error)
+__device__ __forceinline__ Df df_sqrt(Df a) {
+  if (!(a.h > 0.f)) return Df{0.f, 0.f};
+  const float ry = rsqrtf(a.h);
+  const float y = a.h * ry;
+  const float y2 = __fmul_rn(y, y);
+  const Df d = df_sub(a, Df{y2, fmaf(y, y, -y2)});
+  Df out;
+  fast_two_sum(y, d.h * (0.5f * ry), out.h, out.l);
+  return out;
+}
+// FP32 reciprocal estimate (one MUFU instruction, ~1 ulp)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// a / b: an approximate FP32 quotient q1 = a rcp(b), then the quotient of the remainder
+// a - q1 b (exact to 2^-46): ~2^-45 relative in all
+__device__ __forceinline__ Df df_div(Df a, Df b) {
+  const float rb = rcp_approx(b.h);
+  const float q1 = a.h * rb;
+  const Df r = df_sub(a, df_mul(b, Df{q1, 0.f}));
+  Df out;
+  fast_two_sum(q1, r.h * rb, out.h, out.l);
+  return out;
+}
+
 // Householder step j's scalar part on warp 0: the norm of column j below the sub-diagonal,
 // the reflector H = I - tau v v^H with v = x - beta e1, beta = -e^{i arg alpha} |x|,
 // v0 = alpha + e^{i arg alpha} |x|, tau = 1 / (|x| (|x| + |alpha|)) (FP64 on lane 0), and the
@@ -143,30 +209,33 @@ __device__ __forceinline__ void householder_warp0(float4* A, int W, int j, float
   }
   warp_sum_df(sh, sl);
   if (lane == 0) {
-    const double s2 = df_val(sh, sl);
+    // in FP32 pairs: the FP64 pipe would serialise this lane behind 16-cycle slots
+    Df s2;
+    fast_two_sum(sh, sl, s2.h, s2.l);
     const float4 a4 = A[tri(o, j)];
-    const double alx = df_val(a4.x, a4.y), aly = df_val(a4.z, a4.w);
-    double tau = 0.0;
-    double2 beta = make_double2(alx, aly);
-    if (s2 > 0.0) {
-      const double aa2 = fma(alx, alx, aly * aly);
-      const double n2 = aa2 + s2;
-      const double nrm = n2 * rsqrt(n2);
-      double pr = 1.0, pi = 0.0, aa = 0.0;
-      if (aa2 > 0.0) {
-        const double ra = rsqrt(aa2);
-        aa = aa2 * ra;
-        pr = alx * ra;
-        pi = aly * ra;
+    const Df alx = Df{a4.x, a4.y}, aly = Df{a4.z, a4.w};
+    Df tau = Df{0.f, 0.f};
+    Df bx = alx, by = aly;   // beta
+    if (s2.h > 0.f) {
+      const Df aa2 = df_fma(alx, alx, df_mul(aly, aly));
+      const Df nrm = df_sqrt(df_add(aa2, s2));
+      Df pr = Df{1.f, 0.f}, pi = Df{0.f, 0.f}, aa = Df{0.f, 0.f};
+      if (aa2.h > 0.f) {
+        const Df ra = df_rsqrt(aa2);
+        aa = df_mul(aa2, ra);
+        pr = df_mul(alx, ra);
+        pi = df_mul(aly, ra);
       }
-      beta = make_double2(-pr * nrm, -pi * nrm);
-      A[tri(o, j)] = cdf_split(fma(pr, nrm, alx), fma(pi, nrm, aly));
-      tau = 1.0 / (nrm * (nrm + aa));
+      bx = df_neg(df_mul(pr, nrm));
+      by = df_neg(df_mul(pi, nrm));
+      const Df v0x = df_fma(pr, nrm, alx), v0y = df_fma(pi, nrm, aly);
+      A[tri(o, j)] = make_float4(v0x.h, v0x.l, v0y.h, v0y.l);
+      tau = df_div(Df{1.f, 0.f}, df_mul(nrm, df_add(nrm, aa)));
     }
-    *s_tdf = df_split(tau);
-    *s_act = tau != 0.0;
-    be[j] = beta;
-    tb[j] = tau;
+    *s_tdf = make_float2(tau.h, tau.l);
+    *s_act = tau.h != 0.f;
+    be[j] = make_double2(df_val(bx.h, bx.l), df_val(by.h, by.l));
+    tb[j] = df_val(tau.h, tau.l);
   }
   __syncwarp();
   for (int r = lane; r < m; r += 32) vdst[r] = A[tri(o + r, j)];
@@ -208,6 +277,8 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
   float4* sp = pb + W;                              // [NT] symv partial sums
   double2* be = reinterpret_cast<double2*>(sp + NT);   // [W] complex sub-diagonal beta_i
   double* tb = reinterpret_cast<double*>(be + W);      // [W] tau_i
+  // row of each packed lower-triangle index (the same for every triangle in row-packed order)
+  unsigned char* rowof = reinterpret_cast<unsigned char*>(tb + W);   // [W (W + 1) / 2]
   // tau as an FP32 pair and tau != 0, by step parity (warp 0 writes step i + 1's while the
   // other warps may still read step i's)
   __shared__ float2 s_tdf[2];
@@ -218,10 +289,11 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
   const int64_t k = blockIdx.x;
   const double* P = Hp + (size_t)k * ld;
 
+  for (int r = t; r < W; r += NT)
+    for (int c = 0; c <= r; ++c) rowof[tri(r, c)] = (unsigned char)r;
+  __syncthreads();
   for (int idx = t; idx < W * (W + 1) / 2; idx += NT) {
-    int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-    while (tri(r, 0) > idx) --r;
-    while (tri(r + 1, 0) <= idx) ++r;
+    const int r = rowof[idx];
     const int c = idx - tri(r, 0);
     A[idx] = r == c ? cdf_split(P[r * W + r], 0.0)
                     : cdf_split(P[c * W + r], -P[r * W + c]);   // conj(A_cr)
@@ -329,10 +401,8 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
       const int n1 = m - 1;
       const int ntri = n1 * (n1 + 1) / 2;
       for (int idx = t - 32; idx < ntri; idx += NT - 32) {
-        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-        while (r * (r + 1) / 2 > idx) --r;
-        while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-        const int c = idx - r * (r + 1) / 2;
+        const int r = rowof[idx];
+        const int c = idx - tri(r, 0);
         // element (r + 1, c + 1) of the trailing block
         float4 a = A[tri(o + r + 1, o + c + 1)];
         rank2_elem(a, vb[r + 1], pb[r + 1], vb[c + 1], pb[c + 1], r == c);
@@ -394,72 +464,6 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
 }
 
 // ------------------------------------------------------------------ QL in double-float
-// Scalar double-float operations (value h + l): results normalised, ~2^-46 relative.
-struct Df {
-  float h, l;
-};
-__device__ __forceinline__ Df dfv(float h, float l = 0.f) { return Df{h, l}; }
-__device__ __forceinline__ Df df_add(Df a, Df b) {
-  float s, e;
-  two_sum(a.h, b.h, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-  Df r;
-  fast_two_sum(s, e, r.h, r.l);
-  return r;
-}
-__device__ __forceinline__ Df df_neg(Df a) { return Df{-a.h, -a.l}; }
-__device__ __forceinline__ Df df_sub(Df a, Df b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ Df df_mul(Df a, Df b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  Df r;
-  fast_two_sum(p, e, r.h, r.l);
-  return r;
-}
-// a * b + c
-__device__ __forceinline__ Df df_fma(Df a, Df b, Df c) { return df_add(df_mul(a, b), c); }
-// 1 / sqrt(a), a > 0: the FP32 estimate and one Newton step, y + y (1 - a y^2) / 2, whose
-// correction is ~2^-22 of y and needs FP32 precision only
-__device__ __forceinline__ Df df_rsqrt(Df a) {
-  const float y = rsqrtf(a.h);
-  const float y2 = __fmul_rn(y, y);
-  const Df t = df_mul(a, Df{y2, fmaf(y, y, -y2)});
-  const float r = __fadd_rn(__fsub_rn(1.0f, t.h), -t.l);
-  Df out;
-  fast_two_sum(y, 0.5f * y * r, out.h, out.l);
-  return out;
-}
-// sqrt(a), a >= 0: y + (a - y^2) / (2 y) from an approximate FP32 root (the correction
-// absorbs its few-ulp error)
-__device__ __forceinline__ Df df_sqrt(Df a) {
-  if (!(a.h > 0.f)) return Df{0.f, 0.f};
-  const float ry = rsqrtf(a.h);
-  const float y = a.h * ry;
-  const float y2 = __fmul_rn(y, y);
-  const Df d = df_sub(a, Df{y2, fmaf(y, y, -y2)});
-  Df out;
-  fast_two_sum(y, d.h * (0.5f * ry), out.h, out.l);
-  return out;
-}
-// FP32 reciprocal estimate (one MUFU instruction, ~1 ulp)
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-// a / b: an approximate FP32 quotient q1 = a rcp(b), then the quotient of the remainder
-// a - q1 b (exact to 2^-46): ~2^-45 relative in all
-__device__ __forceinline__ Df df_div(Df a, Df b) {
-  const float rb = rcp_approx(b.h);
-  const float q1 = a.h * rb;
-  const Df r = df_sub(a, df_mul(b, Df{q1, 0.f}));
-  Df out;
-  fast_two_sum(q1, r.h * rb, out.h, out.l);
-  return out;
-}
-
 // Eigenvalues of the real symmetric tridiagonal T (FP64 d, |e|) by implicit QL with Wilkinson
 // shifts, one k-point per lane, in double-float: the same chase as the FP64 kernel, with the
 // deflation test |e_m| <= 2^-44 (|d_m| + |d_m+1|) matched to the pair precision.  d and e live
@@ -715,7 +719,7 @@ __global__ void __launch_bounds__(128) iit_df_kernel(int W, int n, EighBufs b,
 
 size_t tridiag_df_smem(int W) {
   return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W + NT) * sizeof(float4) +
-         (size_t)W * (sizeof(double2) + sizeof(double));
+         (size_t)W * (sizeof(double2) + sizeof(double)) + (size_t)W * (W + 1) / 2;
 }
 
 cudaError_t launch_tridiag_df_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
