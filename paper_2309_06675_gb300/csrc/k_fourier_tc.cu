@@ -27,7 +27,8 @@
 //   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, N=64, K=16), operands staged
 //                       by TMA (128-byte swizzle, 2-stage mbarrier pipeline), 4 level
 //                       accumulators x 2 buffers filling the 512 TMEM columns, integer
-//                       epilogue, FP64 rows in HBM.
+//                       epilogue, FP64 rows in HBM; persistent (one CTA per SM over the
+//                       tiles, the epilogue of a tile overlapping the next tile's MMAs).
 //
 // Every mbarrier wait is bounded; on timeout the CTA records ST_TIMEOUT, drains its own
 // copies (bounded), frees its TMEM and returns.
@@ -60,7 +61,9 @@ constexpr int GROUP_M = 8;        // M tiles rasterised together so B tiles are 
 constexpr int TILE_A_BYTES = BM * BK * 2;            // 16 KB per slice
 constexpr int TILE_B_BYTES = BN * BK * 2;            // 8 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 96 KB
-constexpr int TC_THREADS = 192;                      // 6 warps
+constexpr int TC_THREADS = 320;                      // 10 warps: TMA, MMA, 8 epilogue
+constexpr int EPI_THREADS = TC_THREADS - 64;         // 2 per TMEM lane quarter, 32 columns each
+constexpr int EPI_COLS = BN / 2;
 constexpr int TMEM_COLS = 512;                       // = NACC * NLEVEL * BN
 
 // PTX wrappers: tc_ptx.cuh
@@ -184,11 +187,15 @@ __constant__ int c_pj[NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
 __constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 
 // ------------------------------------------------------------------ the tcgen05 GEMM
-// grid: (Npad / BN) * (Mpad / BM) CTAs; out: FP64 [n rows][ldc], rows >= n_rows not written.
+// Persistent: one CTA per SM walks the tiles tau = blockIdx.x, + gridDim.x, ... of the column
+// tiles nt0 .. nt0 + ntc - 1 (grouped rasterisation, below).  The K-block counter of the
+// TMA / MMA pipeline and the drain-group counter of the two TMEM accumulator sets run across
+// tiles, so the epilogue of one tile (its last drain, the FP64 conversion and the stores)
+// overlaps the loads and MMAs of the next, and TMEM, barriers and pipeline fill are paid once
+// per SM.  out: FP64 [n rows][ldc], rows >= n_rows not written.
 // NS = slices per operand kept: 4 (levels i + j <= 3, 10 slice pairs, ~31 fractional bits) or
 // 3 (levels <= 2, 6 pairs, ~23 bits: for the velocity columns when their only consumer is the
-// FP32 rotation, whose own input rounding is 2^-24).  The grid covers the column tiles
-// nt0 .. nt0 + ntc - 1.
+// FP32 rotation, whose own input rounding is 2^-24).
 template <int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
@@ -205,16 +212,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ volatile int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_mt = Mpad / BM, n_tiles = n_mt * ntc;
+  const int groups_per_tile = (nkb + DRAIN - 1) / DRAIN;
   // grouped rasterisation: GROUP_M consecutive M tiles per column tile, so one B tile serves
-  // several CTAs in a row and the group's A tiles stay resident in L2 across column tiles
-  const int n_mt = Mpad / BM, n_nt = ntc;
-  const int id = blockIdx.x;
-  const int per_group = GROUP_M * n_nt;
-  const int grp = id / per_group;
-  const int gm0 = grp * GROUP_M;
-  const int gsz = min(GROUP_M, n_mt - gm0);
-  const int in = id - grp * per_group;
-  const int n0 = (nt0 + in / gsz) * BN, m0 = (gm0 + in % gsz) * BM;
+  // several tiles in a row and the group's A tiles stay resident in L2 across column tiles
+  auto tile_origin = [&](int id, int& m0, int& n0) {
+    const int per_group = GROUP_M * ntc;
+    const int grp = id / per_group;
+    const int gm0 = grp * GROUP_M;
+    const int gsz = min(GROUP_M, n_mt - gm0);
+    const int in = id - grp * per_group;
+    n0 = (nt0 + in / gsz) * BN;
+    m0 = (gm0 + in % gsz) * BM;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int a = 0; a < NACC; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 128);   // every epilogue thread arrives
+      mbar_init(&acc_empty[a], EPI_THREADS);   // every epilogue thread arrives
     }
     mbar_init(&done_bar, 1);
     abort_sh = 0;
@@ -247,112 +257,128 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   };
 
   if (warp == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer (g: K blocks issued by this CTA over all its tiles)
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % NSTAGE;
-        const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
-        if (abort_sh) break;
-        if (kb >= NSTAGE && !mbar_wait(&empty_bar[s], ph ^ 1u)) {
-          atomicOr(&st->bits, ST_TIMEOUT);
-          abort_sh = 1;
-          break;
+      int g = 0;
+      for (int id = blockIdx.x; id < n_tiles && !abort_sh; id += gridDim.x) {
+        int m0, n0;
+        tile_origin(id, m0, n0);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % NSTAGE;
+          if (abort_sh) break;
+          if (g >= NSTAGE && !mbar_wait(&empty_bar[s], ((uint32_t)(g / NSTAGE) & 1u) ^ 1u)) {
+            atomicOr(&st->bits, ST_TIMEOUT);
+            abort_sh = 1;
+            break;
+          }
+          mbar_expect_tx(&full_bar[s], (uint32_t)NS * (TILE_A_BYTES + TILE_B_BYTES));
+          for (int sl = 0; sl < NS; ++sl)
+            tma_load_2d(stageA(s, sl), &mapA, &full_bar[s], kb * BK, sl * Mpad + m0);
+          for (int sl = 0; sl < NS; ++sl)
+            tma_load_2d(stageB(s, sl), &mapB, &full_bar[s], kb * BK, sl * Npad + n0);
         }
-        mbar_expect_tx(&full_bar[s], (uint32_t)NS * (TILE_A_BYTES + TILE_B_BYTES));
-        for (int sl = 0; sl < NS; ++sl)
-          tma_load_2d(stageA(s, sl), &mapA, &full_bar[s], kb * BK, sl * Mpad + m0);
-        for (int sl = 0; sl < NS; ++sl)
-          tma_load_2d(stageB(s, sl), &mapB, &full_bar[s], kb * BK, sl * Npad + n0);
-        ++issued;
       }
       // drain: every issued stage's copies must have landed before the CTA may exit
-      for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
-        mbar_wait(&full_bar[kb % NSTAGE], (uint32_t)(kb / NSTAGE) & 1u);
+      for (int q = (g > NSTAGE ? g - NSTAGE : 0); q < g; ++q)
+        mbar_wait(&full_bar[q % NSTAGE], (uint32_t)(q / NSTAGE) & 1u);
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: stage kb accumulates each level into accumulator set kb % NACC
+    // ---------------- MMA issuer: drain group G (global) accumulates into set G % NACC
     if (lane == 0) {
-      for (int kb = 0; kb < nkb && !abort_sh; ++kb) {
-        const int s = kb % NSTAGE;
-        const int g = kb / DRAIN;            // drain group of this K block
-        const int a = g % NACC;
-        const bool first = kb % DRAIN == 0;
-        const bool last = kb % DRAIN == DRAIN - 1 || kb == nkb - 1;
-        if (first && g >= NACC && !mbar_wait(&acc_empty[a], (uint32_t)(g / NACC - 1) & 1u)) {
-          atomicOr(&st->bits, ST_TIMEOUT);
-          abort_sh = 1;
-          break;
-        }
-        if (!mbar_wait(&full_bar[s], (uint32_t)(kb / NSTAGE) & 1u)) {
-          atomicOr(&st->bits, ST_TIMEOUT);
-          abort_sh = 1;
-          break;
-        }
-        tc_fence_after();
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          int seen = 0;   // bit l set once level l has been written in this drain group
-          for (int p = 0; p < NPR; ++p) {
-            const int l = c_pl[p];
-            const uint32_t acc = (!first || kk > 0 || (seen >> l) & 1) ? 1u : 0u;
-            seen |= 1 << l;
-            const uint64_t da = umma_desc_sw128(smem_u32(stageA(s, c_pi[p])) + kk * 32);
-            const uint64_t db = umma_desc_sw128(smem_u32(stageB(s, c_pj[p])) + kk * 32);
-            umma_bf16(tmem + (uint32_t)((a * NLEVEL + l) * BN), da, db, IDESC, acc);
+      int g = 0, G = 0;
+      for (int id = blockIdx.x; id < n_tiles && !abort_sh; id += gridDim.x) {
+        for (int kb = 0; kb < nkb && !abort_sh; ++kb, ++g) {
+          const int s = g % NSTAGE;
+          const bool first = kb % DRAIN == 0;
+          const bool last = kb % DRAIN == DRAIN - 1 || kb == nkb - 1;
+          const int a = G % NACC;
+          if (first && G >= NACC && !mbar_wait(&acc_empty[a], (uint32_t)(G / NACC - 1) & 1u)) {
+            atomicOr(&st->bits, ST_TIMEOUT);
+            abort_sh = 1;
+            break;
+          }
+          if (!mbar_wait(&full_bar[s], (uint32_t)(g / NSTAGE) & 1u)) {
+            atomicOr(&st->bits, ST_TIMEOUT);
+            abort_sh = 1;
+            break;
+          }
+          tc_fence_after();
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            int seen = 0;   // bit l set once level l has been written in this drain group
+            for (int p = 0; p < NPR; ++p) {
+              const int l = c_pl[p];
+              const uint32_t acc = (!first || kk > 0 || (seen >> l) & 1) ? 1u : 0u;
+              seen |= 1 << l;
+              const uint64_t da = umma_desc_sw128(smem_u32(stageA(s, c_pi[p])) + kk * 32);
+              const uint64_t db = umma_desc_sw128(smem_u32(stageB(s, c_pj[p])) + kk * 32);
+              umma_bf16(tmem + (uint32_t)((a * NLEVEL + l) * BN), da, db, IDESC, acc);
+            }
+          }
+          umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
+          if (last) {
+            umma_commit(&acc_full[a]);  // level sums of this drain group complete
+            ++G;
           }
         }
-        umma_commit(&empty_bar[s]);          // stage free once these MMAs have read it
-        if (last) umma_commit(&acc_full[a]); // level sums of this drain group complete
       }
       umma_commit(&done_bar);         // all issued MMAs complete
     }
   } else {
-    // ---------------- epilogue: warps 2..5 own TMEM lanes 32 * (warp % 4) .. + 31
+    // ---------------- epilogue: warps 2..9; warp w owns TMEM lanes 32 (w % 4) .. + 31 (the
+    // lanes a warp may access) and the column half (w - 2) / 4 of the tile
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
-    const int grow = m0 + row;
+    const int c_lo = ((warp - 2) >> 2) * EPI_COLS;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    // One exact integer per column: sum over drain groups and levels of I_l 2^(32 - 8 l).  A
-    // group's level sum is at most 2^24 in magnitude, so the total stays below 2^57.
-    long long isum[BN];
-#pragma unroll
-    for (int j = 0; j < BN; ++j) isum[j] = 0;
     bool ok = true;
-    const int ngroups = (nkb + DRAIN - 1) / DRAIN;
-    for (int g = 0; g < ngroups; ++g) {
-      const int a = g % NACC;
-      ok = mbar_wait(&acc_full[a], (uint32_t)(g / NACC) & 1u);
-      ok = __all_sync(0xffffffffu, ok && !abort_sh);   // tcgen05.ld is warp-collective
+    int G = 0;
+    for (int id = blockIdx.x; id < n_tiles && ok; id += gridDim.x) {
+      int m0, n0;
+      tile_origin(id, m0, n0);
+      // One exact integer per column: sum over drain groups and levels of I_l 2^(32 - 8 l).  A
+      // group's level sum is at most 2^24 in magnitude, so the total stays below 2^57.
+      long long isum[EPI_COLS];
+#pragma unroll
+      for (int j = 0; j < EPI_COLS; ++j) isum[j] = 0;
+      for (int gi = 0; gi < groups_per_tile; ++gi, ++G) {
+        const int a = G % NACC;
+        ok = mbar_wait(&acc_full[a], (uint32_t)(G / NACC) & 1u);
+        ok = __all_sync(0xffffffffu, ok && !abort_sh);   // tcgen05.ld is warp-collective
+        if (!ok) break;
+        tc_fence_after();
+#pragma unroll
+        for (int l = 0; l < NLEV; ++l) {
+#pragma unroll
+          for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(lane_addr + (uint32_t)((a * NLEVEL + l) * BN + c_lo + c0), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              isum[c0 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[a]);
+      }
       if (!ok) break;
-      tc_fence_after();
+      const int grow = m0 + row;
+      if (grow < n_rows) {
+        // C = 2^e_n * isum * 2^(-14 - 32): a power-of-two scale, exact apart from the final
+        // rounding of the 57-bit integer to FP64
+        double* dst = out + (size_t)grow * ldc + n0 + c_lo;
+        const int* ce = col_exp + n0 + c_lo;
 #pragma unroll
-      for (int l = 0; l < NLEV; ++l) {
-#pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(lane_addr + (uint32_t)((a * NLEVEL + l) * BN + c0), r);
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            isum[c0 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
+        for (int j = 0; j < EPI_COLS; j += 2) {
+          const double s0 = __longlong_as_double((long long)(1023 - 46 + ce[j]) << 52);
+          const double s1 = __longlong_as_double((long long)(1023 - 46 + ce[j + 1]) << 52);
+          *reinterpret_cast<double2*>(dst + j) =
+              make_double2((double)isum[j] * s0, (double)isum[j + 1] * s1);
         }
       }
-      tc_fence_before();
-      mbar_arrive(&acc_empty[a]);
     }
     if (!ok) {
       atomicOr(&st->bits, ST_TIMEOUT);
       abort_sh = 1;
-    } else if (grow < n_rows) {
-      // C = 2^e_n * isum * 2^(-14 - 32): a power-of-two scale, exact apart from the final
-      // rounding of the 57-bit integer to FP64
-      double* dst = out + (size_t)grow * ldc + n0;
-#pragma unroll
-      for (int j = 0; j < BN; j += 2) {
-        const double s0 = __longlong_as_double((long long)(1023 - 46 + col_exp[n0 + j]) << 52);
-        const double s1 = __longlong_as_double((long long)(1023 - 46 + col_exp[n0 + j + 1]) << 52);
-        *reinterpret_cast<double2*>(dst + j) =
-            make_double2((double)isum[j] * s0, (double)isum[j + 1] * s1);
-      }
     }
   }
   tc_fence_before();
@@ -450,8 +476,12 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
     if (tc <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<tc * (Mpad / BM), TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out,
-                                                 ldc, st, t0, tc);
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(tc * (Mpad / BM), std::max(nsm, 1));   // persistent: one per SM
+    kern<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out, ldc, st,
+                                      t0, tc);
     return cudaGetLastError();
   };
   cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt);
