@@ -44,10 +44,14 @@ import tbgen  # noqa: E402
 METRIC = "k-points/sec for σ_xy (W=64, N_R=1331), mixed vs FP64 GPU at rel err ≤1e-5; % roofline"
 WORKLOAD = "w64_r1331_k128"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
-# DRAM bytes (read + write) per k-point of the kernels that can dominate a step, from one ncu
-# capture of the current kernel (profiles/mixed_path_w64_r1331_k128.md, W = 64); a kernel
-# that changes after its capture leaves this table.
-DRAM_BYTES_PER_K = {"tridiag": 97.3e3}
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12   # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (ops/s)
+# minimal FP32 operations of one double-float multiply-accumulate (TwoProd by FMA with the two
+# cross terms, Knuth's TwoSum into the accumulator, the low-part update)
+DF_OPS_PER_MAC = 12
+# DRAM bytes (read + write) per k-point of the kernels that can dominate a step, by (path,
+# stage), from one ncu capture of the current kernel (profiles/, W = 64); a kernel that
+# changes after its capture leaves this table.
+DRAM_BYTES_PER_K = {}
 # algorithmic flops per k-point by stage (W = 64, N_R = 1331), see the design doc
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
@@ -69,6 +73,41 @@ def stage_flops(W, N_R, prec="fp64"):
         "fixup": 0.0,
         "adjoint": 0.0,
     }
+
+
+def measured_bf16_sustained():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback (sustained)"
+
+
+def roofline_of(dom, head, W, N_R, k_per_launch, ms_per_launch):
+    """Roofline of the dominant kernel: algorithmic work per launch / its average duration,
+    against the peak of the pipe that kernel runs on."""
+    t = ms_per_launch / 1e3
+    if head == "mixed" and dom == "tridiag":
+        ops = DF_OPS_PER_MAC * (8.0 / 3.0) * W ** 3 * k_per_launch
+        return {"bound": "alu", "achieved": ops / t / 1e12, "peak": FP32_PEAK_TOPS,
+                "unit": "T FP32-op/s",
+                "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (derived).  Work: the "
+                             "double-float reduction's 8/3 W^3 real multiply-adds at the minimal "
+                             f"{DF_OPS_PER_MAC} FP32 operations each"}
+    if head == "mixed" and dom == "berry":
+        fl = (24.0 + 8.0) * W ** 3 * k_per_launch
+        return {"bound": "alu", "achieved": fl / t / 1e12, "peak": 2 * FP32_PEAK_TOPS,
+                "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"}
+    if head == "mixed" and dom == "fourier":
+        kp = (N_R + 63) // 64 * 64
+        fl = 2.0 * kp * (10 * W * W + 6 * 2 * W * W) * k_per_launch   # issued BF16 slice products
+        peak, how = measured_bf16_sustained()
+        return {"bound": "tensor", "achieved": fl / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_note": f"bf16 dense {how}; work: issued BF16 slice-pair products"}
+    fl = stage_flops(W, N_R, head)[dom] * k_per_launch
+    return {"bound": "alu", "achieved": fl / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk/SM (one DFMA warp instruction per 16 "
+                         "cycles, measured) x 2.07 GHz (derived; measured DFMA loop 1.199 TFLOP/s)"}
 
 
 def parse():
@@ -450,14 +489,14 @@ def main():
     dom = max((s for s in st if st[s]["launches"] > 0), key=lambda s: st[s]["ms"])
     launches = st[dom]["launches"]
     k_per_launch = k_total / launches
-    achieved = fl[dom] * k_per_launch / (st[dom]["ms"] / launches / 1e3) / 1e12
-    traffic = DRAM_BYTES_PER_K[dom] * k_per_launch if dom in DRAM_BYTES_PER_K and model.W == 64 else None
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+    rl = roofline_of(dom, head, model.W, model.N_R, k_per_launch, st[dom]["ms"] / launches)
+    key = (head, dom)
+    traffic = DRAM_BYTES_PER_K[key] * k_per_launch if key in DRAM_BYTES_PER_K and model.W == 64 else None
+    roofline = {"bound": rl["bound"], "kernel": dom, "achieved": rl["achieved"], "peak": rl["peak"],
+                "unit": rl["unit"], "frac": rl["achieved"] / rl["peak"], "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + write.sum, scaled "
                                 "by k-points per launch)",
-                "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk/SM (one DFMA warp instruction per 16 "
-                             "cycles, measured) x 2.07 GHz (derived; measured DFMA loop 1.199 TFLOP/s)"}
+                "peak_note": rl["peak_note"]}
     line = {
         "metric": METRIC, "value": paths[head]["value"], "unit": "k-points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

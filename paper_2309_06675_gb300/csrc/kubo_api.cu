@@ -234,6 +234,30 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
 }
 
 // ------------------------------------------------------------------ call context
+// The library-managed workspace comes from the device's default stream-ordered pool.  With
+// the pool's default release threshold (0) the freed workspace is unmapped at the next
+// synchronisation and every call pays for mapping it again (GBs at the default batch); the
+// threshold is raised to the largest workspace seen, so one workspace stays mapped between
+// calls.  (A caller-supplied workspace bypasses the pool.)
+inline void retain_pool_memory(size_t bytes) {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  uint64_t cur = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (cur < (uint64_t)bytes) {
+    uint64_t thr = (uint64_t)bytes;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess)
+      cudaGetLastError();
+  }
+}
+
 struct Call {
   cudaStream_t s = nullptr;
   char* ws = nullptr;
@@ -271,6 +295,7 @@ struct Call {
       ws = (char*)o.workspace;
       return KUBO_OK;
     }
+    retain_pool_memory(p.total);
     if (cudaMallocAsync((void**)&ws, p.total, s) != cudaSuccess) {
       cudaGetLastError();
       ws = nullptr;
