@@ -345,9 +345,23 @@ __device__ __forceinline__ void unpack_hermitian_f32(const TIn* __restrict__ P, 
 
 // U = Q D Z in FP32, in shared memory, from the FP64 factors of the eigensolver: Z (eigenvectors
 // of the real tridiagonal, [W][W]), the phases D and the Householder reflectors (staged in
-// `stage`, W (W - 1) / 2 complex).  Each column is transformed by its own 4 threads, so the
-// reflectors are applied without block barriers.  The only consumer of this U is the FP32
-// rotation, so it is formed at that precision.
+// `stage`, W (W - 1) / 2 complex, then 2 ceil((W - 2) / 4) x 16 complex of block factors).
+// The only consumer of this U is the FP32 rotation, so it is formed at that precision.
+//
+// Q = H_0 H_1 ... H_{W-3} is applied in blocks of ASM_NB consecutive reflectors in the compact
+// WY form H_j0 ... H_j0+3 = I - V T V^H (T upper triangular: T_ii = tau_i,
+// T[0:i, i] = -tau_i T[0:i, 0:i] V[:, 0:i]^H v_i), last block first: U <- U - V (T (V^H U)).
+// The block factors are formed once from the reflectors' inner products; each group of 8
+// threads then applies a block to two columns with 2 ASM_NB independent dot chains, so the
+// application is ceil((W - 2) / 4) dependent steps instead of W - 2.  (Blocks of 16 applied
+// as register-tiled products were measured slower: their per-block serial phases are not
+// hidden at two CTAs per SM.)
+constexpr int ASM_NB = 4;
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
 __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
                                                const double2* __restrict__ ph,
                                                const double2* __restrict__ R,
@@ -367,38 +381,114 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
       stage[roff(c) + (r - c - 1)] = make_float2((float)v.x, (float)v.y);
     }
   }
+  const int nref = W > 2 ? W - 2 : 0;
+  const int nblk = (nref + ASM_NB - 1) / ASM_NB;
+  float2* G = stage + W * (W - 1) / 2;        // [nblk][NB][NB]: v_a^H v_b (a < b)
+  float2* Tm = G + nblk * ASM_NB * ASM_NB;    // [nblk][NB][NB]: T (upper triangular)
   __syncthreads();
-  const int q = t & 3, c = t >> 2;   // NT / 4 = 64 >= W columns
-  const bool act = c < W;
-  for (int j = W - 3; j >= 0; --j) {
-    const float tj = (float)tau[j];
-    if (tj == 0.f) continue;
-    const int o = j + 1, m = W - 1 - j;
-    const float2* v = stage + roff(j);
-    float sx = 0.f, sy = 0.f;
-    if (act) {
-      for (int r = q; r < m; r += 4) {
-        const float2 vv = v[r];
-        const float2 u = sU[(o + r) * LD + c];
-        sx = fmaf(vv.x, u.x, fmaf(vv.y, u.y, sx));   // conj(v) u
-        sy = fmaf(vv.x, u.y, fmaf(-vv.y, u.x, sy));
+  for (int d = t; d < nblk * ASM_NB * ASM_NB; d += NT) {
+    const int bk = d / (ASM_NB * ASM_NB), a = (d / ASM_NB) % ASM_NB, a2 = d % ASM_NB;
+    const int j0 = bk * ASM_NB, nj = min(ASM_NB, nref - j0), m0 = W - 1 - j0;
+    float2 g = make_float2(0.f, 0.f);
+    if (a < a2 && a2 < nj) {
+      // rows j0 + 1 + rr, rr >= a2 (v_b vanishes above its first row)
+      const float2* va = stage + roff(j0 + a) - a;
+      const float2* vb = stage + roff(j0 + a2) - a2;
+      for (int rr = a2; rr < m0; ++rr) {
+        const float2 x = va[rr], y = vb[rr];
+        g.x = fmaf(x.x, y.x, fmaf(x.y, y.y, g.x));   // conj(x) y
+        g.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, g.y));
       }
     }
-    sx += __shfl_xor_sync(0xffffffffu, sx, 1);
-    sy += __shfl_xor_sync(0xffffffffu, sy, 1);
-    sx += __shfl_xor_sync(0xffffffffu, sx, 2);
-    sy += __shfl_xor_sync(0xffffffffu, sy, 2);
-    sx *= tj; sy *= tj;
-    if (act) {
-      for (int r = q; r < m; r += 4) {
-        const float2 vv = v[r];
-        float2 u = sU[(o + r) * LD + c];
-        u.x = fmaf(-sx, vv.x, fmaf(sy, vv.y, u.x));   // u -= s v
-        u.y = fmaf(-sx, vv.y, fmaf(-sy, vv.x, u.y));
-        sU[(o + r) * LD + c] = u;
+    G[d] = g;
+  }
+  __syncthreads();
+  for (int bk = t; bk < nblk; bk += NT) {
+    const int j0 = bk * ASM_NB, nj = min(ASM_NB, nref - j0);
+    float2* Tb = Tm + bk * ASM_NB * ASM_NB;
+    const float2* Gb = G + bk * ASM_NB * ASM_NB;
+    for (int e = 0; e < ASM_NB * ASM_NB; ++e) Tb[e] = make_float2(0.f, 0.f);
+    for (int i = 0; i < nj; ++i) {
+      const float ti = (float)tau[j0 + i];
+      Tb[i * ASM_NB + i] = make_float2(ti, 0.f);
+      for (int a = 0; a < i; ++a) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k2 = a; k2 < i; ++k2) {
+          const float2 pr = cmulf(Tb[a * ASM_NB + k2], Gb[k2 * ASM_NB + i]);
+          acc.x += pr.x;
+          acc.y += pr.y;
+        }
+        Tb[a * ASM_NB + i] = make_float2(-ti * acc.x, -ti * acc.y);
       }
     }
-    __syncwarp();
+  }
+  __syncthreads();
+  const int q = t & 7, cp = t >> 3;   // NT / 8 = 32 groups, two columns each (W <= 64)
+  const int c0 = 2 * cp, c1 = c0 + 1;
+  const bool act0 = c0 < W, act1 = c1 < W;
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int j0 = bk * ASM_NB, nj = min(ASM_NB, nref - j0), m0 = W - 1 - j0, o = j0 + 1;
+    const float2* Tb = Tm + bk * ASM_NB * ASM_NB;
+    float2 s0[ASM_NB], s1[ASM_NB];
+#pragma unroll
+    for (int a = 0; a < ASM_NB; ++a) {
+      s0[a] = make_float2(0.f, 0.f);
+      s1[a] = make_float2(0.f, 0.f);
+    }
+    for (int rr = q; rr < m0; rr += 8) {
+      const float2 u0 = act0 ? sU[(o + rr) * LD + c0] : make_float2(0.f, 0.f);
+      const float2 u1 = act1 ? sU[(o + rr) * LD + c1] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < ASM_NB; ++a) {
+        if (a < nj && rr >= a) {
+          const float2 v = stage[roff(j0 + a) + rr - a];
+          s0[a].x = fmaf(v.x, u0.x, fmaf(v.y, u0.y, s0[a].x));   // conj(v) u
+          s0[a].y = fmaf(v.x, u0.y, fmaf(-v.y, u0.x, s0[a].y));
+          s1[a].x = fmaf(v.x, u1.x, fmaf(v.y, u1.y, s1[a].x));
+          s1[a].y = fmaf(v.x, u1.y, fmaf(-v.y, u1.x, s1[a].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < ASM_NB; ++a)
+#pragma unroll
+      for (int o2 = 1; o2 < 8; o2 <<= 1) {
+        s0[a].x += __shfl_xor_sync(0xffffffffu, s0[a].x, o2);
+        s0[a].y += __shfl_xor_sync(0xffffffffu, s0[a].y, o2);
+        s1[a].x += __shfl_xor_sync(0xffffffffu, s1[a].x, o2);
+        s1[a].y += __shfl_xor_sync(0xffffffffu, s1[a].y, o2);
+      }
+    // t = T s (upper triangular)
+    float2 t0[ASM_NB], t1[ASM_NB];
+#pragma unroll
+    for (int a = 0; a < ASM_NB; ++a) {
+      t0[a] = make_float2(0.f, 0.f);
+      t1[a] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int a2 = a; a2 < ASM_NB; ++a2) {
+        const float2 tv = Tb[a * ASM_NB + a2];
+        const float2 p0 = cmulf(tv, s0[a2]), p1 = cmulf(tv, s1[a2]);
+        t0[a].x += p0.x; t0[a].y += p0.y;
+        t1[a].x += p1.x; t1[a].y += p1.y;
+      }
+    }
+    for (int rr = q; rr < m0; rr += 8) {
+      float2 u0 = act0 ? sU[(o + rr) * LD + c0] : make_float2(0.f, 0.f);
+      float2 u1 = act1 ? sU[(o + rr) * LD + c1] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < ASM_NB; ++a) {
+        if (a < nj && rr >= a) {
+          const float2 v = stage[roff(j0 + a) + rr - a];
+          u0.x = fmaf(-v.x, t0[a].x, fmaf(v.y, t0[a].y, u0.x));   // u -= v t
+          u0.y = fmaf(-v.x, t0[a].y, fmaf(-v.y, t0[a].x, u0.y));
+          u1.x = fmaf(-v.x, t1[a].x, fmaf(v.y, t1[a].y, u1.x));
+          u1.y = fmaf(-v.x, t1[a].y, fmaf(-v.y, t1[a].x, u1.y));
+        }
+      }
+      if (act0) sU[(o + rr) * LD + c0] = u0;
+      if (act1) sU[(o + rr) * LD + c1] = u1;
+    }
+    __syncwarp();   // the group's rows shift between blocks: updates before the next reads
   }
   __syncthreads();
 }
@@ -891,10 +981,17 @@ cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const doub
                                      eta_stride, s, pad);
 }
 
+// bytes of the U assembly's staging area (reflectors, then the block factors G and T)
+static size_t asm_stage_bytes(int W) {
+  const size_t nref = W > 2 ? (size_t)W - 2 : 0;
+  const size_t nblk = (nref + ASM_NB - 1) / ASM_NB;
+  return ((size_t)W * (W - 1) / 2 + 2 * nblk * ASM_NB * ASM_NB) * sizeof(float2);
+}
+
 size_t berry_mixed_smem(int W, int n_eta) {
   const size_t mat = (size_t)W * mixed_ld(W, 1) * sizeof(float2);
   const size_t red = (size_t)n_eta * W * 2 * 16 * sizeof(double);
-  return mat + (2 * mat > red ? 2 * mat : red);
+  return mat + std::max(std::max(2 * mat, red), asm_stage_bytes(W));
 }
 
 template <typename TIn, bool FROMZ>
