@@ -126,12 +126,6 @@ typedef struct kubo_options {
                                tensor cores (exact fixed-point BF16-slice products, FP32-grade)
                                instead of FP32 on the FMA pipe.  Same accuracy class; currently
                                slower at W = 64, so 0 (FMA pipe) is the default. */
-  int tc_cta_pairs;         /* tensor-core Fourier sum (KUBO_MIXED, KUBO_MIXED_FOURIER): 1 = pairs
-                               of CTAs (a 2-CTA cluster) that share the k-tile's coefficient
-                               slices by TMA multicast (halves the L2 operand traffic; not
-                               faster on GB300, where the per-SM operand intake bounds the
-                               kernel); 0 (default) = one CTA per output tile.  Bit-identical
-                               results. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,

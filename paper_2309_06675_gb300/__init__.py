@@ -86,7 +86,6 @@ class Options(ctypes.Structure):
         ("layout_unpadded", ctypes.c_int),
         ("fourier_separable", ctypes.c_int),
         ("rotation_tc", ctypes.c_int),
-        ("tc_cta_pairs", ctypes.c_int),
     ]
 
 
@@ -235,7 +234,7 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
         stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
-        unpadded=False, separable=False, rotation_tc=False, tc_cta_pairs=False):
+        unpadded=False, separable=False, rotation_tc=False):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
@@ -254,7 +253,6 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     o.layout_unpadded = 1 if unpadded else 0
     o.fourier_separable = 1 if separable else 0
     o.rotation_tc = 1 if rotation_tc else 0
-    o.tc_cta_pairs = 1 if tc_cta_pairs else 0
     code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                           W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                           _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),

@@ -196,13 +196,7 @@ __constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
 // NS = slices per operand kept: 4 (levels i + j <= 3, 10 slice pairs, ~31 fractional bits) or
 // 3 (levels <= 2, 6 pairs, ~23 bits: for the velocity columns when their only consumer is the
 // FP32 rotation, whose own input rounding is 2^-24).
-// CL = 2: clusters of two CTAs take two adjacent column tiles of the same k-tile; the k-tile's
-// coefficient slices (A, two thirds of the operand stream) are loaded half by each CTA and
-// multicast to both, so each A byte crosses L2 -> SM once per pair.  A stage is refilled only
-// when both CTAs' MMAs have released it (each MMA warp's commit arrives on both CTAs' empty
-// barrier); the producer's tail waits for the last releases and a cluster barrier precedes the
-// exit, so no peer write or arrival can land after a CTA has left.  mapA's box is BM / CL rows.
-template <int NS, int CL>
+template <int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, const int* __restrict__ col_exp,
@@ -218,29 +212,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ volatile int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // work units: CL adjacent column tiles of one k-tile (one per CTA of the cluster)
-  const int ntu = ntc / CL;
-  const int n_mt = Mpad / BM, n_units = n_mt * ntu;
-  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
-  const int unit0 = CL > 1 ? (int)cluster_id_x() : (int)blockIdx.x;
-  const int ustep = CL > 1 ? (int)cluster_count_x() : (int)gridDim.x;
+  const int n_mt = Mpad / BM, n_tiles = n_mt * ntc;
   const int groups_per_tile = (nkb + DRAIN - 1) / DRAIN;
-  // grouped rasterisation: GROUP_M consecutive M tiles per column unit, so one B tile serves
-  // several tiles in a row and the group's A tiles stay resident in L2 across column units
-  auto tile_origin = [&](int u, int& m0, int& n0) {
-    const int per_group = GROUP_M * ntu;
-    const int grp = u / per_group;
+  // grouped rasterisation: GROUP_M consecutive M tiles per column tile, so one B tile serves
+  // several tiles in a row and the group's A tiles stay resident in L2 across column tiles
+  auto tile_origin = [&](int id, int& m0, int& n0) {
+    const int per_group = GROUP_M * ntc;
+    const int grp = id / per_group;
     const int gm0 = grp * GROUP_M;
     const int gsz = min(GROUP_M, n_mt - gm0);
-    const int in = u - grp * per_group;
-    n0 = (nt0 + (in / gsz) * CL + rank) * BN;
+    const int in = id - grp * per_group;
+    n0 = (nt0 + in / gsz) * BN;
     m0 = (gm0 + in % gsz) * BM;
   };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], CL);   // the MMA warps of every CTA of the cluster release it
+      mbar_init(&empty_bar[s], 1);
     }
     for (int a = 0; a < NACC; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -259,7 +248,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync();   // the peer's barriers exist before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
 
@@ -272,9 +260,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- TMA producer (g: K blocks issued by this CTA over all its tiles)
     if (lane == 0) {
       int g = 0;
-      for (int u = unit0; u < n_units && !abort_sh; u += ustep) {
+      for (int id = blockIdx.x; id < n_tiles && !abort_sh; id += gridDim.x) {
         int m0, n0;
-        tile_origin(u, m0, n0);
+        tile_origin(id, m0, n0);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % NSTAGE;
           if (abort_sh) break;
@@ -283,33 +271,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             abort_sh = 1;
             break;
           }
-          // this CTA's own B and both halves of A (its own and the peer's multicast)
           mbar_expect_tx(&full_bar[s], (uint32_t)NS * (TILE_A_BYTES + TILE_B_BYTES));
-          for (int sl = 0; sl < NS; ++sl) {
-            if (CL > 1)
-              tma_load_2d_mc(stageA(s, sl) + rank * (TILE_A_BYTES / CL), &mapA, &full_bar[s],
-                             kb * BK, sl * Mpad + m0 + rank * (BM / CL), (uint16_t)((1u << CL) - 1));
-            else
-              tma_load_2d(stageA(s, sl), &mapA, &full_bar[s], kb * BK, sl * Mpad + m0);
-          }
+          for (int sl = 0; sl < NS; ++sl)
+            tma_load_2d(stageA(s, sl), &mapA, &full_bar[s], kb * BK, sl * Mpad + m0);
           for (int sl = 0; sl < NS; ++sl)
             tma_load_2d(stageB(s, sl), &mapB, &full_bar[s], kb * BK, sl * Npad + n0);
         }
       }
-      // drain: every issued stage's copies must have landed before the CTA may exit, and (in a
-      // cluster) every CTA must have released the last stages, so that all multicast writes
-      // and release arrivals aimed at either CTA are complete
+      // drain: every issued stage's copies must have landed before the CTA may exit
       for (int q = (g > NSTAGE ? g - NSTAGE : 0); q < g; ++q)
         mbar_wait(&full_bar[q % NSTAGE], (uint32_t)(q / NSTAGE) & 1u);
-      if (CL > 1)
-        for (int q = (g > NSTAGE ? g - NSTAGE : 0); q < g; ++q)
-          mbar_wait(&empty_bar[q % NSTAGE], (uint32_t)(q / NSTAGE) & 1u);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer: drain group G (global) accumulates into set G % NACC
     if (lane == 0) {
       int g = 0, G = 0;
-      for (int u = unit0; u < n_units && !abort_sh; u += ustep) {
+      for (int id = blockIdx.x; id < n_tiles && !abort_sh; id += gridDim.x) {
         for (int kb = 0; kb < nkb && !abort_sh; ++kb, ++g) {
           const int s = g % NSTAGE;
           const bool first = kb % DRAIN == 0;
@@ -337,9 +314,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               umma_bf16(tmem + (uint32_t)((a * NLEVEL + l) * BN), da, db, IDESC, acc);
             }
           }
-          // stage free (for this CTA's part) once these MMAs have read it
-          if (CL > 1) umma_commit_mc(&empty_bar[s], (uint16_t)((1u << CL) - 1));
-          else umma_commit(&empty_bar[s]);
+          umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
           if (last) {
             umma_commit(&acc_full[a]);  // level sums of this drain group complete
             ++G;
@@ -357,9 +332,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     bool ok = true;
     int G = 0;
-    for (int u = unit0; u < n_units && ok; u += ustep) {
+    for (int id = blockIdx.x; id < n_tiles && ok; id += gridDim.x) {
       int m0, n0;
-      tile_origin(u, m0, n0);
+      tile_origin(id, m0, n0);
       // One exact integer per column: sum over drain groups and levels of I_l 2^(32 - 8 l).  A
       // group's level sum is at most 2^24 in magnitude, so the total stays below 2^57.
       long long isum[EPI_COLS];
@@ -408,7 +383,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync();   // no peer write or arrival aimed at this CTA is still pending
   if (warp == 1) {
     if (lane == 0) mbar_wait(&done_bar, 0);   // no MMA may still be writing TMEM
     __syncwarp();
@@ -488,69 +462,31 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s, int red_n0, bool pairs) {
+                              cudaStream_t s, int red_n0) {
   if (n_rows <= 0) return cudaSuccess;
   if (Mpad % BM || Npad % BN || Kp % BK || ldc % 2) return cudaErrorInvalidValue;
-  CUtensorMap mA, mA2, mB;
+  CUtensorMap mA, mB;
   if (!encode_2d(&mA, A, (uint64_t)Kp, (uint64_t)NSLICE * Mpad, BK, BM)) return cudaErrorInvalidValue;
-  if (!encode_2d(&mA2, A, (uint64_t)Kp, (uint64_t)NSLICE * Mpad, BK, BM / 2)) return cudaErrorInvalidValue;
   if (!encode_2d(&mB, Bt, (uint64_t)Kp, (uint64_t)NSLICE * Npad, BK, BN)) return cudaErrorInvalidValue;
   const size_t sm = fourier_tc_smem();
   const int nt = Npad / BN;
   // first column tile that lies entirely at or after red_n0
   const int rt = std::min(nt, (std::max(red_n0, 0) + BN - 1) / BN);
-  int dev = 0, nsm = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  nsm = std::max(nsm, 1);
-  // single CTAs (any column count): persistent, one per SM
-  auto go1 = [&](auto kern, int t0, int tc) -> cudaError_t {
+  auto go = [&](auto kern, int t0, int tc) -> cudaError_t {
+    if (tc <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(tc * (Mpad / BM), nsm);
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(tc * (Mpad / BM), std::max(nsm, 1));   // persistent: one per SM
     kern<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out, ldc, st,
                                       t0, tc);
     return cudaGetLastError();
   };
-  // pairs of CTAs sharing the k-tile's A operand (even column-tile counts): as many clusters
-  // as can be resident at once
-  auto go2 = [&](auto kern, int t0, int tc) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = sm;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(2);
-    int nclus = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclus, kern, &cfg) != cudaSuccess || nclus < 1) {
-      cudaGetLastError();
-      return cudaErrorNotSupported;
-    }
-    const int units = (tc / 2) * (Mpad / BM);
-    cfg.gridDim = dim3(2 * std::min(units, nclus));
-    e = cudaLaunchKernelEx(&cfg, kern, mA2, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out, ldc, st,
-                           t0, tc);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-  };
-  auto go = [&](auto k1, auto k2, int t0, int tc) -> cudaError_t {
-    if (tc <= 0) return cudaSuccess;
-    if (tc % 2 == 0 && pairs) {
-      cudaError_t e = go2(k2, t0, tc);
-      if (e != cudaErrorNotSupported) return e;
-    }
-    return go1(k1, t0, tc);
-  };
-  cudaError_t e = go(fourier_tc_kernel<NSLICE, 1>, fourier_tc_kernel<NSLICE, 2>, 0, rt);
+  cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt);
   if (e != cudaSuccess) return e;
-  return go(fourier_tc_kernel<NSLICE - 1, 1>, fourier_tc_kernel<NSLICE - 1, 2>, rt, nt - rt);
+  return go(fourier_tc_kernel<NSLICE - 1>, rt, nt - rt);
 }
 
 }  // namespace kubo

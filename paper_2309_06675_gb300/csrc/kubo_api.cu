@@ -92,7 +92,6 @@ struct Plan {
   int kpb = KSUM_KPB;               // k-points per k-sum block
   int pad = 1;                      // leading dimension W + pad in the fused kernels' smem
   bool rot_tc = false;              // FP32-grade rotations on the tensor cores (W <= 64)
-  bool tc_pairs = false;            // tensor-core Fourier sum on CTA pairs (A multicast)
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -501,7 +500,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     const int red_n0 = f32_rotation(p.precision) ? p.W * p.W : p.Npad;
     StageTimer tm(c, KUBO_STAGE_FOURIER, red_n0 < p.Npad ? 3 : 2);
     KCHECK(launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s));
-    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0, p.tc_pairs));
+    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0));
   }
   {
     // MIXED: the reduction and the QL iteration in double-float on the FP32 pipe (both are
@@ -748,7 +747,6 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.pad = o.layout_unpadded ? 0 : 1;
   // the padding ablation concerns the SIMT rotation kernel's shared-memory layout
   p.rot_tc = o.rotation_tc && !o.layout_unpadded;
-  p.tc_pairs = o.tc_cta_pairs != 0;
   if (o.fourier_separable) {
     if (o.workspace) return KUBO_ERR_UNSUPPORTED;   // its size depends on the R set
     r = setup_separable(p, R_vecs, N_R, kb, ke, ri);
@@ -1585,7 +1583,7 @@ kubo_status kubo_bloch(const double* H_R, const int32_t* R_vecs, int W, int N_R,
           KList kl{kidx + t0, 0, (int)std::min<int64_t>(p.chunk, n_k - t0)};
           const int Mb = tc_pad_m(kl.n);
           if (launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s) != cudaSuccess ||
-              launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, p.Npad, o.tc_cta_pairs != 0) != cudaSuccess ||
+              launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, p.Npad) != cudaSuccess ||
               launch_unpack_rows(C64, p.Npad, W, kl.n, Hk + t0 * WW, dHx + t0 * WW, dHy + t0 * WW, c.s) != cudaSuccess) {
             cudaGetLastError();
             r = KUBO_ERR_CUDA;

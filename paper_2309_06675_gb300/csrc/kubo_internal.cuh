@@ -189,7 +189,7 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 // red_n0: first output column whose tile may keep three slices (FP32-grade; Npad = none)
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s, int red_n0, bool pairs = false);
+                              cudaStream_t s, int red_n0);
 // the tensor-core kernel's bounded mbarrier wait on a barrier that never completes
 cudaError_t launch_bounded_wait_check(uint32_t limit, DevStatus* st, cudaStream_t s);
 // rows [n][ld] (H | dxH | dyH packed) -> three packed arrays [n][W*W]

@@ -204,20 +204,3 @@ def test_double_float_reduction_degenerate_bands(kubo, torch):
     S64 = kubo.ahc(H, m.R, kmesh, EF, eta=0.05).cpu().numpy()
     Smx = kubo.ahc(H, m.R, kmesh, EF, eta=0.05, precision="mixed").cpu().numpy()
     assert rel_err(Smx, S64) < REL_MIXED, rel_err(Smx, S64)
-
-
-@pytest.mark.parametrize("W,hw,kmesh,rng", [
-    (64, 5, (128, 128, 128), (3 * 16384, 3 * 16384 + 4096)),   # 64 + 128 column tiles: pairs
-    (16, 2, (32, 32, 32), (100, 3000)),                        # 4 + 8 column tiles: pairs
-    (20, 2, (16, 16, 16), (0, 1500)),                          # 7 + 12: single CTAs, then pairs
-])
-def test_tensor_core_fourier_cta_pairs_bit_identical(kubo, torch, W, hw, kmesh, rng):
-    """The tensor-core Fourier sum on CTA pairs (coefficient slices multicast to both CTAs of
-    a cluster) does the same arithmetic in the same order as one CTA per tile."""
-    m = tbgen.random_tb(W, hw, 1.5, 700 + W)
-    H = cuda(torch, m.H_R)
-    EF = cuda(torch, np.linspace(-1.0, 1.0, 16))
-    for prec in ("mixed", "mixed_fourier"):
-        a = kubo.ahc(H, m.R, kmesh, EF, k_range=rng, precision=prec).cpu().numpy()
-        b = kubo.ahc(H, m.R, kmesh, EF, k_range=rng, precision=prec, tc_cta_pairs=True).cpu().numpy()
-        assert np.array_equal(a, b), (prec, np.max(np.abs(a - b)))
