@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
     // p = tau A22 v, spread densely: thread t takes row r = t mod m and the columns
     // c = part, part + P, ... (part = t / m, P = NT / m); the P partials of a row are added
     // in part order.  Mirrored elements (c > r) are conjugated by flipping the sign bits of
-    // both imaginary halves.
+    // both imaginary halves (one loop for all columns keeps the warp convergent: its threads
+    // have different rows r).
     {
       const int Pp = NT / m;
       const int r = t % m, part = t / m;
@@ -746,11 +747,12 @@ cudaError_t launch_ql_df(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s
 }
 
 // persistent CTAs of the double-float inverse iteration: as many per SM as the iterate
-// arrays (W x ldt pairs of shared memory per CTA) allow; each uses 3 W ldt pairs of the scratch
+// arrays (W x ldt pairs of shared memory per CTA) allow within 220 KB (6 at W = 64: 12 warps
+// per SM, measured faster than 5); each uses 3 W ldt pairs of the scratch
 int iit_df_ctas(int W) {
   const int ldt = (W + 31) / 32 * 32;
   const size_t sm = (size_t)W * ldt * sizeof(float2) + 4 * 1024;
-  return 152 * (int)std::max<size_t>(1, std::min<size_t>(16, (200 * 1024) / sm));
+  return 152 * (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / sm));
 }
 
 cudaError_t launch_iit_df(int W, int n, EighBufs b, double* E, double* Z, double* scratch,
