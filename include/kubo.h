@@ -101,7 +101,8 @@ typedef struct kubo_options {
   void* workspace;          /* device scratch of workspace_bytes; NULL = the library
                                allocates (cudaMallocAsync) and frees it inside the call */
   size_t workspace_bytes;
-  int chunk_k;              /* k-points per internal batch; 0 = automatic */
+  int chunk_k;              /* k-points per internal batch; 0 = automatic (a fixed 24 GiB of
+                               batch buffers, at most 65,536 k-points) */
   kubo_profile* profile;    /* non-NULL: accumulate per-stage launch counts and times */
   double mixed_fixup_rel;   /* KUBO_MIXED / KUBO_MIXED_FOURIER, k-summed entry points; > 0
                                enables an FP64 redo of every k-point with some

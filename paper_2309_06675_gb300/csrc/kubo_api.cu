@@ -137,8 +137,11 @@ size_t bytes_per_k(int W, int n_eta) {
          (size_t)n_eta * W * 8 + 64 + (W > SMALL_W_MAX ? large_region_bytes(W) : 0);
 }
 
+// k-points per batch: a fixed 24 GiB of batch buffers (of GB300's 288 GB), at most 65,536.
+// Larger batches give the lane-per-k QL more resident warps (65,536 at W = 64: 13 per SM);
+// the budget is a constant so that a size query and the call agree.
 int auto_chunk(int W, int n_eta, int64_t n_total, size_t extra_per_k = 0) {
-  const size_t budget = (size_t)12 << 30;
+  const size_t budget = (size_t)24 << 30;
   int64_t c = (int64_t)(budget / (bytes_per_k(W, n_eta) + extra_per_k));
   c = std::max<int64_t>(1024, std::min<int64_t>(c, 65536));
   c = c / 1024 * 1024;
