@@ -104,16 +104,40 @@ __global__ void ksum_step_kernel(const double* __restrict__ E, const double* __r
   }
 }
 
-__global__ void ksum_fold_kernel(const double2* __restrict__ part, int n_blocks, int n_out,
-                                 double2* __restrict__ acc) {
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
-    double s = acc[o].x, c = acc[o].y;
-    for (int b = 0; b < n_blocks; ++b) {
-      double2 p = part[(size_t)b * n_out + o];
+// one CTA per output: thread i folds the partials i, i + FOLD_NT, ... in order (Neumaier),
+// then the per-thread (sum, compensation) pairs are combined in a fixed tree and added to the
+// running accumulator (deterministic: the assignment and the order are fixed)
+constexpr int FOLD_NT = 256;
+__global__ void __launch_bounds__(FOLD_NT) ksum_fold_kernel(const double2* __restrict__ part,
+                                                           int n_blocks, int n_out,
+                                                           double2* __restrict__ acc) {
+  __shared__ double ss[FOLD_NT], cc[FOLD_NT];
+  const int t = threadIdx.x;
+  for (int o = blockIdx.x; o < n_out; o += gridDim.x) {
+    double s = 0.0, c = 0.0;
+    for (int b = t; b < n_blocks; b += FOLD_NT) {
+      const double2 p = part[(size_t)b * n_out + o];
       neumaier_add(s, c, p.x);
       neumaier_add(s, c, p.y);
     }
-    acc[o] = make_double2(s, c);
+    ss[t] = s;
+    cc[t] = c;
+    __syncthreads();
+    for (int h = FOLD_NT / 2; h > 0; h >>= 1) {
+      if (t < h) {
+        double s2 = ss[t], c2 = cc[t];
+        neumaier_add(s2, c2, ss[t + h]);
+        ss[t] = s2;
+        cc[t] = c2 + cc[t + h];
+      }
+      __syncthreads();
+    }
+    if (t == 0) {
+      double s2 = acc[o].x, c2 = acc[o].y;
+      neumaier_add(s2, c2, ss[0]);
+      acc[o] = make_double2(s2, c2 + cc[0]);
+    }
+    __syncthreads();
   }
 }
 
@@ -251,7 +275,7 @@ cudaError_t launch_ksum_partial(const double* E, double* Om, int W, int n, int n
 cudaError_t launch_ksum_fold(const double2* part, int n_blocks, int n_out, double2* acc,
                              cudaStream_t s) {
   if (n_blocks <= 0) return cudaSuccess;
-  ksum_fold_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(part, n_blocks, n_out, acc);
+  ksum_fold_kernel<<<std::min(n_out, 152 * 8), FOLD_NT, 0, s>>>(part, n_blocks, n_out, acc);
   return cudaGetLastError();
 }
 
