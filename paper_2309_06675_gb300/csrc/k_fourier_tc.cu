@@ -67,7 +67,6 @@ constexpr int EPI_COLS = BN / 2;
 constexpr int TMEM_COLS = 512;                       // = NACC * NLEVEL * BN
 
 // PTX wrappers: tc_ptx.cuh
-constexpr uint32_t WAIT_LIMIT = TC_WAIT_LIMIT;
 
 // Failure-detection check: the same bounded wait on a barrier that nothing ever completes.
 // Thread 0 gives up after `limit` tries and records ST_TIMEOUT; the kernel then returns, so
@@ -86,16 +85,11 @@ __global__ void bounded_wait_check_kernel(uint32_t limit, DevStatus* st) {
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
-// Fixed-point slices of x (|x| <= 1): x = sum_i s_i 2^(-7-8i) + O(2^-39), |s_i| <= 128.
-// All operations are exact in FP64 (scaling by powers of two, subtracting integers).
-__device__ __forceinline__ void slice5(double x, __nv_bfloat16 (&sl)[NSLICE]) {
-  double r = x * 128.0;
-#pragma unroll
-  for (int i = 0; i < NSLICE; ++i) {
-    const double q = rint(r);
-    sl[i] = __float2bfloat16_rn((float)q);   // integer with |q| <= 128: exact in BF16
-    r = (r - q) * 256.0;
-  }
+// Fixed-point slices of x 2^-e (|x| <= 2^e): x 2^-e = sum_i s_i 2^(-7-8i) + O(2^-32),
+// |s_i| <= 128, from the FP64 bit pattern with integer operations (fixed31_ll, slice4_bf16 in
+// tc_ptx.cuh): no FP64 instruction, which GB300 issues at 1/64 of the FP32 rate.
+__device__ __forceinline__ void slice_scaled(double x, int e, __nv_bfloat16 (&sl)[NSLICE]) {
+  slice4_bf16(fixed31_ll(x, e), sl);
 }
 
 // ------------------------------------------------------------------ operand preparation
@@ -117,14 +111,22 @@ __device__ __forceinline__ double stacked_basis(const double* __restrict__ Bp,
   return 0.0;
 }
 
-// e[n]: exponent with max_k |basis(n, k)| < 2^e[n] (0 for an all-zero column)
+// e[n]: exponent with max_k |basis(n, k)| < 2^e[n] (0 for an all-zero column).  Block: 128
+// columns (x, coalesced) x SCALE_KY slices of K (y), maxima combined in shared memory.
+constexpr int SCALE_KY = 8;
 __global__ void basis_scale_kernel(const double* __restrict__ Bp, const int* __restrict__ Rh,
                                    int N_h, int W, int Npad, int* __restrict__ e) {
+  __shared__ double red[SCALE_KY][128];
   const int WW = W * W;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < Npad; n += gridDim.x * blockDim.x) {
-    double mx = 0.0;
-    if (n < 3 * WW)
-      for (int k = 0; k <= 2 * N_h; ++k) mx = fmax(mx, fabs(stacked_basis(Bp, Rh, N_h, WW, n, k)));
+  const int n = blockIdx.x * 128 + threadIdx.x;
+  double mx = 0.0;
+  if (n < 3 * WW)
+    for (int k = threadIdx.y; k <= 2 * N_h; k += SCALE_KY)
+      mx = fmax(mx, fabs(stacked_basis(Bp, Rh, N_h, WW, n, k)));
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && n < Npad) {
+    for (int y = 1; y < SCALE_KY; ++y) mx = fmax(mx, red[y][threadIdx.x]);
     int ex = 0;
     if (mx > 0.0) frexp(mx, &ex);   // mx = f 2^ex, f in [0.5, 1)
     e[n] = ex;
@@ -141,9 +143,9 @@ __global__ void basis_slice_kernel(const double* __restrict__ Bp, const int* __r
        t += (int64_t)gridDim.x * blockDim.x) {
     const int n = (int)(t / Kp), k = (int)(t % Kp);
     double v = 0.0;
-    if (n < 3 * WW && k <= 2 * N_h) v = ldexp(stacked_basis(Bp, Rh, N_h, WW, n, k), -e[n]);
+    if (n < 3 * WW && k <= 2 * N_h) v = stacked_basis(Bp, Rh, N_h, WW, n, k);
     __nv_bfloat16 sl[NSLICE];
-    slice5(v, sl);
+    slice_scaled(v, n < 3 * WW ? e[n] : 0, sl);   // |v| < 2^e[n] by construction
 #pragma unroll
     for (int i = 0; i < NSLICE; ++i) Bt[i * plane + t] = sl[i];
   }
@@ -172,8 +174,8 @@ __global__ void coef_slice_kernel(Model md, Mesh mesh, KList kl, int Mpad, int K
       }
     }
     __nv_bfloat16 cs[NSLICE], ss[NSLICE];
-    slice5(c, cs);
-    slice5(s, ss);
+    slice_scaled(c, 0, cs);
+    slice_scaled(s, 0, ss);
     const int64_t o = (int64_t)m * Kp + 2 * h;
 #pragma unroll
     for (int i = 0; i < NSLICE; ++i)
@@ -445,7 +447,7 @@ size_t fourier_tc_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
 
 cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, int Npad, int Kp,
                                int* col_exp, void* Bt, cudaStream_t s) {
-  basis_scale_kernel<<<grid_for(Npad, 128), 128, 0, s>>>(Bp, Rh, N_h, W, Npad, col_exp);
+  basis_scale_kernel<<<(Npad + 127) / 128, dim3(128, SCALE_KY), 0, s>>>(Bp, Rh, N_h, W, Npad, col_exp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   basis_slice_kernel<<<grid_for((int64_t)Npad * Kp, 256), 256, 0, s>>>(Bp, Rh, col_exp, N_h, W, Npad,

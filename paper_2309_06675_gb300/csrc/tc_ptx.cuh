@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace kubo {
@@ -58,6 +59,33 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "%4}], [%2];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
       : "memory");
+}
+
+// ------------------------------------------------------------------ fixed-point slices
+// round(x 2^(31 - e)) for |x| <= 2^e, from the FP64 bit pattern with integer operations only
+// (round half up; zero, subnormal and values below half a unit give 0): |q| <= 2^31
+__device__ __forceinline__ long long fixed31_ll(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int sh = 1044 + e - ex;   // x 2^(31-e) = m 2^(ex - 1075 + 31 - e) = m 2^-sh
+  if (ex == 0 || sh >= 63) return 0;
+  const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const long long q = sh <= 0 ? (long long)(m << (-sh)) : (long long)((m + (1ull << (sh - 1))) >> sh);
+  return (b >> 63) ? -q : q;
+}
+// four signed 8-bit slices of q (|q| <= 2^31) with round-to-nearest carries:
+// q = s0 2^24 + s1 2^16 + s2 2^8 + s3, |s_i| <= 128, each exact in BF16
+__device__ __forceinline__ void slice4_bf16(long long q, __nv_bfloat16 (&o)[4]) {
+  const long long s0 = (q + (1ll << 23)) >> 24;
+  int r = (int)(q - (s0 << 24));   // in [-2^23, 2^23]
+  const int s1 = ((r >> 15) + 1) >> 1;
+  r -= s1 * 65536;
+  const int s2 = ((r >> 7) + 1) >> 1;
+  const int s3 = r - s2 * 256;
+  o[0] = __int2bfloat16_rn((int)s0);
+  o[1] = __int2bfloat16_rn(s1);
+  o[2] = __int2bfloat16_rn(s2);
+  o[3] = __int2bfloat16_rn(s3);
 }
 
 // UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row atoms of 1024 B.
