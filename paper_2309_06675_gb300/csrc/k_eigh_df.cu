@@ -549,11 +549,15 @@ __device__ __forceinline__ float iit_start_f(int i, int j) {
   return 0.5f + (float)(h >> 8) * (1.0f / 16777216.0f);
 }
 
-constexpr int IIT_DF_SOLVES = 3;
+// Two solves: the shifts are the QL eigenvalues to ~2^-45 ||T|| (delta), so one solve from a
+// start with O(1) components leaves a contamination ~delta / gap along the other eigenvectors
+// and two leave (delta / gap)^2 (1e-12 at gap = 1e-7 ||T||), far below the FP32 rounding of U
+// that consumes them; closer eigenvalues form a cluster and are orthogonalised.
+constexpr int IIT_DF_SOLVES = 2;
 
 // Eigenvectors of the tridiagonal T by inverse iteration, as the FP64 kernel (sort, clusters
-// closer than 1e-3 ||T||_1 on one thread, LU of T - lambda I with row interchanges, three
-// solves from a fixed pseudo-random start, modified Gram-Schmidt inside a cluster,
+// closer than 1e-3 ||T||_1 on one thread, LU of T - lambda I with row interchanges, solves
+// (two here, three there) from a fixed pseudo-random start, modified Gram-Schmidt inside a cluster,
 // normalisation), in FP32 pairs: the solves' backward error ~2^-46 ||T|| sets the residual,
 // and the eigenvectors are accurate to ~2^-46 ||T|| / gap.  Coincident eigenvalues are
 // separated by 10 2^-46 ||T||_1.
