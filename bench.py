@@ -52,7 +52,7 @@ DF_OPS_PER_MAC = 12
 # stage), from one ncu capture of the current kernel (profiles/, W = 64); a kernel that
 # changes after its capture leaves this table.
 DRAM_BYTES_PER_K = {("mixed", "tridiag"): 97.2e3}
-# algorithmic flops per k-point by stage (W = 64, N_R = 1331), see the design doc
+# algorithmic flops per k-point by stage (useful work of each step of the method)
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
 
