@@ -74,8 +74,9 @@ __device__ __forceinline__ void store_tile(double2* C, int W, int LD, int ty, in
 template <typename TIn>
 __device__ __forceinline__ void unpack_hermitian(const TIn* __restrict__ P, double2* A, int W,
                                                  int LD, int t) {
+  const FastDiv dW(W);
   for (int idx = t; idx < W * W; idx += NT) {
-    int i = idx / W, j = idx % W;
+    const int i = (int)dW.div(idx), j = idx - i * W;
     double2 a;
     if (i < j) a = make_double2((double)P[i * W + j], (double)P[j * W + i]);
     else if (i > j) a = make_double2((double)P[j * W + i], -(double)P[i * W + j]);
@@ -212,8 +213,9 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
     }
   }
   __syncthreads();
+  const FastDiv dW(W);
   for (int idx = t; idx < n_eta * W; idx += NT) {
-    const int e = idx / W, n = idx % W;
+    const int e = (int)dW.div(idx), n = idx - e * W;
     const double* p = red + (size_t)idx * 2 * 16;
     double sr = 0.0, sc = 0.0;
 #pragma unroll
@@ -247,7 +249,11 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
   const int64_t k = blockIdx.x;
   const size_t WW = (size_t)W * W;
 
-  for (int idx = t; idx < W * W; idx += NT) sU[(idx / W) * LD + idx % W] = U[k * WW + idx];
+  const FastDiv dW(W);
+  for (int idx = t; idx < W * W; idx += NT) {
+    const int r = (int)dW.div(idx);
+    sU[r * LD + idx - r * W] = U[k * WW + idx];
+  }
   unpack_hermitian(Xp + k * ld, sA, W, LD, t);
   for (int j = t; j < W; j += NT) sE[j] = E[k * W + j];
   if (t < n_eta) sEta[t] = etas[t];
@@ -333,8 +339,9 @@ __device__ __forceinline__ void store_tile_f32(float2* C, int W, int LD, int ty,
 template <typename TIn>
 __device__ __forceinline__ void unpack_hermitian_f32(const TIn* __restrict__ P, float2* A, int W,
                                                      int LD, int t) {
+  const FastDiv dW(W);
   for (int idx = t; idx < W * W; idx += NT) {
-    int i = idx / W, j = idx % W;
+    const int i = (int)dW.div(idx), j = idx - i * W;
     float2 a;
     if (i < j) a = make_float2((float)P[i * W + j], (float)P[j * W + i]);
     else if (i > j) a = make_float2((float)P[j * W + i], -(float)P[i * W + j]);
@@ -367,15 +374,20 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
                                                const double2* __restrict__ R,
                                                const double* __restrict__ tau, int W, int LD,
                                                int t, float2* sU, float2* stage) {
-  for (int idx = t; idx < W * W; idx += NT) {
-    const int r = idx / W, c = idx % W;
-    const float z = (float)Zk[idx];
-    const double2 p = ph[r];
-    sU[r * LD + c] = make_float2((float)p.x * z, (float)p.y * z);
-  }
   auto roff = [&](int j) { return j * (W - 1) - (j * (j - 1)) / 2; };   // sum_{j'<j} (W-1-j')
+  // the phases in FP32 once per row (the FP64 -> FP32 conversions issue on the FP64 pipe)
+  __shared__ float2 sPh[64];   // W <= 64
+  for (int j = t; j < W; j += NT) {
+    const double2 p = ph[j];
+    sPh[j] = make_float2((float)p.x, (float)p.y);
+  }
+  __syncthreads();
+  const FastDiv dW(W);
   for (int idx = t; idx < W * W; idx += NT) {
-    const int r = idx / W, c = idx % W;
+    const int r = (int)dW.div(idx), c = idx - r * W;
+    const float z = (float)Zk[idx];
+    const float2 p = sPh[r];
+    sU[r * LD + c] = make_float2(p.x * z, p.y * z);
     if (r > c && c < W - 2) {
       const double2 v = R[idx];
       stage[roff(c) + (r - c - 1)] = make_float2((float)v.x, (float)v.y);
@@ -530,9 +542,11 @@ __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restric
   if (FROMZ) {
     assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, LD, t, sU, sA);
   } else {
+    const FastDiv dW(W);
     for (int idx = t; idx < W * W; idx += NT) {
-      double2 u = U[k * WW + idx];
-      sU[(idx / W) * LD + idx % W] = make_float2((float)u.x, (float)u.y);
+      const double2 u = U[k * WW + idx];
+      const int r = (int)dW.div(idx);
+      sU[r * LD + idx - r * W] = make_float2((float)u.x, (float)u.y);
     }
   }
   unpack_hermitian_f32(Xp + k * ld, sA, W, LD, t);

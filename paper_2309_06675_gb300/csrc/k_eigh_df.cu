@@ -61,13 +61,21 @@ __device__ __forceinline__ float2 df_split(double x) {
 
 // The conversions between FP64 and FP32 pairs run on the FP64 pipe; for the bulk input and
 // output they are done on the bit patterns instead (integer pipe), with the FP64 conversion
-// only for exponents outside a safe range (zero included on the input side).
+// only for exponents outside a safe range.  That rare path is a call, which the compiler
+// branches around: inlined, it would be issued predicated off for every element, and a
+// predicated-off FP64 instruction still takes its slots on the FP64 pipe.
+__device__ __noinline__ float2 df_split_slow(double x);
+__device__ __noinline__ double widen_slow(float f) { return (double)f; }
 // x = hi + lo with hi = x truncated to 24 significant bits and lo the remaining 29 bits
 // rounded to FP32 (|x - hi - lo| <= 2^-48 |x|).
 __device__ __forceinline__ float2 df_split_bits(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex < 1023 - 70 || ex > 1023 + 70) return df_split(x);
+  if (ex < 1023 - 70 || ex > 1023 + 70) {
+    // +-0 as df_split gives it: (+-0, +0)
+    if ((b << 1) == 0ull) return make_float2(__uint_as_float((uint32_t)(b >> 32)), 0.f);
+    return df_split_slow(x);
+  }
   const uint32_t sgn = (uint32_t)(b >> 63) << 31;
   const uint32_t hb = sgn | ((uint32_t)(ex - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
   // the low 29 bits are worth low29 2^(ex - 1075); 2^(ex - 1075) = 2^(ex - 1023 - 52) is a
@@ -83,12 +91,14 @@ __device__ __forceinline__ double widen_bits(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t ex = (u >> 23) & 0xFFu;
   if ((u & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)((unsigned long long)u << 32));
-  if (ex == 0 || ex == 0xFFu) return (double)f;
+  if (ex == 0 || ex == 0xFFu) return widen_slow(f);
   return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
                                           ((unsigned long long)(ex + 896) << 52) |
                                           ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 __device__ __forceinline__ double df_val(float h, float l) { return widen_bits(h) + widen_bits(l); }
+
+__device__ __noinline__ float2 df_split_slow(double x) { return df_split(x); }
 
 // complex element as float4 (re_h, re_l, im_h, im_l)
 __device__ __forceinline__ float4 cdf_split(double re, double im) {
@@ -262,6 +272,19 @@ __device__ __forceinline__ void rank2_elem(float4& a, const float4& vr, const fl
   }
 }
 
+// FastDiv magics ceil(2^32 / d) of the trailing-block orders 2 <= d <= 256: the symv's row /
+// part split of each column step reads one (the same for the whole block) instead of running
+// two integer divides, whose int <-> float conversions would queue on the FP64 pipe.
+struct DivMagic {
+  uint32_t v[257];
+};
+constexpr DivMagic make_div_magic() {
+  DivMagic t{};
+  for (uint32_t d = 2; d <= 256; ++d) t.v[d] = 0xFFFFFFFFu / d + 1u;
+  return t;
+}
+__constant__ DivMagic c_divmag = make_div_magic();
+
 // Packed rows of leading dimension ld (the [H | dxH | dyH] rows of the tensor-core Fourier
 // sum).  Shared memory: the lower triangle packed by rows (element (r, c <= r) at
 // r (r + 1) / 2 + c) as complex double-float, two reflector buffers, p / w, the symv
@@ -321,19 +344,29 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
     // both imaginary halves (one loop for all columns keeps the warp convergent: its threads
     // have different rows r).
     {
-      const int Pp = NT / m;
-      const int r = t % m, part = t / m;
+      const uint32_t mag = c_divmag.v[m];   // floor(a / m) = umulhi(a, mag) for a <= NT
+      const int Pp = (int)__umulhi(NT, mag);
+      const int part = (int)__umulhi(t, mag), r = t - part * m;
       if (part < Pp) {
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int rowb = tri(o + r, o);
+        // running packed indices of (r, c) (row-contiguous, + Pp per step of c) and of the
+        // mirror (c, r) = tri(o + c, o + r), whose step (o + c) Pp + Pp (Pp + 1) / 2 itself
+        // grows by Pp^2
+        int ilo = tri(o + r, o) + part;
+        int iup = tri(o + part, o + r);
+        int dup = (o + part) * Pp + ((Pp * (Pp + 1)) >> 1);
+        const int pp2 = Pp * Pp;
         for (int c = part; c < m; c += Pp) {
           const bool up = c > r;
-          float4 a = A[up ? tri(o + c, o + r) : rowb + c];
+          float4 a = A[up ? iup : ilo];
           if (up) {
             a.z = -a.z;
             a.w = -a.w;
           }
           cdf_mac<false>(acc, a, vb[c]);
+          ilo += Pp;
+          iup += dup;
+          dup += pp2;
         }
         sp[part * m + r] = acc;
       }
@@ -342,7 +375,7 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
     // warps 0..3 (m <= 127 rows): p_t = tau sum of the partials, K = tau Re(v^H p) / 2,
     // w_t = p_t - K v_t
     if (t < 128) {
-      const int Pp = NT / m;
+      const int Pp = (int)__umulhi(NT, c_divmag.v[m]);
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = make_float4(0.f, 0.f, 0.f, 0.f);
       float dh = 0.f, dl = 0.f;
       if (t < m) {
@@ -401,13 +434,16 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
     } else {
       const int n1 = m - 1;
       const int ntri = n1 * (n1 + 1) / 2;
+      // element (r + 1, c + 1) of the trailing block sits at tri(o + r + 1, o + c + 1)
+      // = idx + r (o + 1) + tri(o + 1, o + 1) for idx = tri(r, c)
+      const int o1 = o + 1, base = tri(o + 1, o + 1);
       for (int idx = t - 32; idx < ntri; idx += NT - 32) {
         const int r = rowof[idx];
         const int c = idx - tri(r, 0);
-        // element (r + 1, c + 1) of the trailing block
-        float4 a = A[tri(o + r + 1, o + c + 1)];
+        const int ia = idx + r * o1 + base;
+        float4 a = A[ia];
         rank2_elem(a, vb[r + 1], pb[r + 1], vb[c + 1], pb[c + 1], r == c);
-        A[tri(o + r + 1, o + c + 1)] = a;
+        A[ia] = a;
       }
     }
     __syncthreads();
@@ -453,15 +489,15 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
     tout[j] = j < W - 2 ? tb[j] : 0.0;
   }
   double2* rout = b.refl + (size_t)k * W * W;
-  for (int idx = t; idx < W * W; idx += NT) {
-    const int r = idx / W, c = idx % W;
-    double2 v = make_double2(0.0, 0.0);
-    if (r > c) {
-      const float4 a = A[tri(r, c)];
-      v = make_double2(df_val(a.x, a.y), df_val(a.z, a.w));
+  for (int r = warp; r < W; r += NT / 32)
+    for (int c = lane; c < W; c += 32) {
+      double2 v = make_double2(0.0, 0.0);
+      if (r > c) {
+        const float4 a = A[tri(r, c)];
+        v = make_double2(df_val(a.x, a.y), df_val(a.z, a.w));
+      }
+      rout[r * W + c] = v;
     }
-    rout[idx] = v;
-  }
 }
 
 // ------------------------------------------------------------------ QL in double-float
@@ -542,11 +578,13 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-// deterministic start vector in [0.5, 1.5) from an integer hash of (row, vector)
+// deterministic start vector in [0.5, 1.5) from an integer hash of (row, vector): 23 hash bits
+// as the mantissa of a number in [1, 2), minus 1/2 (no int -> float conversion, which would
+// issue on the FP64 pipe)
 __device__ __forceinline__ float iit_start_f(int i, int j) {
   unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
   h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
-  return 0.5f + (float)(h >> 8) * (1.0f / 16777216.0f);
+  return __fsub_rn(__uint_as_float(0x3F800000u | (h >> 9)), 0.5f);
 }
 
 // Two solves: the shifts are the QL eigenvalues to ~2^-45 ||T|| (delta), so one solve from a

@@ -73,6 +73,17 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
 }
 
+// floor(a / d) by one multiply-high with mag = ceil(2^32 / d), exact for a d < 2^32 (the
+// rounding excess of mag, below 1, times a stays under 2^32 / d).  The integer-divide sequence
+// it replaces converts through float, and those conversions issue on the FP64 pipe.
+// mag = 0 marks d = 1.
+struct FastDiv {
+  uint32_t d, mag;
+  __host__ __device__ static uint32_t magic(uint32_t dd) { return dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u; }
+  __device__ explicit FastDiv(uint32_t dd) : d(dd), mag(magic(dd)) {}
+  __device__ __forceinline__ uint32_t div(uint32_t a) const { return mag ? __umulhi(a, mag) : a; }
+};
+
 // e^{i k.R} from per-axis twiddle tables with exact integer argument reduction.
 __device__ __forceinline__ double2 mesh_phase(const double2* __restrict__ tab, const int* off,
                                               const Mesh& m, int j1, int j2, int j3, int r1,
