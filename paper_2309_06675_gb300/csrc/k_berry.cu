@@ -130,8 +130,13 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
   using R = typename std::conditional<F32, float, double>::type;
   const double thr2 = (1e-12 * emax) * (1e-12 * emax);
   R num[TM][TM];
-  double d2[TM][TM];
-  unsigned small0 = 0;   // bit (i TM + j): d2 <= thr2 (dropped when eta = 0)
+  // (dE)^2 per pair: FP64 for FP64 velocities; for FP32 ones only its FP32 rounding is kept
+  // (the FP64 fallback recomputes it), and the pair / cut-off tests are bit masks, so that the
+  // per-eta loop issues no FP64 compare
+  double d2[F32 ? 1 : TM][F32 ? 1 : TM];
+  float d2f[TM][TM];
+  unsigned pairs = 0;    // bit (i TM + j): n < m < W
+  unsigned small0 = 0;   // bit (i TM + j): (dE)^2 <= thr2 (dropped when eta = 0)
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int n = ty + 16 * i;
@@ -139,29 +144,26 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
     for (int j = 0; j < TM; ++j) {
       const int m = tx + 16 * j;
       num[i][j] = 0;
-      d2[i][j] = -1.0;   // marks "no pair"
+      d2f[i][j] = 0.f;
       if (n < W && m < W && n < m) {
+        pairs |= 1u << (i * TM + j);
         const V vx = sVx[n * LD + m];
         if constexpr (F32)
           num[i][j] = -2.0f * diff_of_products(vx.y, vy[i][j].x, vx.x, vy[i][j].y);
         else
           num[i][j] = -2.0 * (vx.y * vy[i][j].x - vx.x * vy[i][j].y);
         const double dE = sE[n] - sE[m];
-        d2[i][j] = dE * dE;
-        if (d2[i][j] <= thr2) small0 |= 1u << (i * TM + j);
+        const double q = dE * dE;
+        if constexpr (F32) d2f[i][j] = (float)q;
+        else d2[i][j] = q;
+        if (q <= thr2) small0 |= 1u << (i * TM + j);
       }
     }
-  }
-  float d2f[TM][TM];
-  if constexpr (F32) {
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TM; ++j) d2f[i][j] = (float)d2[i][j];
   }
   __syncthreads();
   for (int e = 0; e < n_eta; ++e) {
     const double eta = sEta[e];
+    const bool eta0 = eta == 0.0;
     R rp[TM], cp[TM], rl[TM], cl[TM];   // (rl, cl: the FP32 pairs' low parts)
 #pragma unroll
     for (int i = 0; i < TM; ++i) { rp[i] = 0; cp[i] = 0; rl[i] = 0; cl[i] = 0; }
@@ -172,8 +174,8 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TM; ++j) {
-          if (d2[i][j] < 0.0) continue;
-          if (eta == 0.0 && ((small0 >> (i * TM + j)) & 1u)) continue;
+          if (!((pairs >> (i * TM + j)) & 1u)) continue;
+          if (eta0 && ((small0 >> (i * TM + j)) & 1u)) continue;
           const float den = d2f[i][j] + eta2;
           if (den < 0x1p-86f) fp64 = true;
           const float T = num[i][j] / den;
@@ -189,9 +191,16 @@ __device__ __forceinline__ void curvature_epilogue(const V* sVx, const V (&vy)[T
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TM; ++j) {
-          if (d2[i][j] < 0.0) continue;
-          if (eta == 0.0 && ((small0 >> (i * TM + j)) & 1u)) continue;
-          const double T = (double)num[i][j] / fma(eta, eta, d2[i][j]);
+          if (!((pairs >> (i * TM + j)) & 1u)) continue;
+          if (eta0 && ((small0 >> (i * TM + j)) & 1u)) continue;
+          double q;
+          if constexpr (F32) {
+            const double dE = sE[ty + 16 * i] - sE[tx + 16 * j];
+            q = dE * dE;
+          } else {
+            q = d2[i][j];
+          }
+          const double T = (double)num[i][j] / fma(eta, eta, q);
           rq[i] += T;
           cq[j] -= T;
         }

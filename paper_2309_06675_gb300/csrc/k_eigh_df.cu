@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(128) iit_df_kernel(int W, int n, EighBufs b,
         for (int it = 0; it < IIT_DF_SOLVES; ++it) {
           // forward elimination L y = P b; the running row value is carried in registers
           Df cur = ldf(Zs, 0);
-#pragma unroll 4
+#pragma unroll 8
           for (int i = 0; i + 1 < W; ++i) {
             const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
             const Df mlt = ldf(ML, (size_t)i * ldt + t);
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(128) iit_df_kernel(int W, int n, EighBufs b,
           sdf(Zs, (size_t)(W - 1) * ldt, cur);
           // back substitution U x = y (U2 of row i: e_i+1 on swapped rows, else 0)
           Df x1 = Df{0.f, 0.f}, x2 = Df{0.f, 0.f};
-#pragma unroll 4
+#pragma unroll 8
           for (int i = W - 1; i >= 0; --i) {
             const bool sw = i + 1 < W && (i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull));
             const size_t o = (size_t)i * ldt + t;
