@@ -274,7 +274,7 @@ __device__ __forceinline__ void rank2_elem(float4& a, const float4& vr, const fl
 
 // FastDiv magics ceil(2^32 / d) of the trailing-block orders 2 <= d <= 256: the symv's row /
 // part split of each column step reads one (the same for the whole block) instead of running
-// two integer divides, whose int <-> float conversions would queue on the FP64 pipe.
+// two integer-divide sequences.
 struct DivMagic {
   uint32_t v[257];
 };
@@ -579,8 +579,7 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
 }
 
 // deterministic start vector in [0.5, 1.5) from an integer hash of (row, vector): 23 hash bits
-// as the mantissa of a number in [1, 2), minus 1/2 (no int -> float conversion, which would
-// issue on the FP64 pipe)
+// as the mantissa of a number in [1, 2), minus 1/2
 __device__ __forceinline__ float iit_start_f(int i, int j) {
   unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
   h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;

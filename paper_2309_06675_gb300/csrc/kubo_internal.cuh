@@ -75,8 +75,8 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
 
 // floor(a / d) by one multiply-high with mag = ceil(2^32 / d), exact for a d < 2^32 (the
 // rounding excess of mag, below 1, times a stays under 2^32 / d).  The integer-divide sequence
-// it replaces converts through float, and those conversions issue on the FP64 pipe.
-// mag = 0 marks d = 1.
+// it replaces is about a dozen instructions (a float reciprocal estimate, two conversions and
+// the integer corrections).  mag = 0 marks d = 1.
 struct FastDiv {
   uint32_t d, mag;
   __host__ __device__ static uint32_t magic(uint32_t dd) { return dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u; }
