@@ -62,7 +62,13 @@ typedef enum {
   KUBO_FP64 = 0,            /* every step in FP64 */
   KUBO_MIXED = 1,           /* step (1) on the tensor cores (fixed-point BF16 slices with exact
                                FP32 block accumulation, ~40-bit result), step (3) in FP32;
-                               eigensolver, denominators, curvature sums and k-sum in FP64 */
+                               eigensolver in double-float (pairs of FP32, ~2^-46 per
+                               operation), energy differences and k-sum in FP64, curvature
+                               quotient in FP32 (FP64 below a 2^-86 denominator).  The pairs
+                               need max |H(R)| between about 1e-12 and 1e12 (squares and their
+                               low parts stay normal FP32 numbers); outside that range use
+                               KUBO_FP64, or scale H(R), E_F, eta and kT by one power of two,
+                               which leaves S(E_F) unchanged */
   KUBO_MIXED_FOURIER = 2,   /* error-budget mode: only step (1) mixed, step (3) in FP64 */
   KUBO_MIXED_ROTATION = 3   /* error-budget mode: only step (3) mixed (FP32), step (1) in FP64 */
 } kubo_precision;
