@@ -28,6 +28,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import resource
 import statistics
 import subprocess
 import sys
@@ -206,19 +207,23 @@ def run_reference(args, rank, world):
     plane = kmesh[1] * kmesh[2]
     n_per_step = 64
     rng = np.random.default_rng(0)
-    times = []
+    times, cpus = [], []
     for s in range(args.warmup + args.steps):
         base = (s * args.planes) % kmesh[0] * plane
         kidx = np.sort(rng.choice(args.planes * plane, n_per_step, replace=False)) + base
+        r0 = resource.getrusage(resource.RUSAGE_SELF)
         t0 = time.perf_counter()
         O.ahc(model.H_R, model.R, kmesh, E_F, etas=[eta], kT=kT, kidx=kidx)
         dt = time.perf_counter() - t0
+        r1 = resource.getrusage(resource.RUSAGE_SELF)
         if s >= args.warmup:
             times.append(dt)
+            cpus.append((r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime))
     tot = sum(times)
     value = n_per_step * args.steps / tot
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = f"{n_per_step} random k-points of each step's slab, numpy/LAPACK FP64 oracle"
+    sample = (f"{n_per_step} random k-points of each step's slab, numpy/LAPACK FP64 oracle "
+              f"({sum(cpus) / tot:.1f} cores busy on average)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "k-points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -236,12 +241,16 @@ def run_reference(args, rank, world):
 def cpu_baseline(model, kmesh, E_F, eta, kT, n):
     from oracle import kubo_oracle as O
     kidx = tbgen.k_sample(kmesh, n, seed=123)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
     O.ahc(model.H_R, model.R, kmesh, E_F, etas=[eta], kT=kT, kidx=kidx)
     dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": n / dt, "unit": "k-points/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} seeded random k-points of the 128^3 mesh ({dt:.1f} s), numpy/LAPACK FP64"}
+            "sample": f"{n} seeded random k-points of the 128^3 mesh ({dt:.1f} s wall, "
+                      f"{cpu:.1f} s CPU: {cpu / dt:.1f} cores busy on average), numpy/LAPACK FP64"}
 
 
 def stage_table(st, fl, k_total):
