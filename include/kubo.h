@@ -120,9 +120,11 @@ typedef struct kubo_options {
                                kernel (E_j - E_i) / ((E_j - E_i)^2 + eps^2) (energy units);
                                <= 0 (the default) = 1e-12 max_n |E_n(k)| at each k. */
   int layout_unpadded;      /* 1: shared-memory matrices of the eigenvector and rotation
-                               kernels with leading dimension W instead of W + 1 -- the
-                               padding ablation (Sec. 2.3 pads against memory-bank
-                               conflicts); slower, same results.  0 (default): padded. */
+                               kernels with leading dimension W instead of the padded one
+                               (W + 1 for FP64 matrices, the W + P = 4 mod 16 of the FP32
+                               rotation) -- the padding ablation (Sec. 2.3 pads against
+                               memory-bank conflicts); slower, same results.  0 (default):
+                               padded. */
   int fourier_separable;    /* 1: step (1) as three one-axis sums over the bounding box of the
                                R set instead of the dense contraction (FP64; precision
                                KUBO_FP64 or KUBO_MIXED_ROTATION; kubo_ahc / kubo_ahc_host with a
