@@ -7,7 +7,9 @@ Gamma-centred mesh, 64 Fermi levels in [-1, 1], eta = 1e-3.
 
 One step = one ``kubo_ahc`` call (the whole hot path: Fourier sum, eigensolver, rotations,
 curvature, k-sum) over a slab of ``--planes`` k_1-planes of the mesh (planes x 128 x 128
-k-points).  Ranks (torchrun, one GPU each) take disjoint slabs: weak scaling, no data-path
+k-points).  The headline is the mixed-precision form (tensor-core Fourier sum, FP64
+eigensolver, FP32 rotations); the plain FP64 path and the double-float-eigensolver variant
+are timed beside it on the same slabs, with their errors against the FP64 path.  Ranks (torchrun, one GPU each) take disjoint slabs: weak scaling, no data-path
 collective.  Timed: exactly K steps after W warm-up steps, CUDA events on the library's
 stream (torch's current stream), barrier + synchronize on both sides, max over ranks.
 
@@ -44,15 +46,17 @@ import tbgen  # noqa: E402
 
 METRIC = "k-points/sec for σ_xy (W=64, N_R=1331), mixed vs FP64 GPU at rel err ≤1e-5; % roofline"
 WORKLOAD = "w64_r1331_k128"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
-FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12   # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (ops/s)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz (derived)
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12   # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (derived)
+# padded K of the tensor-core Fourier contraction (N_R = 1331 -> multiple of 64)
+TC_KPAD = (1331 + 63) // 64 * 64
 # minimal FP32 operations of one double-float multiply-accumulate (TwoProd by FMA with the two
 # cross terms, Knuth's TwoSum into the accumulator, the low-part update)
 DF_OPS_PER_MAC = 12
 # DRAM bytes (read + write) per k-point of the kernels that can dominate a step, by (path,
 # stage), from one ncu capture of the current kernel (profiles/, W = 64); a kernel that
 # changes after its capture leaves this table.
-DRAM_BYTES_PER_K = {("mixed", "tridiag"): 97.3e3}
+DRAM_BYTES_PER_K = {}
 # algorithmic flops per k-point by stage (useful work of each step of the method)
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
@@ -60,7 +64,7 @@ def stage_flops(W, N_R, prec="fp64"):
     In the mixed path the eigenvector stage stops at the eigenvectors Z of the tridiagonal
     (inverse iteration) and U = Q D Z is assembled in FP32 inside the rotation kernel.
     """
-    mixed = prec != "fp64"
+    mixed = prec != "fp64"   # every reduced mode assembles U in FP32 inside the rotation kernel
     return {
         "fourier": 6.0 * N_R * W * W,     # real contraction [3 x N_R] . [N_R x W^2]
         "tridiag": 16.0 / 3.0 * W ** 3,   # complex Householder reduction
@@ -76,35 +80,47 @@ def stage_flops(W, N_R, prec="fp64"):
     }
 
 
-def measured_bf16_sustained():
+def measured_peaks():
+    """bf16 burst / sustained TFLOP/s and HBM GB/s from MEASURED_PEAKS.json (else the fallback)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+            d = json.load(f)
+        return {"bf16": float(d["bf16_tflops"]), "bf16_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm_gbs": float(d["hbm_gbs"]), "how": "measured"}
     except (OSError, KeyError, ValueError):
-        return 1700.0, "fallback (sustained)"
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm_gbs": 6800.0, "how": "fallback"}
+
+
+def issued_tc_flops_per_k(W, prec):
+    """BF16 slice-pair products the tensor-core Fourier sum issues per k-point: 10 pairs (4
+    slices per operand) on the W^2 columns of H, 6 pairs (3 slices) on the 2 W^2 velocity
+    columns when the rotation that consumes them is FP32 (else 10 there too); x 2 flops x the
+    padded K."""
+    vel_pairs = 6 if prec in ("mixed", "mixed_df", "mixed_rotation") else 10
+    return 2.0 * TC_KPAD * (10 * W * W + vel_pairs * 2 * W * W)
 
 
 def roofline_of(dom, head, W, N_R, k_per_launch, ms_per_launch):
     """Roofline of the dominant kernel: algorithmic work per launch / its average duration,
     against the peak of the pipe that kernel runs on."""
     t = ms_per_launch / 1e3
-    if head == "mixed" and dom == "tridiag":
+    if head == "mixed_df" and dom == "tridiag":
         ops = DF_OPS_PER_MAC * (8.0 / 3.0) * W ** 3 * k_per_launch
         return {"bound": "alu", "achieved": ops / t / 1e12, "peak": FP32_PEAK_TOPS,
                 "unit": "T FP32-op/s",
                 "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (derived).  Work: the "
                              "double-float reduction's 8/3 W^3 real multiply-adds at the minimal "
                              f"{DF_OPS_PER_MAC} FP32 operations each"}
-    if head == "mixed" and dom == "berry":
+    if head != "fp64" and dom == "berry":
         fl = (24.0 + 8.0) * W ** 3 * k_per_launch
         return {"bound": "alu", "achieved": fl / t / 1e12, "peak": 2 * FP32_PEAK_TOPS,
                 "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"}
-    if head == "mixed" and dom == "fourier":
-        kp = (N_R + 63) // 64 * 64
-        fl = 2.0 * kp * (10 * W * W + 6 * 2 * W * W) * k_per_launch   # issued BF16 slice products
-        peak, how = measured_bf16_sustained()
-        return {"bound": "tensor", "achieved": fl / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_note": f"bf16 dense {how}; work: issued BF16 slice-pair products"}
+    if head != "fp64" and dom == "fourier":
+        fl = issued_tc_flops_per_k(W, head) * k_per_launch   # issued BF16 slice products
+        pk = measured_peaks()
+        return {"bound": "tensor", "achieved": fl / t / 1e12, "peak": pk["bf16_sustained"],
+                "unit": "TFLOP/s",
+                "peak_note": f"bf16 dense sustained, {pk['how']}; work: issued BF16 slice-pair products"}
     fl = stage_flops(W, N_R, head)[dom] * k_per_launch
     return {"bound": "alu", "achieved": fl / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk/SM (one DFMA warp instruction per 16 "
@@ -117,12 +133,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kubo", choices=["kubo", "reference"])
-    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64", "mixed_df"],
+                    help="both = the mixed headline, the FP64 path and the double-float variant")
     ap.add_argument("--planes", type=int, default=4, help="k_1-planes of the 128^3 mesh per step")
     ap.add_argument("--cpu-sample", type=int, default=768, help="k-points for the CPU oracle baseline")
     ap.add_argument("--chunk", type=int, default=0, help="k-points per internal batch (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact batched / grad / sweep results of the default line")
     ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep", "pad", "separable"])
     return ap.parse_args()
 
@@ -278,6 +297,75 @@ def _timed(fn, steps, warmup, local):
     return a.elapsed_time(b) / steps, clocks.stop()
 
 
+def workload_batched(kubo, torch, dev, steps, warmup, local, prec, every=1):
+    """64 uneven models (tbgen.batch_recipe), one kubo_ahc_batched call per step over every
+    model's whole mesh; every > 1 keeps each every-th model (a bounded slab of the batch)."""
+    rec = tbgen.batch_recipe()[::every]
+    P, nk = [], 0
+    for r in rec:
+        m = tbgen.random_tb(r["W"], r["half_width"], r["decay"], r["seed"])
+        H = torch.from_numpy(m.H_R).to(dev)
+        # Fermi level: midpoint of the two middle levels of H(k=0), from the library itself
+        Hp, _, _ = kubo.bloch(H, m.R, (1, 1, 1), torch.zeros(1, dtype=torch.int64, device=dev))
+        E, _ = kubo.eigh_batched(Hp, m.W, vectors=False)
+        E = E[0].cpu().numpy()
+        h = (m.W + 1) // 2
+        ef = 0.5 * (E[h - 1] + E[h])
+        P.append((H, m.R, (r["mesh"],) * 3, torch.tensor([ef], dtype=torch.float64, device=dev)))
+        nk += r["mesh"] ** 3
+    sched = {}
+
+    def step():
+        _, sc, _ = kubo.ahc_batched(P, precision=prec, tune=True)
+        sched.update(sc)
+    ms, clk = _timed(step, steps, warmup, local)
+    return {"value": nk / (ms / 1e3), "unit": "k-points/s", "ms_per_step": ms,
+            "models": len(P), "k_points": nk, "precision": prec, "schedule": sched, "clocks": clk,
+            "workload": "batch64_w8-96_r343-1331_k32-64" + (f"[::{every}]" if every > 1 else "")}
+
+
+def workload_grad(kubo, torch, dev, steps, warmup, local, k_limit=0):
+    """W = 32, N_R = 729, 48^3 mesh, kT = 25 meV, eta = 5e-3: value + gradient (FP64);
+    k_limit > 0 evaluates the first k_limit k-points of the mesh (a bounded slab)."""
+    model, kmesh, E_F, etas, kT = tbgen.config("w32_r729_k48_fd")
+    H = torch.from_numpy(model.H_R).to(dev)
+    EF = torch.from_numpy(E_F).to(dev)
+    g = torch.ones((1, E_F.size), dtype=torch.float64, device=dev)
+    nk = int(np.prod(kmesh)) if k_limit <= 0 else int(k_limit)
+    rng = None if k_limit <= 0 else (0, nk)
+    prof = kubo.Profile()
+
+    def step():
+        kubo.ahc_grad(H, model.R, kmesh, EF, g, eta=float(etas[0]), kT=kT, with_value=True,
+                      profile=prof, k_range=rng)
+    ms, clk = _timed(step, steps, warmup, local)
+    ms_f, _ = _timed(lambda: kubo.ahc(H, model.R, kmesh, EF, eta=float(etas[0]), kT=kT, k_range=rng),
+                     steps, 1, local)
+    return {"value": nk / (ms / 1e3), "unit": "k-points/s", "ms_per_step": ms, "k_per_step": nk,
+            "forward_only": {"value": nk / (ms_f / 1e3), "ms_per_step": ms_f}, "dtype": "f64",
+            "stages": {k: v for k, v in prof.as_dict().items() if v["launches"]}, "clocks": clk,
+            "workload": "w32_r729_k48_fd", "W": model.W, "N_R": model.N_R, "kmesh": list(kmesh),
+            "kT": kT, "eta": float(etas[0])}
+
+
+def workload_sweep(kubo, torch, dev, steps, warmup, local, prec, planes):
+    """W = 128, N_R = 1331, 96^3 mesh, 512 Fermi levels x 4 broadenings, slabs of k1-planes."""
+    model, kmesh, E_F, etas, kT = tbgen.config("w128_r1331_k96")
+    H = torch.from_numpy(model.H_R).to(dev)
+    EF = torch.from_numpy(E_F).to(dev)
+    k_step = planes * kmesh[1] * kmesh[2]
+    state = {"s": 0}
+
+    def step():
+        s = state["s"] % (kmesh[0] // planes)
+        state["s"] += 1
+        kubo.ahc(H, model.R, kmesh, EF, etas=list(etas), kT=kT, precision=prec,
+                 k_range=(s * k_step, (s + 1) * k_step))
+    ms, clk = _timed(step, steps, warmup, local)
+    return {"value": k_step / (ms / 1e3), "unit": "k-points/s", "ms_per_step": ms,
+            "k_per_step": k_step, "precision": prec, "clocks": clk, "workload": "w128_r1331_k96"}
+
+
 def run_extra(args, local):
     """Informational lines for the other workloads (see the module docstring)."""
     import torch
@@ -286,49 +374,19 @@ def run_extra(args, local):
     dev = torch.device("cuda", local)
     line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic (tbgen)", "unit": "k-points/s"}
+    prec = "mixed" if args.precision == "both" else args.precision
     if args.workload == "batched":
-        rec = tbgen.batch_recipe()
-        prec = "mixed" if args.precision == "both" else args.precision
-        P, nk = [], 0
-        for r in rec:
-            m = tbgen.random_tb(r["W"], r["half_width"], r["decay"], r["seed"])
-            H = torch.from_numpy(m.H_R).to(dev)
-            # Fermi level: midpoint of the two middle levels of H(k=0), from the library itself
-            Hp, _, _ = kubo.bloch(H, m.R, (1, 1, 1), torch.zeros(1, dtype=torch.int64, device=dev))
-            E, _ = kubo.eigh_batched(Hp, m.W, vectors=False)
-            E = E[0].cpu().numpy()
-            h = (m.W + 1) // 2
-            ef = 0.5 * (E[h - 1] + E[h])
-            P.append((H, m.R, (r["mesh"],) * 3, torch.tensor([ef], dtype=torch.float64, device=dev)))
-            nk += r["mesh"] ** 3
-        sched = {}
-        def step():
-            _, sc, _ = kubo.ahc_batched(P, precision=prec, tune=True)
-            sched.update(sc)
-        ms, clk = _timed(step, args.steps, args.warmup, local)
+        r = workload_batched(kubo, torch, dev, args.steps, args.warmup, local, prec)
         line.update(metric="k-points/sec over a batch of 64 uneven models (one kubo_ahc_batched call)",
-                    value=nk / (ms / 1e3), ms_per_step=ms, dtype="f64" if prec == "fp64" else prec,
-                    config={"workload": "batch64_w8-96_r343-1331_k32-64", "models": len(P),
-                            "k_points": nk, "precision": prec, "schedule": sched}, clocks=clk)
+                    value=r["value"], ms_per_step=r["ms_per_step"], dtype=prec,
+                    config={k: r[k] for k in ("workload", "models", "k_points", "precision", "schedule")},
+                    clocks=r["clocks"])
     elif args.workload == "grad":
-        model, kmesh, E_F, etas, kT = tbgen.config("w32_r729_k48_fd")
-        H = torch.from_numpy(model.H_R).to(dev)
-        EF = torch.from_numpy(E_F).to(dev)
-        g = torch.ones((1, E_F.size), dtype=torch.float64, device=dev)
-        prof = kubo.Profile()
-        def step():
-            kubo.ahc_grad(H, model.R, kmesh, EF, g, eta=float(etas[0]), kT=kT, with_value=True,
-                          profile=prof)
-        ms, clk = _timed(step, args.steps, args.warmup, local)
-        nk = int(np.prod(kmesh))
-        fwd = kubo.ahc  # forward alone on the same workload, for the adjoint/forward ratio
-        ms_f, _ = _timed(lambda: fwd(H, model.R, kmesh, EF, eta=float(etas[0]), kT=kT), args.steps, 1, local)
+        r = workload_grad(kubo, torch, dev, args.steps, args.warmup, local)
         line.update(metric="k-points/sec for dσ_xy/dH(R) (value and gradient, FP64)",
-                    value=nk / (ms / 1e3), ms_per_step=ms, dtype="f64",
-                    config={"workload": "w32_r729_k48_fd", "W": model.W, "N_R": model.N_R,
-                            "kmesh": list(kmesh), "kT": kT, "eta": float(etas[0])},
-                    forward_only={"value": nk / (ms_f / 1e3), "ms_per_step": ms_f},
-                    stages={k: v for k, v in prof.as_dict().items() if v["launches"]}, clocks=clk)
+                    value=r["value"], ms_per_step=r["ms_per_step"], dtype="f64",
+                    config={k: r[k] for k in ("workload", "W", "N_R", "kmesh", "kT", "eta")},
+                    forward_only=r["forward_only"], stages=r["stages"], clocks=r["clocks"])
     elif args.workload == "pad":
         model, kmesh, E_F, etas, kT = tbgen.config(WORKLOAD)
         H = torch.from_numpy(model.H_R).to(dev)
@@ -336,15 +394,15 @@ def run_extra(args, local):
         plane = kmesh[1] * kmesh[2]
         k_step = args.planes * plane
         res = {}
-        for prec in ("fp64", "mixed"):
+        for p in ("fp64", "mixed"):
             for unp in (False, True):
                 prof = kubo.Profile()
-                ms, _ = _timed(lambda: kubo.ahc(H, model.R, kmesh, EF, eta=float(etas[0]), precision=prec,
+                ms, _ = _timed(lambda: kubo.ahc(H, model.R, kmesh, EF, eta=float(etas[0]), precision=p,
                                                 k_range=(0, k_step), profile=prof, unpadded=unp),
                                args.steps, args.warmup, local)
                 st = prof.as_dict()
                 n = args.steps + args.warmup
-                res[f"{prec}_{'unpadded' if unp else 'padded'}"] = {
+                res[f"{p}_{'unpadded' if unp else 'padded'}"] = {
                     "k_per_s": k_step / (ms / 1e3),
                     "backtransform_ms": st["backtransform"]["ms"] / n, "berry_ms": st["berry"]["ms"] / n}
         line.update(metric="padding ablation: k-points/s with padded vs unpadded shared-memory matrices",
@@ -373,24 +431,17 @@ def run_extra(args, local):
                     value=res["fp64_separable"]["k_per_s"], ms_per_step=None, dtype="f64",
                     config={"workload": WORKLOAD, "k_per_step": k_step}, separable=res)
     else:  # sweep
-        model, kmesh, E_F, etas, kT = tbgen.config("w128_r1331_k96")
-        H = torch.from_numpy(model.H_R).to(dev)
-        EF = torch.from_numpy(E_F).to(dev)
-        plane = kmesh[1] * kmesh[2]
-        prec = "mixed" if args.precision == "both" else args.precision
-        k_step = args.planes * plane
-        state = {"s": 0}
-        def step():
-            s = state["s"] % (kmesh[0] // args.planes)
-            state["s"] += 1
-            kubo.ahc(H, model.R, kmesh, EF, etas=list(etas), kT=kT, precision=prec,
-                     k_range=(s * k_step, (s + 1) * k_step))
-        ms, clk = _timed(step, args.steps, args.warmup, local)
+        r = workload_sweep(kubo, torch, dev, args.steps, args.warmup, local, prec, args.planes)
         line.update(metric="k-points/sec for σ_xy (W=128, N_R=1331, 512 E_F x 4 eta)",
-                    value=k_step / (ms / 1e3), ms_per_step=ms, dtype=prec,
-                    config={"workload": "w128_r1331_k96", "k_per_step": k_step, "precision": prec},
-                    clocks=clk)
+                    value=r["value"], ms_per_step=r["ms_per_step"], dtype=prec,
+                    config={"workload": r["workload"], "k_per_step": r["k_per_step"], "precision": prec},
+                    clocks=r["clocks"])
     print(json.dumps(line))
+
+
+DTYPE = {"mixed": "bf16-slices(Ozaki) Fourier + f64 eigh + f32 rotation + f64 denominators/k-sum",
+         "mixed_df": "bf16-slices(Ozaki) Fourier + double-float(f32 pairs) eigh + f32 rotation",
+         "fp64": "f64"}
 
 
 def main():
@@ -419,7 +470,7 @@ def main():
     H = torch.from_numpy(model.H_R).to(dev)
     EF = torch.from_numpy(E_F).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    precisions = ["mixed", "fp64", "mixed_df"] if args.precision == "both" else [args.precision]
 
     def slab(step):
         s = slab_of(rank, world, step, n_slabs)
@@ -493,56 +544,85 @@ def main():
         paths[p] = {"value": world * k_total / (ms / 1e3), "ms_per_step": ms / args.steps,
                     "stages": stage_table(st, stage_flops(model.W, model.N_R, p), k_total),
                     "gpu_launches": int(sum(v["launches"] for v in st.values())), "clocks": clk}
-    ms, st, clk, outs = res[head]
-    fl = stage_flops(model.W, model.N_R, head)
-    dom = max((s for s in st if st[s]["launches"] > 0), key=lambda s: st[s]["ms"])
-    launches = st[dom]["launches"]
-    k_per_launch = k_total / launches
-    rl = roofline_of(dom, head, model.W, model.N_R, k_per_launch, st[dom]["ms"] / launches)
-    key = (head, dom)
-    traffic = DRAM_BYTES_PER_K[key] * k_per_launch if key in DRAM_BYTES_PER_K and model.W == 64 else None
-    roofline = {"bound": rl["bound"], "kernel": dom, "achieved": rl["achieved"], "peak": rl["peak"],
+
+    def roofline_for(p):
+        st = res[p][1]
+        dom = max((s for s in st if st[s]["launches"] > 0), key=lambda s: st[s]["ms"])
+        launches = st[dom]["launches"]
+        k_per_launch = k_total / launches
+        rl = roofline_of(dom, p, model.W, model.N_R, k_per_launch, st[dom]["ms"] / launches)
+        key = (p, dom)
+        traffic = (DRAM_BYTES_PER_K[key] * k_per_launch
+                   if key in DRAM_BYTES_PER_K and model.W == 64 else None)
+        return {"bound": rl["bound"], "kernel": dom, "achieved": rl["achieved"], "peak": rl["peak"],
                 "unit": rl["unit"], "frac": rl["achieved"] / rl["peak"], "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + write.sum, scaled "
                                 "by k-points per launch)",
                 "peak_note": rl["peak_note"]}
+
+    ms, st, clk, outs = res[head]
     line = {
         "metric": METRIC, "value": paths[head]["value"], "unit": "k-points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16-slices(Ozaki)+f32+f64" if head == "mixed" else "f64",
+        "dtype": DTYPE.get(head, head),
         "data": "synthetic (seeded random TB model, tbgen.random_tb)",
         "config": {"workload": WORKLOAD, "W": model.W, "N_R": model.N_R, "kmesh": list(kmesh),
                    "n_EF": int(E_F.size), "eta": eta, "precision": head,
+                   "eigensolver": "f64" if head in ("mixed", "fp64") else "double-float (f32 pairs)",
                    "k_per_step": k_per_step, "chunk_k": args.chunk or "auto",
                    "parallelism": f"k-slabs x{world}",
                    "l2": "flushed (256 MiB write) before every step; per-step working set >> L2"},
-        "roofline": roofline,
+        "roofline": roofline_for(head),
         "stages": paths[head]["stages"],
         "gpu_launches": paths[head]["gpu_launches"],
         "clocks": clk,
         "e2e": e2e,
     }
-    if "mixed" in res and "fp64" in res:
-        om, of = res["mixed"][3], res["fp64"][3]
-        rel = float(np.max(np.abs(om - of) / np.maximum(np.max(np.abs(of), axis=1, keepdims=True), 1e-300)))
-        tc = res["mixed"][1]["fourier"]
-        # 10 slice-pair products x 2 flops x padded K (1344) x padded 3 W^2 (12288) per k-point
-        issued = 10.0 * 2 * 1344 * 12288
-        line["mixed_vs_fp64"] = {
-            "speedup": paths["mixed"]["value"] / paths["fp64"]["value"],
-            "fixup_fraction": fixup_k["mixed"] / k_total,
-            "rel_err_max_over_steps": rel,
-            "fp64": {k: paths["fp64"][k] for k in ("value", "ms_per_step", "stages", "gpu_launches")},
-            "tensor_core_fourier": {
-                "useful_tflops": fl["fourier"] * k_total / (tc["ms"] / 1e3) / 1e12,
-                "issued_bf16_tflops": issued * k_total / (tc["ms"] / 1e3) / 1e12,
-                "bf16_peak_tflops_measured": 1930.6,
-                "note": "stage = coef_slice + fourier_tc (tcgen05, fixed-point BF16 slices, "
-                        "10 slice-pair products, exact FP32 block sums)"},
-        }
+    if "fp64" in res:
+        of = res["fp64"][3]
+        den = np.maximum(np.max(np.abs(of), axis=1, keepdims=True), 1e-300)
+
+        def rel_vs_fp64(p):
+            return float(np.max(np.abs(res[p][3] - of) / den))
+        if "mixed" in res:
+            tc = res["mixed"][1]["fourier"]
+            fl = stage_flops(model.W, model.N_R, "mixed")
+            pk = measured_peaks()
+            line["mixed_vs_fp64"] = {
+                "speedup": paths["mixed"]["value"] / paths["fp64"]["value"],
+                "fixup_fraction": fixup_k["mixed"] / k_total,
+                "rel_err_max_over_steps": rel_vs_fp64("mixed"),
+                "fp64": {k: paths["fp64"][k] for k in ("value", "ms_per_step", "stages", "gpu_launches")},
+                "fp64_roofline": roofline_for("fp64"),
+                "tensor_core_fourier": {
+                    "useful_tflops": fl["fourier"] * k_total / (tc["ms"] / 1e3) / 1e12,
+                    "issued_bf16_tflops": issued_tc_flops_per_k(model.W, "mixed") * k_total
+                                          / (tc["ms"] / 1e3) / 1e12,
+                    "bf16_peak_tflops": pk["bf16"], "bf16_peak_sustained_tflops": pk["bf16_sustained"],
+                    "peak_source": pk["how"] + " (MEASURED_PEAKS.json)",
+                    "note": "stage = coef_slice + fourier_tc (tcgen05, fixed-point BF16 slices: 10 "
+                            "slice-pair products on the H columns, 6 on the velocity columns; exact "
+                            "FP32 block sums)"},
+            }
+        if "mixed_df" in res:
+            line["mixed_df_variant"] = {
+                "what": "the mixed form with its eigensolver in double-float (FP32 pairs, ~2^-46 "
+                        "per operation) instead of FP64: a labelled variant, not the headline",
+                "value": paths["mixed_df"]["value"], "ms_per_step": paths["mixed_df"]["ms_per_step"],
+                "speedup_vs_fp64": paths["mixed_df"]["value"] / paths["fp64"]["value"],
+                "rel_err_max_over_steps": rel_vs_fp64("mixed_df"),
+                "stages": paths["mixed_df"]["stages"], "roofline": roofline_for("mixed_df"),
+                "gpu_launches": paths["mixed_df"]["gpu_launches"]}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(model, kmesh, E_F, eta, kT, args.cpu_sample)
+    if not args.no_extras and world == 1:
+        # compact results of the other workloads, one bounded slab each
+        line["workloads"] = {
+            "batched": workload_batched(kubo, torch, dev, 1, 1, local, "mixed", every=4),
+            "grad": workload_grad(kubo, torch, dev, 2, 1, local, k_limit=8 * 48 * 48),
+            "sweep": workload_sweep(kubo, torch, dev, 3, 1, local, "mixed", 2),
+        }
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -60,18 +60,28 @@ typedef enum {
 
 typedef enum {
   KUBO_FP64 = 0,            /* every step in FP64 */
-  KUBO_MIXED = 1,           /* step (1) on the tensor cores (fixed-point BF16 slices with exact
-                               FP32 block accumulation, ~40-bit result), step (3) in FP32;
-                               eigensolver in double-float (pairs of FP32, ~2^-46 per
-                               operation), energy differences and k-sum in FP64, curvature
-                               quotient in FP32 (FP64 below a 2^-86 denominator).  The pairs
-                               need max |H(R)| between about 1e-12 and 1e12 (squares and their
-                               low parts stay normal FP32 numbers); outside that range use
-                               KUBO_FP64, or scale H(R), E_F, eta and kT by one power of two,
-                               which leaves S(E_F) unchanged */
+  KUBO_MIXED = 1,           /* the mixed-precision form: step (1) on the tensor cores (fixed-point
+                               BF16 slices with exact FP32 block accumulation: H(k) to ~2^-31
+                               relative, the velocity columns, which feed only step (3), to
+                               ~2^-23); the eigensolver (Householder reduction, QL, inverse
+                               iteration) in FP64; step (3) in FP32, with U = Q D Z formed in FP32
+                               from the FP64 factors; energy differences and the k-sum in FP64;
+                               curvature quotient in FP32 (FP64 below a 2^-86 denominator) */
   KUBO_MIXED_FOURIER = 2,   /* error-budget mode: only step (1) mixed, step (3) in FP64 */
-  KUBO_MIXED_ROTATION = 3   /* error-budget mode: only step (3) mixed (FP32), step (1) in FP64 */
+  KUBO_MIXED_ROTATION = 3,  /* error-budget mode: only step (3) mixed (FP32), step (1) in FP64 */
+  KUBO_MIXED_DF = 4         /* KUBO_MIXED with the eigensolver in double-float instead of FP64:
+                               pairs of FP32 (~2^-46 per operation) on the FP32 pipe, FP64 in and
+                               out; eigenvalues to ~1e-12 relative at W = 64.  Not an FP64
+                               eigensolver: a faster variant at the same 1e-5 target on S. */
 } kubo_precision;
+/* Magnitude range.  S(E_F) is unchanged when H(R), E_F, eta and kT are scaled by one factor
+ * (Omega is homogeneous of degree zero in them).  In the modes whose step (3) runs in FP32
+ * (KUBO_MIXED, KUBO_MIXED_ROTATION, KUBO_MIXED_DF) an H(R) whose largest entry lies outside
+ * [2^-20, 2^20] is therefore scaled inside the call by the power of two that brings that entry
+ * into [1, 2), with eta scaled alike and the eigenvalues scaled back: exact, and it leaves the
+ * FP32 products and the FP32 pairs no magnitude range of their own.  The separable Fourier sum
+ * (kubo_options.fourier_separable) does not scale: with it keep max |H(R)| within [2^-40, 2^40]
+ * in KUBO_MIXED_ROTATION. */
 
 /* Pipeline stages, for the optional per-stage timing in kubo_profile. */
 enum {
@@ -105,7 +115,15 @@ typedef struct kubo_options {
                                partition of the mesh add up to the full-mesh result. */
   void* stream;             /* cudaStream_t; NULL = legacy default stream */
   void* workspace;          /* device scratch of workspace_bytes; NULL = the library
-                               allocates (cudaMallocAsync) and frees it inside the call */
+                               allocates it (cudaMallocAsync from the current device's DEFAULT
+                               memory pool) and frees it inside the call.  Process-wide side
+                               effect of a library allocation: so that the freed workspace stays
+                               mapped for the next call (re-mapping GBs costs ~30 ms per call),
+                               the library raises that default pool's release threshold
+                               (cudaMemPoolAttrReleaseThreshold) to the largest workspace it
+                               has used, and never lowers it; other cudaMallocAsync users of the
+                               same pool in the process see that threshold too.  A caller that
+                               must keep its own threshold passes a workspace here. */
   size_t workspace_bytes;
   int chunk_k;              /* k-points per internal batch; 0 = automatic (a fixed 24 GiB of
                                batch buffers, at most 65,536 k-points) */
@@ -131,10 +149,17 @@ typedef struct kubo_options {
                                k-range of whole k1-planes; bounding box at most 8 N_R vectors;
                                otherwise KUBO_ERR_UNSUPPORTED).  Same result up to rounding
                                order.  0 (default): dense contraction. */
-  int rotation_tc;          /* KUBO_MIXED / KUBO_MIXED_ROTATION, W <= 64: 1 = step (3) on the
-                               tensor cores (exact fixed-point BF16-slice products, FP32-grade)
-                               instead of FP32 on the FMA pipe.  Same accuracy class; currently
-                               slower at W = 64, so 0 (FMA pipe) is the default. */
+  int rotation_tc;          /* KUBO_MIXED / KUBO_MIXED_ROTATION / KUBO_MIXED_DF, W <= 64: 1 =
+                               step (3) on the tensor cores (exact fixed-point BF16-slice
+                               products, FP32-grade) instead of FP32 on the FMA pipe.  Same
+                               accuracy class; currently slower at W = 64, so 0 (FMA pipe) is
+                               the default. */
+  int ql_max_sweeps;        /* cap on the implicit-QL sweeps spent on one eigenvalue; 0 = the
+                               default (60, far above the 2-3 that Wilkinson shifts need).  A
+                               k-point that reaches the cap makes the call return
+                               KUBO_ERR_NO_CONVERGENCE with its outputs untouched; a cap of 1
+                               forces that path on any matrix that needs a second sweep.
+                               < 0: KUBO_ERR_INVALID_ARG. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,
@@ -231,8 +256,10 @@ kubo_status kubo_berry_batched(const double* E, const double* U, const double* d
  *   - W <= 64; a larger W returns KUBO_ERR_UNSUPPORTED without launching anything.
  *   - any n >= 1: the matrices are processed in passes of as many as fit in the block
  *     (about 480 per pass at W = 64, about 6900 at W = 16).
- * The first call on a device looks up the block's device address (once per device, with
- * that device current); make that first call before any stream capture.  Every call
+ * Every call looks up the block's device address on the current device (a symbol lookup,
+ * which allocates nothing), so an address never outlives a device reset.  The first call on a
+ * device also loads the library's device code there; make that first call before any stream
+ * capture.  Every call
  * shares the block and it keeps the previous call's contents (the call clears what must
  * start at zero), so calls that overlap on the GPU -- on different streams or from
  * different host threads on the same device -- race and corrupt each other's results:
@@ -319,6 +346,16 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
  * hang is involved.  spins < 1: KUBO_ERR_INVALID_ARG.  stream: cudaStream_t (NULL = legacy).
  */
 kubo_status kubo_check_bounded_wait(uint32_t spins, void* stream);
+
+/*
+ * Test hook (no counterpart in the paper): the next `n` device allocations that the library
+ * itself attempts (the workspace of kubo_ahc, kubo_ahc_host, kubo_ahc_k, kubo_ahc_grad,
+ * kubo_bloch, kubo_eigh_batched, kubo_berry_batched and the batch buffer of kubo_ahc_batched)
+ * fail as if the device were out of memory, so that callers can exercise their handling of
+ * KUBO_ERR_OOM without exhausting a shared GPU.  Nothing is launched or allocated by this call;
+ * n <= 0 clears a pending count.  Process-wide; thread-safe.
+ */
+void kubo_debug_fail_allocations(int n);
 
 /* Device bytes of scratch a kubo_ahc / kubo_ahc_k call with these sizes needs. */
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,

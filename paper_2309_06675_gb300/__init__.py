@@ -28,15 +28,16 @@ __all__ = [
     "KuboError", "lib", "ahc", "ahc_host", "ahc_k", "bloch", "eigh_batched", "berry_batched",
     "workspace_size", "max_orbitals", "pack_hermitian", "unpack_hermitian", "FP64", "MIXED",
     "LIB_PATH", "Profile", "Options", "STAGES", "ahc_grad", "grad_workspace_size", "AHC",
-    "ahc_batched", "Problem", "BatchSchedule",
+    "ahc_batched", "Problem", "BatchSchedule", "MIXED_DF", "debug_fail_allocations",
 ]
 
 FP64 = 0
-MIXED = 1
+MIXED = 1             # tensor-core Fourier sum, FP64 eigensolver, FP32 rotations
 MIXED_FOURIER = 2     # error-budget mode: only the Fourier sum on the tensor cores
 MIXED_ROTATION = 3    # error-budget mode: only the rotations in FP32
+MIXED_DF = 4          # MIXED with the eigensolver in double-float (FP32 pairs) instead of FP64
 _PREC = {"fp64": FP64, "mixed": MIXED, "mixed_fourier": MIXED_FOURIER,
-         "mixed_rotation": MIXED_ROTATION}
+         "mixed_rotation": MIXED_ROTATION, "mixed_df": MIXED_DF}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libkubo.so")
 
@@ -86,6 +87,7 @@ class Options(ctypes.Structure):
         ("layout_unpadded", ctypes.c_int),
         ("fourier_separable", ctypes.c_int),
         ("rotation_tc", ctypes.c_int),
+        ("ql_max_sweeps", ctypes.c_int),
     ]
 
 
@@ -134,6 +136,7 @@ def lib():
             "kubo_ahc_grad": (I, [P, P, I, I, P, P, I, D, P, P, P, OPT]),
             "kubo_ahc_batched": (I, [ctypes.POINTER(Problem), I, OPT, ctypes.POINTER(BatchSchedule)]),
             "kubo_check_bounded_wait": (I, [ctypes.c_uint32, P]),
+            "kubo_debug_fail_allocations": (None, [I]),
             "kubo_ahc": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_host": (I, [P, P, I, I, P, P, I, D, P, OPT]),
             "kubo_ahc_k": (I, [P, P, I, I, P, P, I64, D, P, P, OPT]),
@@ -185,7 +188,7 @@ def _dev(t, dtype, name):
 
 
 def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk_k=0,
-             workspace=None, keep=None, profile=None):
+             workspace=None, keep=None, profile=None, ql_max_sweeps=0):
     o = Options()
     lib().kubo_options_init(ctypes.byref(o))
     o.precision = _PREC.get(precision, precision)
@@ -205,7 +208,13 @@ def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk
         o.workspace_bytes = workspace.numel() * workspace.element_size()
     if profile is not None:
         o.profile = ctypes.pointer(profile)
+    o.ql_max_sweeps = int(ql_max_sweeps)
     return o
+
+
+def debug_fail_allocations(n: int) -> None:
+    """Make the library's next n device allocations fail as out-of-memory (test hook)."""
+    lib().kubo_debug_fail_allocations(int(n))
 
 
 def max_orbitals(precision=FP64) -> int:
@@ -234,7 +243,7 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
         stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
-        unpadded=False, separable=False, rotation_tc=False):
+        unpadded=False, separable=False, rotation_tc=False, ql_max_sweeps=0):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
@@ -248,7 +257,8 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     if out is None:
         out = torch.empty((n_eta, n_EF), dtype=torch.float64, device=H_R.device)
     keep = []
-    o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile)
+    o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile,
+                 ql_max_sweeps)
     o.mixed_fixup_rel = float(fixup_rel)
     o.layout_unpadded = 1 if unpadded else 0
     o.fourier_separable = 1 if separable else 0
@@ -414,7 +424,7 @@ def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_
 
 
 def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None, chunk_k=0,
-          rotation_tc=False):
+          rotation_tc=False, ql_max_sweeps=0):
     """Per-k eigenvalues and band curvatures for the listed mesh points."""
     torch = _torch()
     Rh = _host_int32(R, 3)
@@ -425,7 +435,8 @@ def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None,
     E = torch.empty((n_k, W), dtype=torch.float64, device=H_R.device)
     Om = torch.empty((n_eta, n_k, W), dtype=torch.float64, device=H_R.device)
     keep = []
-    o = _options(precision, etas, 0.0, None, stream, chunk_k, None, keep)
+    o = _options(precision, etas, 0.0, None, stream, chunk_k, None, keep,
+                 ql_max_sweeps=ql_max_sweeps)
     o.rotation_tc = 1 if rotation_tc else 0
     code = lib().kubo_ahc_k(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                             W, N_R, km.ctypes.data_as(ctypes.c_void_p),
@@ -455,13 +466,13 @@ def bloch(H_R, R, kmesh, kidx, precision=FP64, stream=None):
     return tuple(outs)
 
 
-def eigh_batched(A, W, vectors=True, stream=None, chunk_k=0):
+def eigh_batched(A, W, vectors=True, stream=None, chunk_k=0, ql_max_sweeps=0):
     """Batched FP64 Hermitian eigh of packed matrices A [n, W*W] -> (E [n, W], U [n, W, W] or None)."""
     torch = _torch()
     n = int(A.shape[0])
     E = torch.empty((n, W), dtype=torch.float64, device=A.device)
     U = torch.empty((n, W, W), dtype=torch.complex128, device=A.device) if vectors else None
-    o = _options(stream=stream, chunk_k=chunk_k)
+    o = _options(stream=stream, chunk_k=chunk_k, ql_max_sweeps=ql_max_sweeps)
     code = lib().kubo_eigh_batched(_dev(A, torch.float64, "A"), int(W), n, _dev(E, torch.float64, "E"),
                                    _dev(U, torch.complex128, "U") if vectors else None,
                                    ctypes.byref(o))

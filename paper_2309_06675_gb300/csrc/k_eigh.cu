@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(32) ql_kernel(int W, int n, EighBufs b, DevSta
         if (fabs(E[m * 32]) <= eps * dd) break;
       }
       if (m == l) break;
-      if (++iter > 60) { fail = true; break; }
+      if (++iter > b.ql_cap) { fail = true; break; }
       // Wilkinson shift from the leading 2x2 of the block, then chase up from the bottom.
       double dl = D[l * 32], el = E[l * 32];
       double g = (D[(l + 1) * 32] - dl) / (2.0 * el);

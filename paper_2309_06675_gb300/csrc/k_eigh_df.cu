@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(32) ql_df_kernel(int W, int n, EighBufs b, Dev
         if (fabsf(E[m * 32].x) <= eps * dd) break;
       }
       if (m == l) break;
-      if (++iter > 60) { fail = true; break; }
+      if (++iter > b.ql_cap) { fail = true; break; }
       // Wilkinson shift from the leading 2x2 of the block, then chase up from the bottom
       const Df dl = ld(D, l), el = ld(E, l);
       Df g = df_div(df_sub(ld(D, l + 1), dl), Df{2.0f * el.h, 2.0f * el.l});

@@ -66,7 +66,7 @@ __global__ void hermitian_verdict_kernel(DevStatus* st) {
 //   row 2 + 2h : B_h = i (H(R_h) - H(-R_h))
 // Packed Hermitian: P[i][j] = Re M_ij (i <= j), P[i][j] = Im M_ji (i > j).
 __global__ void pack_basis_kernel(const double2* __restrict__ H, const int* __restrict__ pairs,
-                                  int idx0, int N_h, int W, double* __restrict__ Bp) {
+                                  int idx0, int N_h, int W, double scale, double* __restrict__ Bp) {
   const int WW = W * W;
   const int K = 1 + 2 * N_h;
   const int64_t total = (int64_t)K * WW;
@@ -95,8 +95,14 @@ __global__ void pack_basis_kernel(const double2* __restrict__ H, const int* __re
         m = make_double2(-(a.y - b.y), a.x - b.x);       // B = i (H(R) - H(-R))
       }
     }
-    Bp[t] = want_im ? m.y : m.x;
+    Bp[t] = (want_im ? m.y : m.x) * scale;
   }
+}
+
+__global__ void scale_pow2_kernel(double* __restrict__ x, int64_t n, double f) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    x[t] *= f;
 }
 
 __global__ void twiddle_kernel(double2* tab, int N1, int N2, int N3) {
@@ -134,9 +140,16 @@ cudaError_t launch_hermitian_verdict(DevStatus* st, cudaStream_t s) {
 }
 
 cudaError_t launch_pack_basis(const double2* H_R, const int* pairs, int idx0, int N_h, int W,
-                              double* Bp, cudaStream_t s) {
+                              double* Bp, cudaStream_t s, int escale) {
   int64_t total = (int64_t)(1 + 2 * N_h) * W * W;
-  pack_basis_kernel<<<grid_for(total, 256), 256, 0, s>>>(H_R, pairs, idx0, N_h, W, Bp);
+  pack_basis_kernel<<<grid_for(total, 256), 256, 0, s>>>(H_R, pairs, idx0, N_h, W,
+                                                          ldexp(1.0, escale), Bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_pow2(double* x, int64_t n, int e, cudaStream_t s) {
+  if (n <= 0 || e == 0) return cudaSuccess;
+  scale_pow2_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, n, ldexp(1.0, e));
   return cudaGetLastError();
 }
 

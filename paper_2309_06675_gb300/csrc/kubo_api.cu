@@ -1,6 +1,7 @@
 // C ABI of libkubo (include/kubo.h): argument validation, analysis of the R set, workspace
 // planning and the batched k-point pipeline (the paper's List 2 loop over batches).
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -81,9 +82,28 @@ struct Bump {
   }
 };
 
-// precision modes whose step (1) runs on the tensor cores / whose step (3) runs in FP32
-bool tc_fourier(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_FOURIER; }
-bool f32_rotation(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_ROTATION; }
+// precision modes whose step (1) runs on the tensor cores / whose step (3) runs in FP32 /
+// whose eigensolver runs in double-float
+bool tc_fourier(int prec) {
+  return prec == KUBO_MIXED || prec == KUBO_MIXED_FOURIER || prec == KUBO_MIXED_DF;
+}
+bool f32_rotation(int prec) {
+  return prec == KUBO_MIXED || prec == KUBO_MIXED_ROTATION || prec == KUBO_MIXED_DF;
+}
+bool df_eigh(int prec) { return prec == KUBO_MIXED_DF; }
+
+// Power-of-two exponent s that brings max |H(R)| into [1, 2) when it lies outside
+// [2^-20, 2^20] (0 otherwise, and for zero or non-finite maxima).  S(E_F) is homogeneous of
+// degree zero in (H, eta, E, kT), and scaling by 2^s is exact, so the FP32 steps see O(1)
+// magnitudes whatever the input's units.
+int range_exponent(double mx) {
+  if (!(mx > 0.0) || !std::isfinite(mx)) return 0;
+  int e = 0;
+  std::frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+  const int lg = e - 1; // mx in [2^lg, 2^(lg+1))
+  if (lg >= -20 && lg <= 20) return 0;
+  return -lg;
+}
 
 struct Plan {
   int W = 0, N_R = 0, N_h = 0, K = 0, n_EF = 0, n_eta = 1, chunk = 0;
@@ -92,6 +112,9 @@ struct Plan {
   int kpb = KSUM_KPB;               // k-points per k-sum block
   int pad = 1;                      // leading dimension W + pad in the fused kernels' smem
   bool rot_tc = false;              // FP32-grade rotations on the tensor cores (W <= 64)
+  bool scale_ok = false;            // the call may rescale H(R) by a power of two (range_exponent)
+  int escale = 0;                   // that power: the basis holds 2^escale H(R)
+  int ql_cap = 0;                   // QL sweeps per eigenvalue (0 = the kernels' default)
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -236,6 +259,22 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
   p.total = b.off;
 }
 
+// ------------------------------------------------------------------ device allocations
+// Every device allocation the library makes goes through lib_malloc_async, which honours the
+// test hook kubo_debug_fail_allocations (pending simulated failures).
+std::atomic<int> g_fail_allocs{0};
+
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  int n = g_fail_allocs.load();
+  while (n > 0) {
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
 // ------------------------------------------------------------------ call context
 // The library-managed workspace comes from the device's default stream-ordered pool.  With
 // the pool's default release threshold (0) the freed workspace is unmapped at the next
@@ -299,7 +338,7 @@ struct Call {
       return KUBO_OK;
     }
     retain_pool_memory(p.total);
-    if (cudaMallocAsync((void**)&ws, p.total, s) != cudaSuccess) {
+    if (lib_malloc_async((void**)&ws, p.total, s) != cudaSuccess) {
       cudaGetLastError();
       ws = nullptr;
       return KUBO_ERR_OOM;
@@ -353,11 +392,18 @@ kubo_status bits_to_status(unsigned bits) {
   return KUBO_OK;
 }
 
-kubo_status read_status(Call& c) {
+kubo_status read_status(Call& c, DevStatus* full = nullptr) {
   DevStatus h;
   KCHECK(cudaMemcpyAsync(&h, c.at<DevStatus>(c.p.o_status), sizeof(h), cudaMemcpyDeviceToHost, c.s));
   KCHECK(cudaStreamSynchronize(c.s));
+  if (full) *full = h;
   return bits_to_status(h.bits);
+}
+
+double herm_max(const DevStatus& h) {
+  double mx;
+  std::memcpy(&mx, &h.herm_max_bits, sizeof(mx));
+  return mx;
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
@@ -367,7 +413,7 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
   if (W < 1 || N_R < 1 || !kmesh) return KUBO_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a)
     if (kmesh[a] < 1) return KUBO_ERR_INVALID_ARG;
-  if (o.precision < KUBO_FP64 || o.precision > KUBO_MIXED_ROTATION) return KUBO_ERR_UNSUPPORTED;
+  if (o.precision < KUBO_FP64 || o.precision > KUBO_MIXED_DF) return KUBO_ERR_UNSUPPORTED;
   if (W > MAX_W) return KUBO_ERR_UNSUPPORTED;
   if (!finite_nonneg(o.kT)) return KUBO_ERR_INVALID_ARG;
   if (o.n_eta < 0) return KUBO_ERR_INVALID_ARG;
@@ -377,7 +423,7 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
     for (int e = 0; e < o.n_eta; ++e)
       if (!finite_nonneg(o.etas[e])) return KUBO_ERR_INVALID_ARG;
   }
-  if (o.chunk_k < 0) return KUBO_ERR_INVALID_ARG;
+  if (o.chunk_k < 0 || o.ql_max_sweeps < 0) return KUBO_ERR_INVALID_ARG;
   if (!std::isfinite(o.mixed_fixup_rel)) return KUBO_ERR_INVALID_ARG;
   n_eta = o.n_eta > 0 ? o.n_eta : 1;
   return KUBO_OK;
@@ -390,8 +436,8 @@ kubo_status check_klist(Call& c, const int64_t* kidx, int64_t n) {
   return read_status(c);
 }
 
-// Prepare the model (status reset, Hermitian check, twiddles, packed basis) and return the
-// Hermitian verdict (one host sync).
+// Prepare the model: status reset, Hermitian check (one host sync, which also gives max |H(R)|
+// and so the range exponent of the call), twiddles, packed basis (scaled by 2^escale).
 kubo_status prepare_model(Call& c, const double* H_R, const RInfo& ri) {
   Plan& p = c.p;
   KCHECK(cudaMemsetAsync(c.at<char>(p.o_status), 0, sizeof(DevStatus), c.s));
@@ -402,11 +448,18 @@ kubo_status prepare_model(Call& c, const double* H_R, const RInfo& ri) {
   }
   DevStatus* st = c.at<DevStatus>(p.o_status);
   {
-    StageTimer tm(c, KUBO_STAGE_PREP, 4);
+    StageTimer tm(c, KUBO_STAGE_PREP, 2);
     KCHECK(launch_check_hermitian((const double2*)H_R, c.at<int>(p.o_neg), p.N_R, p.W, st, c.s));
     KCHECK(launch_hermitian_verdict(st, c.s));
+  }
+  DevStatus h;
+  kubo_status hv = read_status(c, &h);
+  if (hv != KUBO_OK) return hv;
+  p.escale = p.scale_ok ? range_exponent(herm_max(h)) : 0;
+  {
+    StageTimer tm(c, KUBO_STAGE_PREP, 2);
     KCHECK(launch_twiddles(c.at<double2>(p.o_tab), p.mesh.N1, p.mesh.N2, p.mesh.N3, c.s));
-    KCHECK(launch_pack_basis((const double2*)H_R, c.at<int>(p.o_pairs), ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s));
+    KCHECK(launch_pack_basis((const double2*)H_R, c.at<int>(p.o_pairs), ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s, p.escale));
   }
   if (p.sep) {
     StageTimer tm(c, KUBO_STAGE_PREP, 1);
@@ -443,6 +496,7 @@ EighBufs make_eigh_bufs(const Call& c) {
   b.refl = c.at<double2>(c.p.o_refl);
   b.tau = c.at<double>(c.p.o_tau);
   b.lam = c.at<double>(c.p.o_lam);
+  if (c.p.ql_cap > 0) b.ql_cap = c.p.ql_cap;
   return b;
 }
 
@@ -454,7 +508,7 @@ cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, do
   const Plan& p = c.p;
   if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s, p.pad);
   double* Z = U ? c.at<double>(p.o_L) : nullptr;
-  cudaError_t e = Z && p.precision == KUBO_MIXED
+  cudaError_t e = Z && df_eigh(p.precision)
                       ? launch_iit_df(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s)
                       : launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
   if (e != cudaSuccess || !U) return e;
@@ -506,17 +560,17 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0));
   }
   {
-    // MIXED: the reduction and the QL iteration in double-float on the FP32 pipe (both are
-    // FP64-pipe-bound otherwise)
+    // MIXED_DF: the reduction and the QL iteration in double-float on the FP32 pipe (both are
+    // FP64-pipe-bound otherwise); every other mode: FP64
     StageTimer tm(c, KUBO_STAGE_TRIDIAG, 1);
-    if (p.precision == KUBO_MIXED)
+    if (df_eigh(p.precision))
       KCHECK(launch_tridiag_df_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
     else
       KCHECK(launch_tridiag_rows(C64, p.Npad, p.W, kl.n, eb, c.s));
   }
   {
     StageTimer tm(c, KUBO_STAGE_QL, 1);
-    if (p.precision == KUBO_MIXED)
+    if (df_eigh(p.precision))
       KCHECK(launch_ql_df(p.W, kl.n, eb, st, c.s));
     else
       KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
@@ -528,7 +582,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     double* Z = reinterpret_cast<double*>(U);
     {
       StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-      if (p.precision == KUBO_MIXED)
+      if (df_eigh(p.precision))
         KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
       else
         KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
@@ -552,8 +606,8 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
 }
 
 // fourier_done: step (1) already wrote Hp / Xp / Yp (separable Fourier sum)
-kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
-                      int64_t om_stride, bool fourier_done = false) {
+kubo_status run_batch_steps(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
+                            int64_t om_stride, bool fourier_done) {
   Plan& p = c.p;
   if (tc_fourier(p.precision)) return run_batch_mixed(c, md, kl, Eout, Om, om_stride);
   double* Hp = c.at<double>(p.o_Hp);
@@ -578,7 +632,7 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
     double* Z = reinterpret_cast<double*>(U);
     {
       StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
-      if (p.precision == KUBO_MIXED)
+      if (df_eigh(p.precision))
         KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
       else
         KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
@@ -601,10 +655,22 @@ kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, d
   return KUBO_OK;
 }
 
+// Steps (1)-(4) of one batch; with a rescaled model (escale != 0) the eigenvalues are brought
+// back to the caller's units (the curvatures are scale-free).
+kubo_status run_batch(Call& c, const Model& md, const KList& kl, double* Eout, double* Om,
+                      int64_t om_stride, bool fourier_done = false) {
+  kubo_status r = run_batch_steps(c, md, kl, Eout, Om, om_stride, fourier_done);
+  if (r != KUBO_OK) return r;
+  KCHECK(launch_scale_pow2(Eout, (int64_t)kl.n * c.p.W, -c.p.escale, c.s));
+  return KUBO_OK;
+}
+
+// The broadenings on the device, scaled like H(R) (2^escale: call after prepare_model).
 kubo_status upload_etas(Call& c, const kubo_options& o, double eta) {
   double h[MAX_ETA] = {0};
   if (o.n_eta > 0) for (int e = 0; e < o.n_eta; ++e) h[e] = o.etas[e];
   else h[0] = eta;
+  for (double& x : h) x = std::ldexp(x, c.p.escale);
   KCHECK(cudaMemcpyAsync(c.at<double>(c.p.o_etas), h, sizeof(h), cudaMemcpyHostToDevice, c.s));
   return KUBO_OK;
 }
@@ -643,6 +709,7 @@ kubo_status fixup_batch(Call& c, const Model& md, const KList& kl, const double*
     KCHECK(launch_ql(p.W, nf, eb, st, c.s));
     KCHECK(eigh_vectors(c, nf, eb, fE, U));
     KCHECK(berry_any(c, fE, U, c.at<double>(p.o_fXp), c.at<double>(p.o_fYp), (int64_t)p.W * p.W, false, nf, false, fOm, fstride));
+    KCHECK(launch_scale_pow2(fE, (int64_t)nf * p.W, -p.escale, c.s));
     KCHECK(launch_fixup_scatter(pos + c0, nf, p.W, p.n_eta, fE, fOm, fstride, E, Om, (int64_t)kl.n * p.W, c.s));
   }
   return KUBO_OK;
@@ -652,9 +719,9 @@ kubo_status fixup_batch(Call& c, const Model& md, const KList& kl, const double*
 kubo_status ahc_device(Call& c, const kubo_options& o, const double* H_R, const RInfo& ri,
                        const double* E_F, double eta, double* out, int64_t kb, int64_t ke) {
   Plan& p = c.p;
-  kubo_status r = upload_etas(c, o, eta);
+  kubo_status r = prepare_model(c, H_R, ri);
   if (r != KUBO_OK) return r;
-  r = prepare_model(c, H_R, ri);
+  r = upload_etas(c, o, eta);
   if (r != KUBO_OK) return r;
   const int n_out = p.n_eta * p.n_EF;
   KCHECK(cudaMemsetAsync(c.at<char>(p.o_acc), 0, sizeof(double2) * n_out, c.s));
@@ -748,6 +815,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.lbuf = W > SMALL_W_MAX;
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   p.pad = o.layout_unpadded ? 0 : 1;
+  p.ql_cap = o.ql_max_sweeps;
   // the padding ablation concerns the SIMT rotation kernel's shared-memory layout
   p.rot_tc = o.rotation_tc && !o.layout_unpadded;
   if (o.fourier_separable) {
@@ -755,6 +823,8 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
     r = setup_separable(p, R_vecs, N_R, kb, ke, ri);
     if (r != KUBO_OK) return r;
   }
+  // the separable stage A reads H(R) itself, not the (scalable) packed basis
+  p.scale_ok = f32_rotation(p.precision) && !p.sep;
   plan_layout(p, host_io, 0);
   c.s = (cudaStream_t)o.stream;
   c.prof = o.profile;
@@ -773,9 +843,9 @@ kubo_status ahc_grad_device(Call& c, const kubo_options& o, const double* H_R, c
                             const double* E_F, double eta, const double* g, double2* G,
                             double* out, int64_t kb, int64_t ke) {
   Plan& p = c.p;
-  kubo_status r = upload_etas(c, o, eta);
+  kubo_status r = prepare_model(c, H_R, ri);
   if (r != KUBO_OK) return r;
-  r = prepare_model(c, H_R, ri);
+  r = upload_etas(c, o, eta);
   if (r != KUBO_OK) return r;
   const int n_out = p.n_eta * p.n_EF;
   const size_t WW = (size_t)p.W * p.W;
@@ -884,7 +954,8 @@ struct Job {
 double job_cost(const Plan& p) {
   const double W = p.W, NR = p.N_R, Nk = (double)p.mesh.Nk;
   const double fourier = 6.0 * NR * W * W * (tc_fourier(p.precision) ? 10.0 / 1500.0 : 1.0);
-  const double eig = 16.0 / 3.0 * W * W * W + 72.0 * W * W;
+  // the double-float eigensolver runs about 2.5x faster than the FP64 one at W = 64
+  const double eig = (16.0 / 3.0 * W * W * W + 72.0 * W * W) * (df_eigh(p.precision) ? 0.4 : 1.0);
   const double rot = 24.0 * W * W * W * (f32_rotation(p.precision) ? 1.0 / 48.0 : 1.0);
   return Nk * (fourier + eig + rot + 1e4);   // + per-k fixed cost (launch/latency share)
 }
@@ -967,7 +1038,7 @@ kubo_status run_job(Call& c, const Job& j, const kubo_problem& pr, const kubo_op
   KCHECK(cudaMemsetAsync(st, 0, sizeof(DevStatus), c.s));
   KCHECK(cudaMemcpyAsync(c.at<double>(p.o_etas), jt.etas, sizeof(double) * MAX_ETA, cudaMemcpyDeviceToDevice, c.s));
   KCHECK(launch_twiddles(c.at<double2>(p.o_tab), p.mesh.N1, p.mesh.N2, p.mesh.N3, c.s));
-  KCHECK(launch_pack_basis((const double2*)pr.H_R, jt.pairs, j.ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s));
+  KCHECK(launch_pack_basis((const double2*)pr.H_R, jt.pairs, j.ri.idx0, p.N_h, p.W, c.at<double>(p.o_Bp), c.s, p.escale));
   if (tc_fourier(p.precision))
     KCHECK(launch_basis_split(c.at<double>(p.o_Bp), jt.Rh, p.N_h, p.W, p.Npad, p.Kp, c.at<int>(p.o_cexp), c.at<char>(p.o_Bt), c.s));
   const int n_out = p.n_eta * p.n_EF;
@@ -1115,8 +1186,10 @@ const char* kubo_status_string(kubo_status s) {
   return "KUBO_ERR_UNKNOWN";
 }
 
+void kubo_debug_fail_allocations(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
+
 int kubo_max_orbitals(int precision) {
-  return (precision >= KUBO_FP64 && precision <= KUBO_MIXED_ROTATION) ? MAX_W : 0;
+  return (precision >= KUBO_FP64 && precision <= KUBO_MIXED_DF) ? MAX_W : 0;
 }
 
 size_t kubo_workspace_size(int W, int N_R, const int32_t* kmesh, int n_EF,
@@ -1311,6 +1384,8 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
       p.model = p.eigh = p.berry = p.ksum = true;
       p.lbuf = q.W > SMALL_W_MAX;
       p.fixup = false;
+      p.scale_ok = f32_rotation(p.precision);
+      p.ql_cap = o.ql_max_sweeps;
       j.cost = job_cost(p);
       br.jobs.push_back(std::move(j));
     }
@@ -1372,7 +1447,7 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
       }
       cudaEventDestroy(ev);
     }
-    if (cudaMallocAsync((void**)&ws, probe_off + sizeof(double) * probe_doubles, origin) != cudaSuccess) {
+    if (lib_malloc_async((void**)&ws, probe_off + sizeof(double) * probe_doubles, origin) != cudaSuccess) {
       cudaGetLastError();
       ws = nullptr;
       return finish(KUBO_ERR_OOM);
@@ -1421,7 +1496,16 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
           probs[br.jobs[i].idx].status = r;
           if (first == KUBO_OK) first = r;
         } else {
-          ok.push_back(std::move(br.jobs[i]));
+          // a model outside the FP32 steps' comfortable range is scaled by a power of two
+          // (basis and broadenings; its eigenvalues are scaled back per batch)
+          Job& j = br.jobs[i];
+          j.p.escale = j.p.scale_ok ? range_exponent(herm_max(hs[i])) : 0;
+          if (j.p.escale != 0) {
+            for (double& x : eta_h[i]) x = std::ldexp(x, j.p.escale);
+            BCHECK(cudaMemcpyAsync(job_tables(ws, j).etas, eta_h[i].data(), sizeof(double) * MAX_ETA,
+                                   cudaMemcpyHostToDevice, origin));
+          }
+          ok.push_back(std::move(j));
         }
       }
       br.jobs.swap(ok);
@@ -1529,8 +1613,8 @@ kubo_status kubo_ahc_k(const double* H_R, const int32_t* R_vecs, int W, int N_R,
     r = c.acquire(o);
     if (r != KUBO_OK) return r;
     r = check_klist(c, kidx, n_k);
-    if (r == KUBO_OK) r = upload_etas(c, o, eta);
     if (r == KUBO_OK) r = prepare_model(c, H_R, ri);
+    if (r == KUBO_OK) r = upload_etas(c, o, eta);
     if (r == KUBO_OK) {
       const Model md = make_model(c);
       for (int64_t t0 = 0; t0 < n_k && r == KUBO_OK; t0 += p.chunk) {
@@ -1616,12 +1700,13 @@ kubo_status kubo_eigh_batched(const double* A, int W, int64_t n, double* E, doub
                               const kubo_options* opt) {
   try {
     kubo_options o = opt ? *opt : defaults();
-    if (!A || !E || n < 1 || W < 1) return KUBO_ERR_INVALID_ARG;
+    if (!A || !E || n < 1 || W < 1 || o.chunk_k < 0 || o.ql_max_sweeps < 0) return KUBO_ERR_INVALID_ARG;
     if (W > MAX_W) return KUBO_ERR_UNSUPPORTED;
     Call c;
     Plan& p = c.p;
     p.W = W; p.n_eta = 1; p.n_EF = 1;
     p.chunk = o.chunk_k > 0 ? o.chunk_k : auto_chunk(W, 1, n);
+    p.ql_cap = o.ql_max_sweeps;
     p.eigh = true;
     p.lbuf = W > SMALL_W_MAX;
     plan_layout(p, false, 0);

@@ -111,6 +111,7 @@ struct EighBufs {
   double2* refl;    // [n][W*W] Householder vectors v_i stored in column i, rows i+1..W-1
   double* tau;      // [n][W]
   double* lam;      // [n][W]  eigenvalues of T (unordered)
+  int ql_cap = 60;  // implicit-QL sweeps allowed per eigenvalue before ST_NO_CONVERGENCE
 };
 
 // ---------------------------------------------------------------- launchers
@@ -120,8 +121,11 @@ cudaError_t launch_check_hermitian(const double2* H_R, const int* neg, int N_R, 
 cudaError_t launch_hermitian_verdict(DevStatus* st, cudaStream_t s);
 cudaError_t launch_check_kidx(const int64_t* kidx, int64_t n, int64_t Nk, DevStatus* st,
                               cudaStream_t s);
+// escale: the basis is multiplied by 2^escale (exact; 0 = unscaled)
 cudaError_t launch_pack_basis(const double2* H_R, const int* pairs, int idx0, int N_h, int W,
-                              double* Bp, cudaStream_t s);
+                              double* Bp, cudaStream_t s, int escale = 0);
+// x[i] *= 2^e for i < n (exact unless the result leaves the FP64 range)
+cudaError_t launch_scale_pow2(double* x, int64_t n, int e, cudaStream_t s);
 cudaError_t launch_twiddles(double2* tab, int N1, int N2, int N3, cudaStream_t s);
 
 cudaError_t launch_fourier_fp64(const Model& md, const Mesh& mesh, const KList& kl, double* Hp,

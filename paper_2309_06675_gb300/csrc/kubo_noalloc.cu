@@ -8,8 +8,6 @@
 // device memory that is part of the library image itself (a file-scope __device__ array),
 // so the call performs no allocation of any kind.  It runs the same three kernels as
 // kubo_eigh_batched, over passes of as many matrices as fit in that block.
-#include <mutex>
-
 #include "kubo_internal.cuh"
 
 namespace kubo {
@@ -17,13 +15,9 @@ namespace {
 
 constexpr size_t kScratchBytes = (size_t)32 << 20;   // 32 MiB, held by every GPU that loads the library
 constexpr int kMaxW = 64;
-constexpr int kMaxDevices = 64;
 constexpr size_t kAlign = 256;
 
 static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
-
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -40,26 +34,18 @@ int64_t pass_capacity(int W) {
   return B;
 }
 
-// Device address of the block on the current device, looked up once per device with that
-// device current (the host-side symbol is only a stand-in and must never reach a kernel).
+// Device address of the block on the current device.  The host-side symbol is only a stand-in
+// and must never reach a kernel.  The address is looked up on every call, with the caller's
+// device current: the lookup allocates nothing, and a cached address could outlive a reset of
+// the device's primary context, after which the block may be loaded elsewhere.
 kubo_status scratch_address(char** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
     cudaGetLastError();
     return KUBO_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return KUBO_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return KUBO_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  *out = (char*)g_scratch_addr[dev];
+  *out = (char*)p;
   return KUBO_OK;
 }
 

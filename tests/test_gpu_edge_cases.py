@@ -37,7 +37,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("W", [1, 2, 3])
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fourier", "mixed_rotation"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fourier", "mixed_rotation", "mixed_df"])
 def test_smallest_orders_every_precision(kubo, torch, W, precision):
     m = tbgen.random_tb(W, 1, 1.0, 60 + W)
     kmesh = (5, 1, 3)                       # a size-1 axis
@@ -67,7 +67,7 @@ def test_maximum_number_of_broadenings(kubo, torch):
     kmesh = (3, 4, 4)
     etas = [0.0, 1e-5, 1e-4, 1e-3, 5e-3, 1e-2, 5e-2, 0.2]
     EF = np.array([0.0, 0.5])
-    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5), ("mixed_df", 1e-5)):
         S = kubo.ahc(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, EF), etas=etas,
                      precision=prec).cpu().numpy()
         ref = O.ahc(m.H_R, m.R, kmesh, EF, etas=etas)

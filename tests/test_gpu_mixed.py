@@ -1,5 +1,6 @@
 """Mixed-precision path (tensor-core Fourier sum with fixed-point BF16 slices, FP32 rotations,
-FP64 eigensolver, denominators and k-sum) against the FP64 oracle and the FP64 GPU path.
+FP64 eigensolver, denominators and k-sum) against the FP64 oracle and the FP64 GPU path; the
+double-float eigensolver variant (MIXED_DF) to the same tolerance.
 
 Tolerance: relative 1e-5 on S(E_F) (max over E_F of |diff| / max |S_ref|).  The tensor-core
 Fourier sum itself is exact up to its 31-bit fixed-point slicing: 2e-8 relative to max |H|
@@ -73,23 +74,35 @@ def test_mixed_w16_full_mesh_vs_golden(kubo, torch):
     assert rel_err(S, np.array(g["S"])) < REL_MIXED
 
 
-def test_mixed_per_k_w64(kubo, torch, m64):
+@pytest.mark.parametrize("prec", ["mixed", "mixed_df"])
+def test_mixed_per_k_w64(kubo, torch, m64, prec):
+    """Per-k parity on 200 k-points of the 128^3 mesh of the W = 64, N_R = 1331 model.
+
+    Error budget per k (relative to ||Omega(k)||_inf): the FP64 (or pair) eigenvalues are
+    within ~1e-12 of the oracle's, so the denominators are exact to FP64 grade; the FP32
+    rotation rounds U and dH to 2^-24 and accumulates W = 64 products, so each v_nm carries
+    ~sqrt(W) 2^-24 ||dH|| ~ 5e-7 ||dH|| of absolute error and a pair term T_nm = -2 Im(v v) /
+    (dE^2 + eta^2) a relative error of ~1e-6 ||dH||^2 / |v_nm v_mn|.  The dominant pair of a
+    k-point has |v_nm| ~ ||dH|| / 10, so ~1e-4 at worst; the median k-point sits near 1e-6."""
     kmesh = (128, 128, 128)
     kidx = tbgen.k_sample(kmesh, 200, seed=21)
     E, Om = kubo.ahc_k(cuda(torch, m64.H_R), m64.R, kmesh, cuda(torch, kidx), eta=1e-3,
-                       precision="mixed")
+                       precision=prec)
     E_ref, Om_ref = O.kubo_per_k(m64.H_R, m64.R, kmesh, kidx, [1e-3])
     E, Om = E.cpu().numpy(), Om.cpu().numpy()[0]
-    assert np.max(np.abs(E - E_ref)) <= 1e-6 * np.max(np.abs(E_ref))
+    # the eigenvalues inherit the tensor-core H(k)'s ~2^-31 entry error (||dH||_2 <= W max|dH|)
+    assert np.max(np.abs(E - E_ref)) <= 1e-7 * np.max(np.abs(E_ref)), np.max(np.abs(E - E_ref))
     scale = np.max(np.abs(Om_ref[0]), axis=-1)
     err = np.max(np.abs(Om - Om_ref[0]), axis=-1) / scale
-    assert np.max(err) < 1e-3, np.max(err)
-    assert np.median(err) < 1e-5, np.median(err)
+    print(f"{prec}: per-k Omega error max {np.max(err):.3e} median {np.median(err):.3e} "
+          f"E error {np.max(np.abs(E - E_ref)) / np.max(np.abs(E_ref)):.3e}")
+    assert np.max(err) < 1e-4, np.max(err)
+    assert np.median(err) < 3e-6, np.median(err)
 
 
 def test_mixed_vs_fp64_on_a_mesh_plane_w64(kubo, torch, m64):
     """One k1-plane (16,384 k-points) of the 128^3 mesh, 64 Fermi levels: the benchmark's
-    batch configuration, mixed vs FP64 GPU."""
+    batch configuration, mixed (and its double-float eigensolver variant) vs FP64 GPU."""
     kmesh = (128, 128, 128)
     EF = np.linspace(-1.0, 1.0, 64)
     H = cuda(torch, m64.H_R)
@@ -98,6 +111,8 @@ def test_mixed_vs_fp64_on_a_mesh_plane_w64(kubo, torch, m64):
     S64 = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng).cpu().numpy()
     Smx = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng, precision="mixed").cpu().numpy()
     assert rel_err(Smx, S64) < REL_MIXED, rel_err(Smx, S64)
+    Sdf = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng, precision="mixed_df").cpu().numpy()
+    assert rel_err(Sdf, S64) < REL_MIXED, rel_err(Sdf, S64)
     # the tensor-core Fourier sum alone is FP64-grade: only the FP32 rotations remain
     Sfo = kubo.ahc(H, m64.R, kmesh, EFt, eta=1e-3, k_range=rng,
                    precision="mixed_fourier").cpu().numpy()
@@ -177,17 +192,17 @@ def test_tensor_core_rotation_small_orders_per_k(kubo, torch, W):
 
 @pytest.mark.parametrize("W,hw", [(2, 1), (5, 2), (33, 1), (64, 5), (100, 1)])
 def test_double_float_eigenvalues(kubo, torch, W, hw):
-    """The MIXED mode's double-float eigenvalues (Householder reduction and QL iteration in
-    FP32 pairs) against the FP64 ones: MIXED and MIXED_FOURIER read the same tensor-core rows
-    of H and differ only there.  Bound: the reduction's backward error ~W 2^-46 max|E| plus at
+    """The MIXED_DF mode's double-float eigenvalues (Householder reduction and QL iteration in
+    FP32 pairs) against the FP64 ones: MIXED_DF and MIXED read the same tensor-core rows of H
+    and differ only there.  Bound: the reduction's backward error ~W 2^-46 max|E| plus at
     most W deflations of the QL at |e| <= 2^-44 (|d_m| + |d_m+1|), each moving the eigenvalues
     by at most |e| (Weyl): 16 W 2^-46 max|E| in all."""
     m = tbgen.random_tb(W, hw, 1.5, 500 + W)
     kmesh = (16, 16, 16)
     kidx = tbgen.k_sample(kmesh, 97, seed=W)
     H, K = cuda(torch, m.H_R), cuda(torch, kidx)
-    Emx, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed")
-    Efx, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed_fourier")
+    Emx, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed_df")
+    Efx, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed")
     Emx, Efx = Emx.cpu().numpy(), Efx.cpu().numpy()
     scale = np.max(np.abs(Efx))
     assert np.max(np.abs(Emx - Efx)) <= 16 * W * 2.0 ** -46 * scale, \
@@ -202,5 +217,5 @@ def test_double_float_reduction_degenerate_bands(kubo, torch):
     EF = cuda(torch, np.array([-0.5, 0.1, 0.7]))
     H = cuda(torch, m.H_R)
     S64 = kubo.ahc(H, m.R, kmesh, EF, eta=0.05).cpu().numpy()
-    Smx = kubo.ahc(H, m.R, kmesh, EF, eta=0.05, precision="mixed").cpu().numpy()
+    Smx = kubo.ahc(H, m.R, kmesh, EF, eta=0.05, precision="mixed_df").cpu().numpy()
     assert rel_err(Smx, S64) < REL_MIXED, rel_err(Smx, S64)

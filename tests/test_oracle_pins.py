@@ -319,3 +319,29 @@ def test_p4_eta_zero_degenerate_pairs_skipped():
     S2 = O.ahc(two.H_R, two.R, kmesh, [0.0], etas=[0.0])
     assert np.isfinite(S2).all()
     assert abs(S2[0, 0] - 2 * S1[0, 0]) < 1e-10
+
+
+def test_theta_at_zero_a_level_exactly_at_the_fermi_energy_is_empty():
+    """Reading of theta(0) (Eqs. 2-3 leave it open): a level exactly at E_F is not occupied.
+
+    QWZ with m = -3/2 at Gamma: every hopping is a dyadic rational and every phase is 1, so
+    H(Gamma) = (m + 2) sigma_z = diag(1/2, -1/2) exactly and the levels are exactly -1/2 and
+    +1/2.  The lower band's curvature there is the closed form d.(d_x d x d_y d) / (2|d|^3)
+    with d = (0, 0, 1/2), d_x d = (1, 0, 0), d_y d = (0, 1, 0): Omega_lower = 2 (eta = 0).
+    S at E_F = +1/2 counts the lower band only (strict reading; "<=" would add the upper
+    band's -2 and give 0); at E_F = -1/2 no band counts (the "<=" reading gives 2 / N_k).
+    """
+    m = tbgen.qwz(-1.5)
+    kmesh = (8, 8, 1)
+    Nk = 64
+    d = np.array([[0.0, 0.0, 0.5]])
+    om = _closed_omega_lower(d, np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 1.0, 0.0]]), 0.0)[0]
+    assert om == 2.0
+    E, Om = O.kubo_per_k(m.H_R, m.R, kmesh, np.array([0]), etas=[0.0])
+    assert E[0, 0] == -0.5 and E[0, 1] == 0.5
+    S = O.ahc(m.H_R, m.R, kmesh, [-0.5, 0.5, 0.75], etas=[0.0], kidx=np.array([0]))
+    assert S[0, 0] == 0.0
+    assert abs(S[0, 1] - om / Nk) < 1e-14
+    assert abs(S[0, 2]) < 1e-14       # both bands occupied: the sum rule gives 0
+    occ = O.occupation(np.array([[-0.5, 0.5]]), [0.5], 0.0)
+    assert occ.tolist() == [[[1.0, 0.0]]]
