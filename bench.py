@@ -397,8 +397,10 @@ def run_extra(args, local):
         for p in ("fp64", "mixed"):
             for unp in (False, True):
                 prof = kubo.Profile()
+                # the ablation's subject is the SIMT rotation kernel's shared-memory layout
                 ms, _ = _timed(lambda: kubo.ahc(H, model.R, kmesh, EF, eta=float(etas[0]), precision=p,
-                                                k_range=(0, k_step), profile=prof, unpadded=unp),
+                                                k_range=(0, k_step), profile=prof, unpadded=unp,
+                                                rotation="simt"),
                                args.steps, args.warmup, local)
                 st = prof.as_dict()
                 n = args.steps + args.warmup

@@ -212,6 +212,15 @@ def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk
     return o
 
 
+_ROTATION = {"tf32": 0, "exact": 1, "simt": 2}
+
+
+def _rotation(rotation, rotation_tc=False) -> int:
+    if rotation is None:
+        return 1 if rotation_tc else 0
+    return _ROTATION[rotation]
+
+
 def debug_fail_allocations(n: int) -> None:
     """Make the library's next n device allocations fail as out-of-memory (test hook)."""
     lib().kubo_debug_fail_allocations(int(n))
@@ -243,8 +252,12 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
         stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
-        unpadded=False, separable=False, rotation_tc=False, ql_max_sweeps=0):
+        unpadded=False, separable=False, rotation_tc=False, ql_max_sweeps=0, rotation=None):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
+
+    rotation: the FP32-grade step (3) kernel of the reduced modes, "tf32" (tensor cores,
+    3xTF32; the default), "exact" (tensor cores, exact BF16 slices; rotation_tc=True) or
+    "simt" (FP32 FMA pipe).
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
     """
@@ -262,7 +275,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     o.mixed_fixup_rel = float(fixup_rel)
     o.layout_unpadded = 1 if unpadded else 0
     o.fourier_separable = 1 if separable else 0
-    o.rotation_tc = 1 if rotation_tc else 0
+    o.rotation_tc = _rotation(rotation, rotation_tc)
     code = lib().kubo_ahc(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                           W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                           _dev(E_F, torch.float64, "E_F"), n_EF, float(eta),
@@ -424,7 +437,7 @@ def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_
 
 
 def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None, chunk_k=0,
-          rotation_tc=False, ql_max_sweeps=0):
+          rotation_tc=False, ql_max_sweeps=0, rotation=None):
     """Per-k eigenvalues and band curvatures for the listed mesh points."""
     torch = _torch()
     Rh = _host_int32(R, 3)
@@ -437,7 +450,7 @@ def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None,
     keep = []
     o = _options(precision, etas, 0.0, None, stream, chunk_k, None, keep,
                  ql_max_sweeps=ql_max_sweeps)
-    o.rotation_tc = 1 if rotation_tc else 0
+    o.rotation_tc = _rotation(rotation, rotation_tc)
     code = lib().kubo_ahc_k(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                             W, N_R, km.ctypes.data_as(ctypes.c_void_p),
                             _dev(kidx, torch.int64, "kidx"), n_k, float(eta),

@@ -964,6 +964,301 @@ __global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
   }
 }
 
+// ------------------------------------------------------------------ rotations in 3xTF32
+// Step (3) on tcgen05 with kind::tf32 operands and FP32 accumulation in TMEM (the split-TF32
+// scheme): every FP32 operand x is cut into hi = tf32(x) and lo = tf32(x - hi) (11 + 11
+// significant bits, the cut exact), and a product is formed as hi hi + hi lo + lo hi in one
+// FP32 accumulator, ~2^-22 relative per product: FP32-grade, like the SIMT rotation it
+// replaces.  K = 128 is short, so FP32 accumulation adds only ~sqrt(48) 2^-24 per entry.
+// The complex products are block-real GEMMs with M = 128, N = 64, K = 128 (W padded to 64):
+//   T = X U:    [T_r; T_i] = [[X_r, -X_i], [X_i, X_r]] [U_r; U_i]
+//   V = U^H T:  [V_r; V_i] = [[U_r^T, U_i^T], [-U_i^T, U_r^T]] [T_r; T_i]
+// T stays in TMEM and in registers (each thread holds 32 entries of one row of [T_r; T_i],
+// which is one K column of the second product's B operand); V^x and V^y accumulate in their
+// own TMEM columns.  The operands are staged one K-quarter (32 TF32 = one 128-byte swizzle
+// row) at a time, 48 KB for A and B with their hi / lo parts, so that with U (FP32, assembled
+// from the FP64 factors in shared memory) a CTA needs ~85 KB and two CTAs share an SM: one
+// stages operands while the other's MMAs run.  Persistent over the k-points; every wait on
+// the tensor core is bounded (ST_TIMEOUT).
+constexpr int TF_NT = 256;
+constexpr int TF_WP = 64;
+constexpr int TF_A_TILE = 128 * 128;   // bytes: 128 rows x 32 TF32
+constexpr int TF_B_TILE = 64 * 128;    // bytes: 64 rows x 32 TF32
+constexpr int TF_OPS_BYTES = 2 * TF_A_TILE + 2 * TF_B_TILE;   // A hi, A lo, B hi, B lo: 48 KB
+constexpr int TF_LDU = 68;                                    // = mixed_ld(64, 1)
+constexpr int TF_U_BYTES = TF_WP * TF_LDU * 8;                // 34,816
+constexpr int TF_TMEM_COLS = 256;                             // T at 0, V^x at 64, V^y at 128
+constexpr uint32_t TF_WAIT_LIMIT = 1u << 20;
+// instruction descriptor: D F32, A and B TF32 (K-major), N = 64, M = 128
+constexpr uint32_t TF_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+// byte offset of element (row, k in 0..31) in a K-major 128-byte-swizzled tile of 4-byte elements
+__device__ __forceinline__ uint32_t sw128_off32(int row, int k) {
+  const uint32_t b = (uint32_t)k * 4u;
+  return (uint32_t)row * 128u + ((((b >> 4) ^ (uint32_t)(row & 7)) & 7u) << 4) + (b & 15u);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo + O(2^-22 |x|), both TF32 (low 13 mantissa bits zero); x - hi is exact in FP32
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// four consecutive K entries (k0 = 4 c4 .. 4 c4 + 3) of one row, hi and lo tiles
+__device__ __forceinline__ void put4_tf32(unsigned char* hi_tile, unsigned char* lo_tile, int row,
+                                          int c4, const float (&x)[4]) {
+  uint4 h, l;
+  tf32_split(x[0], h.x, l.x);
+  tf32_split(x[1], h.y, l.y);
+  tf32_split(x[2], h.z, l.z);
+  tf32_split(x[3], h.w, l.w);
+  const uint32_t off = sw128_off32(row, 4 * c4);
+  *reinterpret_cast<uint4*>(hi_tile + off) = h;
+  *reinterpret_cast<uint4*>(lo_tile + off) = l;
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// the 12 MMAs of one K-quarter: (hi, hi), (hi, lo), (lo, hi) x 4 K8 steps
+__device__ __forceinline__ void tf_issue(uint32_t tmem_d, uint32_t ops, bool first) {
+  const uint32_t a_hi = ops, a_lo = ops + TF_A_TILE;
+  const uint32_t b_hi = ops + 2 * TF_A_TILE, b_lo = b_hi + TF_B_TILE;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const uint32_t a = p == 2 ? a_lo : a_hi, b = p == 1 ? b_lo : b_hi;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+      umma_tf32(tmem_d, tc::umma_desc_sw128(a + kk * 32), tc::umma_desc_sw128(b + kk * 32),
+                TF_IDESC, (first && p == 0 && kk == 0) ? 0u : 1u);
+  }
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
+    const double* __restrict__ E, const double* __restrict__ Z, EighBufs eb,
+    const TIn* __restrict__ Xp, const TIn* __restrict__ Yp, int64_t ld, int W, int n,
+    const double* __restrict__ etas, int n_eta, double* __restrict__ Om, int64_t eta_stride,
+    DevStatus* st) {
+  extern __shared__ unsigned char tf_smem[];
+  __shared__ double sE[64];
+  __shared__ double sEta[MAXE];
+  __shared__ double s_emax;
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int s_ok;
+  float2* sU = reinterpret_cast<float2*>(tf_smem);
+  // the operand tiles start on a 1024-byte boundary (the 128-byte swizzle pattern repeats every
+  // 8 rows of 128 bytes and is taken from the address bits)
+  unsigned char* ops = reinterpret_cast<unsigned char*>(
+      ((uintptr_t)(tf_smem + TF_U_BYTES) + 1023) & ~(uintptr_t)1023);
+  unsigned char* a_hi = ops;
+  unsigned char* a_lo = ops + TF_A_TILE;
+  unsigned char* b_hi = ops + 2 * TF_A_TILE;
+  unsigned char* b_lo = b_hi + TF_B_TILE;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const size_t WW = (size_t)W * W;
+
+  if (t == 0) {
+    tc::mbar_init(&mma_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc::smem_u32(&tmem_sh)), "r"(TF_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  const uint32_t ops_u32 = tc::smem_u32(ops);
+  // TMEM lane quarter and column half of this warp when reading an accumulator
+  const int quarter = warp & 3, chalf = warp >> 2;
+  const int mrow = quarter * 32 + lane;   // row of [.._r; .._i]
+  const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+
+  // the MMAs of the staged K-quarter into TMEM column d_col; bounded wait (false on timeout)
+  auto mma_quarter = [&](uint32_t d_col, bool first) -> bool {
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+      tf_issue(tmem + d_col, ops_u32, first);
+      tc::umma_commit(&mma_bar);
+      s_ok = tc::mbar_wait(&mma_bar, phase, TF_WAIT_LIMIT) ? 1 : 0;
+    }
+    __syncthreads();
+    phase ^= 1u;
+    tc::tc_fence_after();
+    return s_ok != 0;
+  };
+
+  for (int64_t k = blockIdx.x; k < n && ok; k += gridDim.x) {
+    __syncthreads();   // the previous k-point's shared data is no longer read
+    if (t < W) sE[t] = E[k * W + t];
+    if (t < n_eta) sEta[t] = etas[t];
+    for (int idx = t; idx < TF_WP * TF_LDU; idx += TF_NT) sU[idx] = make_float2(0.f, 0.f);
+    __syncthreads();
+    // ---- U = Q D Z in FP32 (the reflectors staged in the operand region)
+    assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, TF_LDU, t,
+                   sU, reinterpret_cast<float2*>(ops));
+    if (t == 0) {
+      double mx = 0.0;
+      for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
+      s_emax = mx;
+    }
+    for (int a = 0; a < 2 && ok; ++a) {
+      const TIn* P = (a == 0 ? Xp : Yp) + k * ld;
+      // ---- product 1: [T_r; T_i] = A1 B1^T into TMEM columns 0..63
+      for (int h = 0; h < 4 && ok; ++h) {
+        __syncthreads();   // the stage area / previous quarter's operands are free
+        // A1 rows i and 64 + i, K columns 32 h + 4 c4 .. + 3 (X column c = that - 64 h2)
+        const bool second = h >= 2;
+        for (int it = t; it < 64 * 8; it += TF_NT) {
+          const int i = it >> 3, c4 = it & 7;
+          float xr[4], xi[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = (h & 1) * 32 + 4 * c4 + q;
+            float re = 0.f, im = 0.f;
+            if (i < W && c < W) {
+              if (i < c) { re = (float)P[i * W + c]; im = (float)P[c * W + i]; }
+              else if (i > c) { re = (float)P[c * W + i]; im = -(float)P[i * W + c]; }
+              else re = (float)P[i * W + i];
+            }
+            xr[q] = re;
+            xi[q] = im;
+          }
+          if (!second) {
+            put4_tf32(a_hi, a_lo, i, c4, xr);        // [X_r | .]
+            put4_tf32(a_hi, a_lo, 64 + i, c4, xi);   // [X_i | .]
+          } else {
+            float nx[4] = {-xi[0], -xi[1], -xi[2], -xi[3]};
+            put4_tf32(a_hi, a_lo, i, c4, nx);        // [. | -X_i]
+            put4_tf32(a_hi, a_lo, 64 + i, c4, xr);   // [. | X_r]
+          }
+        }
+        // B1[n][k] = U_r[k][n] (k < 64), U_i[k - 64][n]
+        for (int it = t; it < 64 * 8; it += TF_NT) {
+          const int nn = it & 63, c4 = it >> 6;
+          float u[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = sU[((h & 1) * 32 + 4 * c4 + q) * TF_LDU + nn];
+            u[q] = second ? v.y : v.x;
+          }
+          put4_tf32(b_hi, b_lo, nn, c4, u);
+        }
+        if (!mma_quarter(0, h == 0)) ok = false;
+      }
+      if (!ok) break;
+      // ---- this thread's 32 entries of row mrow of [T_r; T_i]
+      float tv[32];
+      {
+        uint32_t r[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)(chalf * 32), r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tv[j] = __uint_as_float(r[j]);
+        tc::tmem_ld16(lane_addr + (uint32_t)(chalf * 32 + 16), r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tv[16 + j] = __uint_as_float(r[j]);
+      }
+      tc::tc_fence_before();
+      // ---- product 2: [V_r; V_i] = A2 B2^T into TMEM columns 64 + 64 a
+      for (int h = 0; h < 4 && ok; ++h) {
+        __syncthreads();
+        const bool second = h >= 2;
+        // A2 rows m, 64 + m; K = 32 h + 4 c4 + q is row kk of U (kk = K mod 64)
+        for (int it = t; it < 64 * 8; it += TF_NT) {
+          const int m = it & 63, c4 = it >> 6;
+          float p0[4], p1[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = sU[((h & 1) * 32 + 4 * c4 + q) * TF_LDU + m];   // U[kk][m]
+            p0[q] = second ? v.y : v.x;     // [U_r^T | U_i^T]
+            p1[q] = second ? v.x : -v.y;    // [-U_i^T | U_r^T]
+          }
+          put4_tf32(a_hi, a_lo, m, c4, p0);
+          put4_tf32(a_hi, a_lo, 64 + m, c4, p1);
+        }
+        // B2[n][k] = [T_r; T_i][k][n]: K rows 32 h .. 32 h + 31 are this quarter's TMEM lanes
+        if (quarter == h) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            uint32_t hi, lo;
+            tf32_split(tv[j], hi, lo);
+            const uint32_t off = sw128_off32(chalf * 32 + j, lane);
+            *reinterpret_cast<uint32_t*>(b_hi + off) = hi;
+            *reinterpret_cast<uint32_t*>(b_lo + off) = lo;
+          }
+        }
+        if (!mma_quarter(64 + 64 * a, h == 0)) ok = false;
+      }
+    }
+    if (!ok) break;
+    // ---- V^x, V^y from TMEM into shared memory (float2 [64][TF_LDU]; U and the operands are
+    // no longer needed)
+    __syncthreads();
+    float2* sVx = reinterpret_cast<float2*>(tf_smem);
+    float2* sVy = sVx + TF_WP * TF_LDU;
+    {
+      const int rr = mrow & 63;
+      const int comp = mrow >= 64 ? 1 : 0;
+      for (int a = 0; a < 2; ++a) {
+        float* dst = reinterpret_cast<float*>(a == 0 ? sVx : sVy);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t r[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)(64 + 64 * a + chalf * 32 + 16 * hh), r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            dst[2 * (rr * TF_LDU + chalf * 32 + 16 * hh + j) + comp] = __uint_as_float(r[j]);
+        }
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // ---- curvature (FP64 energy differences), as the SIMT kernels
+    {
+      const int tx = t & 15, ty = t >> 4;
+      float2 vy[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vy[i][j] = sVy[(ty + 16 * i) * TF_LDU + tx + 16 * j];
+      curvature_epilogue<4, float2>(sVx, vy, sE, sEta, n_eta, s_emax, W, TF_LDU, ty, tx, t,
+                                    reinterpret_cast<double*>(tf_smem), Om, eta_stride, k);
+    }
+  }
+  if (!ok && t == 0) atomicOr(&st->bits, ST_TIMEOUT);
+  // no MMA may still write TMEM when it is released
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0 && !ok) tc::mbar_wait(&mma_bar, phase, TF_WAIT_LIMIT);
+    __syncwarp();
+    tc::tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TF_TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 size_t berry_fp64_smem(int W, int n_eta) {
@@ -1088,6 +1383,54 @@ cudaError_t launch_berry_tc_from_f64(const double* E, const double* Z, const Eig
                                      int64_t eta_stride, DevStatus* st, cudaStream_t s) {
   return launch_berry_tc_t<double>(E, Z, eb, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
                                    eta_stride, st, s);
+}
+
+// dynamic shared memory of the 3xTF32 rotation kernel: U and the operand stage, or the
+// curvature's per-eta partial sums if larger (n_eta x 16 KB)
+size_t berry_tf32_smem(int n_eta) {
+  const size_t base = (size_t)TF_U_BYTES + 1024 + TF_OPS_BYTES;
+  const size_t red = (size_t)n_eta * TF_WP * 2 * 16 * sizeof(double);
+  return std::max(base, red);
+}
+
+template <typename TIn>
+static cudaError_t launch_berry_tf32_t(const double* E, const double* Z, const EighBufs& eb,
+                                       const TIn* Xp, const TIn* Yp, int64_t ld, int W, int n,
+                                       const double* etas, int n_eta, double* Om,
+                                       int64_t eta_stride, DevStatus* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > TF_WP || n_eta > MAXE) return cudaErrorInvalidValue;
+  const size_t sm = berry_tf32_smem(n_eta);
+  cudaError_t e = cudaFuncSetAttribute(berry_tf32_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152, per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, berry_tf32_kernel<TIn>, TF_NT, sm) != cudaSuccess)
+    per_sm = 1;
+  cudaGetLastError();
+  // TMEM: TF_TMEM_COLS per CTA out of 512 columns
+  per_sm = std::max(1, std::min(per_sm, 512 / TF_TMEM_COLS));
+  const int grid = (int)std::min<int64_t>(n, (int64_t)std::max(1, sms) * per_sm);
+  berry_tf32_kernel<TIn><<<grid, TF_NT, sm, s>>>(E, Z, eb, Xp, Yp, ld, W, n, etas, n_eta, Om,
+                                                 eta_stride, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_berry_tf32_rows(const double* E, const double* Z, const EighBufs& eb,
+                                   const double* C, int64_t ld, int W, int n, const double* etas,
+                                   int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
+                                   cudaStream_t s) {
+  const int64_t WW = (int64_t)W * W;
+  return launch_berry_tf32_t<double>(E, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
+                                     eta_stride, st, s);
+}
+
+cudaError_t launch_berry_tf32_from_f64(const double* E, const double* Z, const EighBufs& eb,
+                                       const double* Xp, const double* Yp, int W, int n,
+                                       const double* etas, int n_eta, double* Om,
+                                       int64_t eta_stride, DevStatus* st, cudaStream_t s) {
+  return launch_berry_tf32_t<double>(E, Z, eb, Xp, Yp, (int64_t)W * W, W, n, etas, n_eta, Om,
+                                     eta_stride, st, s);
 }
 
 cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,

@@ -33,6 +33,9 @@ kubo_options defaults() {
   return o;
 }
 
+// FP32-grade rotation kernels for W <= 64 (kubo_options.rotation_tc)
+enum { ROT_TF32 = 0, ROT_EXACT_SLICES = 1, ROT_SIMT = 2 };
+
 // ------------------------------------------------------------------ R set
 struct RInfo {
   std::vector<int> neg;     // [N_R] index of -R
@@ -111,7 +114,7 @@ struct Plan {
   int Npad = 0, Kp = 0, Mpad = 0;   // tensor-core operand padding (mixed precision)
   int kpb = KSUM_KPB;               // k-points per k-sum block
   int pad = 1;                      // leading dimension W + pad in the fused kernels' smem
-  bool rot_tc = false;              // FP32-grade rotations on the tensor cores (W <= 64)
+  int rot = 0;                      // FP32-grade rotation kernel (W <= 64): ROT_* below
   bool scale_ok = false;            // the call may rescale H(R) by a power of two (range_exponent)
   int escale = 0;                   // that power: the basis holds 2^escale H(R)
   int ql_cap = 0;                   // QL sweeps per eigenvalue (0 = the kernels' default)
@@ -424,6 +427,7 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
       if (!finite_nonneg(o.etas[e])) return KUBO_ERR_INVALID_ARG;
   }
   if (o.chunk_k < 0 || o.ql_max_sweeps < 0) return KUBO_ERR_INVALID_ARG;
+  if (o.rotation_tc < 0 || o.rotation_tc > 2) return KUBO_ERR_INVALID_ARG;
   if (!std::isfinite(o.mixed_fixup_rel)) return KUBO_ERR_INVALID_ARG;
   n_eta = o.n_eta > 0 ? o.n_eta : 1;
   return KUBO_OK;
@@ -588,7 +592,9 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
         KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    if (p.rot_tc)
+    if (p.rot == ROT_TF32)
+      KCHECK(launch_berry_tf32_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
+    else if (p.rot == ROT_EXACT_SLICES)
       KCHECK(launch_berry_tc_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
     else
       KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
@@ -638,7 +644,9 @@ kubo_status run_batch_steps(Call& c, const Model& md, const KList& kl, double* E
         KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
-    if (p.rot_tc)
+    if (p.rot == ROT_TF32)
+      KCHECK(launch_berry_tf32_from_f64(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
+    else if (p.rot == ROT_EXACT_SLICES)
       KCHECK(launch_berry_tc_from_f64(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
     else
       KCHECK(launch_berry_mixed_from_f64_z(Eout, Z, eb, Xp, Yp, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
@@ -817,7 +825,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.pad = o.layout_unpadded ? 0 : 1;
   p.ql_cap = o.ql_max_sweeps;
   // the padding ablation concerns the SIMT rotation kernel's shared-memory layout
-  p.rot_tc = o.rotation_tc && !o.layout_unpadded;
+  p.rot = o.layout_unpadded ? ROT_SIMT : o.rotation_tc;
   if (o.fourier_separable) {
     if (o.workspace) return KUBO_ERR_UNSUPPORTED;   // its size depends on the R set
     r = setup_separable(p, R_vecs, N_R, kb, ke, ri);

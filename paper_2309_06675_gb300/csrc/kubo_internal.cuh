@@ -181,6 +181,16 @@ cudaError_t launch_berry_tc_rows(const double* E, const double* Z, const EighBuf
                                  const double* C, int64_t ld, int W, int n, const double* etas,
                                  int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
                                  cudaStream_t s);
+// the same two rotations in 3xTF32 on tcgen05 (kind::tf32, FP32 accumulation), W <= 64; U is
+// assembled in FP32 from Z and eb; a stalled MMA completion sets ST_TIMEOUT in st
+cudaError_t launch_berry_tf32_rows(const double* E, const double* Z, const EighBufs& eb,
+                                   const double* C, int64_t ld, int W, int n, const double* etas,
+                                   int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
+                                   cudaStream_t s);
+cudaError_t launch_berry_tf32_from_f64(const double* E, const double* Z, const EighBufs& eb,
+                                       const double* Xp, const double* Yp, int W, int n,
+                                       const double* etas, int n_eta, double* Om,
+                                       int64_t eta_stride, DevStatus* st, cudaStream_t s);
 cudaError_t launch_berry_tc_from_f64(const double* E, const double* Z, const EighBufs& eb,
                                      const double* Xp, const double* Yp, int W, int n,
                                      const double* etas, int n_eta, double* Om,
