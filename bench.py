@@ -478,13 +478,13 @@ def main():
         s = slab_of(rank, world, step, n_slabs)
         return (s * k_per_step, (s + 1) * k_per_step)
 
-    def timed(prec):
+    def timed(prec, rotation=None):
         outs = []
         def one_step(step, prof=None):
             flush.fill_(step & 0xFF)   # evict L2 (256 MiB > 135 MB) before every step
             o = torch.empty((1, E_F.size), dtype=torch.float64, device=dev)
             kubo.ahc(H, model.R, kmesh, EF, eta=eta, kT=kT, precision=prec, k_range=slab(step),
-                     out=o, profile=prof, chunk_k=args.chunk)
+                     out=o, profile=prof, chunk_k=args.chunk, rotation=rotation)
             return o
         for s in range(args.warmup):
             one_step(s)
@@ -510,6 +510,10 @@ def main():
         return ms, d, clk, torch.cat(outs).cpu().numpy()
 
     res = {p: timed(p) for p in precisions}
+    # the mixed form with step (3) on the tensor cores (labelled variants, same slabs)
+    rot_res = {}
+    if args.precision == "both" and not args.no_extras:
+        rot_res = {r: timed("mixed", rotation=r) for r in ("tf32", "exact")}
 
     # ---- end to end through the host-buffer entry point (pinned host memory), headline path
     head = precisions[0]
@@ -607,6 +611,16 @@ def main():
                             "slice-pair products on the H columns, 6 on the velocity columns; exact "
                             "FP32 block sums)"},
             }
+        if rot_res:
+            line["mixed_rotation_kernels"] = {
+                "what": "the mixed form with step (3) on the tensor cores instead of the FP32 "
+                        "FMA pipe: 3xTF32 (tcgen05 kind::tf32, split operands, FP32 "
+                        "accumulation) and exact fixed-point BF16 slices",
+                **{r: {"value": world * k_total / (v[0] / 1e3),
+                       "berry_ms_per_step": v[1]["berry"]["ms"] / args.steps,
+                       "rel_err_max_over_steps": float(np.max(np.abs(v[3] - of) / den))}
+                   for r, v in rot_res.items()},
+                "simt_berry_ms_per_step": res["mixed"][1]["berry"]["ms"] / args.steps}
         if "mixed_df" in res:
             line["mixed_df_variant"] = {
                 "what": "the mixed form with its eigensolver in double-float (FP32 pairs, ~2^-46 "

@@ -11,12 +11,12 @@
 //                    vectorised over matrix rows/elements.  T_c is made real by the diagonal
 //                    unitary D (T_c = D T D^dagger, T[j+1][j] = |beta_j|).
 //   ql_kernel        one LANE per k-point (the paper's batching along the vector length):
-//                    implicit QL with Wilkinson shifts on the real tridiagonal T.  The
-//                    rotation recurrence is inherently scalar, so 32 k-points share each
-//                    warp instruction.  Every Givens rotation (c, s, i) is logged.
-//   backtransform_kernel  one CTA per k-point: replays the logged rotations on Z (T = Z L
-//                    Z^T; rows in parallel), sorts the eigenvalues, and forms
-//                    U = Q D Z by applying the reflectors to the columns of D Z.
+//                    implicit QL with Wilkinson shifts on the real tridiagonal T, eigenvalues
+//                    only.  The rotation recurrence is inherently scalar, so 32 k-points share
+//                    each warp instruction; each lane advances through its own eigenvalues.
+//   backtransform_kernel  one CTA per k-point: sorts the eigenvalues, computes the
+//                    eigenvectors Z of T by inverse iteration and forms U = Q D Z by applying
+//                    the reflectors to the columns of D Z.
 //
 // Padded leading dimensions (W+1) keep column walks conflict-free in shared memory (the
 // GPU counterpart of the paper's padding against memory-bank conflicts).
@@ -78,32 +78,44 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
         s2 = fma(x.x, x.x, fma(x.y, x.y, s2));
       }
       s2 = warp_sum(s2);
-      if (lane == 0) {
-        double2 al = A[tri(o, i)];
-        double tau = 0.0;
-        double2 beta = al;
+      // H = I - tau v v^H with v = x - beta e1, beta = -e^{i arg alpha} |x|:
+      // v0 = alpha + e^{i arg alpha} |x|, tau = 2 / v^H v = 1 / (|x| (|x| + |alpha|)).
+      // Few lanes run this, and every FP64 instruction takes a whole warp slot of the pipe
+      // whatever its active mask, so the two independent halves run side by side in lanes 0
+      // and 1: |x| = n2 rsqrt(n2) and |alpha| = aa2 rsqrt(aa2) in one rsqrt, then the real and
+      // imaginary parts of the unit phase alpha / |alpha|, of beta and of v0 in one instruction
+      // each.
+      if (lane < 2) {
+        const double2 al = A[tri(o, i)];
+        const double aa2 = fma(al.x, al.x, al.y * al.y);
+        const double x2 = lane == 0 ? aa2 + s2 : aa2;     // |x|^2 (lane 0), |alpha|^2 (lane 1)
+        const double rx = x2 > 0.0 ? rsqrt(x2) : 0.0;
+        const double xn = x2 * rx;                         // |x| (lane 0), |alpha| (lane 1)
+        const double nrm = __shfl_sync(0x3u, xn, 0);
+        const double aa = __shfl_sync(0x3u, xn, 1);
+        const double ra = __shfl_sync(0x3u, rx, 1);
+        const double comp = lane == 0 ? al.x : al.y;
+        // the unit phase of alpha (1 for alpha = 0)
+        const double ph = aa2 > 0.0 ? comp * ra : (lane == 0 ? 1.0 : 0.0);
         if (s2 != 0.0) {
-          // H = I - tau v v^H with v = x - beta e1, beta = -e^{i arg alpha} |x|:
-          // v0 = alpha + e^{i arg alpha} |x|, tau = 2 / v^H v = 1 / (|x| (|x| + |alpha|))
-          // (square roots as x * rsqrt(x): one lane runs this, so every FP64 instruction of it
-          // costs a whole warp slot of the pipe)
-          const double aa2 = fma(al.x, al.x, al.y * al.y);
-          const double n2 = aa2 + s2;
-          const double nrm = n2 * rsqrt(n2);
-          double pr = 1.0, pi = 0.0, aa = 0.0;
-          if (aa2 > 0.0) {
-            const double ra = rsqrt(aa2);
-            aa = aa2 * ra;
-            pr = al.x * ra;
-            pi = al.y * ra;
+          const double bet = -ph * nrm;
+          const double v0 = fma(ph, nrm, comp);
+          double* Ao = reinterpret_cast<double*>(&A[tri(o, i)]);
+          double* bo = reinterpret_cast<double*>(&be[i]);
+          Ao[lane] = v0;
+          bo[lane] = bet;
+          if (lane == 0) {
+            const double tau = 1.0 / (nrm * (nrm + aa));
+            s_tau = tau;
+            tb[i] = tau;
           }
-          beta = make_double2(-pr * nrm, -pi * nrm);
-          A[tri(o, i)] = make_double2(fma(pr, nrm, al.x), fma(pi, nrm, al.y));
-          tau = 1.0 / (nrm * (nrm + aa));
+        } else {
+          reinterpret_cast<double*>(&be[i])[lane] = comp;   // beta = alpha, no reflection
+          if (lane == 0) {
+            s_tau = 0.0;
+            tb[i] = 0.0;
+          }
         }
-        s_tau = tau;
-        be[i] = beta;
-        tb[i] = tau;
       }
     }
     __syncthreads();
@@ -112,13 +124,15 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
       for (int r = t; r < m; r += NT) vb[r] = A[tri(o + r, i)];
       __syncthreads();
       // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r).  The m x m
-      // product is spread densely over the block: thread t takes row r = t mod m and the
-      // columns c = part, part + P, ... (part = t / m, P = NT / m parts per row), so every warp
-      // issues full (the m rows of one thread each would leave lanes idle for m < 64 and
-      // partial warps); the P partial sums of a row are added in part order.  The conjugate of
-      // the mirrored element flips a sign bit on the integer side (no FP64 instruction).
+      // product is spread over the block: thread t takes row r = t mod m and the columns
+      // c = part, part + P, ... (part = t / m, P = min(NT / m, 4) parts per row), so that the
+      // warps issue full; the P partial sums of a row are added in part order by the m row
+      // threads.  P is capped at 4: for a small trailing block more parts would shorten the
+      // product but lengthen that sum, whose warps run with m of their 32 lanes (the other
+      // CTAs of the SM keep the FP64 pipe busy meanwhile).  The conjugate of the mirrored
+      // element flips a sign bit on the integer side (no FP64 instruction).
       {
-        const int P = NT / m;
+        const int P = min(NT / m, 4);
         const int r = t % m, part = t / m;
         if (part < P) {
           double ax = 0.0, ay = 0.0;
@@ -246,52 +260,59 @@ __global__ void __launch_bounds__(32) ql_kernel(int W, int n, EighBufs b, DevSta
   }
   bool fail = false;
   const double eps = 2.220446049250313e-16;
-  for (int l = 0; l < W && !fail; ++l) {
-    int iter = 0;
-    while (true) {
-      int m = l;
-      for (; m < W - 1; ++m) {
-        double dd = fabs(D[m * 32]) + fabs(D[(m + 1) * 32]);
-        if (fabs(E[m * 32]) <= eps * dd) break;
-      }
-      if (m == l) break;
-      if (++iter > b.ql_cap) { fail = true; break; }
-      // Wilkinson shift from the leading 2x2 of the block, then chase up from the bottom.
-      double dl = D[l * 32], el = E[l * 32];
-      double g = (D[(l + 1) * 32] - dl) / (2.0 * el);
-      double r = hypot(g, 1.0);
-      g = D[m * 32] - dl + el / (g + copysign(r, g));
-      double s = 1.0, c = 1.0, p = 0.0;
-      bool early = false;
-      for (int i = m - 1; i >= l; --i) {
-        double ei = E[i * 32];
-        double f = s * ei, bb = c * ei;
-        // r = |(f, g)| and (s, c) = (f, g) / r from one reciprocal square root (the entries of
-        // T are far from the FP64 overflow/underflow range, so no scaling is needed)
-        const double r2 = fma(f, f, g * g);
-        if (r2 == 0.0) {   // split: the chase stops here
-          E[(i + 1) * 32] = 0.0;
-          D[(i + 1) * 32] -= p;
-          E[m * 32] = 0.0;
-          early = true;
-          break;
-        }
-        const double ir = rsqrt(r2);
-        r = r2 * ir;
-        E[(i + 1) * 32] = r;
-        s = f * ir;
-        c = g * ir;
-        double gi = D[(i + 1) * 32] - p;
-        double rr = fma(D[i * 32] - gi, s, 2.0 * c * bb);
-        p = s * rr;
-        D[(i + 1) * 32] = gi + p;
-        g = fma(c, rr, -bb);
-      }
-      if (early) continue;
-      D[l * 32] -= p;
-      E[l * 32] = g;
-      E[m * 32] = 0.0;
+  // Each lane advances through its own eigenvalues: one pass of the loop either deflates the
+  // current eigenvalue l (|e| small at m = l) or runs one QL sweep on its block l..m.  A lane is
+  // never held at an eigenvalue by the other lanes of the warp, whose matrices need a
+  // different number of sweeps for it (with the eigenvalue loop outermost, every lane would
+  // wait at each l for the slowest lane's sweeps, about half of the warp's issued work).
+  int l = 0, iter = 0;
+  while (l < W) {
+    int m = l;
+    for (; m < W - 1; ++m) {
+      double dd = fabs(D[m * 32]) + fabs(D[(m + 1) * 32]);
+      if (fabs(E[m * 32]) <= eps * dd) break;
     }
+    if (m == l) {
+      ++l;
+      iter = 0;
+      continue;
+    }
+    if (++iter > b.ql_cap) { fail = true; break; }
+    // Wilkinson shift from the leading 2x2 of the block, then chase up from the bottom.
+    double dl = D[l * 32], el = E[l * 32];
+    double g = (D[(l + 1) * 32] - dl) / (2.0 * el);
+    double r = hypot(g, 1.0);
+    g = D[m * 32] - dl + el / (g + copysign(r, g));
+    double s = 1.0, c = 1.0, p = 0.0;
+    bool early = false;
+    for (int i = m - 1; i >= l; --i) {
+      double ei = E[i * 32];
+      double f = s * ei, bb = c * ei;
+      // r = |(f, g)| and (s, c) = (f, g) / r from one reciprocal square root (the entries of
+      // T are far from the FP64 overflow/underflow range, so no scaling is needed)
+      const double r2 = fma(f, f, g * g);
+      if (r2 == 0.0) {   // split: the chase stops here
+        E[(i + 1) * 32] = 0.0;
+        D[(i + 1) * 32] -= p;
+        E[m * 32] = 0.0;
+        early = true;
+        break;
+      }
+      const double ir = rsqrt(r2);
+      r = r2 * ir;
+      E[(i + 1) * 32] = r;
+      s = f * ir;
+      c = g * ir;
+      double gi = D[(i + 1) * 32] - p;
+      double rr = fma(D[i * 32] - gi, s, 2.0 * c * bb);
+      p = s * rr;
+      D[(i + 1) * 32] = gi + p;
+      g = fma(c, rr, -bb);
+    }
+    if (early) continue;
+    D[l * 32] -= p;
+    E[l * 32] = g;
+    E[m * 32] = 0.0;
   }
   for (int i = 0; i < W; ++i) b.lam[(size_t)k * W + i] = D[i * 32];
   if (fail) atomicOr(&st->bits, ST_NO_CONVERGENCE);

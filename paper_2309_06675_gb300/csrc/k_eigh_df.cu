@@ -520,15 +520,21 @@ __global__ void __launch_bounds__(32) ql_df_kernel(int W, int n, EighBufs b, Dev
   auto st2 = [&](float2* a, int i, Df v) { a[i * 32] = make_float2(v.h, v.l); };
   bool fail = false;
   const float eps = 0x1p-44f;
-  for (int l = 0; l < W && !fail; ++l) {
-    int iter = 0;
-    while (true) {
+  // each lane advances through its own eigenvalues (as the FP64 kernel): one pass deflates the
+  // current eigenvalue or runs one sweep on its block
+  int l = 0, iter = 0;
+  while (l < W) {
+    {
       int m = l;
       for (; m < W - 1; ++m) {
         const float dd = fabsf(D[m * 32].x) + fabsf(D[(m + 1) * 32].x);
         if (fabsf(E[m * 32].x) <= eps * dd) break;
       }
-      if (m == l) break;
+      if (m == l) {
+        ++l;
+        iter = 0;
+        continue;
+      }
       if (++iter > b.ql_cap) { fail = true; break; }
       // Wilkinson shift from the leading 2x2 of the block, then chase up from the bottom
       const Df dl = ld(D, l), el = ld(E, l);
