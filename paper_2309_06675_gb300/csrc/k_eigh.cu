@@ -259,18 +259,23 @@ __global__ void __launch_bounds__(32) ql_kernel(int W, int n, EighBufs b, DevSta
     E[i * 32] = b.e[(size_t)k * W + i];
   }
   bool fail = false;
-  const double eps = 2.220446049250313e-16;
   // Each lane advances through its own eigenvalues: one pass of the loop either deflates the
   // current eigenvalue l (|e| small at m = l) or runs one QL sweep on its block l..m.  A lane is
   // never held at an eigenvalue by the other lanes of the warp, whose matrices need a
   // different number of sweeps for it (with the eigenvalue loop outermost, every lane would
   // wait at each l for the slowest lane's sweeps, about half of the warp's issued work).
+  // The deflation test |e_m| <= eps (|d_m| + |d_m+1|) is taken in its slightly stricter form
+  // |e_m| <= 2^-52 max(|d_m|, |d_m+1|) on the bit patterns (non-negative doubles order like
+  // their bits, and adding 52 to the exponent field multiplies by 2^52), so that the scan,
+  // about a sixth of the kernel's floating-point work, issues no FP64 instruction.
   int l = 0, iter = 0;
   while (l < W) {
     int m = l;
     for (; m < W - 1; ++m) {
-      double dd = fabs(D[m * 32]) + fabs(D[(m + 1) * 32]);
-      if (fabs(E[m * 32]) <= eps * dd) break;
+      const long long e = __double_as_longlong(E[m * 32]) & 0x7FFFFFFFFFFFFFFFll;
+      const long long a = __double_as_longlong(D[m * 32]) & 0x7FFFFFFFFFFFFFFFll;
+      const long long c = __double_as_longlong(D[(m + 1) * 32]) & 0x7FFFFFFFFFFFFFFFll;
+      if (e == 0 || e + (52ll << 52) <= (a > c ? a : c)) break;
     }
     if (m == l) {
       ++l;
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(32) ql_kernel(int W, int n, EighBufs b, DevSta
       // r = |(f, g)| and (s, c) = (f, g) / r from one reciprocal square root (the entries of
       // T are far from the FP64 overflow/underflow range, so no scaling is needed)
       const double r2 = fma(f, f, g * g);
-      if (r2 == 0.0) {   // split: the chase stops here
+      if ((__double_as_longlong(r2) << 1) == 0) {   // r2 = +-0: the chase stops here (split)
         E[(i + 1) * 32] = 0.0;
         D[(i + 1) * 32] -= p;
         E[m * 32] = 0.0;
