@@ -469,16 +469,14 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
     for (int rr = q; rr < m0; rr += 8) {
       const float2 u0 = act0 ? sU[(o + rr) * LD + c0] : make_float2(0.f, 0.f);
       const float2 u1 = act1 ? sU[(o + rr) * LD + c1] : make_float2(0.f, 0.f);
-      // conj(v) u as packed FP32x2 FMAs: (re, im) += (v.y, -v.y) (u.y, u.x), then
-      // += (v.x, v.x) (u.x, u.y) -- the roundings of the scalar form, in its order
-      const float2 u0s = make_float2(u0.y, u0.x), u1s = make_float2(u1.y, u1.x);
 #pragma unroll
       for (int a = 0; a < ASM_NB; ++a) {
         if (a < nj && rr >= a) {
           const float2 v = stage[roff(j0 + a) + rr - a];
-          const float2 vi = make_float2(v.y, -v.y), vr = make_float2(v.x, v.x);
-          s0[a] = __ffma2_rn(vr, u0, __ffma2_rn(vi, u0s, s0[a]));
-          s1[a] = __ffma2_rn(vr, u1, __ffma2_rn(vi, u1s, s1[a]));
+          s0[a].x = fmaf(v.x, u0.x, fmaf(v.y, u0.y, s0[a].x));   // conj(v) u
+          s0[a].y = fmaf(v.x, u0.y, fmaf(-v.y, u0.x, s0[a].y));
+          s1[a].x = fmaf(v.x, u1.x, fmaf(v.y, u1.y, s1[a].x));
+          s1[a].y = fmaf(v.x, u1.y, fmaf(-v.y, u1.x, s1[a].y));
         }
       }
     }
@@ -511,11 +509,11 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
 #pragma unroll
       for (int a = 0; a < ASM_NB; ++a) {
         if (a < nj && rr >= a) {
-          // u -= v t, packed: += (v.y, -v.y) (t.y, t.x), then += (-v.x, -v.x) (t.x, t.y)
           const float2 v = stage[roff(j0 + a) + rr - a];
-          const float2 vi = make_float2(v.y, -v.y), vr = make_float2(-v.x, -v.x);
-          u0 = __ffma2_rn(vr, t0[a], __ffma2_rn(vi, make_float2(t0[a].y, t0[a].x), u0));
-          u1 = __ffma2_rn(vr, t1[a], __ffma2_rn(vi, make_float2(t1[a].y, t1[a].x), u1));
+          u0.x = fmaf(-v.x, t0[a].x, fmaf(v.y, t0[a].y, u0.x));   // u -= v t
+          u0.y = fmaf(-v.x, t0[a].y, fmaf(-v.y, t0[a].x, u0.y));
+          u1.x = fmaf(-v.x, t1[a].x, fmaf(v.y, t1[a].y, u1.x));
+          u1.y = fmaf(-v.x, t1[a].y, fmaf(-v.y, t1[a].x, u1.y));
         }
       }
       if (act0) sU[(o + rr) * LD + c0] = u0;
