@@ -321,24 +321,14 @@ __device__ __forceinline__ void cgemm_tile_f32(const float2* __restrict__ A,
       int c = tx + 16 * j;
       bb[j] = c < W ? B[q * LD + c] : make_float2(0.f, 0.f);
     }
-    // acc += a b as two packed FP32x2 FMAs (one instruction, two lanes of the FMA pipe each):
-    // (re, im) += (a.x, a.x) (b.x, b.y), then += (-a.y, a.y) (b.y, b.x) -- the same two
-    // roundings per component, in the same order, as four scalar FMAs, with half the issue
-    // slots (the kernel is issue-bound, not FMA-pipe-bound)
-    float2 ar[TM], ai[TM], bs[TM];
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      ar[i] = make_float2(a[i].x, a[i].x);
-      ai[i] = make_float2(-a[i].y, a[i].y);
-    }
-#pragma unroll
-    for (int j = 0; j < TM; ++j) bs[j] = make_float2(bb[j].y, bb[j].x);
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TM; ++j) {
-        acc[i][j] = __ffma2_rn(ar[i], bb[j], acc[i][j]);
-        acc[i][j] = __ffma2_rn(ai[i], bs[j], acc[i][j]);
+        acc[i][j].x = fmaf(a[i].x, bb[j].x, acc[i][j].x);
+        acc[i][j].x = fmaf(-a[i].y, bb[j].y, acc[i][j].x);
+        acc[i][j].y = fmaf(a[i].x, bb[j].y, acc[i][j].y);
+        acc[i][j].y = fmaf(a[i].y, bb[j].x, acc[i][j].y);
       }
   }
 }
