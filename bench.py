@@ -140,6 +140,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="k-points per internal batch (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--rotation", default=None, choices=["simt", "exact", "tf32"],
+                    help="step (3) kernel of the reduced modes (default: the library's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the compact batched / grad / sweep results of the default line")
     ap.add_argument("--workload", default="w64", choices=["w64", "batched", "grad", "sweep", "pad", "separable"])
@@ -509,7 +511,7 @@ def main():
         d["_fixup_k"] = int(prof.fixup_k)
         return ms, d, clk, torch.cat(outs).cpu().numpy()
 
-    res = {p: timed(p) for p in precisions}
+    res = {p: timed(p, rotation=args.rotation) for p in precisions}
     # the mixed form with step (3) on the tensor cores (labelled variants, same slabs)
     rot_res = {}
     if args.precision == "both" and not args.no_extras:
