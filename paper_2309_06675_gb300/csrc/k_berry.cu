@@ -1403,13 +1403,15 @@ static cudaError_t launch_berry_tf32_t(const double* E, const double* Z, const E
   const size_t sm = berry_tf32_smem(n_eta);
   cudaError_t e = cudaFuncSetAttribute(berry_tf32_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 152, per_sm = 1;
+  // the whole unified L1 / shared-memory array as shared memory, so that two CTAs fit
+  cudaFuncSetAttribute(berry_tf32_kernel<TIn>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, berry_tf32_kernel<TIn>, TF_NT, sm) != cudaSuccess)
-    per_sm = 1;
   cudaGetLastError();
-  // TMEM: TF_TMEM_COLS per CTA out of 512 columns
-  per_sm = std::max(1, std::min(per_sm, 512 / TF_TMEM_COLS));
+  // two CTAs per SM (128 registers x 256 threads each, 2 x 256 of the 512 TMEM columns) while
+  // the shared memory allows (up to five broadenings); the CTAs are independent, so a grid
+  // larger than what is resident only queues
+  const int per_sm = sm <= (size_t)100 * 1024 ? 2 : 1;
   const int grid = (int)std::min<int64_t>(n, (int64_t)std::max(1, sms) * per_sm);
   berry_tf32_kernel<TIn><<<grid, TF_NT, sm, s>>>(E, Z, eb, Xp, Yp, ld, W, n, etas, n_eta, Om,
                                                  eta_stride, st);
