@@ -987,7 +987,7 @@ constexpr int TF_B_TILE = 64 * 128;    // bytes: 64 rows x 32 TF32
 constexpr int TF_OPS_BYTES = 2 * TF_A_TILE + 2 * TF_B_TILE;   // A hi, A lo, B hi, B lo: 48 KB
 constexpr int TF_LDU = 68;                                    // = mixed_ld(64, 1)
 constexpr int TF_U_BYTES = TF_WP * TF_LDU * 8;                // 34,816
-constexpr int TF_TMEM_COLS = 256;                             // T at 0, V^x at 64, V^y at 128
+constexpr int TF_TMEM_COLS = 256;   // partial T at 0, partial V at 64, parked V^x at 128
 constexpr uint32_t TF_WAIT_LIMIT = 1u << 20;
 // instruction descriptor: D F32, A and B TF32 (K-major), N = 64, M = 128
 constexpr uint32_t TF_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
@@ -1123,9 +1123,17 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
       for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
       s_emax = mx;
     }
+    float vacc[32];   // this thread's 32 entries of row mrow of [V_r; V_i]
     for (int a = 0; a < 2 && ok; ++a) {
       const TIn* P = (a == 0 ? Xp : Yp) + k * ld;
-      // ---- product 1: [T_r; T_i] = A1 B1^T into TMEM columns 0..63
+      // ---- product 1: [T_r; T_i] = A1 B1^T.  Each K-quarter accumulates into TMEM columns
+      // 0..63 from zero and is added here in FP32 with round-to-nearest: the tensor core's
+      // FP32 accumulation truncates, and one accumulator per quarter keeps that to 12 steps
+      // (all 48 in one accumulator left the result ten times less accurate than the SIMT
+      // rotation's).  tv: this thread's 32 entries of row mrow of [T_r; T_i].
+      float tv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tv[j] = 0.f;
       for (int h = 0; h < 4 && ok; ++h) {
         __syncthreads();   // the stage area / previous quarter's operands are free
         // A1 rows i and 64 + i, K columns 32 h + 4 c4 .. + 3 (X column c = that - 64 h2)
@@ -1165,22 +1173,21 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
           }
           put4_tf32(b_hi, b_lo, nn, c4, u);
         }
-        if (!mma_quarter(0, h == 0)) ok = false;
+        if (!mma_quarter(0, true)) { ok = false; break; }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t r[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)(chalf * 32 + 16 * hh), r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            tv[16 * hh + j] += __uint_as_float(r[j]);
+        }
+        tc::tc_fence_before();
       }
       if (!ok) break;
-      // ---- this thread's 32 entries of row mrow of [T_r; T_i]
-      float tv[32];
-      {
-        uint32_t r[16];
-        tc::tmem_ld16(lane_addr + (uint32_t)(chalf * 32), r);
+      // ---- product 2: [V_r; V_i] = A2 B2^T, per K-quarter in TMEM columns 64..127, summed here
 #pragma unroll
-        for (int j = 0; j < 16; ++j) tv[j] = __uint_as_float(r[j]);
-        tc::tmem_ld16(lane_addr + (uint32_t)(chalf * 32 + 16), r);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) tv[16 + j] = __uint_as_float(r[j]);
-      }
-      tc::tc_fence_before();
-      // ---- product 2: [V_r; V_i] = A2 B2^T into TMEM columns 64 + 64 a
+      for (int j = 0; j < 32; ++j) vacc[j] = 0.f;
       for (int h = 0; h < 4 && ok; ++h) {
         __syncthreads();
         const bool second = h >= 2;
@@ -1208,27 +1215,50 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
             *reinterpret_cast<uint32_t*>(b_lo + off) = lo;
           }
         }
-        if (!mma_quarter(64 + 64 * a, h == 0)) ok = false;
+        if (!mma_quarter(64, true)) { ok = false; break; }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t r[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)(64 + chalf * 32 + 16 * hh), r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            vacc[16 * hh + j] += __uint_as_float(r[j]);
+        }
+        tc::tc_fence_before();
+      }
+      if (!ok) break;
+      if (a == 0) {
+        // park V^x in TMEM columns 128..191 while V^y is formed
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t r[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(vacc[16 * hh + j]);
+          tc::tmem_st16(lane_addr + (uint32_t)(128 + chalf * 32 + 16 * hh), r);
+        }
+        tc::tc_fence_before();
       }
     }
     if (!ok) break;
-    // ---- V^x, V^y from TMEM into shared memory (float2 [64][TF_LDU]; U and the operands are
-    // no longer needed)
+    // ---- V^x (TMEM) and V^y (registers) into shared memory (float2 [64][TF_LDU]; U and the
+    // operands are no longer needed)
     __syncthreads();
     float2* sVx = reinterpret_cast<float2*>(tf_smem);
     float2* sVy = sVx + TF_WP * TF_LDU;
     {
       const int rr = mrow & 63;
       const int comp = mrow >= 64 ? 1 : 0;
-      for (int a = 0; a < 2; ++a) {
-        float* dst = reinterpret_cast<float*>(a == 0 ? sVx : sVy);
+      float* dx = reinterpret_cast<float*>(sVx);
+      float* dy = reinterpret_cast<float*>(sVy);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          uint32_t r[16];
-          tc::tmem_ld16(lane_addr + (uint32_t)(64 + 64 * a + chalf * 32 + 16 * hh), r);
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t r[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)(128 + chalf * 32 + 16 * hh), r);
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            dst[2 * (rr * TF_LDU + chalf * 32 + 16 * hh + j) + comp] = __uint_as_float(r[j]);
+        for (int j = 0; j < 16; ++j) {
+          const int o = 2 * (rr * TF_LDU + chalf * 32 + 16 * hh + j) + comp;
+          dx[o] = __uint_as_float(r[j]);
+          dy[o] = vacc[16 * hh + j];
         }
       }
     }
