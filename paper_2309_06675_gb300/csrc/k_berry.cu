@@ -1033,13 +1033,16 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t
       : "memory");
 }
 
-// the 12 MMAs of one K-quarter: (hi, hi), (hi, lo), (lo, hi) x 4 K8 steps
+// the 12 MMAs of one K-quarter: (hi, lo), (lo, hi), then (hi, hi), x 4 K8 steps.  The small
+// cross terms go first: each MMA's addition into the FP32 accumulator truncates at the
+// accumulator's magnitude, so they are added while it is still ~2^-11 of its final size and
+// only the four (hi, hi) steps truncate at full size.
 __device__ __forceinline__ void tf_issue(uint32_t tmem_d, uint32_t ops, bool first) {
   const uint32_t a_hi = ops, a_lo = ops + TF_A_TILE;
   const uint32_t b_hi = ops + 2 * TF_A_TILE, b_lo = b_hi + TF_B_TILE;
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    const uint32_t a = p == 2 ? a_lo : a_hi, b = p == 1 ? b_lo : b_hi;
+    const uint32_t a = p == 1 ? a_lo : a_hi, b = p == 0 ? b_lo : b_hi;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)
       umma_tf32(tmem_d, tc::umma_desc_sw128(a + kk * 32), tc::umma_desc_sw128(b + kk * 32),
