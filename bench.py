@@ -114,7 +114,8 @@ def roofline_of(dom, head, W, N_R, k_per_launch, ms_per_launch):
     if head != "fp64" and dom == "berry":
         fl = (24.0 + 8.0) * W ** 3 * k_per_launch
         return {"bound": "alu", "achieved": fl / t / 1e12, "peak": 2 * FP32_PEAK_TOPS,
-                "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"}
+                "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz "
+                                                "(derived); the rotations' 24 W^3 and the U assembly's 8 W^3"}
     if head != "fp64" and dom == "fourier":
         fl = issued_tc_flops_per_k(W, head) * k_per_launch   # issued BF16 slice products
         pk = measured_peaks()
@@ -443,8 +444,8 @@ def run_extra(args, local):
     print(json.dumps(line))
 
 
-DTYPE = {"mixed": "bf16-slices(Ozaki) Fourier + f64 eigh + f32 rotation + f64 denominators/k-sum",
-         "mixed_df": "bf16-slices(Ozaki) Fourier + double-float(f32 pairs) eigh + f32 rotation",
+DTYPE = {"mixed": "bf16-slices(Ozaki) Fourier + f64 eigh + 3xtf32 rotation + f64 denominators/k-sum",
+         "mixed_df": "bf16-slices(Ozaki) Fourier + double-float(f32 pairs) eigh + 3xtf32 rotation",
          "fp64": "f64"}
 
 
@@ -512,10 +513,10 @@ def main():
         return ms, d, clk, torch.cat(outs).cpu().numpy()
 
     res = {p: timed(p, rotation=args.rotation) for p in precisions}
-    # the mixed form with step (3) on the tensor cores (labelled variants, same slabs)
+    # the mixed form with the other step (3) kernels (labelled variants, same slabs)
     rot_res = {}
-    if args.precision == "both" and not args.no_extras:
-        rot_res = {r: timed("mixed", rotation=r) for r in ("tf32", "exact")}
+    if args.precision == "both" and not args.no_extras and args.rotation is None:
+        rot_res = {r: timed("mixed", rotation=r) for r in ("simt", "exact")}
 
     # ---- end to end through the host-buffer entry point (pinned host memory), headline path
     head = precisions[0]
@@ -615,14 +616,14 @@ def main():
             }
         if rot_res:
             line["mixed_rotation_kernels"] = {
-                "what": "the mixed form with step (3) on the tensor cores instead of the FP32 "
-                        "FMA pipe: 3xTF32 (tcgen05 kind::tf32, split operands, FP32 "
-                        "accumulation) and exact fixed-point BF16 slices",
+                "what": "the mixed form with step (3) in FP32 on the FMA pipe (simt) or on the "
+                        "tensor cores with exact fixed-point BF16 slices (exact), instead of the "
+                        "default 3xTF32 tensor-core kernel (tcgen05 kind::tf32)",
                 **{r: {"value": world * k_total / (v[0] / 1e3),
                        "berry_ms_per_step": v[1]["berry"]["ms"] / args.steps,
                        "rel_err_max_over_steps": float(np.max(np.abs(v[3] - of) / den))}
                    for r, v in rot_res.items()},
-                "simt_berry_ms_per_step": res["mixed"][1]["berry"]["ms"] / args.steps}
+                "tf32_berry_ms_per_step": res["mixed"][1]["berry"]["ms"] / args.steps}
         if "mixed_df" in res:
             line["mixed_df_variant"] = {
                 "what": "the mixed form with its eigensolver in double-float (FP32 pairs, ~2^-46 "

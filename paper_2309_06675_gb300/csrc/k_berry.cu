@@ -967,19 +967,22 @@ __global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
 // ------------------------------------------------------------------ rotations in 3xTF32
 // Step (3) on tcgen05 with kind::tf32 operands and FP32 accumulation in TMEM (the split-TF32
 // scheme): every FP32 operand x is cut into hi = tf32(x) and lo = tf32(x - hi) (11 + 11
-// significant bits, the cut exact), and a product is formed as hi hi + hi lo + lo hi in one
-// FP32 accumulator, ~2^-22 relative per product: FP32-grade, like the SIMT rotation it
-// replaces.  K = 128 is short, so FP32 accumulation adds only ~sqrt(48) 2^-24 per entry.
+// significant bits, the cut exact), and a product is formed as hi lo + lo hi + hi hi; the
+// dropped lo lo and the cut's residual are ~2^-24 relative: FP32-grade.  The tensor core's
+// additions into its FP32 accumulator truncate, so each K-quarter (12 MMAs, the small cross
+// terms first) starts a fresh accumulator and the quarters are summed in registers with
+// round-to-nearest: on the W = 64 workload this rotation is then slightly more accurate than
+// the SIMT FP32 one (all 48 MMAs in one accumulator were ten times less accurate).
 // The complex products are block-real GEMMs with M = 128, N = 64, K = 128 (W padded to 64):
 //   T = X U:    [T_r; T_i] = [[X_r, -X_i], [X_i, X_r]] [U_r; U_i]
 //   V = U^H T:  [V_r; V_i] = [[U_r^T, U_i^T], [-U_i^T, U_r^T]] [T_r; T_i]
-// T stays in TMEM and in registers (each thread holds 32 entries of one row of [T_r; T_i],
-// which is one K column of the second product's B operand); V^x and V^y accumulate in their
-// own TMEM columns.  The operands are staged one K-quarter (32 TF32 = one 128-byte swizzle
-// row) at a time, 48 KB for A and B with their hi / lo parts, so that with U (FP32, assembled
-// from the FP64 factors in shared memory) a CTA needs ~85 KB and two CTAs share an SM: one
-// stages operands while the other's MMAs run.  Persistent over the k-points; every wait on
-// the tensor core is bounded (ST_TIMEOUT).
+// T is held in registers (each thread 32 entries of one row of [T_r; T_i], which is one K
+// column of the second product's B operand); V^x waits in TMEM while V^y is formed.  The
+// operands are staged one K-quarter (32 TF32 = one 128-byte swizzle row) at a time, 48 KB for
+// A and B with their hi / lo parts, so that with U (FP32, assembled from the FP64 factors in
+// shared memory) a CTA needs ~85 KB and two CTAs share an SM: one stages operands while the
+// other's MMAs run.  Persistent over the k-points; every wait on the tensor core is bounded
+// (ST_TIMEOUT).
 constexpr int TF_NT = 256;
 constexpr int TF_WP = 64;
 constexpr int TF_A_TILE = 128 * 128;   // bytes: 128 rows x 32 TF32

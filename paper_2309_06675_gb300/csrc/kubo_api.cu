@@ -34,7 +34,7 @@ kubo_options defaults() {
 }
 
 // FP32-grade rotation kernels for W <= 64 (kubo_options.rotation_tc)
-enum { ROT_SIMT = 0, ROT_EXACT_SLICES = 1, ROT_TF32 = 2 };
+enum { ROT_TF32 = 0, ROT_EXACT_SLICES = 1, ROT_SIMT = 2 };
 
 // ------------------------------------------------------------------ R set
 struct RInfo {
