@@ -152,16 +152,17 @@ typedef struct kubo_options {
   int rotation_tc;          /* kernel of the FP32-grade step (3) in KUBO_MIXED /
                                KUBO_MIXED_ROTATION / KUBO_MIXED_DF for W <= 64 (larger W: batched
                                FP32 GEMMs), one accuracy class:
-                               0 (default) = tensor cores in 3xTF32: tcgen05 kind::tf32 with
-                                 every FP32 operand split into two TF32 parts (hi lo + lo hi +
-                                 hi hi per product, a fresh FP32 accumulator per K-quarter of
-                                 32, the quarters summed with round-to-nearest);
+                               3 = tensor cores in 3xTF32: tcgen05 kind::tf32 with every FP32
+                                 operand split into two TF32 parts (hi lo + lo hi + hi hi per
+                                 product, a fresh FP32 accumulator per K-quarter of 32, the
+                                 quarters summed with round-to-nearest), k-points padded to 64;
                                1 = tensor cores with exact fixed-point BF16-slice products;
-                               2 = FP32 on the FMA pipe (SIMT).
-                               At W = 64 the default is at least as fast and as accurate as
-                               the other two.  Other values: KUBO_ERR_INVALID_ARG.
-                               layout_unpadded = 1 implies 2 (the ablation concerns the SIMT
-                               kernel's shared-memory layout). */
+                               2 = FP32 on the FMA pipe (SIMT);
+                               0 (default) = automatic: 3 for 56 < W <= 64, where it is at least
+                                 as fast as 2 (and at W = 64 the more accurate), else 2.
+                               Other values: KUBO_ERR_INVALID_ARG.  layout_unpadded = 1 implies
+                               2 (the ablation concerns the SIMT kernel's shared-memory
+                               layout). */
   int ql_max_sweeps;        /* cap on the implicit-QL sweeps spent on one eigenvalue; 0 = the
                                default (60, far above the 2-3 that Wilkinson shifts need).  A
                                k-point that reaches the cap makes the call return

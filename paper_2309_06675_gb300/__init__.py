@@ -212,7 +212,7 @@ def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk
     return o
 
 
-_ROTATION = {"tf32": 0, "exact": 1, "simt": 2}
+_ROTATION = {"auto": 0, "exact": 1, "simt": 2, "tf32": 3}
 
 
 def _rotation(rotation, rotation_tc=False) -> int:
@@ -255,9 +255,9 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
         unpadded=False, separable=False, rotation_tc=False, ql_max_sweeps=0, rotation=None):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
-    rotation: the FP32-grade step (3) kernel of the reduced modes, "tf32" (tensor cores,
-    3xTF32; the default), "exact" (tensor cores, exact BF16 slices; rotation_tc=True) or
-    "simt" (FP32 FMA pipe).
+    rotation: the FP32-grade step (3) kernel of the reduced modes, "auto" (the default:
+    "tf32" above W = 56, else "simt"), "tf32" (tensor cores, 3xTF32), "exact" (tensor cores,
+    exact BF16 slices; rotation_tc=True) or "simt" (FP32 FMA pipe).
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].
     """

@@ -159,8 +159,8 @@ def test_mixed_haldane_chern(kubo, torch):
 
 
 def test_rotation_kernels_vs_fp64(kubo, torch, m64):
-    """Step (3) on the tensor cores in 3xTF32 (the default), with exact fixed-point BF16-slice
-    products, and in FP32 on the FMA pipe, against the FP64 path on a slab of the W = 64
+    """Step (3) on the tensor cores in 3xTF32 (the default at W = 64), with exact fixed-point
+    BF16-slice products, and in FP32 on the FMA pipe, against the FP64 path on a slab of the W = 64
     workload: all three within 1e-5 of FP64 (one accuracy class), through the FP64 Fourier
     sum (MIXED_ROTATION) and the tensor-core one (MIXED)."""
     kmesh = (128, 128, 128)
@@ -208,7 +208,7 @@ def test_tf32_rotation_many_broadenings_and_ragged_persistent_grid(kubo, torch):
     EF = np.array([-0.6, 0.0, 0.4])
     for chunk in (1, 97, 315):
         S = kubo.ahc(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, EF), etas=etas,
-                     precision="mixed", chunk_k=chunk).cpu().numpy()
+                     precision="mixed", chunk_k=chunk, rotation="tf32").cpu().numpy()
         ref = O.ahc(m.H_R, m.R, kmesh, EF, etas=etas)
         for e in range(len(etas)):
             assert rel_err(S[e], ref[e]) < REL_MIXED, (chunk, e, rel_err(S[e], ref[e]))
