@@ -330,7 +330,18 @@ typedef struct kubo_batch_schedule {
   int chunk_k;              /* upper bound on the k-points per internal batch of a model */
   int graph;                /* in: 0 = capture the batch in a CUDA graph (default), -1 = no */
   double probe_ms;          /* out: the tuner's time for the chosen schedule (0 if not tuned) */
-  int tuned_candidates;     /* out: schedules the tuner timed (0 if cached or not tuned) */
+  int tuned_candidates;     /* out: configurations the tuner timed (0 if cached or not tuned) */
+  /* Kernel parameters, applied to every model (in: 0 = the default, or tuned when tune = 1;
+   * out: the values used).  The tuner first picks streams and chunk_k on the default kernel
+   * parameters, then tries each parameter's alternatives in turn on that schedule. */
+  int fourier_group_m;      /* tensor-core Fourier sum: 128-k tiles rasterised together per
+                               column tile (L2 reuse of the basis tiles); default 8, tuned over
+                               {4, 8, 16}; 1..64 */
+  int symv_parts;           /* Householder reduction: column partitions per row of its symv;
+                               default 4, tuned over {2, 4, 8}; 1..8 */
+  int rotation;             /* step (3) kernel as kubo_options.rotation_tc (1..3 fix it);
+                               0 = opt->rotation_tc, tuned over {automatic, 2, 3} when that is
+                               0 and the precision has an FP32-grade step (3) */
 } kubo_batch_schedule;
 
 /*

@@ -106,6 +106,7 @@ class BatchSchedule(ctypes.Structure):
     _fields_ = [
         ("tune", ctypes.c_int), ("streams", ctypes.c_int), ("chunk_k", ctypes.c_int),
         ("graph", ctypes.c_int), ("probe_ms", ctypes.c_double), ("tuned_candidates", ctypes.c_int),
+        ("fourier_group_m", ctypes.c_int), ("symv_parts", ctypes.c_int), ("rotation", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -315,7 +316,7 @@ def ahc_grad(H_R, R, kmesh, E_F, dL_dout, eta=1e-3, etas=None, kT=0.0, k_range=N
 
 
 def ahc_batched(problems, etas=None, kT=0.0, precision=FP64, stream=None, tune=False, streams=0,
-                chunk_k=0, graph=True):
+                chunk_k=0, graph=True, fourier_group_m=0, symv_parts=0, rotation=0):
     """S(E_F) of many models in one call (kubo_ahc_batched).
 
     problems: sequence of (H_R complex128 CUDA [N_R, W, W], R host [N_R, 3], kmesh,
@@ -351,6 +352,9 @@ def ahc_batched(problems, etas=None, kT=0.0, precision=FP64, stream=None, tune=F
     sc.streams = int(streams)
     sc.chunk_k = int(chunk_k)
     sc.graph = 0 if graph else -1
+    sc.fourier_group_m = int(fourier_group_m)
+    sc.symv_parts = int(symv_parts)
+    sc.rotation = _ROTATION[rotation] if isinstance(rotation, str) else int(rotation)
     code = lib().kubo_ahc_batched(arr, n, ctypes.byref(o), ctypes.byref(sc))
     status = [_STATUS.get(arr[i].status, str(arr[i].status)) for i in range(n)]
     _check(code, f"kubo_ahc_batched (per-model status: {status})")

@@ -125,14 +125,14 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
       __syncthreads();
       // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r).  The m x m
       // product is spread over the block: thread t takes row r = t mod m and the columns
-      // c = part, part + P, ... (part = t / m, P = min(NT / m, 4) parts per row), so that the
-      // warps issue full; the P partial sums of a row are added in part order by the m row
-      // threads.  P is capped at 4: for a small trailing block more parts would shorten the
-      // product but lengthen that sum, whose warps run with m of their 32 lanes (the other
-      // CTAs of the SM keep the FP64 pipe busy meanwhile).  The conjugate of the mirrored
+      // c = part, part + P, ... (part = t / m, P = min(NT / m, cap) parts per row, cap = 4 by
+      // default), so that the warps issue full; the P partial sums of a row are added in part
+      // order by the m row threads.  P is capped: for a small trailing block more parts would
+      // shorten the product but lengthen that sum, whose warps run with m of their 32 lanes
+      // (the other CTAs of the SM keep the FP64 pipe busy meanwhile).  The conjugate of the mirrored
       // element flips a sign bit on the integer side (no FP64 instruction).
       {
-        const int P = min(NT / m, 4);
+        const int P = max(1, min(NT / m, b.symv_parts));
         const int r = t % m, part = t / m;
         if (part < P) {
           double ax = 0.0, ay = 0.0;

@@ -57,7 +57,7 @@ constexpr int NPAIR = 10;
 constexpr int NACC = 2;           // level-accumulator sets in flight (double buffer)
 constexpr int DRAIN = 4;          // K blocks summed in TMEM before the epilogue drains a set:
                                   // 4 blocks x 4 pairs x 64 x 2^14 = 2^24, still exact in FP32
-constexpr int GROUP_M = 8;        // M tiles rasterised together so B tiles are reused from L2
+constexpr int GROUP_M = 8;        // default of the M tiles rasterised together (B tiles reused from L2)
 constexpr int TILE_A_BYTES = BM * BK * 2;            // 16 KB per slice
 constexpr int TILE_B_BYTES = BN * BK * 2;            // 8 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 96 KB
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, const int* __restrict__ col_exp,
                       int Mpad, int Npad, int nkb, int n_rows, double* __restrict__ out, int ldc,
-                      DevStatus* st, int nt0, int ntc) {
+                      DevStatus* st, int nt0, int ntc, int group_m) {
   constexpr int NLEV = NS;
   constexpr int NPR = NS * (NS + 1) / 2;   // pairs with i + j < NS (listed first in c_p*)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -216,13 +216,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_mt = Mpad / BM, n_tiles = n_mt * ntc;
   const int groups_per_tile = (nkb + DRAIN - 1) / DRAIN;
-  // grouped rasterisation: GROUP_M consecutive M tiles per column tile, so one B tile serves
+  // grouped rasterisation: group_m consecutive M tiles per column tile, so one B tile serves
   // several tiles in a row and the group's A tiles stay resident in L2 across column tiles
   auto tile_origin = [&](int id, int& m0, int& n0) {
-    const int per_group = GROUP_M * ntc;
+    const int per_group = group_m * ntc;
     const int grp = id / per_group;
-    const int gm0 = grp * GROUP_M;
-    const int gsz = min(GROUP_M, n_mt - gm0);
+    const int gm0 = grp * group_m;
+    const int gsz = min(group_m, n_mt - gm0);
     const int in = id - grp * per_group;
     n0 = (nt0 + in / gsz) * BN;
     m0 = (gm0 + in % gsz) * BM;
@@ -464,9 +464,10 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s, int red_n0) {
+                              cudaStream_t s, int red_n0, int group_m) {
   if (n_rows <= 0) return cudaSuccess;
   if (Mpad % BM || Npad % BN || Kp % BK || ldc % 2) return cudaErrorInvalidValue;
+  if (group_m < 1 || group_m > 64) return cudaErrorInvalidValue;
   CUtensorMap mA, mB;
   if (!encode_2d(&mA, A, (uint64_t)Kp, (uint64_t)NSLICE * Mpad, BK, BM)) return cudaErrorInvalidValue;
   if (!encode_2d(&mB, Bt, (uint64_t)Kp, (uint64_t)NSLICE * Npad, BK, BN)) return cudaErrorInvalidValue;
@@ -483,7 +484,7 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(tc * (Mpad / BM), std::max(nsm, 1));   // persistent: one per SM
     kern<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out, ldc, st,
-                                      t0, tc);
+                                      t0, tc, group_m);
     return cudaGetLastError();
   };
   cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt);

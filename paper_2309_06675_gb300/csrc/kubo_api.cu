@@ -132,6 +132,8 @@ struct Plan {
   bool scale_ok = false;            // the call may rescale H(R) by a power of two (range_exponent)
   int escale = 0;                   // that power: the basis holds 2^escale H(R)
   int ql_cap = 0;                   // QL sweeps per eigenvalue (0 = the kernels' default)
+  int group_m = 8;                  // tensor-core Fourier sum: M tiles rasterised together
+  int symv_parts = 4;               // Householder reduction: column partitions of its symv
   bool model = false;   // needs the prepared Fourier basis
   bool eigh = false;    // needs eigensolver buffers
   bool berry = false;   // needs velocity / curvature buffers
@@ -515,6 +517,7 @@ EighBufs make_eigh_bufs(const Call& c) {
   b.tau = c.at<double>(c.p.o_tau);
   b.lam = c.at<double>(c.p.o_lam);
   if (c.p.ql_cap > 0) b.ql_cap = c.p.ql_cap;
+  b.symv_parts = c.p.symv_parts;
   return b;
 }
 
@@ -575,7 +578,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     const int red_n0 = f32_rotation(p.precision) ? p.W * p.W : p.Npad;
     StageTimer tm(c, KUBO_STAGE_FOURIER, red_n0 < p.Npad ? 3 : 2);
     KCHECK(launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s));
-    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0));
+    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0, p.group_m));
   }
   {
     // MIXED_DF: the reduction and the QL iteration in double-float on the FP32 pipe (both are
@@ -981,8 +984,16 @@ double job_cost(const Plan& p) {
   return Nk * (fourier + eig + rot + 1e4);   // + per-k fixed cost (launch/latency share)
 }
 
+// Kernel parameters of a batch, chosen by the autotuner (applied to every model): the tensor-
+// core Fourier sum's rasterisation group, the reduction's symv partition cap and the option
+// value of the FP32-grade rotation kernel (kubo_options.rotation_tc).
+struct KernelParams {
+  int group_m = 8, symv_parts = 4, rotation = 0;
+};
+
 struct BatchRun {
   std::vector<Job> jobs;
+  KernelParams kp;
   int streams = 1;
   std::vector<size_t> stream_off, stream_bytes;   // stream buffers inside the workspace
   size_t tables_bytes = 0, total = 0;
@@ -1019,6 +1030,9 @@ void layout_batch(BatchRun& br, int S, int chunk_cap, int n_eta) {
   br.stream_bytes.assign(S, 0);
   for (auto& j : br.jobs) {
     Plan& p = j.p;
+    p.group_m = br.kp.group_m;
+    p.symv_parts = br.kp.symv_parts;
+    p.rot = rotation_kernel(br.kp.rotation, p.W, false);
     const int64_t nk = p.mesh.Nk;
     int64_t c = (int64_t)(stream_budget / bytes_per_k(p.W, n_eta));
     c = std::max<int64_t>(1, std::min<int64_t>(c, chunk_cap));
@@ -1171,10 +1185,14 @@ kubo_status run_batch_once(const BatchRun& br, const std::vector<kubo_problem>& 
 
 // process-wide cache of tuned schedules, keyed by the batch signature
 std::mutex g_tune_mutex;
-std::map<std::vector<int64_t>, std::array<int, 2>> g_tune_cache;
+struct TunedSchedule {
+  int streams, chunk;
+  KernelParams kp;
+};
+std::map<std::vector<int64_t>, TunedSchedule> g_tune_cache;
 
 std::vector<int64_t> batch_signature(const std::vector<Job>& jobs, const kubo_options& o) {
-  std::vector<int64_t> sig{o.precision, o.kT > 0.0 ? 1 : 0, o.n_eta};
+  std::vector<int64_t> sig{o.precision, o.kT > 0.0 ? 1 : 0, o.n_eta, o.rotation_tc, o.layout_unpadded};
   std::vector<std::array<int64_t, 3>> m;
   for (const auto& j : jobs) m.push_back({j.p.W, j.p.N_R, j.p.mesh.Nk});
   std::sort(m.begin(), m.end());
@@ -1420,15 +1438,29 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
     const bool graph = sc.graph >= 0;
     sc.probe_ms = 0.0;
     sc.tuned_candidates = 0;
+    if (sc.fourier_group_m < 0 || sc.fourier_group_m > 64 || sc.symv_parts < 0 || sc.symv_parts > 8 ||
+        sc.rotation < 0 || sc.rotation > 3)
+      return KUBO_ERR_INVALID_ARG;
+    // kernel parameters: given, else the defaults (tuned below when tune = 1)
+    br.kp.group_m = sc.fourier_group_m > 0 ? sc.fourier_group_m : 8;
+    br.kp.symv_parts = sc.symv_parts > 0 ? sc.symv_parts : 4;
+    br.kp.rotation = o.layout_unpadded ? 2 : (sc.rotation > 0 ? sc.rotation : o.rotation_tc);
+    const bool tune_gm = sc.tune && sc.fourier_group_m == 0 && tc_fourier(o.precision);
+    const bool tune_sp = sc.tune && sc.symv_parts == 0;
+    const bool tune_rot = sc.tune && sc.rotation == 0 && !o.layout_unpadded && o.rotation_tc == 0 &&
+                          f32_rotation(o.precision);
     std::vector<int64_t> sig;
-    bool need_tune = sc.tune && (S == 0 || chunk == 0);
+    bool need_tune = sc.tune && (S == 0 || chunk == 0 || tune_gm || tune_sp || tune_rot);
     if (need_tune) {
       sig = batch_signature(br.jobs, o);
       std::lock_guard<std::mutex> lock(g_tune_mutex);
       auto it = g_tune_cache.find(sig);
       if (it != g_tune_cache.end()) {
-        if (S == 0) S = std::min(it->second[0], n_jobs);
-        if (chunk == 0) chunk = it->second[1];
+        if (S == 0) S = std::min(it->second.streams, n_jobs);
+        if (chunk == 0) chunk = it->second.chunk;
+        if (tune_gm) br.kp.group_m = it->second.kp.group_m;
+        if (tune_sp) br.kp.symv_parts = it->second.kp.symv_parts;
+        if (tune_rot) br.kp.rotation = it->second.kp.rotation;
         need_tune = false;
       }
     }
@@ -1553,9 +1585,45 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
         }
       S = bS;
       chunk = bC;
+      // then the kernel parameters, one at a time from the defaults (coordinate search), on
+      // the chosen schedule
+      layout_batch(br, std::min(S, (int)br.jobs.size()), chunk, n_eta);
+      auto try_params = [&](KernelParams kp) -> kubo_status {
+        const KernelParams keep = br.kp;
+        br.kp = kp;
+        layout_batch(br, std::min(S, (int)br.jobs.size()), chunk, n_eta);
+        float ms = 0.f;
+        kubo_status r = run_batch_once(br, PP, o, ws, origin, streams, graph, probe_out, probe_nk, &ms);
+        if (r != KUBO_OK) return r;
+        ++sc.tuned_candidates;
+        if (ms < best) best = ms;
+        else br.kp = keep;
+        return KUBO_OK;
+      };
+      if (tune_gm)
+        for (int v : {4, 16}) {
+          KernelParams kp = br.kp;
+          kp.group_m = v;
+          kubo_status r = try_params(kp);
+          if (r != KUBO_OK) return finish(r);
+        }
+      if (tune_sp)
+        for (int v : {2, 8}) {
+          KernelParams kp = br.kp;
+          kp.symv_parts = v;
+          kubo_status r = try_params(kp);
+          if (r != KUBO_OK) return finish(r);
+        }
+      if (tune_rot)
+        for (int v : {2, 3}) {   // FP32 SIMT everywhere, 3xTF32 everywhere (vs the automatic rule)
+          KernelParams kp = br.kp;
+          kp.rotation = v;
+          kubo_status r = try_params(kp);
+          if (r != KUBO_OK) return finish(r);
+        }
       sc.probe_ms = best;
       std::lock_guard<std::mutex> lock(g_tune_mutex);
-      g_tune_cache[sig] = {S, chunk};
+      g_tune_cache[sig] = TunedSchedule{S, chunk, br.kp};
     } else {
       S = cand_S[0];
       chunk = cand_C[0];
@@ -1575,6 +1643,9 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
     sc.streams = br.streams;
     sc.chunk_k = chunk;
     sc.graph = graph ? 1 : -1;
+    sc.fourier_group_m = br.kp.group_m;
+    sc.symv_parts = br.kp.symv_parts;
+    sc.rotation = br.kp.rotation;
     if (sched) *sched = sc;
     return finish(first);
 #undef BCHECK

@@ -112,6 +112,7 @@ struct EighBufs {
   double* tau;      // [n][W]
   double* lam;      // [n][W]  eigenvalues of T (unordered)
   int ql_cap = 60;  // implicit-QL sweeps allowed per eigenvalue before ST_NO_CONVERGENCE
+  int symv_parts = 4;  // Householder reduction: column partitions per row of its symv (1..8)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -214,7 +215,8 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 // red_n0: first output column whose tile may keep three slices (FP32-grade; Npad = none)
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s, int red_n0);
+                              cudaStream_t s, int red_n0,
+                              int group_m = 8);
 // the tensor-core kernel's bounded mbarrier wait on a barrier that never completes
 cudaError_t launch_bounded_wait_check(uint32_t limit, DevStatus* st, cudaStream_t s);
 // rows [n][ld] (H | dxH | dyH packed) -> three packed arrays [n][W*W]

@@ -106,10 +106,42 @@ def test_autotuner_runs_once_per_signature(kubo, torch, small_batch):
     assert s1["tuned_candidates"] >= 2 and s1["probe_ms"] > 0
     assert s2["tuned_candidates"] == 0
     assert (s1["streams"], s1["chunk_k"]) == (s2["streams"], s2["chunk_k"])
+    # the tuner also chose the reduction's symv partition cap (FP64: no tensor-core Fourier sum,
+    # no FP32 rotation to tune), and the cached schedule carries it
+    assert s1["symv_parts"] in (2, 4, 8) and s1["symv_parts"] == s2["symv_parts"]
+    assert s1["fourier_group_m"] == 8 and s1["rotation"] == 0
     for x, y, r in zip(a, b, ref):
         assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
         rr = r.cpu().numpy()
         assert np.max(np.abs(x.cpu().numpy() - rr)) <= 1e-12 * np.max(np.abs(rr))
+
+
+def test_autotuned_kernel_parameters_mixed(kubo, torch, small_batch):
+    """Mixed batch: the tuner picks the Fourier rasterisation group, the symv partition cap and
+    the rotation kernel as well; every choice stays within the mixed tolerance, and fixed
+    parameters are respected and reported."""
+    P = problems(torch, small_batch)
+    outs, sc, _ = kubo.ahc_batched(P, precision="mixed", tune=True)
+    assert sc["tuned_candidates"] >= 2 + 6
+    assert sc["fourier_group_m"] in (4, 8, 16)
+    assert sc["symv_parts"] in (2, 4, 8)
+    assert sc["rotation"] in (0, 2, 3)
+    for (m, mesh, ef), S in zip(small_batch, outs):
+        ref = O.ahc(m.H_R, m.R, mesh, ef)
+        assert np.max(np.abs(S.cpu().numpy() - ref)) <= 1e-5 * np.max(np.abs(ref))
+    fixed, sf, _ = kubo.ahc_batched(P, precision="mixed", streams=2, chunk_k=8192,
+                                   fourier_group_m=2, symv_parts=1, rotation="tf32")
+    assert (sf["fourier_group_m"], sf["symv_parts"], sf["rotation"]) == (2, 1, 3)
+    for (m, mesh, ef), S in zip(small_batch, fixed):
+        ref = O.ahc(m.H_R, m.R, mesh, ef)
+        assert np.max(np.abs(S.cpu().numpy() - ref)) <= 1e-5 * np.max(np.abs(ref))
+    # the rasterisation order does not change any tile's sums
+    g4, _, _ = kubo.ahc_batched(P, precision="mixed", streams=2, chunk_k=8192, fourier_group_m=4,
+                                symv_parts=4, rotation="simt")
+    g16, _, _ = kubo.ahc_batched(P, precision="mixed", streams=2, chunk_k=8192, fourier_group_m=16,
+                                 symv_parts=4, rotation="simt")
+    for x, y in zip(g4, g16):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
 
 
 def test_mixed_precision_batch(kubo, torch, small_batch):
