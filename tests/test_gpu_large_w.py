@@ -152,11 +152,15 @@ def test_ahc_k_w128_mixed(kubo, torch, m128):
                        precision="mixed")
     E_ref, Om_ref = O.kubo_per_k(m128.H_R, m128.R, kmesh, kidx, [1e-3])
     E, Om = E.cpu().numpy(), Om.cpu().numpy()[0]
-    assert np.max(np.abs(E - E_ref)) <= 1e-6 * np.max(np.abs(E_ref))
+    # FP64 eigensolver on the tensor-core H(k) (2^-31 slicing): eigenvalues to ~1e-9
+    assert np.max(np.abs(E - E_ref)) <= 1e-7 * np.max(np.abs(E_ref)), np.max(np.abs(E - E_ref))
     scale = np.max(np.abs(Om_ref[0]), axis=-1)
     err = np.max(np.abs(Om - Om_ref[0]), axis=-1) / scale
-    assert np.max(err) < 1e-3, np.max(err)
-    assert np.median(err) < 1e-5, np.median(err)
+    # the per-k budget of the W = 64 test (FP32 rotation: ~1e-6 typical, 1e-4 at the worst
+    # k-point's dominant pair), W = 128 accumulating twice as many products
+    print(f"W=128 mixed per-k Omega error max {np.max(err):.3e} median {np.median(err):.3e}")
+    assert np.max(err) < 2e-4, np.max(err)
+    assert np.median(err) < 5e-6, np.median(err)
 
 
 def test_ahc_large_w_full_small_mesh_vs_oracle(kubo, torch):
