@@ -41,10 +41,13 @@ __device__ __forceinline__ double iit_start(int i, int j) {
 // thread j handles the cluster starting at sorted index j.  Z: [n][W][W] real, column m =
 // eigenvector of sorted eigenvalue m.  scratch: per CTA [4][W][ldt] (reciprocal pivots, U1,
 // U2, multipliers), lane-interleaved so every access of a warp is one coalesced row segment.
+// rq: the eigenvalues written are the FP64 Rayleigh quotients z^T T z of the finished unit
+// eigenvectors (kept non-decreasing within a cluster) instead of the shifts b.lam -- for
+// shifts from a reduced-precision QL, whose only role is then to make the iteration converge.
 __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
                                                      double* __restrict__ Eout,
                                                      double* __restrict__ Z,
-                                                     double* __restrict__ scratch) {
+                                                     double* __restrict__ scratch, int rq) {
   __shared__ double ws[LW_MAX], dd[LW_MAX], ee[LW_MAX];
   __shared__ int newc[LW_MAX];
   __shared__ double s_onenrm;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
     double* Zk = Z + (size_t)k * W * W;
     const int j = t;
     if (j < W && newc[j]) {
-      double lprev = 0.0;
+      double lprev = 0.0, rprev = 0.0;
       for (int m = j; m < W && (m == j || !newc[m]); ++m) {
         double lam = ws[m];
         if (m > j && lam - lprev <= pertol) lam = lprev + pertol;
@@ -163,6 +166,19 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
           if (i < W) { const double u = Zk[(size_t)i * W + m]; s0 = fma(u, u, s0); }
           const double inv = 1.0 / sqrt(s0 + s1);
           for (int i2 = 0; i2 < W; ++i2) Zk[(size_t)i2 * W + m] *= inv;
+        }
+        if (rq) {
+          // z^T T z = sum_i d_i z_i^2 + 2 sum_i e_i z_i z_{i+1} (z of unit norm)
+          double q = 0.0, zi = Zk[m];
+          for (int i = 0; i < W; ++i) {
+            const double zn = i + 1 < W ? Zk[(size_t)(i + 1) * W + m] : 0.0;
+            q = fma(dd[i] * zi, zi, q);
+            if (i + 1 < W) q = fma(2.0 * ee[i] * zi, zn, q);
+            zi = zn;
+          }
+          if (m > j && q < rprev) q = rprev;   // ascending order within the cluster
+          rprev = q;
+          Eout[k * W + m] = q;
         }
       }
     }
@@ -464,11 +480,11 @@ int iit_max_slots(int W) { return IIT_SMS * std::min(32, 1024 / iit_threads(W));
 size_t iit_scratch_doubles(int W, int slots) { return (size_t)slots * 4 * W * iit_threads(W); }
 
 cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* scratch, int slots,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool rq) {
   if (n <= 0) return cudaSuccess;
   if (W > LW_MAX || slots < 1) return cudaErrorInvalidValue;
   const int grid = std::min(n, slots);
-  iit_kernel<<<grid, iit_threads(W), 0, s>>>(W, n, b, E, Z, scratch);
+  iit_kernel<<<grid, iit_threads(W), 0, s>>>(W, n, b, E, Z, scratch, (rq && Z) ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,11 @@ bool f32_rotation(int prec) {
   return prec == KUBO_MIXED || prec == KUBO_MIXED_ROTATION || prec == KUBO_MIXED_DF;
 }
 bool df_eigh(int prec) { return prec == KUBO_MIXED_DF; }
+// MIXED: the QL iteration runs in double-float as well, but only to supply the shifts of the
+// FP64 inverse iteration; the eigenvalues reported are the FP64 Rayleigh quotients of its
+// eigenvectors
+bool df_ql(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_DF; }
+bool rq_eigenvalues(int prec) { return prec == KUBO_MIXED; }
 
 // Power-of-two exponent s that brings max |H(R)| into [1, 2) when it lies outside
 // [2^-20, 2^20] (0 otherwise, and for zero or non-finite maxima).  S(E_F) is homogeneous of
@@ -523,15 +528,16 @@ EighBufs make_eigh_bufs(const Call& c) {
 
 // Eigenvalues (sorted) and eigenvectors U = Q D Z of n tridiagonalised matrices whose
 // eigenvalues QL left in eb.lam (U may be null: eigenvalues only).  f32u (W > 64 only): U is
-// formed in FP32 (float2) for the FP32 rotations, its only consumer in that mode.
+// formed in FP32 (float2) for the FP32 rotations, its only consumer in that mode.  rq (W > 64
+// only): eigenvalues from the Rayleigh quotients of the eigenvectors instead of eb.lam.
 cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, double2* U,
-                         bool f32u = false) {
+                         bool f32u = false, bool rq = false) {
   const Plan& p = c.p;
   if (p.W <= SMALL_W_MAX) return launch_backtransform(p.W, n, eb, E, U, c.s, p.pad);
   double* Z = U ? c.at<double>(p.o_L) : nullptr;
   cudaError_t e = Z && df_eigh(p.precision)
                       ? launch_iit_df(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s)
-                      : launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s);
+                      : launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s, rq);
   if (e != cudaSuccess || !U) return e;
   return launch_reflect_large(p.W, n, eb, Z, U, f32u, c.s);
 }
@@ -591,7 +597,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   }
   {
     StageTimer tm(c, KUBO_STAGE_QL, 1);
-    if (df_eigh(p.precision))
+    if (df_ql(p.precision))
       KCHECK(launch_ql_df(p.W, kl.n, eb, st, c.s));
     else
       KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
@@ -606,7 +612,8 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
       if (df_eigh(p.precision))
         KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
       else
-        KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
+        KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s,
+                           rq_eigenvalues(p.precision)));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
     if (p.rot == ROT_TF32)
@@ -619,7 +626,8 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   }
   {
     StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
-    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U, f32_rotation(p.precision)));
+    KCHECK(eigh_vectors(c, kl.n, eb, Eout, U, f32_rotation(p.precision),
+                        rq_eigenvalues(p.precision)));
   }
   {
     StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);

@@ -253,7 +253,8 @@ constexpr int LARGE_W_MAX = 128;
 int iit_max_slots(int W);
 size_t iit_scratch_doubles(int W, int slots);
 cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* scratch, int slots,
-                       cudaStream_t s);
+                       cudaStream_t s,
+                       bool rq = false);
 // U: float2 [n][W][W] when f32 (formed in FP32 for the FP32 rotations), else double2
 cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, void* U, bool f32,
                                  cudaStream_t s);

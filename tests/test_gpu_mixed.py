@@ -1,5 +1,5 @@
 """Mixed-precision path (tensor-core Fourier sum with fixed-point BF16 slices, FP32 rotations,
-FP64 eigensolver, denominators and k-sum) against the FP64 oracle and the FP64 GPU path; the
+FP64 eigenvectors and eigenvalues, denominators and k-sum) against the FP64 oracle and the FP64 GPU path; the
 double-float eigensolver variant (MIXED_DF) to the same tolerance.
 
 Tolerance: relative 1e-5 on S(E_F) (max over E_F of |diff| / max |S_ref|).  The tensor-core
@@ -231,6 +231,32 @@ def test_double_float_eigenvalues(kubo, torch, W, hw):
     scale = np.max(np.abs(Efx))
     assert np.max(np.abs(Emx - Efx)) <= 16 * W * 2.0 ** -46 * scale, \
         np.max(np.abs(Emx - Efx)) / scale
+
+
+@pytest.mark.parametrize("W,hw,layers", [(2, 1, 1), (5, 2, 1), (33, 1, 1), (64, 5, 1),
+                                         (100, 1, 1), (4, 1, 2)])
+def test_rayleigh_quotient_eigenvalues(kubo, torch, W, hw, layers):
+    """MIXED reports the FP64 Rayleigh quotients z^T T z of its FP64 inverse-iteration vectors
+    (its QL iteration, in FP32 pairs, only supplies the shifts); MIXED_FOURIER reads the same
+    tensor-core rows of H and takes its eigenvalues from the FP64 QL iteration.  Both are
+    backward stable for the same tridiagonal T, so they agree to a few W eps ||T||; the
+    quotients of a unit vector with residual r lie within ||r|| of an eigenvalue, and the
+    reported levels stay ascending.  layers = 2: exactly degenerate pairs (a doubled model)."""
+    if layers == 1:
+        m = tbgen.random_tb(W, hw, 1.5, 700 + W)
+    else:
+        m = tbgen.stack_layers(tbgen.qwz(-1.2, tz=0.3, c0=0.2), 2)
+        W = m.H_R.shape[-1]
+    kmesh = (16, 16, 16)
+    kidx = tbgen.k_sample(kmesh, 97, seed=W + 1)
+    H, K = cuda(torch, m.H_R), cuda(torch, kidx)
+    Erq, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed")
+    Eql, _ = kubo.ahc_k(H, m.R, kmesh, K, precision="mixed_fourier")
+    Erq, Eql = Erq.cpu().numpy(), Eql.cpu().numpy()
+    scale = np.max(np.abs(Eql))
+    assert np.all(np.diff(Erq, axis=-1) >= 0)
+    assert np.max(np.abs(Erq - Eql)) <= 16 * W * 2.0 ** -52 * scale, \
+        np.max(np.abs(Erq - Eql)) / scale
 
 
 def test_double_float_reduction_degenerate_bands(kubo, torch):
