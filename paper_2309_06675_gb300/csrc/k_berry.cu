@@ -514,6 +514,26 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
   __syncthreads();
 }
 
+// U = Q D Z in FP32 as a kernel of its own (one CTA per k-point, several per SM), for the
+// tensor-core rotation: U32 [n][W][W] float2, row-major.
+__global__ void __launch_bounds__(NT) assemble_u_kernel(const double* __restrict__ Z, EighBufs eb,
+                                                        float2* __restrict__ U32, int W, int LD) {
+  extern __shared__ float2 au_smem[];
+  float2* sU = au_smem;
+  float2* stage = au_smem + (size_t)W * LD;
+  const int64_t k = blockIdx.x;
+  const int t = threadIdx.x;
+  const size_t WW = (size_t)W * W;
+  assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, LD, t, sU,
+                 stage);
+  float2* dst = U32 + k * WW;
+  const FastDiv dW(W);
+  for (int idx = t; idx < W * W; idx += NT) {
+    const int r = (int)dW.div(idx);
+    dst[idx] = sU[r * LD + (idx - r * W)];
+  }
+}
+
 // Leading dimension (in float2) of the FP32 shared-memory matrices.  Padded: W + P with
 // W + P = 4 (mod 16), so that a row step moves 8 banks: the 4 rows x 2 columns of float2 that
 // a quarter of a warp touches in the reflector application, and the 16 consecutive columns of
@@ -980,9 +1000,10 @@ __global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
 // column of the second product's B operand); V^x waits in TMEM while V^y is formed.  The
 // operands are staged one K-quarter (32 TF32 = one 128-byte swizzle row) at a time, 48 KB for
 // A and B with their hi / lo parts, so that with U (FP32, assembled from the FP64 factors in
-// shared memory) a CTA needs ~85 KB and two CTAs share an SM: one stages operands while the
-// other's MMAs run.  Persistent over the k-points; every wait on the tensor core is bounded
-// (ST_TIMEOUT).
+// shared memory) and the packed FP32 velocity rows (copied asynchronously into shared memory,
+// rows of W + 1 floats: X while U is assembled, Y while the second product of X runs) a CTA
+// needs ~100 KB and two CTAs share an SM: one stages operands while the other's MMAs run.
+// Persistent over the k-points; every wait on the tensor core is bounded (ST_TIMEOUT).
 constexpr int TF_NT = 256;
 constexpr int TF_WP = 64;
 constexpr int TF_A_TILE = 128 * 128;   // bytes: 128 rows x 32 TF32
@@ -990,6 +1011,7 @@ constexpr int TF_B_TILE = 64 * 128;    // bytes: 64 rows x 32 TF32
 constexpr int TF_OPS_BYTES = 2 * TF_A_TILE + 2 * TF_B_TILE;   // A hi, A lo, B hi, B lo: 48 KB
 constexpr int TF_LDU = 68;                                    // = mixed_ld(64, 1)
 constexpr int TF_U_BYTES = TF_WP * TF_LDU * 8;                // 34,816
+constexpr int TF_X_BYTES = TF_WP * (TF_WP + 1) * 4;         // FP32 velocity, rows of W + 1
 constexpr int TF_TMEM_COLS = 256;   // partial T at 0, partial V at 64, parked V^x at 128
 constexpr uint32_t TF_WAIT_LIMIT = 1u << 20;
 // instruction descriptor: D F32, A and B TF32 (K-major), N = 64, M = 128
@@ -1000,6 +1022,19 @@ constexpr uint32_t TF_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(6
 __device__ __forceinline__ uint32_t sw128_off32(int row, int k) {
   const uint32_t b = (uint32_t)k * 4u;
   return (uint32_t)row * 128u + ((((b >> 4) ^ (uint32_t)(row & 7)) & 7u) << 4) + (b & 15u);
+}
+
+// 4-byte asynchronous global -> shared copy (completion: cp_async_wait_all, then a barrier)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -1053,12 +1088,14 @@ __device__ __forceinline__ void tf_issue(uint32_t tmem_d, uint32_t ops, bool fir
   }
 }
 
+// U32 (nullable): U = Q D Z already formed in FP32 ([n][W][W], assemble_u_kernel), copied
+// into shared memory instead of being assembled here
 template <typename TIn>
 __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
     const double* __restrict__ E, const double* __restrict__ Z, EighBufs eb,
     const TIn* __restrict__ Xp, const TIn* __restrict__ Yp, int64_t ld, int W, int n,
     const double* __restrict__ etas, int n_eta, double* __restrict__ Om, int64_t eta_stride,
-    DevStatus* st) {
+    DevStatus* st, const float2* __restrict__ U32) {
   extern __shared__ unsigned char tf_smem[];
   __shared__ double sE[64];
   __shared__ double sEta[MAXE];
@@ -1075,8 +1112,21 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
   unsigned char* a_lo = ops + TF_A_TILE;
   unsigned char* b_hi = ops + 2 * TF_A_TILE;
   unsigned char* b_lo = b_hi + TF_B_TILE;
+  // FP32 velocity input: the packed row of the current direction, rows of LDX floats
+  constexpr bool XS = std::is_same<TIn, float>::value;
+  float* sX = reinterpret_cast<float*>(ops + TF_OPS_BYTES);
+  const int LDX = W + 1;   // odd: row and column walks of a warp fall on distinct banks
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const size_t WW = (size_t)W * W;
+  const FastDiv dWx(W > 0 ? W : 1);
+  auto fetch_x = [&](const TIn* P) {
+    if constexpr (XS) {
+      for (int idx = t; idx < W * W; idx += TF_NT) {
+        const int r = (int)dWx.div(idx);
+        cp_async4(sX + r * LDX + (idx - r * W), P + idx);
+      }
+    }
+  };
 
   if (t == 0) {
     tc::mbar_init(&mma_bar, 1);
@@ -1121,9 +1171,22 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
     if (t < n_eta) sEta[t] = etas[t];
     for (int idx = t; idx < TF_WP * TF_LDU; idx += TF_NT) sU[idx] = make_float2(0.f, 0.f);
     __syncthreads();
-    // ---- U = Q D Z in FP32 (the reflectors staged in the operand region)
-    assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, TF_LDU, t,
-                   sU, reinterpret_cast<float2*>(ops));
+    fetch_x(Xp + k * ld);   // lands while U is assembled (or copied)
+    if (U32) {
+      // ---- U = Q D Z, formed in FP32 by the assembly kernel: asynchronous copy (the zero
+      // padding of rows / columns >= W is written above, behind the barrier)
+      const float2* src = U32 + k * WW;
+      for (int idx = t; idx < W * W; idx += TF_NT) {
+        const int r = (int)dWx.div(idx);
+        cp_async8(sU + r * TF_LDU + (idx - r * W), src + idx);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    } else {
+      // ---- U = Q D Z in FP32 (the reflectors staged in the operand region)
+      assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, TF_LDU,
+                     t, sU, reinterpret_cast<float2*>(ops));
+    }
     if (t == 0) {
       double mx = 0.0;
       for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
@@ -1140,21 +1203,28 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
       float tv[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) tv[j] = 0.f;
+      if constexpr (XS) cp_async_wait_all();   // this direction's rows (the barrier follows)
       for (int h = 0; h < 4 && ok; ++h) {
         __syncthreads();   // the stage area / previous quarter's operands are free
         // A1 rows i and 64 + i, K columns 32 h + 4 c4 .. + 3 (X column c = that - 64 h2)
         const bool second = h >= 2;
         for (int it = t; it < 64 * 8; it += TF_NT) {
-          const int i = it >> 3, c4 = it & 7;
+          const int i = it & 63, c4 = it >> 6;
           float xr[4], xi[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int c = (h & 1) * 32 + 4 * c4 + q;
             float re = 0.f, im = 0.f;
             if (i < W && c < W) {
-              if (i < c) { re = (float)P[i * W + c]; im = (float)P[c * W + i]; }
-              else if (i > c) { re = (float)P[c * W + i]; im = -(float)P[i * W + c]; }
-              else re = (float)P[i * W + i];
+              if constexpr (XS) {
+                if (i < c) { re = sX[i * LDX + c]; im = sX[c * LDX + i]; }
+                else if (i > c) { re = sX[c * LDX + i]; im = -sX[i * LDX + c]; }
+                else re = sX[i * LDX + i];
+              } else {
+                if (i < c) { re = (float)P[i * W + c]; im = (float)P[c * W + i]; }
+                else if (i > c) { re = (float)P[c * W + i]; im = -(float)P[i * W + c]; }
+                else re = (float)P[i * W + i];
+              }
             }
             xr[q] = re;
             xi[q] = im;
@@ -1180,6 +1250,9 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
           put4_tf32(b_hi, b_lo, nn, c4, u);
         }
         if (!mma_quarter(0, true)) { ok = false; break; }
+        // the last read of this direction's rows is behind the barrier: fetch Y (lands while
+        // the second product of X runs)
+        if (h == 3 && a == 0) fetch_x(Yp + k * ld);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           uint32_t r[16];
@@ -1377,8 +1450,13 @@ cudaError_t launch_berry_mixed_rows(const double* E, const double2* U, const dou
 cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const EighBufs& eb,
                                       const double* C, int64_t ld, int W, int n,
                                       const double* etas, int n_eta, double* Om,
-                                      int64_t eta_stride, cudaStream_t s, int pad) {
+                                      int64_t eta_stride, cudaStream_t s, int pad, bool vel32) {
   const int64_t WW = (int64_t)W * W;
+  if (vel32) {
+    const float* X = reinterpret_cast<const float*>(C) + vel32_x0(W);
+    return launch_berry_mixed_t<float, true>(E, nullptr, Z, eb, X, X + vel32_yoff(W), 2 * ld, W,
+                                             n, etas, n_eta, Om, eta_stride, s, pad);
+  }
   return launch_berry_mixed_t<double, true>(E, nullptr, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas,
                                             n_eta, Om, eta_stride, s, pad);
 }
@@ -1407,8 +1485,13 @@ static cudaError_t launch_berry_tc_t(const double* E, const double* Z, const Eig
 cudaError_t launch_berry_tc_rows(const double* E, const double* Z, const EighBufs& eb,
                                  const double* C, int64_t ld, int W, int n, const double* etas,
                                  int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool vel32) {
   const int64_t WW = (int64_t)W * W;
+  if (vel32) {
+    const float* X = reinterpret_cast<const float*>(C) + vel32_x0(W);
+    return launch_berry_tc_t<float>(E, Z, eb, X, X + vel32_yoff(W), 2 * ld, W, n, etas, n_eta,
+                                    Om, eta_stride, st, s);
+  }
   return launch_berry_tc_t<double>(E, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
                                    eta_stride, st, s);
 }
@@ -1421,10 +1504,26 @@ cudaError_t launch_berry_tc_from_f64(const double* E, const double* Z, const Eig
                                    eta_stride, st, s);
 }
 
+size_t assemble_u_smem(int W) {
+  return (size_t)W * mixed_ld(W, 1) * sizeof(float2) + asm_stage_bytes(W);
+}
+
+cudaError_t launch_assemble_u32(const double* Z, const EighBufs& eb, float2* U32, int W, int n,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > 64 || W < 1) return cudaErrorInvalidValue;
+  const size_t sm = assemble_u_smem(W);
+  cudaError_t e = cudaFuncSetAttribute(assemble_u_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  assemble_u_kernel<<<n, NT, sm, s>>>(Z, eb, U32, W, mixed_ld(W, 1));
+  return cudaGetLastError();
+}
+
 // dynamic shared memory of the 3xTF32 rotation kernel: U and the operand stage, or the
 // curvature's per-eta partial sums if larger (n_eta x 16 KB)
-size_t berry_tf32_smem(int n_eta) {
-  const size_t base = (size_t)TF_U_BYTES + 1024 + TF_OPS_BYTES;
+size_t berry_tf32_smem(int n_eta, bool xs) {
+  const size_t base = (size_t)TF_U_BYTES + 1024 + TF_OPS_BYTES + (xs ? TF_X_BYTES : 0);
   const size_t red = (size_t)n_eta * TF_WP * 2 * 16 * sizeof(double);
   return std::max(base, red);
 }
@@ -1433,10 +1532,11 @@ template <typename TIn>
 static cudaError_t launch_berry_tf32_t(const double* E, const double* Z, const EighBufs& eb,
                                        const TIn* Xp, const TIn* Yp, int64_t ld, int W, int n,
                                        const double* etas, int n_eta, double* Om,
-                                       int64_t eta_stride, DevStatus* st, cudaStream_t s) {
+                                       int64_t eta_stride, DevStatus* st, cudaStream_t s,
+                                       const float2* U32 = nullptr) {
   if (n <= 0) return cudaSuccess;
   if (W > TF_WP || n_eta > MAXE) return cudaErrorInvalidValue;
-  const size_t sm = berry_tf32_smem(n_eta);
+  const size_t sm = berry_tf32_smem(n_eta, std::is_same<TIn, float>::value);
   cudaError_t e = cudaFuncSetAttribute(berry_tf32_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   // the whole unified L1 / shared-memory array as shared memory, so that two CTAs fit
@@ -1445,20 +1545,25 @@ static cudaError_t launch_berry_tf32_t(const double* E, const double* Z, const E
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   // two CTAs per SM (128 registers x 256 threads each, 2 x 256 of the 512 TMEM columns) while
-  // the shared memory allows (up to five broadenings); the CTAs are independent, so a grid
+  // the shared memory allows (up to six broadenings); the CTAs are independent, so a grid
   // larger than what is resident only queues
-  const int per_sm = sm <= (size_t)100 * 1024 ? 2 : 1;
+  const int per_sm = sm <= (size_t)110 * 1024 ? 2 : 1;
   const int grid = (int)std::min<int64_t>(n, (int64_t)std::max(1, sms) * per_sm);
   berry_tf32_kernel<TIn><<<grid, TF_NT, sm, s>>>(E, Z, eb, Xp, Yp, ld, W, n, etas, n_eta, Om,
-                                                 eta_stride, st);
+                                                 eta_stride, st, U32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_berry_tf32_rows(const double* E, const double* Z, const EighBufs& eb,
                                    const double* C, int64_t ld, int W, int n, const double* etas,
                                    int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool vel32, const float2* U32) {
   const int64_t WW = (int64_t)W * W;
+  if (vel32) {
+    const float* X = reinterpret_cast<const float*>(C) + vel32_x0(W);
+    return launch_berry_tf32_t<float>(E, Z, eb, X, X + vel32_yoff(W), 2 * ld, W, n, etas, n_eta,
+                                      Om, eta_stride, st, s, U32);
+  }
   return launch_berry_tf32_t<double>(E, Z, eb, C + WW, C + 2 * WW, ld, W, n, etas, n_eta, Om,
                                      eta_stride, st, s);
 }

@@ -33,6 +33,7 @@
 // Every mbarrier wait is bounded; on timeout the CTA records ST_TIMEOUT, drains its own
 // copies (bounded), frees its TMEM and returns.
 #include <algorithm>
+#include <climits>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -203,7 +204,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     fourier_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, const int* __restrict__ col_exp,
                       int Mpad, int Npad, int nkb, int n_rows, double* __restrict__ out, int ldc,
-                      DevStatus* st, int nt0, int ntc, int group_m) {
+                      DevStatus* st, int nt0, int ntc, int group_m, int vel0, int vw2,
+                      int vx0, int vyoff) {
   constexpr int NLEV = NS;
   constexpr int NPR = NS * (NS + 1) / 2;   // pairs with i + j < NS (listed first in c_p*)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -369,12 +371,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // rounding of the 57-bit integer to FP64
         double* dst = out + (size_t)grow * ldc + n0 + c_lo;
         const int* ce = col_exp + n0 + c_lo;
+        if (n0 + c_lo + EPI_COLS <= vel0) {
 #pragma unroll
-        for (int j = 0; j < EPI_COLS; j += 2) {
-          const double s0 = __longlong_as_double((long long)(1023 - 46 + ce[j]) << 52);
-          const double s1 = __longlong_as_double((long long)(1023 - 46 + ce[j + 1]) << 52);
-          *reinterpret_cast<double2*>(dst + j) =
-              make_double2((double)isum[j] * s0, (double)isum[j + 1] * s1);
+          for (int j = 0; j < EPI_COLS; j += 2) {
+            const double s0 = __longlong_as_double((long long)(1023 - 46 + ce[j]) << 52);
+            const double s1 = __longlong_as_double((long long)(1023 - 46 + ce[j + 1]) << 52);
+            *reinterpret_cast<double2*>(dst + j) =
+                make_double2((double)isum[j] * s0, (double)isum[j + 1] * s1);
+          }
+        } else {
+          // velocity columns as FP32 (vel32_x0 layout of the row), padding columns dropped
+          // (pairs: even W^2 keeps both entries of a pair in one row, 8-byte aligned)
+          float* o32 = reinterpret_cast<float*>(out) + (size_t)grow * 2 * ldc;
+#pragma unroll
+          for (int j = 0; j < EPI_COLS; j += 2) {
+            const int cc = n0 + c_lo + j;
+            const double v0 =
+                (double)isum[j] * __longlong_as_double((long long)(1023 - 46 + ce[j]) << 52);
+            const double v1 =
+                (double)isum[j + 1] * __longlong_as_double((long long)(1023 - 46 + ce[j + 1]) << 52);
+            if (!(vw2 & 1) && cc >= vel0 && cc + 1 < vel0 + 2 * vw2) {
+              const int u = cc - vel0;
+              *reinterpret_cast<float2*>(o32 + (u < vw2 ? vx0 + u : vx0 + vyoff + (u - vw2))) =
+                  make_float2((float)v0, (float)v1);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                const int c2 = cc + q;
+                const double v = q ? v1 : v0;
+                if (c2 < vel0) {
+                  dst[j + q] = v;
+                } else if (c2 < vel0 + 2 * vw2) {
+                  const int u = c2 - vel0;
+                  o32[u < vw2 ? vx0 + u : vx0 + vyoff + (u - vw2)] = (float)v;
+                }
+              }
+            }
+          }
         }
       }
     }
@@ -464,10 +497,15 @@ cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl
 
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
-                              cudaStream_t s, int red_n0, int group_m) {
+                              cudaStream_t s, int red_n0, int group_m, int vel_w) {
   if (n_rows <= 0) return cudaSuccess;
   if (Mpad % BM || Npad % BN || Kp % BK || ldc % 2) return cudaErrorInvalidValue;
   if (group_m < 1 || group_m > 64) return cudaErrorInvalidValue;
+  const int vw2 = vel_w * vel_w;
+  if (vel_w < 0 || (vel_w > 0 && (3 * vw2 > Npad ||
+                                  vel32_x0(vel_w) + vel32_yoff(vel_w) + vw2 > 2 * ldc)))
+    return cudaErrorInvalidValue;
+  const int vel0 = vel_w > 0 ? vw2 : INT_MAX;
   CUtensorMap mA, mB;
   if (!encode_2d(&mA, A, (uint64_t)Kp, (uint64_t)NSLICE * Mpad, BK, BM)) return cudaErrorInvalidValue;
   if (!encode_2d(&mB, Bt, (uint64_t)Kp, (uint64_t)NSLICE * Npad, BK, BN)) return cudaErrorInvalidValue;
@@ -484,7 +522,8 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(tc * (Mpad / BM), std::max(nsm, 1));   // persistent: one per SM
     kern<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out, ldc, st,
-                                      t0, tc, group_m);
+                                      t0, tc, group_m, vel0, vw2, vel32_x0(vel_w),
+                                      vel32_yoff(vel_w));
     return cudaGetLastError();
   };
   cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt);

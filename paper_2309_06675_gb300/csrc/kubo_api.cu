@@ -578,13 +578,16 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   double2* U = c.at<double2>(p.o_U);
   double* C64 = c.at<double>(p.o_C64);
   const int Mb = tc_pad_m(kl.n);
+  // W <= 64 with an FP32-grade rotation: the velocity rows are stored in FP32 (their only
+  // consumer reads them in FP32: half the bytes, no conversions on the FP64 pipe)
+  const bool vel32 = f32_rotation(p.precision) && p.W <= SMALL_W_MAX;
   {
     // the velocity columns feed only the FP32 rotation in the MIXED mode: FP32-grade slices
     // (a second tensor-core launch over those column tiles)
     const int red_n0 = f32_rotation(p.precision) ? p.W * p.W : p.Npad;
     StageTimer tm(c, KUBO_STAGE_FOURIER, red_n0 < p.Npad ? 3 : 2);
     KCHECK(launch_coef_split(md, p.mesh, kl, Mb, p.Kp, c.at<char>(p.o_A), c.s));
-    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0, p.group_m));
+    KCHECK(launch_fourier_tc(c.at<char>(p.o_A), c.at<char>(p.o_Bt), c.at<int>(p.o_cexp), Mb, p.Npad, p.Kp, kl.n, C64, p.Npad, st, c.s, red_n0, p.group_m, vel32 ? p.W : 0));
   }
   {
     // MIXED_DF: the reduction and the QL iteration in double-float on the FP32 pipe (both are
@@ -607,21 +610,25 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
     // FP32 rotations: U = Q D Z is assembled in FP32 inside the rotation kernel from the FP64
     // eigenvectors Z of the tridiagonal (kept in the U buffer) and the reflectors
     double* Z = reinterpret_cast<double*>(U);
+    // the tensor-core rotation takes U = Q D Z formed by a kernel of its own (FP32, in the
+    // second half of the U buffer: Z holds the first n W^2 doubles)
+    float2* U32 = p.rot == ROT_TF32 ? reinterpret_cast<float2*>(Z + (size_t)kl.n * WW) : nullptr;
     {
-      StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, 1);
+      StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, U32 ? 2 : 1);
       if (df_eigh(p.precision))
         KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
       else
         KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s,
                            rq_eigenvalues(p.precision)));
+      if (U32) KCHECK(launch_assemble_u32(Z, eb, U32, p.W, kl.n, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
     if (p.rot == ROT_TF32)
-      KCHECK(launch_berry_tf32_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
+      KCHECK(launch_berry_tf32_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s, vel32, U32));
     else if (p.rot == ROT_EXACT_SLICES)
-      KCHECK(launch_berry_tc_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s));
+      KCHECK(launch_berry_tc_rows(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, st, c.s, vel32));
     else
-      KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad));
+      KCHECK(launch_berry_mixed_rows_z(Eout, Z, eb, C64, p.Npad, p.W, kl.n, c.at<double>(p.o_etas), p.n_eta, Om, om_stride, c.s, p.pad, vel32));
     return KUBO_OK;
   }
   {

@@ -166,11 +166,13 @@ cudaError_t launch_berry_fp64_rows(const double* E, const double2* U, const doub
                                    double* Om, int64_t eta_stride, cudaStream_t s, int pad = 1);
 
 // FP32 rotations with U = Q D Z assembled in FP32 inside the kernel from Z and the eigensolver
-// factors in eb (phase, refl, tau), W <= 64
+// factors in eb (phase, refl, tau), W <= 64.  vel32 (these and the two tensor-core forms
+// below): the velocity rows of C are FP32 (vel32_x0 layout), else FP64 after the H columns.
 cudaError_t launch_berry_mixed_rows_z(const double* E, const double* Z, const EighBufs& eb,
                                       const double* C, int64_t ld, int W, int n,
                                       const double* etas, int n_eta, double* Om,
-                                      int64_t eta_stride, cudaStream_t s, int pad = 1);
+                                      int64_t eta_stride, cudaStream_t s, int pad = 1,
+                                      bool vel32 = false);
 cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, const EighBufs& eb,
                                           const double* Xp, const double* Yp, int W, int n,
                                           const double* etas, int n_eta, double* Om,
@@ -181,13 +183,18 @@ cudaError_t launch_berry_mixed_from_f64_z(const double* E, const double* Z, cons
 cudaError_t launch_berry_tc_rows(const double* E, const double* Z, const EighBufs& eb,
                                  const double* C, int64_t ld, int W, int n, const double* etas,
                                  int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool vel32 = false);
 // the same two rotations in 3xTF32 on tcgen05 (kind::tf32, FP32 accumulation), W <= 64; U is
 // assembled in FP32 from Z and eb; a stalled MMA completion sets ST_TIMEOUT in st
 cudaError_t launch_berry_tf32_rows(const double* E, const double* Z, const EighBufs& eb,
                                    const double* C, int64_t ld, int W, int n, const double* etas,
                                    int n_eta, double* Om, int64_t eta_stride, DevStatus* st,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool vel32 = false,
+                                   const float2* U32 = nullptr);
+// U = Q D Z in FP32 from Z and the eigensolver factors in eb, W <= 64: U32 [n][W][W] float2
+// (the tensor-core rotation's input when it is formed by a kernel of its own)
+cudaError_t launch_assemble_u32(const double* Z, const EighBufs& eb, float2* U32, int W, int n,
+                                cudaStream_t s);
 cudaError_t launch_berry_tf32_from_f64(const double* E, const double* Z, const EighBufs& eb,
                                        const double* Xp, const double* Yp, int W, int n,
                                        const double* etas, int n_eta, double* Om,
@@ -212,11 +219,18 @@ cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, 
                                int* col_exp, void* Bt, cudaStream_t s);
 cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl, int Mpad, int Kp,
                               void* A, cudaStream_t s);
-// red_n0: first output column whose tile may keep three slices (FP32-grade; Npad = none)
+// FP32 velocity rows: the packed dH_x and dH_y of an output row r (ldc doubles, the packed H
+// in its first W^2) as FP32, at float indices vel32_x0(W) and vel32_x0(W) + vel32_yoff(W) of
+// the row (float row stride 2 ldc; both 16-byte aligned, after the H columns)
+inline int vel32_x0(int W) { return (2 * W * W + 3) / 4 * 4; }
+inline int vel32_yoff(int W) { return (W * W + 3) / 4 * 4; }
+// red_n0: first output column whose tile may keep three slices (FP32-grade; Npad = none).
+// vel_w > 0: the 2 W^2 velocity columns after the first W^2 = vel_w^2 are stored as FP32 in the
+// layout above (their only consumer is an FP32 rotation); 0: every column as FP64.
 cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp, int Mpad, int Npad,
                               int Kp, int n_rows, double* out, int ldc, DevStatus* st,
                               cudaStream_t s, int red_n0,
-                              int group_m = 8);
+                              int group_m = 8, int vel_w = 0);
 // the tensor-core kernel's bounded mbarrier wait on a barrier that never completes
 cudaError_t launch_bounded_wait_check(uint32_t limit, DevStatus* st, cudaStream_t s);
 // rows [n][ld] (H | dxH | dyH packed) -> three packed arrays [n][W*W]
