@@ -61,18 +61,20 @@ DRAM_BYTES_PER_K = {("mixed", "tridiag"): 86.0e3, ("mixed_df", "tridiag"): 97.3e
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
 
-    In the mixed path the eigenvector stage stops at the eigenvectors Z of the tridiagonal
-    (inverse iteration) and U = Q D Z is assembled in FP32 inside the rotation kernel.
+    Eigenvector stage ("backtransform"): inverse iteration for the eigenvectors Z of the
+    tridiagonal, then U = Q D Z (8 W^3) -- in FP64 on the FP64 path, in FP32 on the reduced
+    ones: by a kernel of its own before the 3xTF32 rotation (W > 56, the default there), inside
+    the SIMT rotation kernel otherwise (counted in "berry").
     """
-    mixed = prec != "fp64"   # every reduced mode assembles U in FP32 inside the rotation kernel
+    mixed = prec != "fp64"
+    asm_in_rotation = mixed and W <= 56
     return {
         "fourier": 6.0 * N_R * W * W,     # real contraction [3 x N_R] . [N_R x W^2]
         "tridiag": 16.0 / 3.0 * W ** 3,   # complex Householder reduction
         "ql": 25.0 * 1.2 * W * W,         # ~1.2 W^2 Givens steps of ~25 flops
-        # inverse iteration (+ reflectors U = Q D Z in the FP64 path)
-        "backtransform": 42.0 * W * W + (0.0 if mixed else 8.0 * W ** 3),
-        # two Hermitian rotations U^H dH U (+ FP32 assembly of U in the mixed path)
-        "berry": 24.0 * W ** 3 + (8.0 * W ** 3 if mixed else 0.0),
+        "backtransform": 42.0 * W * W + (0.0 if asm_in_rotation else 8.0 * W ** 3),
+        # two Hermitian rotations U^H dH U (+ the FP32 assembly of U when it runs inside)
+        "berry": 24.0 * W ** 3 + (8.0 * W ** 3 if asm_in_rotation else 0.0),
         "ksum": 2.0 * W * 64,
         "prep": 0.0,
         "fixup": 0.0,
@@ -112,10 +114,10 @@ def roofline_of(dom, head, W, N_R, k_per_launch, ms_per_launch):
                              "double-float reduction's 8/3 W^3 real multiply-adds at the minimal "
                              f"{DF_OPS_PER_MAC} FP32 operations each"}
     if head != "fp64" and dom == "berry":
-        fl = (24.0 + 8.0) * W ** 3 * k_per_launch
+        fl = stage_flops(W, N_R, head)["berry"] * k_per_launch
         return {"bound": "alu", "achieved": fl / t / 1e12, "peak": 2 * FP32_PEAK_TOPS,
                 "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz "
-                                                "(derived); the rotations' 24 W^3 and the U assembly's 8 W^3"}
+                                                "(derived); the rotations' 24 W^3 (+ the U assembly's 8 W^3 at W <= 56)"}
     if head != "fp64" and dom == "fourier":
         fl = issued_tc_flops_per_k(W, head) * k_per_launch   # issued BF16 slice products
         pk = measured_peaks()
@@ -444,7 +446,9 @@ def run_extra(args, local):
     print(json.dumps(line))
 
 
-DTYPE = {"mixed": "bf16-slices(Ozaki) Fourier + f64 eigh + 3xtf32 rotation + f64 denominators/k-sum",
+DTYPE = {"mixed": "bf16-slices(Ozaki) Fourier + f64 eigh (f64 Householder, inverse iteration and "
+                  "Rayleigh-quotient eigenvalues; QL shifts in f32 pairs) + 3xtf32 rotation + "
+                  "f64 denominators/k-sum",
          "mixed_df": "bf16-slices(Ozaki) Fourier + double-float(f32 pairs) eigh + 3xtf32 rotation",
          "fp64": "f64"}
 
@@ -578,7 +582,10 @@ def main():
         "data": "synthetic (seeded random TB model, tbgen.random_tb)",
         "config": {"workload": WORKLOAD, "W": model.W, "N_R": model.N_R, "kmesh": list(kmesh),
                    "n_EF": int(E_F.size), "eta": eta, "precision": head,
-                   "eigensolver": "f64" if head in ("mixed", "fp64") else "double-float (f32 pairs)",
+                   "eigensolver": {"fp64": "f64",
+                                   "mixed": "f64 (Householder, inverse iteration, Rayleigh-quotient "
+                                            "eigenvalues; QL shifts in f32 pairs)"}.get(
+                                       head, "double-float (f32 pairs)"),
                    "k_per_step": k_per_step, "chunk_k": args.chunk or "auto",
                    "parallelism": f"k-slabs x{world}",
                    "l2": "flushed (256 MiB write) before every step; per-step working set >> L2"},

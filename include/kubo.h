@@ -63,10 +63,14 @@ typedef enum {
   KUBO_MIXED = 1,           /* the mixed-precision form: step (1) on the tensor cores (fixed-point
                                BF16 slices with exact FP32 block accumulation: H(k) to ~2^-31
                                relative, the velocity columns, which feed only step (3), to
-                               ~2^-23); the eigensolver (Householder reduction, QL, inverse
-                               iteration) in FP64; step (3) in FP32, with U = Q D Z formed in FP32
-                               from the FP64 factors; energy differences and the k-sum in FP64;
-                               curvature quotient in FP32 (FP64 below a 2^-86 denominator) */
+                               ~2^-23, stored in FP32 for W <= 64); the eigensolver in FP64:
+                               Householder reduction, inverse iteration for the eigenvectors,
+                               and as eigenvalues the FP64 Rayleigh quotients of those vectors
+                               (the QL iteration, which only supplies the inverse iteration's
+                               shifts, runs in double-float); step (3) in FP32, with U = Q D Z
+                               formed in FP32 from the FP64 factors; energy differences and the
+                               k-sum in FP64; curvature quotient in FP32 (FP64 below a 2^-86
+                               denominator) */
   KUBO_MIXED_FOURIER = 2,   /* error-budget mode: only step (1) mixed, step (3) in FP64 */
   KUBO_MIXED_ROTATION = 3,  /* error-budget mode: only step (3) mixed (FP32), step (1) in FP64 */
   KUBO_MIXED_DF = 4         /* KUBO_MIXED with the eigensolver in double-float instead of FP64:
