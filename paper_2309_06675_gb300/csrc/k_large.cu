@@ -100,29 +100,24 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
         lprev = lam;
         unsigned long long piv0 = 0ull, piv1 = 0ull;   // row interchanges, bits 0..127
         double q0 = dd[0] - lam, q1 = W > 1 ? ee[0] : 0.0, q2 = 0.0;
+        // Gaussian elimination with partial pivoting of T - lam I (q2 is zero at every step).
+        // The row interchange only selects operands (integer selects), so the lanes of a warp,
+        // whose interchanges differ, issue one common sequence of FP64 instructions.
         for (int i = 0; i + 1 < W; ++i) {
           const double ei = ee[i];
           const double a = dd[i + 1] - lam;
           const double bb = i + 2 < W ? ee[i + 1] : 0.0;
           const size_t o = (size_t)i * ldt + t;
-          if (fabs(q0) >= fabs(ei)) {
-            if (q0 == 0.0) q0 = tiny;
-            const double r = 1.0 / q0;
-            const double mlt = ei * r;
-            rU0[o] = r; U1[o] = q1; U2[o] = q2; ML[o] = mlt;
-            q0 = fma(-mlt, q1, a);
-            q1 = fma(-mlt, q2, bb);
-            q2 = 0.0;
-          } else {
-            const double r = 1.0 / ei;
-            const double mlt = q0 * r;
-            rU0[o] = r; U1[o] = a; U2[o] = bb; ML[o] = mlt;
-            if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64);
-            const double n0 = fma(-mlt, a, q1);
-            q1 = fma(-mlt, bb, q2);
-            q0 = n0;
-            q2 = 0.0;
-          }
+          const bool sw = !(fabs(q0) >= fabs(ei));   // interchange rows i and i + 1
+          const double den = sw ? ei : (q0 == 0.0 ? tiny : q0);
+          const double r = 1.0 / den;
+          const double mlt = (sw ? q0 : ei) * r;
+          rU0[o] = r; U1[o] = sw ? a : q1; U2[o] = sw ? bb : q2; ML[o] = mlt;
+          if (sw) { if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64); }
+          const double n0 = fma(-mlt, sw ? a : q1, sw ? q1 : a);
+          q1 = fma(-mlt, sw ? bb : q2, sw ? q2 : bb);
+          q0 = n0;
+          q2 = 0.0;
         }
         if (q0 == 0.0) q0 = tiny;
         {
@@ -135,12 +130,8 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
             const double mlt = ML[(size_t)i * ldt + t];
             const double yi = Zk[(size_t)i * W + m], yn = Zk[(size_t)(i + 1) * W + m];
             const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
-            if (sw) {
-              Zk[(size_t)i * W + m] = yn;
-              Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yn, yi);
-            } else {
-              Zk[(size_t)(i + 1) * W + m] = fma(-mlt, yi, yn);
-            }
+            if (sw) Zk[(size_t)i * W + m] = yn;
+            Zk[(size_t)(i + 1) * W + m] = fma(-mlt, sw ? yn : yi, sw ? yi : yn);
           }
           double x1 = 0.0, x2 = 0.0;
           for (int i = W - 1; i >= 0; --i) {
