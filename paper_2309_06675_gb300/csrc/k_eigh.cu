@@ -423,26 +423,18 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
           const double ei = ee[i];
           const double a = dd[i + 1] - lam;
           const double bb = i + 2 < W ? ee[i + 1] : 0.0;
-          if (fabs(q0) >= fabs(ei)) {
-            if (q0 == 0.0) q0 = tiny;
-            const double r = 1.0 / q0;
-            const double mlt = ei * r;
-            rU0[i * 32 + lane] = r; U1[i * 32 + lane] = q1; U2[i * 32 + lane] = q2;
-            ML[i * 32 + lane] = mlt;
-            q0 = fma(-mlt, q1, a);
-            q1 = fma(-mlt, q2, bb);
-            q2 = 0.0;
-          } else {
-            const double r = 1.0 / ei;
-            const double mlt = q0 * r;
-            rU0[i * 32 + lane] = r; U1[i * 32 + lane] = a; U2[i * 32 + lane] = bb;
-            ML[i * 32 + lane] = mlt;
-            piv |= 1ull << i;
-            const double n0 = fma(-mlt, a, q1);
-            q1 = fma(-mlt, bb, q2);
-            q0 = n0;
-            q2 = 0.0;
-          }
+          // the interchange only selects operands: one FP64 sequence for the whole warp
+          const bool sw = !(fabs(q0) >= fabs(ei));
+          const double den = sw ? ei : (q0 == 0.0 ? tiny : q0);
+          const double r = 1.0 / den;
+          const double mlt = (sw ? q0 : ei) * r;
+          rU0[i * 32 + lane] = r; U1[i * 32 + lane] = sw ? a : q1; U2[i * 32 + lane] = sw ? bb : q2;
+          ML[i * 32 + lane] = mlt;
+          if (sw) piv |= 1ull << i;
+          const double n0 = fma(-mlt, sw ? a : q1, sw ? q1 : a);
+          q1 = fma(-mlt, sw ? bb : q2, sw ? q2 : bb);
+          q0 = n0;
+          q2 = 0.0;
         }
         if (q0 == 0.0) q0 = tiny;
         rU0[(W - 1) * 32 + lane] = 1.0 / q0;
@@ -455,12 +447,9 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
           for (int i = 0; i + 1 < W; ++i) {
             const double mlt = ML[i * 32 + lane];
             const double yi = Z[i * LDU + m], yn = Z[(i + 1) * LDU + m];
-            if ((piv >> i) & 1ull) {
-              Z[i * LDU + m] = yn;
-              Z[(i + 1) * LDU + m] = fma(-mlt, yn, yi);
-            } else {
-              Z[(i + 1) * LDU + m] = fma(-mlt, yi, yn);
-            }
+            const bool sw = (piv >> i) & 1ull;
+            if (sw) Z[i * LDU + m] = yn;
+            Z[(i + 1) * LDU + m] = fma(-mlt, sw ? yn : yi, sw ? yi : yn);
           }
           double x1 = 0.0, x2 = 0.0;   // x_{i+1}, x_{i+2}
           for (int i = W - 1; i >= 0; --i) {

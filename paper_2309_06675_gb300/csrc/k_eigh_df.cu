@@ -677,22 +677,17 @@ __global__ void __launch_bounds__(128) iit_df_kernel(int W, int n, EighBufs b,
           const Df a = df_sub(ldf(dd, i + 1), lam);
           const Df bb = i + 2 < W ? ldf(ee, i + 1) : Df{0.f, 0.f};
           const size_t o = (size_t)i * ldt + t;
-          if (fabsf(q0.h) >= fabsf(ei.h)) {
-            if (q0.h == 0.f) q0 = Df{tiny, 0.f};
-            const Df r = df_div(Df{1.f, 0.f}, q0);
-            const Df mlt = df_mul(ei, r);
-            sdf(RP, o, r); sdf(ML, o, mlt); sdf(U1, o, q1);
-            q0 = df_sub(a, df_mul(mlt, q1));
-            q1 = bb;
-          } else {
-            const Df r = df_div(Df{1.f, 0.f}, ei);
-            const Df mlt = df_mul(q0, r);
-            sdf(RP, o, r); sdf(ML, o, mlt); sdf(U1, o, a);
-            if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64);
-            const Df n0 = df_sub(q1, df_mul(mlt, a));
-            q1 = df_neg(df_mul(mlt, bb));
-            q0 = n0;
-          }
+          // the interchange only selects operands: one instruction sequence for the warp
+          const bool sw = !(fabsf(q0.h) >= fabsf(ei.h));
+          const Df den = sw ? ei : (q0.h == 0.f ? Df{tiny, 0.f} : q0);
+          const Df r = df_div(Df{1.f, 0.f}, den);
+          const Df mlt = df_mul(sw ? q0 : ei, r);
+          sdf(RP, o, r); sdf(ML, o, mlt); sdf(U1, o, sw ? a : q1);
+          if (sw) { if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64); }
+          const Df n0 = df_sub(sw ? q1 : a, df_mul(mlt, sw ? a : q1));
+          const Df mb = df_mul(mlt, bb);
+          q1 = sw ? df_neg(mb) : bb;
+          q0 = n0;
         }
         if (q0.h == 0.f) q0 = Df{tiny, 0.f};
         sdf(RP, (size_t)(W - 1) * ldt + t, df_div(Df{1.f, 0.f}, q0));
@@ -706,13 +701,9 @@ __global__ void __launch_bounds__(128) iit_df_kernel(int W, int n, EighBufs b,
             const bool sw = i < 64 ? ((piv0 >> i) & 1ull) : ((piv1 >> (i - 64)) & 1ull);
             const Df mlt = ldf(ML, (size_t)i * ldt + t);
             const Df yn = ldf(Zs, (size_t)(i + 1) * ldt);
-            if (sw) {
-              sdf(Zs, (size_t)i * ldt, yn);
-              cur = df_sub(cur, df_mul(mlt, yn));
-            } else {
-              sdf(Zs, (size_t)i * ldt, cur);
-              cur = df_sub(yn, df_mul(mlt, cur));
-            }
+            const Df f = sw ? yn : cur, g = sw ? cur : yn;
+            sdf(Zs, (size_t)i * ldt, f);
+            cur = df_sub(g, df_mul(mlt, f));
           }
           sdf(Zs, (size_t)(W - 1) * ldt, cur);
           // back substitution U x = y (U2 of row i: e_i+1 on swapped rows, else 0)
