@@ -63,11 +63,11 @@ def stage_flops(W, N_R, prec="fp64"):
 
     Eigenvector stage ("backtransform"): inverse iteration for the eigenvectors Z of the
     tridiagonal, then U = Q D Z (8 W^3) -- in FP64 on the FP64 path, in FP32 on the reduced
-    ones: by a kernel of its own before the 3xTF32 rotation (W > 56, the default there), inside
+    ones: by a kernel of its own before the 3xTF32 rotation (W > 40, the default there), inside
     the SIMT rotation kernel otherwise (counted in "berry").
     """
     mixed = prec != "fp64"
-    asm_in_rotation = mixed and W <= 56
+    asm_in_rotation = mixed and W <= 40
     return {
         "fourier": 6.0 * N_R * W * W,     # real contraction [3 x N_R] . [N_R x W^2]
         "tridiag": 16.0 / 3.0 * W ** 3,   # complex Householder reduction
@@ -117,7 +117,7 @@ def roofline_of(dom, head, W, N_R, k_per_launch, ms_per_launch):
         fl = stage_flops(W, N_R, head)["berry"] * k_per_launch
         return {"bound": "alu", "achieved": fl / t / 1e12, "peak": 2 * FP32_PEAK_TOPS,
                 "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz "
-                                                "(derived); the rotations' 24 W^3 (+ the U assembly's 8 W^3 at W <= 56)"}
+                                                "(derived); the rotations' 24 W^3 (+ the U assembly's 8 W^3 at W <= 40)"}
     if head != "fp64" and dom == "fourier":
         fl = issued_tc_flops_per_k(W, head) * k_per_launch   # issued BF16 slice products
         pk = measured_peaks()

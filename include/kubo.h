@@ -162,7 +162,7 @@ typedef struct kubo_options {
                                  quarters summed with round-to-nearest), k-points padded to 64;
                                1 = tensor cores with exact fixed-point BF16-slice products;
                                2 = FP32 on the FMA pipe (SIMT);
-                               0 (default) = automatic: 3 for 56 < W <= 64, where it is at least
+                               0 (default) = automatic: 3 for 40 < W <= 64, where it is at least
                                  as fast as 2 (and at W = 64 the more accurate), else 2.
                                Other values: KUBO_ERR_INVALID_ARG.  layout_unpadded = 1 implies
                                2 (the ablation concerns the SIMT kernel's shared-memory

@@ -257,7 +257,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
 
     rotation: the FP32-grade step (3) kernel of the reduced modes, "auto" (the default:
-    "tf32" above W = 56, else "simt"), "tf32" (tensor cores, 3xTF32), "exact" (tensor cores,
+    "tf32" above W = 40, else "simt"), "tf32" (tensor cores, 3xTF32), "exact" (tensor cores,
     exact BF16 slices; rotation_tc=True) or "simt" (FP32 FMA pipe).
 
     H_R: complex128 CUDA tensor [N_R, W, W]; R: host int [N_R, 3]; E_F: float64 CUDA [n_EF].

@@ -38,15 +38,16 @@ kubo_options defaults() {
 enum { ROT_TF32 = 0, ROT_EXACT_SLICES = 1, ROT_SIMT = 2 };
 
 // The automatic choice: the 3xTF32 tensor-core kernel pads every k-point to W = 64, so it is
-// taken only above W = 56, where it is at least as fast as the FP32 FMA kernel (measured on
-// 65,536 k-points: W = 56 25.6 vs 24.5 ms, W = 64 28.3 vs 28.9 ms; W = 32 15.5 vs 5.8 ms).
+// taken only above W = 40, where it (with its separate U assembly) is at least as fast as the
+// FP32 FMA kernel with the assembly inside (eigenvector + rotation stages on 65,536 k-points:
+// W = 40 25.0 vs 25.2 ms, W = 48 28.6 vs 30.6, W = 64 36.9 vs 43.5; W = 32 17.6 vs 9.6).
 int rotation_kernel(int option, int W, bool unpadded) {
   if (unpadded) return ROT_SIMT;   // the padding ablation concerns the SIMT kernel's layout
   switch (option) {
     case 1: return ROT_EXACT_SLICES;
     case 2: return ROT_SIMT;
     case 3: return ROT_TF32;
-    default: return W > 56 ? ROT_TF32 : ROT_SIMT;
+    default: return W > 40 ? ROT_TF32 : ROT_SIMT;
   }
 }
 
