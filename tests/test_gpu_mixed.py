@@ -182,16 +182,23 @@ def test_rotation_kernels_vs_fp64(kubo, torch, m64):
     assert errs[("mixed_rotation", "tf32")] <= 1.5 * errs[("mixed_rotation", "simt")]
 
 
+@pytest.mark.parametrize("prec", ["mixed_rotation", "mixed"])
 @pytest.mark.parametrize("rot", ["tf32", "exact"])
 @pytest.mark.parametrize("W", [5, 16, 33, 64])
-def test_tensor_core_rotation_small_orders_per_k(kubo, torch, W, rot):
+def test_tensor_core_rotation_small_orders_per_k(kubo, torch, W, rot, prec):
+    """Per-k parity of the tensor-core rotations at orders padded to 64, odd ones included:
+    from the FP64 Fourier sum (MIXED_ROTATION: FP64 velocity rows, U assembled inside the
+    kernel) and from the tensor-core one (MIXED: FP32 velocity rows, 3xTF32 with U formed by
+    its own kernel)."""
     m = tbgen.random_tb(W, 2 if W < 64 else 1, 1.2, 300 + W)
     kmesh = (16, 16, 16)
     kidx = tbgen.k_sample(kmesh, 150, seed=W)
     E, Om = kubo.ahc_k(cuda(torch, m.H_R), m.R, kmesh, cuda(torch, kidx), etas=[1e-3, 0.05],
-                       precision="mixed_rotation", rotation=rot)
+                       precision=prec, rotation=rot)
     E_ref, Om_ref = O.kubo_per_k(m.H_R, m.R, kmesh, kidx, [1e-3, 0.05])
-    assert np.max(np.abs(E.cpu().numpy() - E_ref)) <= 1e-12 * np.max(np.abs(E_ref))
+    # FP64 Fourier sum: FP64-grade eigenvalues; tensor-core one: its 2^-31 slicing of H(k)
+    etol = 1e-12 if prec == "mixed_rotation" else 1e-7
+    assert np.max(np.abs(E.cpu().numpy() - E_ref)) <= etol * np.max(np.abs(E_ref))
     for e in range(2):
         scale = np.max(np.abs(Om_ref[e]), axis=-1)
         err = np.max(np.abs(Om.cpu().numpy()[e] - Om_ref[e]), axis=-1) / scale
