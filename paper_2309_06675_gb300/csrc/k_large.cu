@@ -8,8 +8,10 @@
 //   cgemm_herm_u_kernel   T = dH U   (dH from packed Hermitian rows)          } FP64 or FP32
 //   cgemm_uh_t_kernel     V = U^H T                                            } arithmetic
 //   curvature_large_kernel Omega_n = sum_{m != n} T_nm, every pair evaluated from the upper
-//                         triangle (exact antisymmetry), FP64 denominators for every eta
+//                         triangle (exact antisymmetry), FP64 energy differences for every
+//                         eta (FP32 quotients for FP32 velocities)
 #include <algorithm>
+#include <type_traits>
 
 #include "kubo_internal.cuh"
 
@@ -408,6 +410,23 @@ __global__ void __launch_bounds__(256) cgemm_uh_t_kernel(const typename cx<T>::t
     }
 }
 
+// a b - c d within 2 ulp (Kahan: the rounding error of c d is recovered exactly by an FMA)
+__device__ __forceinline__ float large_diff_of_products(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = fmaf(-c, d, w);
+  const float f = fmaf(a, b, -w);
+  return __fadd_rn(f, e);
+}
+// (hi, lo) += x with the rounding error of hi + x carried exactly into lo (Knuth's TwoSum)
+__device__ __forceinline__ void large_two_sum_acc(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float ap = __fsub_rn(s, bp);
+  const float err = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
 // ------------------------------------------------------------------ curvature, thread per band
 template <typename T>
 __global__ void __launch_bounds__(LW_MAX) curvature_large_kernel(const double* __restrict__ E,
@@ -432,10 +451,58 @@ __global__ void __launch_bounds__(LW_MAX) curvature_large_kernel(const double* _
   const int n = t;
   if (n >= W) return;
   const double thr2 = (1e-12 * s_emax) * (1e-12 * s_emax);
+  const size_t base = (size_t)k * W * W;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 velocities: the numerator is FP32-grade already, so the quotient is formed in FP32
+    // as in the W <= 64 kernels -- dE = E_p - E_q, its square and the eta = 0 cut-off in FP64,
+    // Kahan's difference of products for Im(v^x v^y), the sums as exact FP32 pairs (Knuth's
+    // TwoSum), and the FP64 quotient for a denominator below 2^-86 (eta and a gap below
+    // ~1e-13).  Both orders of a pair read the same (p < q) entry with the same arithmetic, so
+    // T_mn = -T_nm holds exactly.
+    float hi[MAXE], lo[MAXE];
+    float eta2[MAXE];
+#pragma unroll
+    for (int e = 0; e < MAXE; ++e) {
+      hi[e] = 0.f;
+      lo[e] = 0.f;
+      eta2[e] = e < n_eta ? (float)(etas[e] * etas[e]) : 0.f;
+    }
+    double fb[MAXE];   // FP64 fallback terms
+#pragma unroll
+    for (int e = 0; e < MAXE; ++e) fb[e] = 0.0;
+    for (int m = 0; m < W; ++m) {
+      if (m == n) continue;
+      const int p = n < m ? n : m, q = n < m ? m : n;
+      const float2 vx = Vx[base + (size_t)p * W + q];
+      const float2 vy = Vy[base + (size_t)p * W + q];
+      const float num = -2.0f * large_diff_of_products(vx.y, vy.x, vx.x, vy.y);
+      const double dE = sE[p] - sE[q];
+      const double d2 = dE * dE;
+      const float d2f = (float)d2;
+      const bool small0 = d2 <= thr2;
+      const float sgn = n < m ? 1.f : -1.f;
+#pragma unroll
+      for (int e = 0; e < MAXE; ++e) {
+        if (e >= n_eta) break;
+        if (eta2[e] == 0.f && small0) continue;
+        const float den = d2f + eta2[e];
+        if (den < 0x1p-86f) {
+          fb[e] += (double)sgn * ((double)num / fma(etas[e], etas[e], d2));
+        } else {
+          large_two_sum_acc(hi[e], lo[e], sgn * (num / den));
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < MAXE; ++e) {
+      if (e >= n_eta) break;
+      Om[e * eta_stride + k * W + n] = ((double)hi[e] + (double)lo[e]) + fb[e];
+    }
+    return;
+  }
   double rp[MAXE];
 #pragma unroll
   for (int e = 0; e < MAXE; ++e) rp[e] = 0.0;
-  const size_t base = (size_t)k * W * W;
   for (int m = 0; m < W; ++m) {
     if (m == n) continue;
     const int p = n < m ? n : m, q = n < m ? m : n;
