@@ -272,6 +272,216 @@ __global__ void __launch_bounds__(RB_NT) reflect_large_kernel(int W, EighBufs b,
   }
 }
 
+// ------------------------------------------------------------------ U = Q D Z in FP32, blocked
+// For the FP32 rotations: Q = H_0 ... H_{W-3} applied in blocks of WY_NB = 8 reflectors in the
+// compact WY form I - V T V^H (T upper triangular: T_ii = tau_i,
+// T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i], G = V^H V), last block first.
+//   wy_factors_kernel: one CTA per k-point; V of every block in FP32, row-major [W][WY_LDV]
+//     (8 reflectors per row, zeros above each reflector's first row, rows padded to 80 bytes),
+//     and T, into a per-k scratch.
+//   reflect_wy_kernel: one CTA per (k-point, 32-column block); D Z of the block in shared
+//     memory; thread (column c, row lane q) owns rows q, q + 8, ...; per block s = V^H u
+//     (partial sums over the lane's rows from the block's first row down, three shuffles),
+//     y_q = (T s)_q, an exchange, u -= V y.  Blocks are double-buffered by cp.async.
+constexpr int WY_NB = 8;
+constexpr int WY_LDV = 10;   // float2 per staged row (8 + 2 pad: 80 bytes)
+
+__host__ __device__ __forceinline__ int wy_nblk(int W) { return W > 2 ? (W - 2 + WY_NB - 1) / WY_NB : 0; }
+__host__ __device__ __forceinline__ size_t wy_v_elems(int W) { return (size_t)wy_nblk(W) * W * WY_LDV; }
+__host__ __device__ __forceinline__ size_t wy_bytes_per_k(int W) {
+  return (wy_v_elems(W) + (size_t)wy_nblk(W) * WY_NB * WY_NB) * sizeof(float2);
+}
+
+__device__ __forceinline__ float2 wy_cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__global__ void __launch_bounds__(256) wy_factors_kernel(int W, EighBufs b,
+                                                         float2* __restrict__ wy) {
+  __shared__ float2 sV[LW_MAX * WY_LDV];
+  __shared__ float2 sG[WY_NB * WY_NB];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t k = blockIdx.x;
+  const int nref = W - 2, nblk = wy_nblk(W);
+  const double2* R = b.refl + (size_t)k * W * W;
+  const double* tau = b.tau + k * W;
+  float2* Vk = wy + (size_t)k * (wy_bytes_per_k(W) / sizeof(float2));
+  float2* Tk = Vk + wy_v_elems(W);
+  for (int bk = 0; bk < nblk; ++bk) {
+    const int j0 = bk * WY_NB;
+    __syncthreads();   // the previous block's stage is no longer read
+    for (int idx = t; idx < W * WY_NB; idx += 256) {
+      const int r = idx >> 3, a = idx & 7, c = j0 + a;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < nref && r > c) {
+        const double2 d = R[(size_t)r * W + c];
+        v = make_float2((float)d.x, (float)d.y);
+      }
+      sV[r * WY_LDV + a] = v;
+      Vk[((size_t)bk * W + r) * WY_LDV + a] = v;
+    }
+    __syncthreads();
+    // G[a][a2] (a < a2): 32 lane groups of 8, group g sums pair g over rows q, q + 8, ...
+    {
+      const int g = warp * 4 + (lane >> 3), q = lane & 7;
+      int a = 0, rem = g < WY_NB * (WY_NB - 1) / 2 ? g : 0;
+      while (rem >= WY_NB - 1 - a) {
+        rem -= WY_NB - 1 - a;
+        ++a;
+      }
+      const int a2 = a + 1 + rem;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int r = j0 + a2 + 1 + q; r < W; r += 8) {
+        const float2 x = sV[r * WY_LDV + a], y = sV[r * WY_LDV + a2];
+        acc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x));   // conj(x) y
+        acc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc.y));
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, 8);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, 8);
+      }
+      if (q == 0 && g < WY_NB * (WY_NB - 1) / 2) sG[a * WY_NB + a2] = acc;
+    }
+    __syncthreads();
+    // T: lane a of warp 0 keeps row a
+    if (warp == 0) {
+      float2 trow[WY_NB];
+#pragma unroll
+      for (int i = 0; i < WY_NB; ++i) {
+        const float ti = j0 + i < nref ? (float)tau[j0 + i] : 0.f;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k2 = 0; k2 < i; ++k2) {
+          if (k2 >= lane) {
+            const float2 pr = wy_cmul(trow[k2], sG[k2 * WY_NB + i]);
+            acc.x += pr.x;
+            acc.y += pr.y;
+          }
+        }
+        trow[i] = lane < i ? make_float2(-ti * acc.x, -ti * acc.y)
+                           : (lane == i ? make_float2(ti, 0.f) : make_float2(0.f, 0.f));
+      }
+      if (lane < WY_NB)
+#pragma unroll
+        for (int i = 0; i < WY_NB; ++i) Tk[((size_t)bk * WY_NB + lane) * WY_NB + i] = trow[i];
+    }
+  }
+}
+
+__device__ __forceinline__ void wy_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+__global__ void __launch_bounds__(RB_NT) reflect_wy_kernel(int W, EighBufs b,
+                                                           const double* __restrict__ Z,
+                                                           const float2* __restrict__ wy,
+                                                           float2* __restrict__ Uout) {
+  extern __shared__ __align__(16) unsigned char wy_smem[];
+  const int LDB = RB_COLS + 1;
+  float2* ub = reinterpret_cast<float2*>(wy_smem);                        // [W][LDB]
+  float2* vbuf = ub + (((size_t)W * LDB + 1) & ~(size_t)1);             // 2 x [W][WY_LDV]
+  float2* tbuf = vbuf + 2 * (size_t)W * WY_LDV;                           // 2 x [NB][NB]
+  const int t = threadIdx.x;
+  const int c0 = blockIdx.y * RB_COLS;
+  const int64_t k = blockIdx.x;
+  const int ncol = min(RB_COLS, W - c0);
+  const int nblk = wy_nblk(W);
+  const float2* Vk = wy + (size_t)k * (wy_bytes_per_k(W) / sizeof(float2));
+  const float2* Tk = Vk + wy_v_elems(W);
+  const size_t vblk = (size_t)W * WY_LDV;   // float2 per staged V block (a multiple of 2)
+  auto fetch = [&](int bk, int buf) {
+    const float4* src = reinterpret_cast<const float4*>(Vk + (size_t)bk * vblk);
+    float4* dst = reinterpret_cast<float4*>(vbuf + (size_t)buf * vblk);
+    for (int i = t; i < (int)(vblk / 2); i += RB_NT) wy_cp16(dst + i, src + i);
+    const float4* ts = reinterpret_cast<const float4*>(Tk + (size_t)bk * WY_NB * WY_NB);
+    float4* td = reinterpret_cast<float4*>(tbuf + (size_t)buf * WY_NB * WY_NB);
+    if (t < WY_NB * WY_NB / 2) wy_cp16(td + t, ts + t);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (nblk > 0) fetch(nblk - 1, (nblk - 1) & 1);
+  const double* Zk = Z + (size_t)k * W * W;
+  const double2* ph = b.phase + k * W;
+  for (int idx = t; idx < W * RB_COLS; idx += RB_NT) {
+    const int r = idx / RB_COLS, c = idx % RB_COLS;
+    float2 u = make_float2(0.f, 0.f);
+    if (c < ncol) {
+      const float z = (float)Zk[(size_t)r * W + c0 + c];
+      const double2 p = ph[r];
+      u = make_float2((float)p.x * z, (float)p.y * z);
+    }
+    ub[r * LDB + c] = u;
+  }
+  const int c = t >> 3, q = t & 7;
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int buf = bk & 1;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // block bk landed; the other buffer (block bk + 1) is no longer read
+    if (bk > 0) fetch(bk - 1, buf ^ 1);
+    const float4* V4 = reinterpret_cast<const float4*>(vbuf + (size_t)buf * vblk);
+    const float2* T = tbuf + (size_t)buf * WY_NB * WY_NB;
+    const int r0 = bk * WY_NB + 1;   // first row a reflector of the block touches
+    const int rs = q >= r0 ? q : q + ((r0 - q + 7) >> 3) * 8;   // first own row >= r0
+    float2 sv[WY_NB];
+#pragma unroll
+    for (int a = 0; a < WY_NB; ++a) sv[a] = make_float2(0.f, 0.f);
+    for (int r = rs; r < W; r += 8) {
+      const float2 u = ub[r * LDB + c];
+#pragma unroll
+      for (int a2 = 0; a2 < WY_NB / 2; ++a2) {
+        const float4 v = V4[r * (WY_LDV / 2) + a2];
+        sv[2 * a2].x = fmaf(v.x, u.x, fmaf(v.y, u.y, sv[2 * a2].x));   // conj(v) u
+        sv[2 * a2].y = fmaf(v.x, u.y, fmaf(-v.y, u.x, sv[2 * a2].y));
+        sv[2 * a2 + 1].x = fmaf(v.z, u.x, fmaf(v.w, u.y, sv[2 * a2 + 1].x));
+        sv[2 * a2 + 1].y = fmaf(v.z, u.y, fmaf(-v.w, u.x, sv[2 * a2 + 1].y));
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < WY_NB; ++a)
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        sv[a].x += __shfl_xor_sync(0xffffffffu, sv[a].x, o);
+        sv[a].y += __shfl_xor_sync(0xffffffffu, sv[a].y, o);
+      }
+    // lane q forms y_q = sum_{a2 >= q} T[q][a2] s[a2]; then every lane gathers all eight
+    float2 yq = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a2 = 0; a2 < WY_NB; ++a2) {
+      if (a2 >= q) {
+        const float2 pr = wy_cmul(T[q * WY_NB + a2], sv[a2]);
+        yq.x += pr.x;
+        yq.y += pr.y;
+      }
+    }
+    float2 y[WY_NB];
+#pragma unroll
+    for (int a = 0; a < WY_NB; ++a) {
+      y[a].x = __shfl_sync(0xffffffffu, yq.x, a, 8);
+      y[a].y = __shfl_sync(0xffffffffu, yq.y, a, 8);
+    }
+    for (int r = rs; r < W; r += 8) {
+      float2 u = ub[r * LDB + c];
+#pragma unroll
+      for (int a2 = 0; a2 < WY_NB / 2; ++a2) {
+        const float4 v = V4[r * (WY_LDV / 2) + a2];
+        u.x = fmaf(-v.x, y[2 * a2].x, fmaf(v.y, y[2 * a2].y, u.x));   // u -= v y
+        u.y = fmaf(-v.x, y[2 * a2].y, fmaf(-v.y, y[2 * a2].x, u.y));
+        u.x = fmaf(-v.z, y[2 * a2 + 1].x, fmaf(v.w, y[2 * a2 + 1].y, u.x));
+        u.y = fmaf(-v.z, y[2 * a2 + 1].y, fmaf(-v.w, y[2 * a2 + 1].x, u.y));
+      }
+      ub[r * LDB + c] = u;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  float2* Uk = Uout + (size_t)k * W * W;
+  for (int idx = t; idx < W * RB_COLS; idx += RB_NT) {
+    const int r = idx / RB_COLS, cc = idx % RB_COLS;
+    if (cc < ncol) Uk[(size_t)r * W + c0 + cc] = ub[r * LDB + cc];
+  }
+}
+
 // ------------------------------------------------------------------ batched complex GEMMs
 // 64 x 64 output tile per CTA, 16 x 16 threads with 4 x 4 strided micro-tiles, K tiles of 16.
 
@@ -561,6 +771,23 @@ cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, void
     if (e != cudaSuccess) return e;
     reflect_large_kernel<double><<<grid, RB_NT, sm, s>>>(W, b, Z, (double2*)U);
   }
+  return cudaGetLastError();
+}
+
+size_t reflect_wy_scratch_bytes(int W) { return wy_bytes_per_k(W); }
+
+cudaError_t launch_reflect_wy(int W, int n, EighBufs b, const double* Z, float2* U, float2* wy,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (W > LW_MAX || W < 3 || ((uintptr_t)wy & 15)) return cudaErrorInvalidValue;
+  wy_factors_kernel<<<n, 256, 0, s>>>(W, b, wy);
+  const size_t sm = ((((size_t)W * (RB_COLS + 1) + 1) & ~(size_t)1) + 2 * (size_t)W * WY_LDV +
+                     2 * WY_NB * WY_NB) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(reflect_wy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(n, (W + RB_COLS - 1) / RB_COLS);
+  reflect_wy_kernel<<<grid, RB_NT, sm, s>>>(W, b, Z, wy, U);
   return cudaGetLastError();
 }
 

@@ -173,7 +173,10 @@ struct Plan {
 // the tridiagonal, then the FP64 rotation products T, V^x, V^y (the larger of the two).
 size_t large_region_bytes(int W) {
   const size_t WW = (size_t)W * W;
-  return std::max(WW * sizeof(double), 3 * WW * sizeof(double2));
+  // (Z and the FP32 compact-WY factors of the U assembly, 256 bytes of alignment per batch
+  // included, fit in the rotation products' share at every W > 64)
+  return std::max(WW * sizeof(double) + reflect_wy_scratch_bytes(W) + 256,
+                  3 * WW * sizeof(double2));
 }
 
 // persistent inverse-iteration CTAs of a plan (their LU scratch is per CTA)
@@ -540,6 +543,12 @@ cudaError_t eigh_vectors(const Call& c, int n, const EighBufs& eb, double* E, do
                       ? launch_iit_df(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s)
                       : launch_iit(p.W, n, eb, E, Z, c.at<double>(p.o_iit), p.iit_slots, c.s, rq);
   if (e != cudaSuccess || !U) return e;
+  if (f32u) {
+    // the blocked WY factors in the large region after Z (16-byte aligned, within its size)
+    const uintptr_t after_z = (uintptr_t)(Z + (size_t)std::max(1, p.chunk) * p.W * p.W);
+    float2* wy = reinterpret_cast<float2*>((after_z + 255) & ~(uintptr_t)255);
+    return launch_reflect_wy(p.W, n, eb, Z, reinterpret_cast<float2*>(U), wy, c.s);
+  }
   return launch_reflect_large(p.W, n, eb, Z, U, f32u, c.s);
 }
 

@@ -272,6 +272,11 @@ cudaError_t launch_iit(int W, int n, EighBufs b, double* E, double* Z, double* s
 // U: float2 [n][W][W] when f32 (formed in FP32 for the FP32 rotations), else double2
 cudaError_t launch_reflect_large(int W, int n, EighBufs b, const double* Z, void* U, bool f32,
                                  cudaStream_t s);
+// U = Q D Z in FP32 by blocked compact-WY products (W > 64, the FP32-rotation modes): per-k
+// FP32 factors in wy (reflect_wy_scratch_bytes(W) per k-point, 16-byte aligned)
+size_t reflect_wy_scratch_bytes(int W);
+cudaError_t launch_reflect_wy(int W, int n, EighBufs b, const double* Z, float2* U, float2* wy,
+                              cudaStream_t s);
 // steps (3)-(4) as batched complex GEMMs: X, Y packed Hermitian rows of leading dimension ld;
 // f32 = FP32 products.  Tbuf, Vx, Vy: n * W * W complex elements (of the product type) each.
 cudaError_t launch_berry_large(const double* E, const void* U, const double* X, const double* Y,
