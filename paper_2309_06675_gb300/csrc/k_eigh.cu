@@ -42,23 +42,29 @@ __device__ __forceinline__ int tri(int r, int c) { return (r * (r + 1) >> 1) + c
 
 // Packed rows of leading dimension ld (W*W for the FP64 Fourier kernel, the padded row of
 // H | dxH | dyH for the tensor-core one).  The reduction is FP64.
-template <typename T>
-__global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
+// threads of the reduction's CTA
+__host__ __device__ __forceinline__ int tridiag_threads(int W) { return W > 64 ? 512 : 256; }
+
+// NTT threads: 256 (five CTAs per SM at W <= 64), or 512 for W > 64, where one CTA (136 KB of
+// shared memory at W = 128) holds an SM and more warps cover its barriers (W = 128: 235 ->
+// 229 ms per 18,432 k-points; 1,024 threads with twice the symv parts: 240 ms)
+template <typename T, int NTT>
+__global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
                                                      EighBufs b) {
   extern __shared__ double2 smem2[];
   double2* A = smem2;                              // lower triangle, packed by rows
   double2* vb = A + (size_t)W * (W + 1) / 2;       // [W] reflector (contiguous copy)
   double2* pb = vb + W;                            // [W] p, then w
   double2* be = pb + W;                            // [W] complex sub-diagonal beta_i
-  double2* sp = be + W;                            // [NT] partial sums of the symv
-  double* tb = (double*)(sp + NT);                 // [W] tau_i
+  double2* sp = be + W;                            // [NTT] partial sums of the symv
+  double* tb = (double*)(sp + NTT);                 // [W] tau_i
   __shared__ double s_tau, s_K;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t k = blockIdx.x;
   const T* P = Hp + (size_t)k * ld;
 
-  for (int idx = t; idx < W * (W + 1) / 2; idx += NT) {
+  for (int idx = t; idx < W * (W + 1) / 2; idx += NTT) {
     int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
     while (tri(r, 0) > idx) --r;
     while (tri(r + 1, 0) <= idx) ++r;
@@ -121,18 +127,18 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
     __syncthreads();
     const double tau = s_tau;
     if (tau != 0.0) {
-      for (int r = t; r < m; r += NT) vb[r] = A[tri(o + r, i)];
+      for (int r = t; r < m; r += NTT) vb[r] = A[tri(o + r, i)];
       __syncthreads();
       // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r).  The m x m
       // product is spread over the block: thread t takes row r = t mod m and the columns
-      // c = part, part + P, ... (part = t / m, P = min(NT / m, cap) parts per row, cap = 4 by
+      // c = part, part + P, ... (part = t / m, P = min(NTT / m, cap) parts per row, cap = 4 by
       // default), so that the warps issue full; the P partial sums of a row are added in part
       // order by the m row threads.  P is capped: for a small trailing block more parts would
       // shorten the product but lengthen that sum, whose warps run with m of their 32 lanes
       // (the other CTAs of the SM keep the FP64 pipe busy meanwhile).  The conjugate of the mirrored
       // element flips a sign bit on the integer side (no FP64 instruction).
       {
-        const int P = max(1, min(NT / m, b.symv_parts));
+        const int P = max(1, min(NTT / m, b.symv_parts));
         const int r = t % m, part = t / m;
         if (part < P) {
           double ax = 0.0, ay = 0.0;
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
           sp[part * m + r] = make_double2(ax, ay);
         }
         __syncthreads();
-        for (int rr = t; rr < m; rr += NT) {
+        for (int rr = t; rr < m; rr += NTT) {
           double sx = 0.0, sy = 0.0;
           for (int q = 0; q < P; ++q) {
             const double2 v = sp[q * m + rr];
@@ -171,14 +177,14 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
       }
       __syncthreads();
       const double K = s_K;
-      for (int r = t; r < m; r += NT) {
+      for (int r = t; r < m; r += NTT) {
         const double2 p = pb[r], v = vb[r];
         pb[r] = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
       }
       __syncthreads();
       // A22 <- A22 - v w^H - w v^H on the lower triangle (c <= r)
       const int ntri = m * (m + 1) / 2;
-      for (int idx = t; idx < ntri; idx += NT) {
+      for (int idx = t; idx < ntri; idx += NTT) {
         int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
         while (r * (r + 1) / 2 > idx) --r;
         while ((r + 1) * (r + 2) / 2 <= idx) ++r;
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
   // D_{j+1} = D_j beta_j / |beta_j| by one thread (4 FP64 operations per step)
   if (t == 0 && W >= 2) be[W - 2] = A[tri(W - 1, W - 2)];
   __syncthreads();
-  for (int j = t; j + 1 < W; j += NT) {
+  for (int j = t; j + 1 < W; j += NTT) {
     const double2 bj = be[j];
     const double a2 = fma(bj.x, bj.x, bj.y * bj.y);
     double a = 0.0;
@@ -232,12 +238,12 @@ __global__ void __launch_bounds__(NT, 5) tridiag_kernel(const T* __restrict__ Hp
     }
     eout[W - 1] = 0.0;
   }
-  for (int j = t; j < W; j += NT) {
+  for (int j = t; j < W; j += NTT) {
     dout[j] = A[tri(j, j)].x;
     tout[j] = j < W - 2 ? tb[j] : 0.0;
   }
   double2* rout = b.refl + (size_t)k * W * W;
-  for (int idx = t; idx < W * W; idx += NT) {
+  for (int idx = t; idx < W * W; idx += NTT) {
     int r = idx / W, c = idx % W;
     rout[idx] = r > c ? A[tri(r, c)] : make_double2(0.0, 0.0);
   }
@@ -547,7 +553,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
 }  // namespace
 
 size_t tridiag_smem(int W) {
-  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W + NT) * sizeof(double2) +
+  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W + tridiag_threads(W)) * sizeof(double2) +
          (size_t)W * sizeof(double);
 }
 size_t backtransform_smem(int W) {
@@ -559,23 +565,27 @@ size_t backtransform_smem(int W) {
 static int ql_threads(int W) { (void)W; return 32; }
 size_t ql_smem(int W) { return (size_t)(ql_threads(W) / 32) * 2 * W * 32 * sizeof(double); }
 
-cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s) {
+static cudaError_t launch_tridiag_ld(const double* Hp, int64_t ld, int W, int n, EighBufs b,
+                                     cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  size_t sm = tridiag_smem(W);
-  cudaError_t e = cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  tridiag_kernel<double><<<n, NT, sm, s>>>(Hp, (int64_t)W * W, W, b);
-  return cudaGetLastError();
+  const size_t sm = tridiag_smem(W);
+  auto go = [&](auto kern, int nt) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<n, nt, sm, s>>>(Hp, ld, W, b);
+    return cudaGetLastError();
+  };
+  return tridiag_threads(W) == 256 ? go(tridiag_kernel<double, 256>, 256)
+                                   : go(tridiag_kernel<double, 512>, 512);
+}
+
+cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s) {
+  return launch_tridiag_ld(Hp, (int64_t)W * W, W, n, b, s);
 }
 
 cudaError_t launch_tridiag_rows(const double* Hp, int64_t ld, int W, int n, EighBufs b,
                                 cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  size_t sm = tridiag_smem(W);
-  cudaError_t e = cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  tridiag_kernel<double><<<n, NT, sm, s>>>(Hp, ld, W, b);
-  return cudaGetLastError();
+  return launch_tridiag_ld(Hp, ld, W, n, b, s);
 }
 
 cudaError_t launch_ql(int W, int n, EighBufs b, DevStatus* st, cudaStream_t s) {
