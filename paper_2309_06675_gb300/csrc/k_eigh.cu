@@ -49,16 +49,18 @@ __host__ __device__ __forceinline__ int tridiag_threads(int W) { return W > 64 ?
 // shared memory at W = 128) holds an SM and more warps cover its barriers (W = 128: 235 ->
 // 229 ms per 18,432 k-points; 1,024 threads with twice the symv parts: 240 ms)
 template <typename T, int NTT>
-__global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
+__global__ void __launch_bounds__(NTT, NTT == 256 ? 6 : 1) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
                                                      EighBufs b) {
+  // 37.4 KB at W = 64, so that six CTAs share an SM: the reflector is read from its column of
+  // A (not copied), the symv partials share their array with p, and beta_i, tau_i go to the
+  // outputs as they are formed (beta_i into the phase row, which is rewritten at the end)
   extern __shared__ double2 smem2[];
   double2* A = smem2;                              // lower triangle, packed by rows
-  double2* vb = A + (size_t)W * (W + 1) / 2;       // [W] reflector (contiguous copy)
-  double2* pb = vb + W;                            // [W] p, then w
-  double2* be = pb + W;                            // [W] complex sub-diagonal beta_i
-  double2* sp = be + W;                            // [NTT] partial sums of the symv
-  double* tb = (double*)(sp + NTT);                 // [W] tau_i
+  double2* sp = A + (size_t)W * (W + 1) / 2;       // [NTT] partial sums of the symv
+  double2* pb = sp;                                // [W] p, then w (the symv's part-0 slots)
   __shared__ double s_tau, s_K;
+  double2* beg = b.phase + blockIdx.x * (int64_t)W;   // beta_i until the phases replace them
+  double* tout = b.tau + blockIdx.x * (int64_t)W;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t k = blockIdx.x;
@@ -107,19 +109,19 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const 
           const double bet = -ph * nrm;
           const double v0 = fma(ph, nrm, comp);
           double* Ao = reinterpret_cast<double*>(&A[tri(o, i)]);
-          double* bo = reinterpret_cast<double*>(&be[i]);
+          double* bo = reinterpret_cast<double*>(&beg[i]);
           Ao[lane] = v0;
           bo[lane] = bet;
           if (lane == 0) {
             const double tau = 1.0 / (nrm * (nrm + aa));
             s_tau = tau;
-            tb[i] = tau;
+            tout[i] = tau;
           }
         } else {
-          reinterpret_cast<double*>(&be[i])[lane] = comp;   // beta = alpha, no reflection
+          reinterpret_cast<double*>(&beg[i])[lane] = comp;   // beta = alpha, no reflection
           if (lane == 0) {
             s_tau = 0.0;
-            tb[i] = 0.0;
+            tout[i] = 0.0;
           }
         }
       }
@@ -127,8 +129,9 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const 
     __syncthreads();
     const double tau = s_tau;
     if (tau != 0.0) {
-      for (int r = t; r < m; r += NTT) vb[r] = A[tri(o + r, i)];
-      __syncthreads();
+      // v: column i of A from row o (its first entry v0 written by the scalar step); the symv
+      // reads it there (one address per warp), the later phases from a copy at sp + W
+      double2* vb = sp + W;
       // p = tau * A22 v  (lower storage: A22[r][c] = conj(A22[c][r]) for c > r).  The m x m
       // product is spread over the block: thread t takes row r = t mod m and the columns
       // c = part, part + P, ... (part = t / m, P = min(NTT / m, cap) parts per row, cap = 4 by
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const 
             double2 a = A[idx];
             const unsigned long long flip = c > r ? 0x8000000000000000ull : 0ull;
             a.y = __longlong_as_double(__double_as_longlong(a.y) ^ flip);
-            const double2 v = vb[c];
+            const double2 v = A[tri(o + c, i)];
             ax = fma(a.x, v.x, ax); ax = fma(-a.y, v.y, ax);
             ay = fma(a.x, v.y, ay); ay = fma(a.y, v.x, ay);
           }
@@ -169,11 +172,13 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const 
       if (warp == 0) {
         double sum = 0.0;   // Re(v^H p)
         for (int r = lane; r < m; r += 32) {
-          const double2 v = vb[r], p = pb[r];
+          const double2 v = A[tri(o + r, i)], p = pb[r];
           sum = fma(v.x, p.x, fma(v.y, p.y, sum));
         }
         sum = warp_sum(sum);
         if (lane == 0) s_K = 0.5 * tau * sum;
+      } else {
+        for (int r = t - 32; r < m; r += NTT - 32) vb[r] = A[tri(o + r, i)];
       }
       __syncthreads();
       const double K = s_K;
@@ -209,14 +214,13 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const 
   // outputs: d, |e|, phases D, tau, reflectors
   double* dout = b.d + k * W;
   double* eout = b.e + k * W;
-  double2* phout = b.phase + k * W;
-  double* tout = b.tau + k * W;
+  double2* phout = b.phase + k * W;   // = beg: beta_j until the running product replaces them
   // |beta_j| and the unit phases beta_j / |beta_j| in parallel, then their running product
   // D_{j+1} = D_j beta_j / |beta_j| by one thread (4 FP64 operations per step)
-  if (t == 0 && W >= 2) be[W - 2] = A[tri(W - 1, W - 2)];
+  if (t == 0 && W >= 2) beg[W - 2] = A[tri(W - 1, W - 2)];
   __syncthreads();
   for (int j = t; j + 1 < W; j += NTT) {
-    const double2 bj = be[j];
+    const double2 bj = beg[j];
     const double a2 = fma(bj.x, bj.x, bj.y * bj.y);
     double a = 0.0;
     double2 u = make_double2(1.0, 0.0);
@@ -226,21 +230,21 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 5 : 1) tridiag_kernel(const 
       u = make_double2(bj.x * ra, bj.y * ra);
     }
     eout[j] = a;
-    vb[j] = u;
+    sp[j] = u;
   }
   __syncthreads();
   if (t == 0) {
     double2 D = make_double2(1.0, 0.0);
     phout[0] = D;
     for (int j = 0; j + 1 < W; ++j) {
-      D = cmul(D, vb[j]);
+      D = cmul(D, sp[j]);
       phout[j + 1] = D;
     }
     eout[W - 1] = 0.0;
   }
   for (int j = t; j < W; j += NTT) {
     dout[j] = A[tri(j, j)].x;
-    tout[j] = j < W - 2 ? tb[j] : 0.0;
+    if (j >= W - 2) tout[j] = 0.0;   // tau_j of the reflections: written as formed
   }
   double2* rout = b.refl + (size_t)k * W * W;
   for (int idx = t; idx < W * W; idx += NTT) {
@@ -553,8 +557,8 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
 }  // namespace
 
 size_t tridiag_smem(int W) {
-  return ((size_t)W * (W + 1) / 2 + 3 * (size_t)W + tridiag_threads(W)) * sizeof(double2) +
-         (size_t)W * sizeof(double);
+  // packed triangle + the symv partials (at least 2 W: p and the copy of v)
+  return ((size_t)W * (W + 1) / 2 + std::max(tridiag_threads(W), 2 * W)) * sizeof(double2);
 }
 size_t backtransform_smem(int W) {
   return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
