@@ -253,6 +253,225 @@ __global__ void __launch_bounds__(NTT, NTT == 256 ? 6 : 1) tridiag_kernel(const 
   }
 }
 
+// Two k-points per 512-thread CTA (W <= 64; three CTAs per SM, the same six k-points per SM
+// as the one-k kernel).  Half h = t / 256 works on k-point 2 blockIdx + h with the one-k
+// kernel's thread layout; the per-column steps that one warp runs -- the norm of the column,
+// the Householder scalar step and Re(v^H p) -- run for both k-points in warp 0 (lanes 0-15 /
+// 16-31 for the reductions, lanes 0-1 / 2-3 for the scalar step), so each of those FP64
+// instructions serves two k-points, and every block barrier serves two.  A half whose
+// k-point is absent (odd count) or whose column needs no reflection idles through the phases.
+__global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restrict__ Hp,
+                                                          int64_t ld, int W, int n, EighBufs b) {
+  extern __shared__ double2 smem2[];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int h = t >> 8, th = t & 255;
+  const size_t per_k = (size_t)W * (W + 1) / 2 + 256;   // triangle + partials
+  double2* A = smem2 + h * per_k;
+  double2* sp = A + (size_t)W * (W + 1) / 2;
+  double2* pb = sp;
+  __shared__ double s_tau[2], s_K[2];
+  const int64_t k = 2 * (int64_t)blockIdx.x + h;
+  const bool live = k < n;
+  double2* beg = b.phase + k * W;
+  double* tout = b.tau + k * W;
+  const double* P = Hp + (size_t)k * ld;
+
+  if (live)
+    for (int idx = th; idx < W * (W + 1) / 2; idx += 256) {
+      int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+      while (tri(r, 0) > idx) --r;
+      while (tri(r + 1, 0) <= idx) ++r;
+      const int c = idx - tri(r, 0);
+      A[idx] = r == c ? make_double2(P[r * W + r], 0.0)
+                      : make_double2(P[c * W + r], -P[r * W + c]);   // conj(A_cr)
+    }
+  __syncthreads();
+
+  for (int i = 0; i < W - 2; ++i) {
+    const int o = i + 1;       // first row of the trailing block
+    const int m = W - 1 - i;   // its size
+    if (warp == 0) {
+      // lanes 0-15: k-point of half 0, 16-31: half 1
+      const int hh = lane >> 4, l16 = lane & 15;
+      const double2* Ah = smem2 + hh * per_k;
+      const bool lv = 2 * (int64_t)blockIdx.x + hh < n;
+      double s2 = 0.0;
+      if (lv)
+        for (int r = o + 1 + l16; r < W; r += 16) {
+          const double2 x = Ah[tri(r, i)];
+          s2 = fma(x.x, x.x, fma(x.y, x.y, s2));
+        }
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      // the scalar step (see the one-k kernel): lanes 2 kk, 2 kk + 1 for the k-point of half kk
+      const double s2k = __shfl_sync(0xffffffffu, s2, (lane >> 1) << 4);
+      if (lane < 4) {
+        const int kk = lane >> 1, sub = lane & 1;
+        const bool lk = 2 * (int64_t)blockIdx.x + kk < n;
+        double2* Ak = smem2 + kk * per_k;
+        const double2 al = lk ? Ak[tri(o, i)] : make_double2(0.0, 0.0);
+        const double aa2 = fma(al.x, al.x, al.y * al.y);
+        const double x2 = sub == 0 ? aa2 + s2k : aa2;    // |x|^2, |alpha|^2
+        const double rx = x2 > 0.0 ? rsqrt(x2) : 0.0;
+        const double xn = x2 * rx;                         // |x|, |alpha|
+        const double nrm = __shfl_sync(0xFu, xn, 2 * kk);
+        const double aa = __shfl_sync(0xFu, xn, 2 * kk + 1);
+        const double ra = __shfl_sync(0xFu, rx, 2 * kk + 1);
+        const double comp = sub == 0 ? al.x : al.y;
+        const double ph = aa2 > 0.0 ? comp * ra : (sub == 0 ? 1.0 : 0.0);
+        double2* begk = b.phase + (2 * (int64_t)blockIdx.x + kk) * W;
+        double* toutk = b.tau + (2 * (int64_t)blockIdx.x + kk) * W;
+        if (lk) {
+          if (s2k != 0.0) {
+            const double bet = -ph * nrm;
+            const double v0 = fma(ph, nrm, comp);
+            reinterpret_cast<double*>(&Ak[tri(o, i)])[sub] = v0;
+            reinterpret_cast<double*>(&begk[i])[sub] = bet;
+            if (sub == 0) {
+              const double tau = 1.0 / (nrm * (nrm + aa));
+              s_tau[kk] = tau;
+              toutk[i] = tau;
+            }
+          } else {
+            reinterpret_cast<double*>(&begk[i])[sub] = comp;   // beta = alpha, no reflection
+            if (sub == 0) {
+              s_tau[kk] = 0.0;
+              toutk[i] = 0.0;
+            }
+          }
+        } else if (sub == 0) {
+          s_tau[kk] = 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    const double tau = s_tau[h];
+    const bool act = live && tau != 0.0;
+    double2* vb = sp + W;
+    // p = tau * A22 v (the one-k kernel's partition over the half's 256 threads)
+    const int P2 = max(1, min(256 / m, b.symv_parts));
+    {
+      const int r = th % m, part = th / m;
+      if (act && part < P2) {
+        double ax = 0.0, ay = 0.0;
+        const int rowb = tri(o + r, o);
+        for (int c = part; c < m; c += P2) {
+          const int idx = c <= r ? rowb + c : tri(o + c, o + r);
+          double2 a = A[idx];
+          const unsigned long long flip = c > r ? 0x8000000000000000ull : 0ull;
+          a.y = __longlong_as_double(__double_as_longlong(a.y) ^ flip);
+          const double2 v = A[tri(o + c, i)];
+          ax = fma(a.x, v.x, ax); ax = fma(-a.y, v.y, ax);
+          ay = fma(a.x, v.y, ay); ay = fma(a.y, v.x, ay);
+        }
+        sp[part * m + r] = make_double2(ax, ay);
+      }
+    }
+    __syncthreads();
+    if (act)
+      for (int rr = th; rr < m; rr += 256) {
+        double sx = 0.0, sy = 0.0;
+        for (int q = 0; q < P2; ++q) {
+          const double2 v = sp[q * m + rr];
+          sx += v.x;
+          sy += v.y;
+        }
+        pb[rr] = make_double2(tau * sx, tau * sy);
+      }
+    __syncthreads();
+    if (warp == 0) {
+      const int hh = lane >> 4, l16 = lane & 15;
+      const double2* Ah = smem2 + hh * per_k;
+      const double2* ph2 = Ah + (size_t)W * (W + 1) / 2;
+      const double tk = s_tau[hh];
+      double sum = 0.0;   // Re(v^H p)
+      if (tk != 0.0)
+        for (int r = l16; r < m; r += 16) {
+          const double2 v = Ah[tri(o + r, i)], p = ph2[r];
+          sum = fma(v.x, p.x, fma(v.y, p.y, sum));
+        }
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+      if (l16 == 0) s_K[hh] = 0.5 * tk * sum;
+    } else if (act) {
+      // the copy of v: half 0 without its warp 0 (busy above), half 1 whole
+      const int base = h == 0 ? 32 : 0;
+      for (int r = th - base; r < m; r += 256 - base) vb[r] = A[tri(o + r, i)];
+    }
+    __syncthreads();
+    const double K = s_K[h];
+    if (act)
+      for (int r = th; r < m; r += 256) {
+        const double2 p = pb[r], v = vb[r];
+        pb[r] = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
+      }
+    __syncthreads();
+    if (act) {
+      // A22 <- A22 - v w^H - w v^H on the lower triangle (c <= r)
+      const int ntri = m * (m + 1) / 2;
+      for (int idx = th; idx < ntri; idx += 256) {
+        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+        while (r * (r + 1) / 2 > idx) --r;
+        while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+        const int c = idx - r * (r + 1) / 2;
+        const double2 vr = vb[r], wr = pb[r], vc = vb[c], wc = pb[c];
+        double2 a = A[tri(o + r, o + c)];
+        a.x = fma(-vr.x, wc.x, a.x); a.x = fma(-vr.y, wc.y, a.x);
+        a.x = fma(-wr.x, vc.x, a.x); a.x = fma(-wr.y, vc.y, a.x);
+        if (c == r) {
+          a.y = 0.0;
+        } else {
+          a.y = fma(-vr.y, wc.x, a.y); a.y = fma(vr.x, wc.y, a.y);
+          a.y = fma(-wr.y, vc.x, a.y); a.y = fma(wr.x, vc.y, a.y);
+        }
+        A[tri(o + r, o + c)] = a;
+      }
+    }
+    __syncthreads();
+  }
+  if (!live) return;   // no block barrier follows
+
+  // outputs (as the one-k kernel)
+  double* dout = b.d + k * W;
+  double* eout = b.e + k * W;
+  double2* phout = beg;
+  if (th == 0 && W >= 2) beg[W - 2] = A[tri(W - 1, W - 2)];
+  // the half's own threads only from here: named barrier 1 + h over its 256 threads
+  asm volatile("bar.sync %0, 256;" ::"r"(1 + h) : "memory");
+  for (int j = th; j + 1 < W; j += 256) {
+    const double2 bj = beg[j];
+    const double a2 = fma(bj.x, bj.x, bj.y * bj.y);
+    double a = 0.0;
+    double2 u = make_double2(1.0, 0.0);
+    if (a2 > 0.0) {
+      const double ra = rsqrt(a2);
+      a = a2 * ra;
+      u = make_double2(bj.x * ra, bj.y * ra);
+    }
+    eout[j] = a;
+    sp[j] = u;
+  }
+  asm volatile("bar.sync %0, 256;" ::"r"(1 + h) : "memory");
+  if (th == 0) {
+    double2 D = make_double2(1.0, 0.0);
+    phout[0] = D;
+    for (int j = 0; j + 1 < W; ++j) {
+      D = cmul(D, sp[j]);
+      phout[j + 1] = D;
+    }
+    eout[W - 1] = 0.0;
+  }
+  for (int j = th; j < W; j += 256) {
+    dout[j] = A[tri(j, j)].x;
+    if (j >= W - 2) tout[j] = 0.0;
+  }
+  double2* rout = b.refl + (size_t)k * W * W;
+  for (int idx = th; idx < W * W; idx += 256) {
+    int r = idx / W, c = idx % W;
+    rout[idx] = r > c ? A[tri(r, c)] : make_double2(0.0, 0.0);
+  }
+}
+
 // ------------------------------------------------------------------ K2b: QL, lane per k
 // Eigenvalues of the real symmetric tridiagonal T by implicit QL with Wilkinson shifts, one
 // k-point per lane.  Smem per warp: d and e as [W][32] (lane-interleaved: conflict-free for
@@ -579,6 +798,15 @@ static cudaError_t launch_tridiag_ld(const double* Hp, int64_t ld, int W, int n,
     kern<<<n, nt, sm, s>>>(Hp, ld, W, b);
     return cudaGetLastError();
   };
+  if (W <= 64) {
+    // two k-points per 512-thread CTA
+    const size_t sm2 = 2 * ((size_t)W * (W + 1) / 2 + 256) * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(tridiag2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm2);
+    if (e != cudaSuccess) return e;
+    tridiag2_kernel<<<(n + 1) / 2, 512, sm2, s>>>(Hp, ld, W, n, b);
+    return cudaGetLastError();
+  }
   return tridiag_threads(W) == 256 ? go(tridiag_kernel<double, 256>, 256)
                                    : go(tridiag_kernel<double, 512>, 512);
 }
