@@ -42,18 +42,19 @@ __device__ __forceinline__ int tri(int r, int c) { return (r * (r + 1) >> 1) + c
 
 // Packed rows of leading dimension ld (W*W for the FP64 Fourier kernel, the padded row of
 // H | dxH | dyH for the tensor-core one).  The reduction is FP64.
-// threads of the reduction's CTA
-__host__ __device__ __forceinline__ int tridiag_threads(int W) { return W > 64 ? 512 : 256; }
+// threads of the one-k reduction's CTA (orders W > 64; W <= 64 runs two k-points per CTA in
+// tridiag2_kernel below)
+constexpr int TRI_NT = 512;
 
-// NTT threads: 256 (five CTAs per SM at W <= 64), or 512 for W > 64, where one CTA (136 KB of
-// shared memory at W = 128) holds an SM and more warps cover its barriers (W = 128: 235 ->
-// 229 ms per 18,432 k-points; 1,024 threads with twice the symv parts: 240 ms)
+// NTT = 512 threads: one CTA (136 KB of shared memory at W = 128) holds an SM, and more warps
+// than 256 cover its barriers (W = 128: 235 -> 229 ms per 18,432 k-points; 1,024 threads
+// with twice the symv parts: 240 ms)
 template <typename T, int NTT>
-__global__ void __launch_bounds__(NTT, NTT == 256 ? 6 : 1) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
+__global__ void __launch_bounds__(NTT, 1) tridiag_kernel(const T* __restrict__ Hp, int64_t ld, int W,
                                                      EighBufs b) {
-  // 37.4 KB at W = 64, so that six CTAs share an SM: the reflector is read from its column of
-  // A (not copied), the symv partials share their array with p, and beta_i, tau_i go to the
-  // outputs as they are formed (beta_i into the phase row, which is rewritten at the end)
+  // the reflector is read from its column of A (not copied), the symv partials share their
+  // array with p, and beta_i, tau_i go to the outputs as they are formed (beta_i into the phase
+  // row, which is rewritten at the end): the triangle plus NTT partials of shared memory
   extern __shared__ double2 smem2[];
   double2* A = smem2;                              // lower triangle, packed by rows
   double2* sp = A + (size_t)W * (W + 1) / 2;       // [NTT] partial sums of the symv
@@ -777,7 +778,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
 
 size_t tridiag_smem(int W) {
   // packed triangle + the symv partials (at least 2 W: p and the copy of v)
-  return ((size_t)W * (W + 1) / 2 + std::max(tridiag_threads(W), 2 * W)) * sizeof(double2);
+  return ((size_t)W * (W + 1) / 2 + std::max(TRI_NT, 2 * W)) * sizeof(double2);
 }
 size_t backtransform_smem(int W) {
   return bt_u_slots(W) * sizeof(double2) + (size_t)W * (W + 1) * sizeof(double) +
@@ -807,8 +808,7 @@ static cudaError_t launch_tridiag_ld(const double* Hp, int64_t ld, int W, int n,
     tridiag2_kernel<<<(n + 1) / 2, 512, sm2, s>>>(Hp, ld, W, n, b);
     return cudaGetLastError();
   }
-  return tridiag_threads(W) == 256 ? go(tridiag_kernel<double, 256>, 256)
-                                   : go(tridiag_kernel<double, 512>, 512);
+  return go(tridiag_kernel<double, TRI_NT>, TRI_NT);
 }
 
 cudaError_t launch_tridiag(const double* Hp, int W, int n, EighBufs b, cudaStream_t s) {
