@@ -110,6 +110,9 @@ def test_eigh_batched(kubo, torch, W):
         X = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
         Q, _ = np.linalg.qr(X)
         A[4] = (Q * lam) @ np.conj(Q.T)
+        # a diagonal matrix beside a dense one: the two k-points of one reduction CTA at
+        # W <= 64 (one half reflects every column, the other none)
+        A[6] = np.diag(rng.standard_normal(W))
     At = cuda(torch, A)
     E, U = kubo.eigh_batched(kubo.pack_hermitian(At), W)
     E, U = E.cpu().numpy(), U.cpu().numpy()
