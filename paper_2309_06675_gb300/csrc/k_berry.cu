@@ -85,6 +85,27 @@ __device__ __forceinline__ void unpack_hermitian(const TIn* __restrict__ P, doub
   }
 }
 
+// max_j |E_j| of a shared array, by warp 0 on the bit patterns (for non-negative doubles the
+// integer order is the numeric order; NaN patterns count as 0): no FP64 instruction, where a
+// serial loop of FP64 maxima by one thread queued behind the FP64 pipe.  Every thread calls
+// it; the value is read after a later barrier.
+__device__ __forceinline__ void emax_warp0(const double* sE, int W, int t, double* out) {
+  if (t < 32) {
+    unsigned long long m = 0ull;
+    for (int j = t; j < W; j += 32) {
+      unsigned long long u = (unsigned long long)__double_as_longlong(sE[j]) & 0x7FFFFFFFFFFFFFFFull;
+      if (u > 0x7FF0000000000000ull) u = 0ull;
+      m = u > m ? u : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if (t == 0) *out = __longlong_as_double((long long)m);
+  }
+}
+
 // a b - c d within 2 ulp (Kahan: the rounding error of c d is recovered exactly by an FMA)
 __device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
   const float w = __fmul_rn(c, d);
@@ -267,11 +288,7 @@ __global__ void __launch_bounds__(NT) berry_fp64_kernel(const double* __restrict
   for (int j = t; j < W; j += NT) sE[j] = E[k * W + j];
   if (t < n_eta) sEta[t] = etas[t];
   __syncthreads();
-  if (t == 0) {
-    double mx = 0.0;
-    for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
-    s_emax = mx;
-  }
+  emax_warp0(sE, W, t, &s_emax);
 
   double2 acc[TM][TM];
   cgemm_tile<TM, false>(sA, sU, W, LD, ty, tx, acc);        // T = X U
@@ -582,11 +599,7 @@ __global__ void __launch_bounds__(NT) berry_mixed_kernel(const double* __restric
   for (int j = t; j < W; j += NT) sE[j] = E[k * W + j];
   if (t < n_eta) sEta[t] = etas[t];
   __syncthreads();
-  if (t == 0) {
-    double mx = 0.0;
-    for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
-    s_emax = mx;
-  }
+  emax_warp0(sE, W, t, &s_emax);
 
   float2 acc[TM][TM];
   cgemm_tile_f32<TM, false>(sA, sU, W, LD, ty, tx, acc);   // T = X U
@@ -843,11 +856,7 @@ __global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
     __syncthreads();
     assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, RT_WP, t, sU,
                    reinterpret_cast<float2*>(opA));
-    if (t == 0) {
-      double mx = 0.0;
-      for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
-      s_emax = mx;
-    }
+    emax_warp0(sE, W, t, &s_emax);
     for (int a = 0; a < 2 && ok; ++a) {
       const TIn* P = (a == 0 ? Xp : Yp) + k * ld;
       // ---- A1 = [[X_r, -X_i], [X_i, X_r]] 2^-eX (W padded to 64)
@@ -1187,11 +1196,7 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
       assemble_u_f32(Z + k * WW, eb.phase + k * W, eb.refl + k * WW, eb.tau + k * W, W, TF_LDU,
                      t, sU, reinterpret_cast<float2*>(ops));
     }
-    if (t == 0) {
-      double mx = 0.0;
-      for (int j = 0; j < W; ++j) mx = fmax(mx, fabs(sE[j]));
-      s_emax = mx;
-    }
+    emax_warp0(sE, W, t, &s_emax);
     float vacc[32];   // this thread's 32 entries of row mrow of [V_r; V_i]
     for (int a = 0; a < 2 && ok; ++a) {
       const TIn* P = (a == 0 ? Xp : Yp) + k * ld;
