@@ -453,14 +453,29 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
     sp[j] = u;
   }
   asm volatile("bar.sync %0, 256;" ::"r"(1 + h) : "memory");
-  if (th == 0) {
-    double2 D = make_double2(1.0, 0.0);
-    phout[0] = D;
-    for (int j = 0; j + 1 < W; ++j) {
-      D = cmul(D, sp[j]);
-      phout[j + 1] = D;
+  if (th < 32) {
+    // D_0 = 1, D_{j+1} = D_j u_j as a warp scan (a serial chain of 63 complex products in one
+    // thread would hold the CTA's shared memory while it queues behind the FP64 pipe): lane l
+    // takes u_2l, u_2l+1, then the lanes' products are scanned in five steps
+    const int j0 = 2 * th, j1 = j0 + 1;
+    const double2 u0 = j0 + 1 < W ? sp[j0] : make_double2(1.0, 0.0);
+    const double2 u1 = j1 + 1 < W ? sp[j1] : make_double2(1.0, 0.0);
+    const double2 pr = cmul(u0, u1);
+    double2 sc = pr;   // inclusive scan of the lanes' pair products
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      double2 o2;
+      o2.x = __shfl_up_sync(0xffffffffu, sc.x, off);
+      o2.y = __shfl_up_sync(0xffffffffu, sc.y, off);
+      if (th >= off) sc = cmul(o2, sc);
     }
-    eout[W - 1] = 0.0;
+    double2 ex;        // product of u_0 .. u_{2l-1}
+    ex.x = __shfl_up_sync(0xffffffffu, sc.x, 1);
+    ex.y = __shfl_up_sync(0xffffffffu, sc.y, 1);
+    if (th == 0) ex = make_double2(1.0, 0.0);
+    if (j0 < W) phout[j0] = ex;
+    if (j1 < W) phout[j1] = cmul(ex, u0);
+    if (th == 0) eout[W - 1] = 0.0;
   }
   for (int j = th; j < W; j += 256) {
     dout[j] = A[tri(j, j)].x;
