@@ -474,14 +474,36 @@ __global__ void __launch_bounds__(NT, 5) tridiag_df_kernel(const double* __restr
     ub[j] = u;
   }
   __syncthreads();
-  if (t == 0) {
-    double2 D = make_double2(1.0, 0.0);
-    phout[0] = D;
-    for (int j = 0; j + 1 < W; ++j) {
-      D = cmul(D, ub[j]);
-      phout[j + 1] = D;
+  if (t < 32) {
+    // D_0 = 1, D_{j+1} = D_j u_j as a warp scan (lane l takes u_4l .. u_4l+3, W <= 128)
+    // rather than one thread's serial chain of complex products on the FP64 pipe
+    double2 u[4];
+    double2 pr = make_double2(1.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * t + q;
+      u[q] = j + 1 < W ? ub[j] : make_double2(1.0, 0.0);
+      pr = cmul(pr, u[q]);
     }
-    eout[W - 1] = 0.0;
+    double2 sc = pr;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      double2 o2;
+      o2.x = __shfl_up_sync(0xffffffffu, sc.x, off);
+      o2.y = __shfl_up_sync(0xffffffffu, sc.y, off);
+      if (t >= off) sc = cmul(o2, sc);
+    }
+    double2 D;
+    D.x = __shfl_up_sync(0xffffffffu, sc.x, 1);
+    D.y = __shfl_up_sync(0xffffffffu, sc.y, 1);
+    if (t == 0) D = make_double2(1.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * t + q;
+      if (j < W) phout[j] = D;
+      D = cmul(D, u[q]);
+    }
+    if (t == 0) eout[W - 1] = 0.0;
   }
   for (int j = t; j < W; j += NT) {
     const float4 a = A[tri(j, j)];
