@@ -617,8 +617,9 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   }
   const size_t WW = (size_t)p.W * p.W;
   if (f32_rotation(p.precision) && p.W <= SMALL_W_MAX) {
-    // FP32 rotations: U = Q D Z is assembled in FP32 inside the rotation kernel from the FP64
-    // eigenvectors Z of the tridiagonal (kept in the U buffer) and the reflectors
+    // FP32 rotations: U = Q D Z is formed in FP32 (inside the SIMT and exact-slice rotation
+    // kernels, by assemble_u_kernel for the 3xTF32 one) from the FP64 eigenvectors Z of the
+    // tridiagonal (kept in the U buffer) and the reflectors
     double* Z = reinterpret_cast<double*>(U);
     // the tensor-core rotation takes U = Q D Z formed by a kernel of its own (FP32, in the
     // second half of the U buffer: Z holds the first n W^2 doubles)
