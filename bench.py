@@ -485,13 +485,13 @@ def main():
         s = slab_of(rank, world, step, n_slabs)
         return (s * k_per_step, (s + 1) * k_per_step)
 
-    def timed(prec, rotation=None):
+    def timed(prec, rotation=None, ql_fp64=False):
         outs = []
         def one_step(step, prof=None):
             flush.fill_(step & 0xFF)   # evict L2 (256 MiB > 135 MB) before every step
             o = torch.empty((1, E_F.size), dtype=torch.float64, device=dev)
             kubo.ahc(H, model.R, kmesh, EF, eta=eta, kT=kT, precision=prec, k_range=slab(step),
-                     out=o, profile=prof, chunk_k=args.chunk, rotation=rotation)
+                     out=o, profile=prof, chunk_k=args.chunk, rotation=rotation, ql_fp64=ql_fp64)
             return o
         for s in range(args.warmup):
             one_step(s)
@@ -521,6 +521,8 @@ def main():
     rot_res = {}
     if args.precision == "both" and not args.no_extras and args.rotation is None:
         rot_res = {r: timed("mixed", rotation=r) for r in ("simt", "exact")}
+    # the mixed form with its QL iteration in FP64 as well (every eigensolver operation FP64)
+    ql64 = timed("mixed", rotation=args.rotation, ql_fp64=True) if args.precision == "both" else None
 
     # ---- end to end through the host-buffer entry point (pinned host memory), headline path
     head = precisions[0]
@@ -631,6 +633,15 @@ def main():
                        "rel_err_max_over_steps": float(np.max(np.abs(v[3] - of) / den))}
                    for r, v in rot_res.items()},
                 "tf32_berry_ms_per_step": res["mixed"][1]["berry"]["ms"] / args.steps}
+        if ql64 is not None:
+            line["mixed_ql_fp64_variant"] = {
+                "what": "the headline form with kubo_options.ql_fp64 = 1: the QL iteration in FP64 "
+                        "too and its eigenvalues reported (the default runs QL in FP32 pairs for "
+                        "the inverse iteration's shifts and reports FP64 Rayleigh quotients)",
+                "value": world * k_total / (ql64[0] / 1e3), "ms_per_step": ql64[0] / args.steps,
+                "ql_ms_per_step": ql64[1]["ql"]["ms"] / args.steps,
+                "speedup_vs_fp64": world * k_total / (ql64[0] / 1e3) / paths["fp64"]["value"],
+                "rel_err_max_over_steps": float(np.max(np.abs(ql64[3] - of) / den))}
         if "mixed_df" in res:
             line["mixed_df_variant"] = {
                 "what": "the mixed form with its eigensolver in double-float (FP32 pairs, ~2^-46 "

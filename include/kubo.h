@@ -173,6 +173,13 @@ typedef struct kubo_options {
                                KUBO_ERR_NO_CONVERGENCE with its outputs untouched; a cap of 1
                                forces that path on any matrix that needs a second sweep.
                                < 0: KUBO_ERR_INVALID_ARG. */
+  int ql_fp64;              /* KUBO_MIXED: 1 = its QL iteration in FP64 as well and the QL
+                               eigenvalues reported (every operation of the eigensolver in
+                               FP64); 0 (default) = the QL iteration in double-float, used only
+                               for the inverse iteration's shifts, and the eigenvalues reported
+                               as the FP64 Rayleigh quotients of the FP64 eigenvectors (equal to
+                               the FP64 QL ones within a few W eps max|E|).  Ignored by the other
+                               modes.  Other values: KUBO_ERR_INVALID_ARG. */
 } kubo_options;
 
 /* Fill *opt with the defaults (FP64, single eta, kT = 0, whole mesh, default stream,

@@ -88,6 +88,7 @@ class Options(ctypes.Structure):
         ("fourier_separable", ctypes.c_int),
         ("rotation_tc", ctypes.c_int),
         ("ql_max_sweeps", ctypes.c_int),
+        ("ql_fp64", ctypes.c_int),
     ]
 
 
@@ -189,7 +190,7 @@ def _dev(t, dtype, name):
 
 
 def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk_k=0,
-             workspace=None, keep=None, profile=None, ql_max_sweeps=0):
+             workspace=None, keep=None, profile=None, ql_max_sweeps=0, ql_fp64=False):
     o = Options()
     lib().kubo_options_init(ctypes.byref(o))
     o.precision = _PREC.get(precision, precision)
@@ -210,6 +211,7 @@ def _options(precision=FP64, etas=None, kT=0.0, k_range=None, stream=None, chunk
     if profile is not None:
         o.profile = ctypes.pointer(profile)
     o.ql_max_sweeps = int(ql_max_sweeps)
+    o.ql_fp64 = 1 if ql_fp64 else 0
     return o
 
 
@@ -253,8 +255,12 @@ def workspace_size(W, N_R, kmesh, n_EF, precision=FP64, n_eta=1, kT=0.0, k_range
 
 def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range=None,
         stream=None, chunk_k=0, workspace=None, out=None, profile=None, fixup_rel=0.0,
-        unpadded=False, separable=False, rotation_tc=False, ql_max_sweeps=0, rotation=None):
+        unpadded=False, separable=False, rotation_tc=False, ql_max_sweeps=0, rotation=None,
+        ql_fp64=False):
     """S(E_F) for every broadening: returns a float64 CUDA tensor [n_eta, n_EF].
+
+    ql_fp64 (MIXED): the QL iteration in FP64 too, its eigenvalues reported (default: QL shifts
+    in double-float, eigenvalues the FP64 Rayleigh quotients of the FP64 eigenvectors).
 
     rotation: the FP32-grade step (3) kernel of the reduced modes, "auto" (the default:
     "tf32" above W = 40, else "simt"), "tf32" (tensor cores, 3xTF32), "exact" (tensor cores,
@@ -272,7 +278,7 @@ def ahc(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_range
         out = torch.empty((n_eta, n_EF), dtype=torch.float64, device=H_R.device)
     keep = []
     o = _options(precision, etas, kT, k_range, stream, chunk_k, workspace, keep, profile,
-                 ql_max_sweeps)
+                 ql_max_sweeps, ql_fp64)
     o.mixed_fixup_rel = float(fixup_rel)
     o.layout_unpadded = 1 if unpadded else 0
     o.fourier_separable = 1 if separable else 0
@@ -441,7 +447,7 @@ def ahc_host(H_R, R, kmesh, E_F, eta=1e-3, etas=None, kT=0.0, precision=FP64, k_
 
 
 def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None, chunk_k=0,
-          rotation_tc=False, ql_max_sweeps=0, rotation=None):
+          rotation_tc=False, ql_max_sweeps=0, rotation=None, ql_fp64=False):
     """Per-k eigenvalues and band curvatures for the listed mesh points."""
     torch = _torch()
     Rh = _host_int32(R, 3)
@@ -453,7 +459,7 @@ def ahc_k(H_R, R, kmesh, kidx, eta=1e-3, etas=None, precision=FP64, stream=None,
     Om = torch.empty((n_eta, n_k, W), dtype=torch.float64, device=H_R.device)
     keep = []
     o = _options(precision, etas, 0.0, None, stream, chunk_k, None, keep,
-                 ql_max_sweeps=ql_max_sweeps)
+                 ql_max_sweeps=ql_max_sweeps, ql_fp64=ql_fp64)
     o.rotation_tc = _rotation(rotation, rotation_tc)
     code = lib().kubo_ahc_k(_dev(H_R, torch.complex128, "H_R"), Rh.ctypes.data_as(ctypes.c_void_p),
                             W, N_R, km.ctypes.data_as(ctypes.c_void_p),

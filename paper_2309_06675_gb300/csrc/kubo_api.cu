@@ -112,8 +112,11 @@ bool df_eigh(int prec) { return prec == KUBO_MIXED_DF; }
 // MIXED: the QL iteration runs in double-float as well, but only to supply the shifts of the
 // FP64 inverse iteration; the eigenvalues reported are the FP64 Rayleigh quotients of its
 // eigenvectors
-bool df_ql(int prec) { return prec == KUBO_MIXED || prec == KUBO_MIXED_DF; }
-bool rq_eigenvalues(int prec) { return prec == KUBO_MIXED; }
+// (kubo_options.ql_fp64 keeps the MIXED mode's QL in FP64 and its eigenvalues)
+bool df_ql(int prec, bool ql_fp64) {
+  return (prec == KUBO_MIXED && !ql_fp64) || prec == KUBO_MIXED_DF;
+}
+bool rq_eigenvalues(int prec, bool ql_fp64) { return prec == KUBO_MIXED && !ql_fp64; }
 
 // Power-of-two exponent s that brings max |H(R)| into [1, 2) when it lies outside
 // [2^-20, 2^20] (0 otherwise, and for zero or non-finite maxima).  S(E_F) is homogeneous of
@@ -138,6 +141,7 @@ struct Plan {
   bool scale_ok = false;            // the call may rescale H(R) by a power of two (range_exponent)
   int escale = 0;                   // that power: the basis holds 2^escale H(R)
   int ql_cap = 0;                   // QL sweeps per eigenvalue (0 = the kernels' default)
+  bool ql_fp64 = false;             // MIXED: FP64 QL and its eigenvalues (kubo_options.ql_fp64)
   int group_m = 8;                  // tensor-core Fourier sum: M tiles rasterised together
   int symv_parts = 4;               // Householder reduction: column partitions of its symv
   bool model = false;   // needs the prepared Fourier basis
@@ -452,6 +456,7 @@ kubo_status validate_common(int W, int N_R, const int32_t* kmesh, const kubo_opt
       if (!finite_nonneg(o.etas[e])) return KUBO_ERR_INVALID_ARG;
   }
   if (o.chunk_k < 0 || o.ql_max_sweeps < 0) return KUBO_ERR_INVALID_ARG;
+  if (o.ql_fp64 < 0 || o.ql_fp64 > 1) return KUBO_ERR_INVALID_ARG;
   if (o.rotation_tc < 0 || o.rotation_tc > 3) return KUBO_ERR_INVALID_ARG;
   if (!std::isfinite(o.mixed_fixup_rel)) return KUBO_ERR_INVALID_ARG;
   n_eta = o.n_eta > 0 ? o.n_eta : 1;
@@ -610,7 +615,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   }
   {
     StageTimer tm(c, KUBO_STAGE_QL, 1);
-    if (df_ql(p.precision))
+    if (df_ql(p.precision, p.ql_fp64))
       KCHECK(launch_ql_df(p.W, kl.n, eb, st, c.s));
     else
       KCHECK(launch_ql(p.W, kl.n, eb, st, c.s));
@@ -630,7 +635,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
         KCHECK(launch_iit_df(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s));
       else
         KCHECK(launch_iit(p.W, kl.n, eb, Eout, Z, c.at<double>(p.o_iit), p.iit_slots, c.s,
-                           rq_eigenvalues(p.precision)));
+                           rq_eigenvalues(p.precision, p.ql_fp64)));
       if (U32) KCHECK(launch_assemble_u32(Z, eb, U32, p.W, kl.n, c.s));
     }
     StageTimer tm(c, KUBO_STAGE_BERRY, 1);
@@ -645,7 +650,7 @@ kubo_status run_batch_mixed(Call& c, const Model& md, const KList& kl, double* E
   {
     StageTimer tm(c, KUBO_STAGE_BACKTRANSFORM, p.W > SMALL_W_MAX ? 2 : 1);
     KCHECK(eigh_vectors(c, kl.n, eb, Eout, U, f32_rotation(p.precision),
-                        rq_eigenvalues(p.precision)));
+                        rq_eigenvalues(p.precision, p.ql_fp64)));
   }
   {
     StageTimer tm(c, KUBO_STAGE_BERRY, p.W > SMALL_W_MAX ? 5 : 1);
@@ -867,6 +872,7 @@ kubo_status setup_ahc(Call& c, const kubo_options& o, const int32_t* R_vecs, int
   p.fixup = tc_fourier(p.precision) && o.mixed_fixup_rel > 0.0;
   p.pad = o.layout_unpadded ? 0 : 1;
   p.ql_cap = o.ql_max_sweeps;
+  p.ql_fp64 = o.ql_fp64 != 0;
   p.rot = rotation_kernel(o.rotation_tc, W, o.layout_unpadded != 0);
   if (o.fourier_separable) {
     if (o.workspace) return KUBO_ERR_UNSUPPORTED;   // its size depends on the R set
@@ -1451,6 +1457,7 @@ kubo_status kubo_ahc_batched(kubo_problem* probs, int n_probs, const kubo_option
       p.fixup = false;
       p.scale_ok = f32_rotation(p.precision);
       p.ql_cap = o.ql_max_sweeps;
+      p.ql_fp64 = o.ql_fp64 != 0;
       p.rot = rotation_kernel(o.rotation_tc, q.W, o.layout_unpadded != 0);
       j.cost = job_cost(p);
       br.jobs.push_back(std::move(j));

@@ -266,6 +266,24 @@ def test_rayleigh_quotient_eigenvalues(kubo, torch, W, hw, layers):
         np.max(np.abs(Erq - Eql)) / scale
 
 
+def test_mixed_with_fp64_ql_option(kubo, torch, m64):
+    """kubo_options.ql_fp64 = 1 keeps the MIXED mode's QL iteration in FP64 and reports its
+    eigenvalues: the eigenvalues agree with the default's Rayleigh quotients within a few
+    W eps max|E| and S(E_F) to rounding (both eigensolvers FP64-accurate)."""
+    kmesh = (128, 128, 128)
+    H = cuda(torch, m64.H_R)
+    kidx = cuda(torch, tbgen.k_sample(kmesh, 300, seed=5))
+    Erq, Orq = kubo.ahc_k(H, m64.R, kmesh, kidx, precision="mixed")
+    Eql, Oql = kubo.ahc_k(H, m64.R, kmesh, kidx, precision="mixed", ql_fp64=True)
+    Erq, Eql = Erq.cpu().numpy(), Eql.cpu().numpy()
+    assert np.max(np.abs(Erq - Eql)) <= 16 * 64 * 2.0 ** -52 * np.max(np.abs(Eql))
+    EF = cuda(torch, np.linspace(-1.0, 1.0, 64))
+    rng = (11 * 16384, 11 * 16384 + 4096)
+    S0 = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision="mixed").cpu().numpy()
+    S1 = kubo.ahc(H, m64.R, kmesh, EF, k_range=rng, precision="mixed", ql_fp64=True).cpu().numpy()
+    assert rel_err(S1, S0) < 1e-9, rel_err(S1, S0)
+
+
 def test_double_float_reduction_degenerate_bands(kubo, torch):
     """Exactly degenerate bands (two identical layers): the double-float reduction keeps the
     pairs degenerate to its precision and the curvature sums match the FP64 path."""
