@@ -652,7 +652,6 @@ __global__ void unpack_rows_kernel(const double* __restrict__ C, int64_t ld, int
 constexpr int RT_NT = 256;
 constexpr int RT_WP = 64;                                 // padded order
 constexpr int RT_NS = 4;                                  // slices per operand
-constexpr int RT_NPAIR = 10;
 constexpr int RT_A_BLOCK = 128 * 128;                     // bytes: 128 rows x 64 K (BF16)
 constexpr int RT_B_BLOCK = 64 * 128;                      // bytes: 64 rows x 64 K
 constexpr int RT_A_BYTES = RT_NS * 2 * RT_A_BLOCK;        // 128 KB (4 slices x 2 K halves)
@@ -661,11 +660,10 @@ constexpr int RT_U_BYTES = RT_WP * RT_WP * 8;             // float2 [64][64]
 constexpr int RT_TMEM_COLS = 512;                         // 4 levels x 64 + V^x (64)
 constexpr int RT_VX_COL = 256;
 constexpr uint32_t RT_WAIT_LIMIT = 1u << 20;              // a product takes microseconds
-constexpr uint32_t RT_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
-__constant__ int c_rpi[RT_NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-__constant__ int c_rpj[RT_NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-__constant__ int c_rpl[RT_NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+// instruction descriptor: kind::f16, BF16 operands, F32 accumulator, K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t rt_idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
 // byte offset of element (row, k in 0..63) in a K-major 128-byte-swizzled block of 2-byte elements
 __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
@@ -727,25 +725,26 @@ __device__ __forceinline__ void put2(unsigned char* region, int block_bytes, int
   const int kc = k >> 6, kin = k & 63;
 #pragma unroll
   for (int i = 0; i < RT_NS; ++i) {
-    unsigned char* blk = region + (size_t)(i * 2 + kc) * block_bytes;
+    unsigned char* blk = region + (size_t)(kc * RT_NS + i) * block_bytes;
     *reinterpret_cast<uint32_t*>(blk + sw128_off(row, kin)) = (uint32_t)a[i] | ((uint32_t)b[i] << 16);
   }
 }
 
-// issue the 80 MMAs of one block-real product (10 slice pairs x 2 K halves x 4 K16 steps)
+// issue the 32 MMAs of one block-real product (4 A slices x 2 K halves x 4 K16 steps): the
+// slice blocks of a K half are consecutive ([K half][slice]), so slices 0 .. 3-i of B form one
+// K-major operand of N = 64 (4 - i) rows whose accumulator columns are those of levels i + j
+// (levels contiguous in TMEM); A_0 comes first and initialises every level.
 __device__ __forceinline__ void rot_issue(uint32_t tmem, uint32_t a_base, uint32_t b_base) {
-  int seen = 0;
-  for (int p = 0; p < RT_NPAIR; ++p) {
-    const int i = c_rpi[p], j = c_rpj[p], l = c_rpl[p];
-    for (int kc = 0; kc < 2; ++kc)
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t acc = ((seen >> l) & 1) ? 1u : 0u;
-        seen |= 1 << l;
-        const uint64_t da = tc::umma_desc_sw128(a_base + (uint32_t)((i * 2 + kc) * RT_A_BLOCK + kk * 32));
-        const uint64_t db = tc::umma_desc_sw128(b_base + (uint32_t)((j * 2 + kc) * RT_B_BLOCK + kk * 32));
-        tc::umma_bf16(tmem + (uint32_t)(l * 64), da, db, RT_IDESC, acc);
+  for (int kc = 0; kc < 2; ++kc)
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint64_t db = tc::umma_desc_sw128(b_base + (uint32_t)(kc * RT_NS * RT_B_BLOCK + kk * 32));
+#pragma unroll
+      for (int i = 0; i < RT_NS; ++i) {
+        const uint32_t acc = (i > 0 || kc > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t da = tc::umma_desc_sw128(a_base + (uint32_t)((kc * RT_NS + i) * RT_A_BLOCK + kk * 32));
+        tc::umma_bf16(tmem + (uint32_t)(i * 64), da, db, rt_idesc_n(64 * (RT_NS - i)), acc);
       }
-  }
+    }
 }
 
 // the 32 columns c0 .. c0 + 31 of this thread's TMEM lane, folded over the four levels:

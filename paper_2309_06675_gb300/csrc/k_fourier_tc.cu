@@ -24,7 +24,8 @@
 //   basis_scale_kernel  once per call: column exponents e_n of the stacked basis
 //   basis_slice_kernel  once per call: stacked basis -> Bt[4 slices][Npad][Kp] (K-major, bf16)
 //   coef_slice_kernel   per batch: FP64 phases with exact argument reduction -> A[4][Mpad][Kp]
-//   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, N=64, K=16), operands staged
+//   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, K=16; one MMA per A slice
+//                       against the stacked B slices, N = 64 x (slices - i)), operands staged
 //                       by TMA (128-byte swizzle, 2-stage mbarrier pipeline), 4 level
 //                       accumulators x 2 buffers filling the 512 TMEM columns, integer
 //                       epilogue, FP64 rows in HBM; persistent (one CTA per SM over the
@@ -54,7 +55,6 @@ constexpr int BK = 64;            // K per stage (one 128-byte swizzle row of bf
 constexpr int NSTAGE = 2;
 constexpr int NSLICE = 4;         // slices per operand: 7 + 3 x 8 = 31 fractional bits
 constexpr int NLEVEL = 4;         // levels l = i + j <= 3 kept: 10 slice pairs
-constexpr int NPAIR = 10;
 constexpr int NACC = 2;           // level-accumulator sets in flight (double buffer)
 constexpr int DRAIN = 4;          // K blocks summed in TMEM before the epilogue drains a set:
                                   // 4 blocks x 4 pairs x 64 x 2^14 = 2^24, still exact in FP32
@@ -82,9 +82,10 @@ __global__ void bounded_wait_check_kernel(uint32_t limit, DevStatus* st) {
   if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) atomicOr(&st->bits, ST_TIMEOUT);
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 64.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 // Fixed-point slices of x 2^-e (|x| <= 2^e): x 2^-e = sum_i s_i 2^(-7-8i) + O(2^-32),
 // |s_i| <= 128, from the FP64 bit pattern with integer operations (fixed31_ll, slice4_bf16 in
@@ -184,11 +185,6 @@ __global__ void coef_slice_kernel(Model md, Mesh mesh, KList kl, int Mpad, int K
   }
 }
 
-// slice pairs (i, j) with i + j <= 3, grouped by level l = i + j
-__constant__ int c_pi[NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-__constant__ int c_pj[NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-__constant__ int c_pl[NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
-
 // ------------------------------------------------------------------ the tcgen05 GEMM
 // Persistent: one CTA per SM walks the tiles tau = blockIdx.x, + gridDim.x, ... of the column
 // tiles nt0 .. nt0 + ntc - 1 (grouped rasterisation, below).  The K-block counter of the
@@ -207,7 +203,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                       DevStatus* st, int nt0, int ntc, int group_m, int vel0, int vw2,
                       int vx0, int vyoff) {
   constexpr int NLEV = NS;
-  constexpr int NPR = NS * (NS + 1) / 2;   // pairs with i + j < NS (listed first in c_p*)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
@@ -307,15 +302,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           tc_fence_after();
+          // One MMA per A slice i against the stacked B slices 0 .. NS-1-i: the B tiles of a
+          // stage are consecutive 8-row-group runs of one 128-byte-swizzled K-major operand,
+          // so rows j*BN .. j*BN+BN-1 of the N = (NS-i) BN operand are slice j, and the
+          // accumulator columns they write are those of level i + j (levels are contiguous
+          // within a set).  A_i is read from shared memory once per K step instead of once per
+          // pair; A_0 comes first and initialises every level of a drain group.
           for (int kk = 0; kk < BK / 16; ++kk) {
-            int seen = 0;   // bit l set once level l has been written in this drain group
-            for (int p = 0; p < NPR; ++p) {
-              const int l = c_pl[p];
-              const uint32_t acc = (!first || kk > 0 || (seen >> l) & 1) ? 1u : 0u;
-              seen |= 1 << l;
-              const uint64_t da = umma_desc_sw128(smem_u32(stageA(s, c_pi[p])) + kk * 32);
-              const uint64_t db = umma_desc_sw128(smem_u32(stageB(s, c_pj[p])) + kk * 32);
-              umma_bf16(tmem + (uint32_t)((a * NLEVEL + l) * BN), da, db, IDESC, acc);
+            const uint64_t db = umma_desc_sw128(smem_u32(stageB(s, 0)) + kk * 32);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+              const uint32_t acc = (i > 0 || !first || kk > 0) ? 1u : 0u;
+              const uint64_t da = umma_desc_sw128(smem_u32(stageA(s, i)) + kk * 32);
+              umma_bf16(tmem + (uint32_t)((a * NLEVEL + i) * BN), da, db, idesc_n((NS - i) * BN), acc);
             }
           }
           umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
