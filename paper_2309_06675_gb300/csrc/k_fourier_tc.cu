@@ -349,16 +349,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ok = __all_sync(0xffffffffu, ok && !abort_sh);   // tcgen05.ld is warp-collective
         if (!ok) break;
         tc_fence_after();
+        // NLEV x 2 loads of 16 columns, double-buffered: the conversion of one buffer overlaps
+        // the TMEM load of the next
+        constexpr int NQ = EPI_COLS / 16, NSTEP = NLEV * NQ;
+        uint32_t rb[2][16];
+        const uint32_t set_addr = lane_addr + (uint32_t)(a * NLEVEL * BN + c_lo);
+        tmem_ld16_async(set_addr, rb[0]);
+        tmem_wait_ld16(rb[0]);
 #pragma unroll
-        for (int l = 0; l < NLEV; ++l) {
+        for (int q = 0; q < NSTEP; ++q) {
+          const int l = q / NQ, c0 = (q % NQ) * 16;
+          if (q + 1 < NSTEP)
+            tmem_ld16_async(set_addr + (uint32_t)(((q + 1) / NQ) * BN + ((q + 1) % NQ) * 16), rb[(q + 1) & 1]);
 #pragma unroll
-          for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(lane_addr + (uint32_t)((a * NLEVEL + l) * BN + c_lo + c0), r);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              isum[c0 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (32 - 8 * l);
-          }
+          for (int j = 0; j < 16; ++j)
+            isum[c0 + j] += (long long)__float2int_rn(__uint_as_float(rb[q & 1][j])) << (32 - 8 * l);
+          if (q + 1 < NSTEP) tmem_wait_ld16(rb[(q + 1) & 1]);
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[a]);
