@@ -611,13 +611,6 @@ __host__ __device__ __forceinline__ size_t bt_u_slots(int W) {
   return mat > lu ? mat : lu;
 }
 
-// deterministic start vector in [0.5, 1.5): integer hash of (row, vector)
-__device__ __forceinline__ double iit_start(int i, int j) {
-  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
-  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
-  return 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
-}
-
 constexpr int IIT_SOLVES = 3;
 
 __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, double* __restrict__ Eout,
@@ -690,8 +683,8 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
           const double a = dd[i + 1] - lam;
           const double bb = i + 2 < W ? ee[i + 1] : 0.0;
           // the interchange only selects operands: one FP64 sequence for the whole warp
-          const bool sw = !(fabs(q0) >= fabs(ei));
-          const double den = sw ? ei : (q0 == 0.0 ? tiny : q0);
+          const bool sw = mag_bits(q0) < mag_bits(ei);
+          const double den = sw ? ei : (mag_bits(q0) == 0ull ? tiny : q0);
           const double r = 1.0 / den;
           const double mlt = (sw ? q0 : ei) * r;
           rU0[i * 32 + lane] = r; U1[i * 32 + lane] = sw ? a : q1; U2[i * 32 + lane] = sw ? bb : q2;
@@ -702,13 +695,13 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
           q0 = n0;
           q2 = 0.0;
         }
-        if (q0 == 0.0) q0 = tiny;
+        if (mag_bits(q0) == 0ull) q0 = tiny;
         rU0[(W - 1) * 32 + lane] = 1.0 / q0;
         U1[(W - 1) * 32 + lane] = 0.0;   // the last row of U has no super-diagonals; the
         U2[(W - 1) * 32 + lane] = 0.0;   // back-substitution reads them (times zero)
         if (W >= 2) U2[(W - 2) * 32 + lane] = 0.0;
         // ---- inverse iteration in column m of Z
-        for (int i = 0; i < W; ++i) Z[i * LDU + m] = iit_start(i, m);
+        for (int i = 0; i < W; ++i) Z[i * LDU + m] = iit_start_vec(i, m);
         for (int it = 0; it < IIT_SOLVES; ++it) {
           for (int i = 0; i + 1 < W; ++i) {
             const double mlt = ML[i * 32 + lane];

@@ -32,12 +32,6 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-__device__ __forceinline__ double iit_start(int i, int j) {
-  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
-  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
-  return 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
-}
-
 // ------------------------------------------------------------------ inverse iteration
 // Persistent: CTA b handles k = b, b + gridDim.x, ...; block = ldt = W rounded up to a warp;
 // thread j handles the cluster starting at sorted index j.  Z: [n][W][W] real, column m =
@@ -110,8 +104,8 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
           const double a = dd[i + 1] - lam;
           const double bb = i + 2 < W ? ee[i + 1] : 0.0;
           const size_t o = (size_t)i * ldt + t;
-          const bool sw = !(fabs(q0) >= fabs(ei));   // interchange rows i and i + 1
-          const double den = sw ? ei : (q0 == 0.0 ? tiny : q0);
+          const bool sw = mag_bits(q0) < mag_bits(ei);   // interchange rows i and i + 1
+          const double den = sw ? ei : (mag_bits(q0) == 0ull ? tiny : q0);
           const double r = 1.0 / den;
           const double mlt = (sw ? q0 : ei) * r;
           rU0[o] = r; U1[o] = sw ? a : q1; U2[o] = sw ? bb : q2; ML[o] = mlt;
@@ -121,12 +115,12 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
           q0 = n0;
           q2 = 0.0;
         }
-        if (q0 == 0.0) q0 = tiny;
+        if (mag_bits(q0) == 0ull) q0 = tiny;
         {
           const size_t o = (size_t)(W - 1) * ldt + t;
           rU0[o] = 1.0 / q0; U1[o] = 0.0; U2[o] = 0.0;
         }
-        for (int i = 0; i < W; ++i) Zk[(size_t)i * W + m] = iit_start(i, m);
+        for (int i = 0; i < W; ++i) Zk[(size_t)i * W + m] = iit_start_vec(i, m);
         for (int it = 0; it < IIT_SOLVES; ++it) {
           for (int i = 0; i + 1 < W; ++i) {
             const double mlt = ML[(size_t)i * ldt + t];
@@ -162,13 +156,14 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
         }
         if (rq) {
           // z^T T z = sum_i d_i z_i^2 + 2 sum_i e_i z_i z_{i+1} (z of unit norm)
-          double q = 0.0, zi = Zk[m];
+          double q = 0.0, qe = 0.0, zi = Zk[m];
           for (int i = 0; i < W; ++i) {
             const double zn = i + 1 < W ? Zk[(size_t)(i + 1) * W + m] : 0.0;
             q = fma(dd[i] * zi, zi, q);
-            if (i + 1 < W) q = fma(2.0 * ee[i] * zi, zn, q);
+            if (i + 1 < W) qe = fma(ee[i] * zi, zn, qe);
             zi = zn;
           }
+          q = fma(2.0, qe, q);
           if (m > j && q < rprev) q = rprev;   // ascending order within the cluster
           rprev = q;
           Eout[k * W + m] = q;

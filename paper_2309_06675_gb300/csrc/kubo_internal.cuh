@@ -65,6 +65,23 @@ struct SepBox {
 };
 
 // ---------------------------------------------------------------- small helpers
+// |x| as an ordered integer (non-NaN x): |x| < |y| iff mag_bits(x) < mag_bits(y), and x == 0
+// iff mag_bits(x) == 0 -- integer compares in place of FP64 compares (GB300 issues those on the
+// FP64 pipe, at 1/64 of the FP32 rate)
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// start vector of the inverse iterations: 0.5 + (h >> 8) 2^-24 in [0.5, 1.5) from an integer hash
+// of (row, vector); 1 + (h >> 8) 2^-24 is assembled from its bits (exponent of 1, the 24-bit
+// integer as the leading mantissa bits) and 0.5 subtracted exactly, instead of an integer ->
+// FP64 conversion and a multiply-add, both on the FP64 pipe
+__device__ __forceinline__ double iit_start_vec(int i, int j) {
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j * 0x85EBCA77u + 0x165667B1u);
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return __longlong_as_double((long long)((0x3FFull << 52) | ((unsigned long long)(h >> 8) << 28))) - 0.5;
+}
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
