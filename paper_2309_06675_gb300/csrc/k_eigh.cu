@@ -20,6 +20,8 @@
 //
 // Padded leading dimensions (W+1) keep column walks conflict-free in shared memory (the
 // GPU counterpart of the paper's padding against memory-bank conflicts).
+#include <climits>
+
 #include "kubo_internal.cuh"
 
 namespace kubo {
@@ -292,9 +294,23 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
   double2* sp = A + (size_t)W * (W + 1) / 2;
   double2* pb = sp;
   __shared__ double s_tau[2], s_K[2];
+  __shared__ unsigned char s_parts[64];   // symv column partitions for trailing order m
   const int64_t k = 2 * (int64_t)blockIdx.x + h;
   const bool live = k < n;
   double2* beg = b.phase + k * W;
+  if (t >= 1 && t < W) {
+    // the partition count P <= min(256 / m, symv_parts) with the fewest FP64 warp instructions
+    // for the symv (warp w's lanes start at part 32 w / m and run ceil((m - part) / P) columns,
+    // 4 FMAs each) plus the partial-sum pass (ceil(m / 32) warps, 2 P + 2 operations each)
+    const int m = t, pmax = max(1, min(256 / m, b.symv_parts));
+    int best = 1, bcost = INT_MAX;
+    for (int P = 1; P <= pmax; ++P) {
+      int c = ((m + 31) >> 5) * (2 * P + 2);
+      for (int w = 0; 32 * w < m * P; ++w) c += 4 * ((m - (32 * w) / m + P - 1) / P);
+      if (c < bcost) { bcost = c; best = P; }
+    }
+    s_parts[m] = (unsigned char)best;
+  }
   double* tout = b.tau + k * W;
   const double* P = Hp + (size_t)k * ld;
 
@@ -370,8 +386,9 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
     const double tau = s_tau[h];
     const bool act = live && tau != 0.0;
     double2* vb = sp + W;
-    // p = tau * A22 v (the one-k kernel's partition over the half's 256 threads)
-    const int P2 = max(1, min(256 / m, b.symv_parts));
+    // p = tau * A22 v (the one-k kernel's partition over the half's 256 threads, with the
+    // partition count of the table)
+    const int P2 = s_parts[m];
     {
       const int r = th % m, part = th / m;
       if (act && part < P2) {
@@ -429,24 +446,29 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
       }
     __syncthreads();
     if (act) {
-      // A22 <- A22 - v w^H - w v^H on the lower triangle (c <= r)
-      const int ntri = m * (m + 1) / 2;
-      for (int idx = th; idx < ntri; idx += 256) {
-        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-        while (r * (r + 1) / 2 > idx) --r;
-        while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-        const int c = idx - r * (r + 1) / 2;
+      // A22 <- A22 - v w^H - w v^H on the lower triangle: the strictly lower elements (c < r),
+      // eight FMAs each with every lane busy, then the diagonal (real part only)
+      const int nlow = m * (m - 1) / 2;
+      for (int idx = th; idx < nlow; idx += 256) {
+        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) + 1.0f) * 0.5f);
+        while (r * (r - 1) / 2 > idx) --r;
+        while ((r + 1) * r / 2 <= idx) ++r;
+        const int c = idx - r * (r - 1) / 2;
         const double2 vr = vb[r], wr = pb[r], vc = vb[c], wc = pb[c];
         double2 a = A[tri(o + r, o + c)];
         a.x = fma(-vr.x, wc.x, a.x); a.x = fma(-vr.y, wc.y, a.x);
         a.x = fma(-wr.x, vc.x, a.x); a.x = fma(-wr.y, vc.y, a.x);
-        if (c == r) {
-          a.y = 0.0;
-        } else {
-          a.y = fma(-vr.y, wc.x, a.y); a.y = fma(vr.x, wc.y, a.y);
-          a.y = fma(-wr.y, vc.x, a.y); a.y = fma(wr.x, vc.y, a.y);
-        }
+        a.y = fma(-vr.y, wc.x, a.y); a.y = fma(vr.x, wc.y, a.y);
+        a.y = fma(-wr.y, vc.x, a.y); a.y = fma(wr.x, vc.y, a.y);
         A[tri(o + r, o + c)] = a;
+      }
+      for (int r = th; r < m; r += 256) {
+        const double2 vr = vb[r], wr = pb[r];
+        double2 a = A[tri(o + r, o + r)];
+        a.x = fma(-vr.x, wr.x, a.x); a.x = fma(-vr.y, wr.y, a.x);
+        a.x = fma(-wr.x, vr.x, a.x); a.x = fma(-wr.y, vr.y, a.x);
+        a.y = 0.0;
+        A[tri(o + r, o + r)] = a;
       }
     }
     __syncthreads();
