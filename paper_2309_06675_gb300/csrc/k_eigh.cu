@@ -48,6 +48,23 @@ __device__ __forceinline__ int tri(int r, int c) { return (r * (r + 1) >> 1) + c
 // tridiag2_kernel below)
 constexpr int TRI_NT = 512;
 
+// Column partitions of the symv for trailing order m on nt threads: the count P up to
+// min(nt / m, cap) with the fewest FP64 warp instructions -- thread t takes row t mod m and part
+// t / m, so warp w's lanes start at part 32 w / m and run ceil((m - part) / P) columns of 4 FMAs,
+// and the partial-sum pass runs ceil(m / 32) warps of 2 P + 2 operations.  For the two-k
+// reduction, whose three CTAs per SM keep the FP64 pipe fed while one of them runs a phase on
+// few warps.
+__device__ __forceinline__ int symv_partitions(int m, int nt, int cap) {
+  const int pmax = max(1, min(nt / m, cap));
+  int best = 1, bcost = INT_MAX;
+  for (int P = 1; P <= pmax; ++P) {
+    int c = ((m + 31) >> 5) * (2 * P + 2);
+    for (int w = 0; 32 * w < m * P; ++w) c += 4 * ((m - (32 * w) / m + P - 1) / P);
+    if (c < bcost) { bcost = c; best = P; }
+  }
+  return best;
+}
+
 // NTT = 512 threads: one CTA (136 KB of shared memory at W = 128) holds an SM, and more warps
 // than 256 cover its barriers (W = 128: 235 -> 229 ms per 18,432 k-points; 1,024 threads
 // with twice the symv parts: 240 ms)
@@ -140,9 +157,11 @@ __global__ void __launch_bounds__(NTT, 1) tridiag_kernel(const T* __restrict__ H
       // c = part, part + P, ... (part = t / m, P = min(NTT / m, cap) parts per row, cap = 4 by
       // default), so that the warps issue full; the P partial sums of a row are added in part
       // order by the m row threads.  P is capped: for a small trailing block more parts would
-      // shorten the product but lengthen that sum, whose warps run with m of their 32 lanes
-      // (the other CTAs of the SM keep the FP64 pipe busy meanwhile).  The conjugate of the mirrored
-      // element flips a sign bit on the integer side (no FP64 instruction).
+      // shorten the product but lengthen that sum, whose warps run with m of their 32 lanes.
+      // (The two-k kernel picks P per m by instruction count instead; here, with one CTA per
+      // SM at W = 128, fewer parts leave the FP64 pipe without other warps to issue: 6 %
+      // slower.)  The conjugate of the mirrored element flips a sign bit on the integer side
+      // (no FP64 instruction).
       {
         const int P = max(1, min(NTT / m, b.symv_parts));
         const int r = t % m, part = t / m;
@@ -190,25 +209,30 @@ __global__ void __launch_bounds__(NTT, 1) tridiag_kernel(const T* __restrict__ H
         pb[r] = make_double2(fma(-K, v.x, p.x), fma(-K, v.y, p.y));
       }
       __syncthreads();
-      // A22 <- A22 - v w^H - w v^H on the lower triangle (c <= r)
-      const int ntri = m * (m + 1) / 2;
-      for (int idx = t; idx < ntri; idx += NTT) {
-        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-        while (r * (r + 1) / 2 > idx) --r;
-        while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-        const int c = idx - r * (r + 1) / 2;
+      // A22 <- A22 - v w^H - w v^H on the lower triangle: the strictly lower elements (c < r),
+      // eight FMAs each with every lane busy, then the diagonal (real part only)
+      const int nlow = m * (m - 1) / 2;
+      for (int idx = t; idx < nlow; idx += NTT) {
+        int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) + 1.0f) * 0.5f);
+        while (r * (r - 1) / 2 > idx) --r;
+        while ((r + 1) * r / 2 <= idx) ++r;
+        const int c = idx - r * (r - 1) / 2;
         const double2 vr = vb[r], wr = pb[r], vc = vb[c], wc = pb[c];
         double2 a = A[tri(o + r, o + c)];
         // v_r conj(w_c) + w_r conj(v_c)
         a.x = fma(-vr.x, wc.x, a.x); a.x = fma(-vr.y, wc.y, a.x);
         a.x = fma(-wr.x, vc.x, a.x); a.x = fma(-wr.y, vc.y, a.x);
-        if (c == r) {
-          a.y = 0.0;
-        } else {
-          a.y = fma(-vr.y, wc.x, a.y); a.y = fma(vr.x, wc.y, a.y);
-          a.y = fma(-wr.y, vc.x, a.y); a.y = fma(wr.x, vc.y, a.y);
-        }
+        a.y = fma(-vr.y, wc.x, a.y); a.y = fma(vr.x, wc.y, a.y);
+        a.y = fma(-wr.y, vc.x, a.y); a.y = fma(wr.x, vc.y, a.y);
         A[tri(o + r, o + c)] = a;
+      }
+      for (int r = t; r < m; r += NTT) {
+        const double2 vr = vb[r], wr = pb[r];
+        double2 a = A[tri(o + r, o + r)];
+        a.x = fma(-vr.x, wr.x, a.x); a.x = fma(-vr.y, wr.y, a.x);
+        a.x = fma(-wr.x, vr.x, a.x); a.x = fma(-wr.y, vr.y, a.x);
+        a.y = 0.0;
+        A[tri(o + r, o + r)] = a;
       }
     }
     __syncthreads();
@@ -298,19 +322,7 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
   const int64_t k = 2 * (int64_t)blockIdx.x + h;
   const bool live = k < n;
   double2* beg = b.phase + k * W;
-  if (t >= 1 && t < W) {
-    // the partition count P <= min(256 / m, symv_parts) with the fewest FP64 warp instructions
-    // for the symv (warp w's lanes start at part 32 w / m and run ceil((m - part) / P) columns,
-    // 4 FMAs each) plus the partial-sum pass (ceil(m / 32) warps, 2 P + 2 operations each)
-    const int m = t, pmax = max(1, min(256 / m, b.symv_parts));
-    int best = 1, bcost = INT_MAX;
-    for (int P = 1; P <= pmax; ++P) {
-      int c = ((m + 31) >> 5) * (2 * P + 2);
-      for (int w = 0; 32 * w < m * P; ++w) c += 4 * ((m - (32 * w) / m + P - 1) / P);
-      if (c < bcost) { bcost = c; best = P; }
-    }
-    s_parts[m] = (unsigned char)best;
-  }
+  if (t >= 1 && t < W) s_parts[t] = (unsigned char)symv_partitions(t, 256, b.symv_parts);
   double* tout = b.tau + k * W;
   const double* P = Hp + (size_t)k * ld;
 
