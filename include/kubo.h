@@ -348,8 +348,10 @@ typedef struct kubo_batch_schedule {
   int fourier_group_m;      /* tensor-core Fourier sum: 128-k tiles rasterised together per
                                column tile (L2 reuse of the basis tiles); default 8, tuned over
                                {4, 8, 16}; 1..64 */
-  int symv_parts;           /* Householder reduction: column partitions per row of its symv;
-                               default 4, tuned over {2, 4, 8}; 1..8 */
+  int symv_parts;           /* Householder reduction: cap on the column partitions per row of
+                               its symv (W <= 64: the count up to the cap with the fewest FP64
+                               instructions for each trailing order; W > 64: the cap where
+                               the threads allow); default 4, tuned over {2, 4, 8}; 1..8 */
   int rotation;             /* step (3) kernel as kubo_options.rotation_tc (1..3 fix it);
                                0 = opt->rotation_tc, tuned over {automatic, 2, 3} when that is
                                0 and the precision has an FP32-grade step (3) */
