@@ -1056,17 +1056,43 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) 
   lo = to_tf32(x - __uint_as_float(hi));
 }
 
-// four consecutive K entries (k0 = 4 c4 .. 4 c4 + 3) of one row, hi and lo tiles
-__device__ __forceinline__ void put4_tf32(unsigned char* hi_tile, unsigned char* lo_tile, int row,
-                                          int c4, const float (&x)[4]) {
-  uint4 h, l;
-  tf32_split(x[0], h.x, l.x);
-  tf32_split(x[1], h.y, l.y);
-  tf32_split(x[2], h.z, l.z);
-  tf32_split(x[3], h.w, l.w);
-  const uint32_t off = sw128_off32(row, 4 * c4);
-  *reinterpret_cast<uint4*>(hi_tile + off) = h;
-  *reinterpret_cast<uint4*>(lo_tile + off) = l;
+// The block-real rows of a complex operand in K columns 4 c4 .. + 3 (left) and 16 + 4 c4 .. + 3
+// (right): NEG_TOP: row r0 = [x | -y], row r1 = [y | x]; else row r0 = [x | y], row r1 =
+// [-y | x].  Each value is split once; a negation flips the sign bits of both parts (exact).
+template <bool NEG_TOP>
+__device__ __forceinline__ void put4_tf32_twin(unsigned char* hi_tile, unsigned char* lo_tile,
+                                               int r0, int r1, int c4, const float (&x)[4],
+                                               const float (&y)[4]) {
+  uint4 xh, xl, yh, yl;
+  tf32_split(x[0], xh.x, xl.x); tf32_split(x[1], xh.y, xl.y);
+  tf32_split(x[2], xh.z, xl.z); tf32_split(x[3], xh.w, xl.w);
+  tf32_split(y[0], yh.x, yl.x); tf32_split(y[1], yh.y, yl.y);
+  tf32_split(y[2], yh.z, yl.z); tf32_split(y[3], yh.w, yl.w);
+  const uint32_t S = 0x80000000u;
+  const uint4 nyh = make_uint4(yh.x ^ S, yh.y ^ S, yh.z ^ S, yh.w ^ S);
+  const uint4 nyl = make_uint4(yl.x ^ S, yl.y ^ S, yl.z ^ S, yl.w ^ S);
+  const uint32_t a0 = sw128_off32(r0, 4 * c4), a1 = sw128_off32(r0, 16 + 4 * c4);
+  const uint32_t b0 = sw128_off32(r1, 4 * c4), b1 = sw128_off32(r1, 16 + 4 * c4);
+  *reinterpret_cast<uint4*>(hi_tile + a0) = xh;
+  *reinterpret_cast<uint4*>(lo_tile + a0) = xl;
+  *reinterpret_cast<uint4*>(hi_tile + a1) = NEG_TOP ? nyh : yh;
+  *reinterpret_cast<uint4*>(lo_tile + a1) = NEG_TOP ? nyl : yl;
+  *reinterpret_cast<uint4*>(hi_tile + b0) = NEG_TOP ? yh : nyh;
+  *reinterpret_cast<uint4*>(lo_tile + b0) = NEG_TOP ? yl : nyl;
+  *reinterpret_cast<uint4*>(hi_tile + b1) = xh;
+  *reinterpret_cast<uint4*>(lo_tile + b1) = xl;
+}
+// row r of a tile: [x | y] in K columns 4 c4 .. + 3 and 16 + 4 c4 .. + 3
+__device__ __forceinline__ void put4_tf32_pair(unsigned char* hi_tile, unsigned char* lo_tile, int r,
+                                               int c4, const float (&x)[4], const float (&y)[4]) {
+  uint4 xh, xl, yh, yl;
+  tf32_split(x[0], xh.x, xl.x); tf32_split(x[1], xh.y, xl.y);
+  tf32_split(x[2], xh.z, xl.z); tf32_split(x[3], xh.w, xl.w);
+  tf32_split(y[0], yh.x, yl.x); tf32_split(y[1], yh.y, yl.y);
+  tf32_split(y[2], yh.z, yl.z); tf32_split(y[3], yh.w, yl.w);
+  const uint32_t a0 = sw128_off32(r, 4 * c4), a1 = sw128_off32(r, 16 + 4 * c4);
+  *reinterpret_cast<uint4*>(hi_tile + a0) = xh; *reinterpret_cast<uint4*>(lo_tile + a0) = xl;
+  *reinterpret_cast<uint4*>(hi_tile + a1) = yh; *reinterpret_cast<uint4*>(lo_tile + a1) = yl;
 }
 
 __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
@@ -1209,15 +1235,17 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
       for (int j = 0; j < 32; ++j) tv[j] = 0.f;
       if constexpr (XS) cp_async_wait_all();   // this direction's rows (the barrier follows)
       for (int h = 0; h < 4 && ok; ++h) {
-        __syncthreads();   // the stage area / previous quarter's operands are free
-        // A1 rows i and 64 + i, K columns 32 h + 4 c4 .. + 3 (X column c = that - 64 h2)
-        const bool second = h >= 2;
-        for (int it = t; it < 64 * 8; it += TF_NT) {
-          const int i = it & 63, c4 = it >> 6;
+        __syncthreads();   // the stage area / previous phase's operands are free
+        // Phase h pairs the X columns c = 16 h .. 16 h + 15 of both K halves: tile K columns
+        // 0..15 are K = c (real parts), 16..31 are K = 64 + c (imaginary parts), in A and B
+        // alike (the product sums over K in any order).  A1 rows i: [X_r | -X_i], rows
+        // 64 + i: [X_i | X_r], each X value loaded and split once (-X_i by the sign bits).
+        {
+          const int i = t & 63, c4 = t >> 6;   // 64 rows x 4 groups of 4 columns: one per thread
           float xr[4], xi[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int c = (h & 1) * 32 + 4 * c4 + q;
+            const int c = 16 * h + 4 * c4 + q;
             float re = 0.f, im = 0.f;
             if (i < W && c < W) {
               if constexpr (XS) {
@@ -1233,25 +1261,19 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
             xr[q] = re;
             xi[q] = im;
           }
-          if (!second) {
-            put4_tf32(a_hi, a_lo, i, c4, xr);        // [X_r | .]
-            put4_tf32(a_hi, a_lo, 64 + i, c4, xi);   // [X_i | .]
-          } else {
-            float nx[4] = {-xi[0], -xi[1], -xi[2], -xi[3]};
-            put4_tf32(a_hi, a_lo, i, c4, nx);        // [. | -X_i]
-            put4_tf32(a_hi, a_lo, 64 + i, c4, xr);   // [. | X_r]
-          }
+          put4_tf32_twin<true>(a_hi, a_lo, i, 64 + i, c4, xr, xi);
         }
-        // B1[n][k] = U_r[k][n] (k < 64), U_i[k - 64][n]
-        for (int it = t; it < 64 * 8; it += TF_NT) {
-          const int nn = it & 63, c4 = it >> 6;
-          float u[4];
+        // B1 rows n: [U_r[c][n] | U_i[c][n]]
+        {
+          const int nn = t & 63, c4 = t >> 6;
+          float ur[4], ui[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 v = sU[((h & 1) * 32 + 4 * c4 + q) * TF_LDU + nn];
-            u[q] = second ? v.y : v.x;
+            const float2 v = sU[(16 * h + 4 * c4 + q) * TF_LDU + nn];
+            ur[q] = v.x;
+            ui[q] = v.y;
           }
-          put4_tf32(b_hi, b_lo, nn, c4, u);
+          put4_tf32_pair(b_hi, b_lo, nn, c4, ur, ui);
         }
         if (!mma_quarter(0, true)) { ok = false; break; }
         // the last read of this direction's rows is behind the barrier: fetch Y (lands while
@@ -1273,29 +1295,36 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
       for (int j = 0; j < 32; ++j) vacc[j] = 0.f;
       for (int h = 0; h < 4 && ok; ++h) {
         __syncthreads();
-        const bool second = h >= 2;
-        // A2 rows m, 64 + m; K = 32 h + 4 c4 + q is row kk of U (kk = K mod 64)
-        for (int it = t; it < 64 * 8; it += TF_NT) {
-          const int m = it & 63, c4 = it >> 6;
-          float p0[4], p1[4];
+        // Phase h pairs the rows r = 16 h .. 16 h + 15 of T_r (tile K 0..15) and of T_i (16..31).
+        // A2 rows m: [U_r[r][m] | U_i[r][m]], rows 64 + m: [-U_i[r][m] | U_r[r][m]]
+        {
+          const int m = t & 63, c4 = t >> 6;
+          float ur[4], ui[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 v = sU[((h & 1) * 32 + 4 * c4 + q) * TF_LDU + m];   // U[kk][m]
-            p0[q] = second ? v.y : v.x;     // [U_r^T | U_i^T]
-            p1[q] = second ? v.x : -v.y;    // [-U_i^T | U_r^T]
+            const float2 v = sU[(16 * h + 4 * c4 + q) * TF_LDU + m];   // U[r][m]
+            ur[q] = v.x;
+            ui[q] = v.y;
           }
-          put4_tf32(a_hi, a_lo, m, c4, p0);
-          put4_tf32(a_hi, a_lo, 64 + m, c4, p1);
+          put4_tf32_twin<false>(a_hi, a_lo, m, 64 + m, c4, ur, ui);
         }
-        // B2[n][k] = [T_r; T_i][k][n]: K rows 32 h .. 32 h + 31 are this quarter's TMEM lanes
-        if (quarter == h) {
+        // B2[n][K]: T_r[r][n] (K = r - 16 h) and T_i[r][n] (K = 16 + r - 16 h); row r of T_r is
+        // TMEM lane r, of T_i lane 64 + r: held in tv by the threads of lanes 16 h .. 16 h + 15
+        // (quarter h / 2) and 64 + those (quarter 2 + h / 2), each for its 32 columns n
+        {
+          const int r0 = 16 * (h & 1);   // lane offset within the quarter
+          const bool mine = (quarter == (h >> 1) || quarter == 2 + (h >> 1)) && lane >= r0 &&
+                            lane < r0 + 16;
+          if (mine) {
+            const int kc = (quarter >= 2 ? 16 : 0) + (lane - r0);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            uint32_t hi, lo;
-            tf32_split(tv[j], hi, lo);
-            const uint32_t off = sw128_off32(chalf * 32 + j, lane);
-            *reinterpret_cast<uint32_t*>(b_hi + off) = hi;
-            *reinterpret_cast<uint32_t*>(b_lo + off) = lo;
+            for (int j = 0; j < 32; ++j) {
+              uint32_t hi, lo;
+              tf32_split(tv[j], hi, lo);
+              const uint32_t off = sw128_off32(chalf * 32 + j, kc);
+              *reinterpret_cast<uint32_t*>(b_hi + off) = hi;
+              *reinterpret_cast<uint32_t*>(b_lo + off) = lo;
+            }
           }
         }
         if (!mma_quarter(64, true)) { ok = false; break; }
