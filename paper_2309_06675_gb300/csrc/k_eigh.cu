@@ -758,6 +758,10 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(int W, EighBufs b, do
             for (int i = 0; i < W; ++i) c = fma(Z[i * LDU + q], Z[i * LDU + m], c);
             for (int i = 0; i < W; ++i) Z[i * LDU + m] = fma(-c, Z[i * LDU + q], Z[i * LDU + m]);
           }
+          if (it + 1 < IIT_SOLVES) {   // between solves: a power-of-two rescale (exact)
+            pow2_rescale(Z + m, W, (size_t)LDU);
+            continue;
+          }
           double s0 = 0.0, s1 = 0.0;
           int i = 0;
           for (; i + 1 < W; i += 2) {

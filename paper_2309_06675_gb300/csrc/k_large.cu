@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
             for (int i = 0; i < W; ++i)
               Zk[(size_t)i * W + m] = fma(-c, Zk[(size_t)i * W + q], Zk[(size_t)i * W + m]);
           }
+          if (it + 1 < IIT_SOLVES) {   // between solves: a power-of-two rescale (exact)
+            pow2_rescale(Zk + m, W, (size_t)W);
+            continue;
+          }
           double s0 = 0.0, s1 = 0.0;
           int i = 0;
           for (; i + 1 < W; i += 2) {

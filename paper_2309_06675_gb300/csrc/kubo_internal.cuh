@@ -72,6 +72,30 @@ __device__ __forceinline__ unsigned long long mag_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
+// x_i <- x_i 2^-e (i < n, stride apart), e the exponent of max |x_i|, on the bit patterns: the
+// exponent fields are shifted by integer subtraction (exact), zeros, subnormals and entries
+// that would leave the normal range become signed zeros (all below 2^-1022 of the largest or
+// of the normal range), and a zero or non-finite vector is left alone.  The inverse iterations rescale their iterate this way
+// between solves (no FP64 square root, reciprocal or multiplies; only the last solve's vector
+// is normalised in FP64).
+__device__ __forceinline__ void pow2_rescale(double* x, int n, size_t stride) {
+  unsigned long long mx = 0ull;
+  for (int i = 0; i < n; ++i) {
+    const unsigned long long u = mag_bits(x[i * stride]);
+    mx = u > mx ? u : mx;
+  }
+  const int ex = (int)(mx >> 52);
+  if (ex == 0 || ex >= 0x7FF || ex == 1023) return;
+  const int e = ex - 1023;
+  for (int i = 0; i < n; ++i) {
+    const long long b = __double_as_longlong(x[i * stride]);
+    const int bex = (int)((b >> 52) & 0x7FF);
+    const long long r = (bex >= 1 && bex - e >= 1) ? b - ((long long)e << 52)
+                                                   : (b & (long long)0x8000000000000000ull);
+    x[i * stride] = __longlong_as_double(r);
+  }
+}
+
 // start vector of the inverse iterations: 0.5 + (h >> 8) 2^-24 in [0.5, 1.5) from an integer hash
 // of (row, vector); 1 + (h >> 8) 2^-24 is assembled from its bits (exponent of 1, the 24-bit
 // integer as the leading mantissa bits) and 0.5 subtracted exactly, instead of an integer ->
