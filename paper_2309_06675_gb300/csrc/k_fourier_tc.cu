@@ -153,35 +153,113 @@ __global__ void basis_slice_kernel(const double* __restrict__ Bp, const int* __r
   }
 }
 
-// A[s][m][k] for m < Mpad (rows >= n are zero), k < Kp.  One thread per (m, h).
-__global__ void coef_slice_kernel(Model md, Mesh mesh, KList kl, int Mpad, int Kp,
-                                  __nv_bfloat16* __restrict__ A) {
+// ---- FP32-pair (double-float) arithmetic for the phases: ~2^-46 relative, on the FP32 pipe
+struct Pf {
+  float h, l;
+};
+// exact h + l = a + b (Knuth's TwoSum)
+__device__ __forceinline__ Pf pf_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  return Pf{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ Pf pf_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return Pf{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ Pf pf_mul(Pf a, Pf b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);   // the rounding error of p, exactly
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return pf_norm(p, e);
+}
+__device__ __forceinline__ Pf pf_add(Pf a, Pf b) {
+  const Pf s = pf_two_sum(a.h, b.h);
+  return pf_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ Pf pf_neg(Pf a) { return Pf{-a.h, -a.l}; }
+// (a.re + i a.im)(b.re + i b.im), operands as float4 (re_h, re_l, im_h, im_l)
+__device__ __forceinline__ float4 pf_cmul(const float4& a, const float4& b) {
+  const Pf ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+  const Pf re = pf_add(pf_mul(ar, br), pf_neg(pf_mul(ai, bi)));
+  const Pf im = pf_add(pf_mul(ar, bi), pf_mul(ai, br));
+  return make_float4(re.h, re.l, im.h, im.l);
+}
+// v 2^62 as an integer for an FP32 v with |v| <= 2 (bits below 2^-62 dropped), from the bits
+__device__ __forceinline__ long long f32_fix62(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int ex = (int)((b >> 23) & 0xFFu);
+  if (ex == 0) return 0;   // zero or subnormal (below 2^-126)
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = ex - 150 + 62;   // v 2^62 = m 2^(ex - 150 + 62)
+  const long long mag = sh >= 0 ? (m << sh) : (sh > -40 ? (m >> -sh) : 0);
+  return (b >> 31) ? -mag : mag;
+}
+// round((h + l) 2^31) for |h + l| <= 1 + 2^-40: the pair's parts as 62-bit fixed-point
+// integers, summed exactly, rounded to 31 fractional bits (ties away from zero)
+__device__ __forceinline__ long long pf_fixed31(float h, float l) {
+  const long long q = f32_fix62(h) + f32_fix62(l);
+  const long long aq = q < 0 ? -q : q;
+  const long long r = (aq + (1ll << 30)) >> 31;
+  return q < 0 ? -r : r;
+}
+// x mod d in [0, d) for |x| < 2^32, by the multiply-high division
+__device__ __forceinline__ int posmod(long long x, const FastDiv& f) {
+  const unsigned long long ax = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  uint32_t r;
+  if (ax < 0x100000000ull) {
+    const uint32_t a = (uint32_t)ax;
+    r = a - f.div(a) * f.d;
+  } else {
+    r = (uint32_t)(ax % f.d);
+  }
+  return (x < 0 && r) ? (int)(f.d - r) : (int)r;
+}
+
+// A[s][m][k] for m < Mpad (rows >= n are zero), k < Kp.  Persistent CTAs over the rows
+// (k-points); a row's mesh coordinates once per row, then per (m, h) the three per-axis
+// twiddles by exact integer argument reduction (multiply-high modulo) and their product as two
+// complex multiplies in FP32 pairs (~2^-46: the FP64 products would run on the FP64 pipe, at
+// 1/64 of the FP32 rate), rounded to 31 fractional bits from the pair with integer operations.
+constexpr int CS_NT = 256;
+__global__ void __launch_bounds__(CS_NT) coef_slice_kernel(Model md, Mesh mesh, KList kl, int Mpad,
+                                                           int Kp, __nv_bfloat16* __restrict__ A) {
   const int npair = Kp / 2;
-  const int64_t total = (int64_t)Mpad * npair;
   const int64_t plane = (int64_t)Mpad * Kp;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int m = (int)(t / npair), h = (int)(t % npair);
-    double c = 0.0, s = 0.0;
-    if (m < kl.n) {
-      if (h < md.N_h) {
-        int j1, j2, j3;
-        mesh_coords(mesh, klist_get(kl, m), j1, j2, j3);
-        const int* r = md.Rh + 3 * h;
-        const double2 e = mesh_phase(md.tab, md.tab_off, mesh, j1, j2, j3, r[0], r[1], r[2]);
-        c = e.x;
-        s = e.y;
-      } else if (h == md.N_h) {
-        c = 1.0;   // the R = 0 term (column 2 N_h); its partner column stays 0
+  const FastDiv f1((uint32_t)mesh.N1), f2((uint32_t)mesh.N2), f3((uint32_t)mesh.N3);
+  const float4* t1 = md.tab_df + md.tab_off[0];
+  const float4* t2 = md.tab_df + md.tab_off[1];
+  const float4* t3 = md.tab_df + md.tab_off[2];
+  __shared__ int s_j[3];
+  for (int m = blockIdx.x; m < Mpad; m += gridDim.x) {
+    const bool live = m < kl.n;
+    if (threadIdx.x == 0 && live) mesh_coords(mesh, klist_get(kl, m), s_j[0], s_j[1], s_j[2]);
+    __syncthreads();
+    const int j1 = s_j[0], j2 = s_j[1], j3 = s_j[2];
+    for (int h = threadIdx.x; h < npair; h += CS_NT) {
+      long long qc = 0, qs = 0;
+      if (live) {
+        if (h < md.N_h) {
+          const int* r = md.Rh + 3 * h;
+          const float4 e = pf_cmul(pf_cmul(t1[posmod((long long)j1 * r[0], f1)],
+                                           t2[posmod((long long)j2 * r[1], f2)]),
+                                   t3[posmod((long long)j3 * r[2], f3)]);
+          qc = pf_fixed31(e.x, e.y);
+          qs = pf_fixed31(e.z, e.w);
+        } else if (h == md.N_h) {
+          qc = 1ll << 31;   // the R = 0 term (column 2 N_h); its partner column stays 0
+        }
       }
-    }
-    __nv_bfloat16 cs[NSLICE], ss[NSLICE];
-    slice_scaled(c, 0, cs);
-    slice_scaled(s, 0, ss);
-    const int64_t o = (int64_t)m * Kp + 2 * h;
+      __nv_bfloat16 cs[NSLICE], ss[NSLICE];
+      slice4_bf16(qc, cs);
+      slice4_bf16(qs, ss);
+      const int64_t o = (int64_t)m * Kp + 2 * h;
 #pragma unroll
-    for (int i = 0; i < NSLICE; ++i)
-      *reinterpret_cast<__nv_bfloat162*>(A + i * plane + o) = __halves2bfloat162(cs[i], ss[i]);
+      for (int i = 0; i < NSLICE; ++i)
+        *reinterpret_cast<__nv_bfloat162*>(A + i * plane + o) = __halves2bfloat162(cs[i], ss[i]);
+    }
+    __syncthreads();   // s_j is rewritten for the next row
   }
 }
 
@@ -495,8 +573,10 @@ cudaError_t launch_basis_split(const double* Bp, const int* Rh, int N_h, int W, 
 
 cudaError_t launch_coef_split(const Model& md, const Mesh& mesh, const KList& kl, int Mpad, int Kp,
                               void* A, cudaStream_t s) {
-  coef_slice_kernel<<<grid_for((int64_t)Mpad * (Kp / 2), 256), 256, 0, s>>>(md, mesh, kl, Mpad, Kp,
-                                                                             (__nv_bfloat16*)A);
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(Mpad, 8 * std::max(nsm, 1)));   // persistent over the rows
+  coef_slice_kernel<<<grid, CS_NT, 0, s>>>(md, mesh, kl, Mpad, Kp, (__nv_bfloat16*)A);
   return cudaGetLastError();
 }
 

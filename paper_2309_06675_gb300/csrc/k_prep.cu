@@ -115,6 +115,10 @@ __global__ void twiddle_kernel(double2* tab, int N1, int N2, int N3) {
     double s, c;
     sincospi(2.0 * (double)j / (double)N, &s, &c);
     tab[t] = make_double2(c, s);
+    // the FP32-pair copy: h = fl32(x), l = fl32(x - h)
+    const float ch = __double2float_rn(c), sh = __double2float_rn(s);
+    reinterpret_cast<float4*>(tab + n)[t] =
+        make_float4(ch, __double2float_rn(c - (double)ch), sh, __double2float_rn(s - (double)sh));
   }
 }
 

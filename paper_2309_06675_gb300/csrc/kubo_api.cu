@@ -213,7 +213,7 @@ void plan_layout(Plan& p, bool host_io, int64_t n_list_outputs_unused) {
     p.o_neg = b.take(sizeof(int) * p.N_R);
     p.o_pairs = b.take(sizeof(int) * 2 * std::max(1, p.N_h));
     p.o_Rh = b.take(sizeof(int) * 3 * std::max(1, p.N_h));
-    p.o_tab = b.take(sizeof(double2) * (p.mesh.N1 + p.mesh.N2 + p.mesh.N3));
+    p.o_tab = b.take(twiddle_bytes(p.mesh.N1, p.mesh.N2, p.mesh.N3));
     p.o_Bp = b.take(sizeof(double) * (size_t)p.K * WW);
     if (p.sep) {
       p.o_box = b.take(sizeof(int) * (size_t)(2 * p.sb.h1 + 1) * (2 * p.sb.h2 + 1) * (2 * p.sb.h3 + 1));
@@ -516,6 +516,7 @@ Model make_model(const Call& c) {
   md.Bp = c.at<double>(c.p.o_Bp);
   md.Rh = c.at<int>(c.p.o_Rh);
   md.tab = c.at<double2>(c.p.o_tab);
+  md.tab_df = reinterpret_cast<const float4*>(md.tab + (c.p.mesh.N1 + c.p.mesh.N2 + c.p.mesh.N3));
   md.tab_off[0] = 0;
   md.tab_off[1] = c.p.mesh.N1;
   md.tab_off[2] = c.p.mesh.N1 + c.p.mesh.N2;

@@ -55,6 +55,7 @@ struct Model {
   const double* Bp;       // [K][W*W]
   const int* Rh;          // [N_h][3]
   const double2* tab;     // twiddles: tab[tab_off[a] + j] = e^{2 pi i j / N_a}
+  const float4* tab_df;   // the same twiddles as FP32 pairs (re_h, re_l, im_h, im_l)
   int tab_off[3];
 };
 
@@ -73,11 +74,11 @@ __device__ __forceinline__ unsigned long long mag_bits(double x) {
 }
 
 // x_i <- x_i 2^-e (i < n, stride apart), e the exponent of max |x_i|, on the bit patterns: the
-// exponent fields are shifted by integer subtraction (exact), zeros, subnormals and entries
+// exponent fields are shifted by integer subtraction (exact); zeros, subnormals and entries
 // that would leave the normal range become signed zeros (all below 2^-1022 of the largest or
-// of the normal range), and a zero or non-finite vector is left alone.  The inverse iterations rescale their iterate this way
-// between solves (no FP64 square root, reciprocal or multiplies; only the last solve's vector
-// is normalised in FP64).
+// of the normal range), and a zero or non-finite vector is left alone.  The inverse
+// iterations rescale their iterate this way between solves (no FP64 square root, reciprocal
+// or multiplies; only the last solve's vector is normalised in FP64).
 __device__ __forceinline__ void pow2_rescale(double* x, int n, size_t stride) {
   unsigned long long mx = 0ull;
   for (int i = 0; i < n; ++i) {
@@ -168,7 +169,12 @@ cudaError_t launch_pack_basis(const double2* H_R, const int* pairs, int idx0, in
                               double* Bp, cudaStream_t s, int escale = 0);
 // x[i] *= 2^e for i < n (exact unless the result leaves the FP64 range)
 cudaError_t launch_scale_pow2(double* x, int64_t n, int e, cudaStream_t s);
+// tab: [N1 + N2 + N3] double2, followed by the same twiddles as FP32 pairs ([N1 + N2 + N3]
+// float4: re_h, re_l, im_h, im_l; twiddle_bytes(...) in all)
 cudaError_t launch_twiddles(double2* tab, int N1, int N2, int N3, cudaStream_t s);
+inline size_t twiddle_bytes(int N1, int N2, int N3) {
+  return (sizeof(double2) + sizeof(float4)) * (size_t)(N1 + N2 + N3);
+}
 
 cudaError_t launch_fourier_fp64(const Model& md, const Mesh& mesh, const KList& kl, double* Hp,
                                 double* Xp, double* Yp, cudaStream_t s);
