@@ -126,6 +126,28 @@ def test_eigh_batched(kubo, torch, W):
     assert np.all(orth <= 1e-13 * max(W, 8))
 
 
+@pytest.mark.parametrize("W", [24, 80])
+@pytest.mark.parametrize("lg", [-400, 400])
+def test_fp64_eigensolver_at_extreme_magnitudes(kubo, torch, W, lg):
+    """A scaling by 2^lg (exact) scales the eigenvalues by 2^lg and leaves the eigenvectors:
+    the inverse iterations (the fused FP64 kernel at W <= 64, the persistent one above) rescale
+    their iterate between solves by powers of two on the bit patterns and compare pivots as
+    integers, so FP64 results hold far outside the FP32 range too."""
+    rng = np.random.default_rng(W + 7)
+    A = _random_hermitian(rng, 9, W)
+    f = 2.0 ** lg
+    E0, _ = kubo.eigh_batched(kubo.pack_hermitian(cuda(torch, A)), W)
+    E1, U1 = kubo.eigh_batched(kubo.pack_hermitian(cuda(torch, A * f)), W)
+    E0, E1, U1 = E0.cpu().numpy(), E1.cpu().numpy() / f, U1.cpu().numpy()
+    nrm = np.max(np.abs(E0), axis=-1)[:, None]
+    assert np.all(np.isfinite(E1)) and np.all(np.isfinite(U1))
+    assert np.all(np.abs(E1 - E0) <= 1e-12 * nrm)
+    res = np.abs(A @ U1 - U1 * E1[:, None, :]).max(axis=(1, 2))
+    assert np.all(res <= 1e-12 * nrm[:, 0])
+    orth = np.abs(np.conj(np.swapaxes(U1, -1, -2)) @ U1 - np.eye(W)).max(axis=(1, 2))
+    assert np.all(orth <= 1e-13 * max(W, 8))
+
+
 def test_eigh_values_only(kubo, torch):
     rng = np.random.default_rng(1)
     A = _random_hermitian(rng, 9, 12)
