@@ -32,6 +32,20 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// 1 / d by Newton-Raphson (r <- r + r (1 - d r), the relative error squaring each step) from
+// the hardware's approximate FP64 reciprocal (~2^-22): 2^-44, then below an ulp before the
+// final rounding.  Four FMAs after the estimate, where an IEEE division issues more FP64
+// instructions (the LU of every inverse-iteration vector takes W of these).  |d| stays in the
+// normal range here (pivots of T - lam I are at least eps ||T||).
+__device__ __forceinline__ double recip_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // ------------------------------------------------------------------ inverse iteration
 // Persistent: CTA b handles k = b, b + gridDim.x, ...; block = ldt = W rounded up to a warp;
 // thread j handles the cluster starting at sorted index j.  Z: [n][W][W] real, column m =
@@ -40,7 +54,10 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
 // rq: the eigenvalues written are the FP64 Rayleigh quotients z^T T z of the finished unit
 // eigenvectors (kept non-decreasing within a cluster) instead of the shifts b.lam -- for
 // shifts from a reduced-precision QL, whose only role is then to make the iteration converge.
-__global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
+// (launch bounds: LW_MAX threads and 8 CTAs of them per SM = 64 registers a thread, the budget
+// of the 16 (W <= 64) or 8 (W = 128) resident CTAs of iit_max_slots; without the CTA count,
+// ptxas settled on 56 registers and spilled)
+__global__ void __launch_bounds__(LW_MAX, 8) iit_kernel(int W, int n, EighBufs b,
                                                      double* __restrict__ Eout,
                                                      double* __restrict__ Z,
                                                      double* __restrict__ scratch, int rq) {
@@ -106,7 +123,7 @@ __global__ void __launch_bounds__(LW_MAX) iit_kernel(int W, int n, EighBufs b,
           const size_t o = (size_t)i * ldt + t;
           const bool sw = mag_bits(q0) < mag_bits(ei);   // interchange rows i and i + 1
           const double den = sw ? ei : (mag_bits(q0) == 0ull ? tiny : q0);
-          const double r = 1.0 / den;
+          const double r = recip_nr(den);
           const double mlt = (sw ? q0 : ei) * r;
           rU0[o] = r; U1[o] = sw ? a : q1; U2[o] = sw ? bb : q2; ML[o] = mlt;
           if (sw) { if (i < 64) piv0 |= 1ull << i; else piv1 |= 1ull << (i - 64); }
