@@ -117,15 +117,15 @@ __global__ void __launch_bounds__(NTT, 1) tridiag_kernel(const T* __restrict__ H
         const double2 al = A[tri(o, i)];
         const double aa2 = fma(al.x, al.x, al.y * al.y);
         const double x2 = lane == 0 ? aa2 + s2 : aa2;     // |x|^2 (lane 0), |alpha|^2 (lane 1)
-        const double rx = x2 > 0.0 ? rsqrt(x2) : 0.0;
+        const double rx = mag_bits(x2) != 0ull ? rsqrt(x2) : 0.0;   // (sums of squares: integer tests)
         const double xn = x2 * rx;                         // |x| (lane 0), |alpha| (lane 1)
         const double nrm = __shfl_sync(0x3u, xn, 0);
         const double aa = __shfl_sync(0x3u, xn, 1);
         const double ra = __shfl_sync(0x3u, rx, 1);
         const double comp = lane == 0 ? al.x : al.y;
         // the unit phase of alpha (1 for alpha = 0)
-        const double ph = aa2 > 0.0 ? comp * ra : (lane == 0 ? 1.0 : 0.0);
-        if (s2 != 0.0) {
+        const double ph = mag_bits(aa2) != 0ull ? comp * ra : (lane == 0 ? 1.0 : 0.0);
+        if (mag_bits(s2) != 0ull) {
           const double bet = -ph * nrm;
           const double v0 = fma(ph, nrm, comp);
           double* Ao = reinterpret_cast<double*>(&A[tri(o, i)]);
@@ -362,17 +362,19 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
         const double2 al = lk ? Ak[tri(o, i)] : make_double2(0.0, 0.0);
         const double aa2 = fma(al.x, al.x, al.y * al.y);
         const double x2 = sub == 0 ? aa2 + s2k : aa2;    // |x|^2, |alpha|^2
-        const double rx = x2 > 0.0 ? rsqrt(x2) : 0.0;
+        // (x2, aa2 and s2k are sums of squares: "> 0" is a non-zero bit pattern, tested on the
+        // integer side -- these FP64 instructions would issue with four lanes active)
+        const double rx = mag_bits(x2) != 0ull ? rsqrt(x2) : 0.0;
         const double xn = x2 * rx;                         // |x|, |alpha|
         const double nrm = __shfl_sync(0xFu, xn, 2 * kk);
         const double aa = __shfl_sync(0xFu, xn, 2 * kk + 1);
         const double ra = __shfl_sync(0xFu, rx, 2 * kk + 1);
         const double comp = sub == 0 ? al.x : al.y;
-        const double ph = aa2 > 0.0 ? comp * ra : (sub == 0 ? 1.0 : 0.0);
+        const double ph = mag_bits(aa2) != 0ull ? comp * ra : (sub == 0 ? 1.0 : 0.0);
         double2* begk = b.phase + (2 * (int64_t)blockIdx.x + kk) * W;
         double* toutk = b.tau + (2 * (int64_t)blockIdx.x + kk) * W;
         if (lk) {
-          if (s2k != 0.0) {
+          if (mag_bits(s2k) != 0ull) {
             const double bet = -ph * nrm;
             const double v0 = fma(ph, nrm, comp);
             reinterpret_cast<double*>(&Ak[tri(o, i)])[sub] = v0;
