@@ -384,8 +384,8 @@ __device__ __forceinline__ void unpack_hermitian_f32(const TIn* __restrict__ P, 
 // Q = H_0 H_1 ... H_{W-3} is applied in blocks of ASM_NB consecutive reflectors in the compact
 // WY form H_j0 ... H_j0+3 = I - V T V^H (T upper triangular: T_ii = tau_i,
 // T[0:i, i] = -tau_i T[0:i, 0:i] V[:, 0:i]^H v_i), last block first: U <- U - V (T (V^H U)).
-// The block factors are formed once from the reflectors' inner products; each group of 8
-// threads then applies a block to two columns with 2 ASM_NB independent dot chains, so the
+// The block factors are formed once from the reflectors' inner products; each group of 4
+// threads then applies a block to one column with ASM_NB independent dot chains, so the
 // application is ceil((W - 2) / 4) dependent steps instead of W - 2.  (Blocks of 16 applied
 // as register-tiled products were measured slower: their per-block serial phases are not
 // hidden at two CTAs per SM.)
@@ -461,70 +461,59 @@ __device__ __forceinline__ void assemble_u_f32(const double* __restrict__ Zk,
     }
   }
   __syncthreads();
-  const int q = t & 7, cp = t >> 3;   // NT / 8 = 32 groups, two columns each (W <= 64)
-  const int c0 = 2 * cp, c1 = c0 + 1;
-  const bool act0 = c0 < W, act1 = c1 < W;
+  // NT / 4 = 64 groups of four row lanes, one column each (W <= 64): the dot products of a
+  // block are reduced over four lanes (two shuffle rounds of 2 ASM_NB values; with two columns
+  // per group of eight lanes the three rounds of 4 ASM_NB values cost as much as the dot
+  // products themselves).  A warp touches 4 rows x 8 columns of U: conflict-free with the
+  // padded row (8 banks per row step).
+  const int q = t & 3, c0 = t >> 2;
+  const bool act0 = c0 < W;
   for (int bk = nblk - 1; bk >= 0; --bk) {
     const int j0 = bk * ASM_NB, nj = min(ASM_NB, nref - j0), m0 = W - 1 - j0, o = j0 + 1;
     const float2* Tb = Tm + bk * ASM_NB * ASM_NB;
-    float2 s0[ASM_NB], s1[ASM_NB];
+    float2 s0[ASM_NB];
 #pragma unroll
-    for (int a = 0; a < ASM_NB; ++a) {
-      s0[a] = make_float2(0.f, 0.f);
-      s1[a] = make_float2(0.f, 0.f);
-    }
-    for (int rr = q; rr < m0; rr += 8) {
+    for (int a = 0; a < ASM_NB; ++a) s0[a] = make_float2(0.f, 0.f);
+    for (int rr = q; rr < m0; rr += 4) {
       const float2 u0 = act0 ? sU[(o + rr) * LD + c0] : make_float2(0.f, 0.f);
-      const float2 u1 = act1 ? sU[(o + rr) * LD + c1] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int a = 0; a < ASM_NB; ++a) {
         if (a < nj && rr >= a) {
           const float2 v = stage[roff(j0 + a) + rr - a];
           s0[a].x = fmaf(v.x, u0.x, fmaf(v.y, u0.y, s0[a].x));   // conj(v) u
           s0[a].y = fmaf(v.x, u0.y, fmaf(-v.y, u0.x, s0[a].y));
-          s1[a].x = fmaf(v.x, u1.x, fmaf(v.y, u1.y, s1[a].x));
-          s1[a].y = fmaf(v.x, u1.y, fmaf(-v.y, u1.x, s1[a].y));
         }
       }
     }
 #pragma unroll
     for (int a = 0; a < ASM_NB; ++a)
 #pragma unroll
-      for (int o2 = 1; o2 < 8; o2 <<= 1) {
+      for (int o2 = 1; o2 < 4; o2 <<= 1) {
         s0[a].x += __shfl_xor_sync(0xffffffffu, s0[a].x, o2);
         s0[a].y += __shfl_xor_sync(0xffffffffu, s0[a].y, o2);
-        s1[a].x += __shfl_xor_sync(0xffffffffu, s1[a].x, o2);
-        s1[a].y += __shfl_xor_sync(0xffffffffu, s1[a].y, o2);
       }
     // t = T s (upper triangular)
-    float2 t0[ASM_NB], t1[ASM_NB];
+    float2 t0[ASM_NB];
 #pragma unroll
     for (int a = 0; a < ASM_NB; ++a) {
       t0[a] = make_float2(0.f, 0.f);
-      t1[a] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int a2 = a; a2 < ASM_NB; ++a2) {
-        const float2 tv = Tb[a * ASM_NB + a2];
-        const float2 p0 = cmulf(tv, s0[a2]), p1 = cmulf(tv, s1[a2]);
+        const float2 p0 = cmulf(Tb[a * ASM_NB + a2], s0[a2]);
         t0[a].x += p0.x; t0[a].y += p0.y;
-        t1[a].x += p1.x; t1[a].y += p1.y;
       }
     }
-    for (int rr = q; rr < m0; rr += 8) {
+    for (int rr = q; rr < m0; rr += 4) {
       float2 u0 = act0 ? sU[(o + rr) * LD + c0] : make_float2(0.f, 0.f);
-      float2 u1 = act1 ? sU[(o + rr) * LD + c1] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int a = 0; a < ASM_NB; ++a) {
         if (a < nj && rr >= a) {
           const float2 v = stage[roff(j0 + a) + rr - a];
           u0.x = fmaf(-v.x, t0[a].x, fmaf(v.y, t0[a].y, u0.x));   // u -= v t
           u0.y = fmaf(-v.x, t0[a].y, fmaf(-v.y, t0[a].x, u0.y));
-          u1.x = fmaf(-v.x, t1[a].x, fmaf(v.y, t1[a].y, u1.x));
-          u1.y = fmaf(-v.x, t1[a].y, fmaf(-v.y, t1[a].x, u1.y));
         }
       }
       if (act0) sU[(o + rr) * LD + c0] = u0;
-      if (act1) sU[(o + rr) * LD + c1] = u1;
     }
     __syncwarp();   // the group's rows shift between blocks: updates before the next reads
   }
