@@ -58,7 +58,6 @@ constexpr int NLEVEL = 4;         // levels l = i + j <= 3 kept: 10 slice pairs
 constexpr int NACC = 2;           // level-accumulator sets in flight (double buffer)
 constexpr int DRAIN = 4;          // K blocks summed in TMEM before the epilogue drains a set:
                                   // 4 blocks x 4 pairs x 64 x 2^14 = 2^24, still exact in FP32
-constexpr int GROUP_M = 8;        // default of the M tiles rasterised together (B tiles reused from L2)
 constexpr int TILE_A_BYTES = BM * BK * 2;            // 16 KB per slice
 constexpr int TILE_B_BYTES = BN * BK * 2;            // 8 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (TILE_A_BYTES + TILE_B_BYTES);   // 96 KB

@@ -724,32 +724,32 @@ __global__ void __launch_bounds__(LW_MAX) curvature_large_kernel(const double* _
       if (e >= n_eta) break;
       Om[e * eta_stride + k * W + n] = ((double)hi[e] + (double)lo[e]) + fb[e];
     }
-    return;
-  }
-  double rp[MAXE];
+  } else {
+    double rp[MAXE];
 #pragma unroll
-  for (int e = 0; e < MAXE; ++e) rp[e] = 0.0;
-  for (int m = 0; m < W; ++m) {
-    if (m == n) continue;
-    const int p = n < m ? n : m, q = n < m ? m : n;
-    const typename cx<T>::type vx = Vx[base + (size_t)p * W + q];
-    const typename cx<T>::type vy = Vy[base + (size_t)p * W + q];
-    const double num = -2.0 * ((double)vx.y * (double)vy.x - (double)vx.x * (double)vy.y);
-    const double dE = sE[p] - sE[q];
-    const double d2 = dE * dE;
-    const double sgn = n < m ? 1.0 : -1.0;   // T_nm = -T_mn: evaluated from the (p < q) entry
+    for (int e = 0; e < MAXE; ++e) rp[e] = 0.0;
+    for (int m = 0; m < W; ++m) {
+      if (m == n) continue;
+      const int p = n < m ? n : m, q = n < m ? m : n;
+      const typename cx<T>::type vx = Vx[base + (size_t)p * W + q];
+      const typename cx<T>::type vy = Vy[base + (size_t)p * W + q];
+      const double num = -2.0 * ((double)vx.y * (double)vy.x - (double)vx.x * (double)vy.y);
+      const double dE = sE[p] - sE[q];
+      const double d2 = dE * dE;
+      const double sgn = n < m ? 1.0 : -1.0;   // T_nm = -T_mn: evaluated from the (p < q) entry
+#pragma unroll
+      for (int e = 0; e < MAXE; ++e) {
+        if (e >= n_eta) break;
+        const double eta = etas[e];
+        if (eta == 0.0 && d2 <= thr2) continue;
+        rp[e] += sgn * (num / fma(eta, eta, d2));
+      }
+    }
 #pragma unroll
     for (int e = 0; e < MAXE; ++e) {
       if (e >= n_eta) break;
-      const double eta = etas[e];
-      if (eta == 0.0 && d2 <= thr2) continue;
-      rp[e] += sgn * (num / fma(eta, eta, d2));
+      Om[e * eta_stride + k * W + n] = rp[e];
     }
-  }
-#pragma unroll
-  for (int e = 0; e < MAXE; ++e) {
-    if (e >= n_eta) break;
-    Om[e * eta_stride + k * W + n] = rp[e];
   }
 }
 
