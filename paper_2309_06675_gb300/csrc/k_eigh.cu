@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NTT, 1) tridiag_kernel(const T* __restrict__ H
           Ao[lane] = v0;
           bo[lane] = bet;
           if (lane == 0) {
-            const double tau = 1.0 / (nrm * (nrm + aa));
+            const double tau = recip_nr(nrm * (nrm + aa));
             s_tau = tau;
             tout[i] = tau;
           }
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(512, 3) tridiag2_kernel(const double* __restri
             reinterpret_cast<double*>(&Ak[tri(o, i)])[sub] = v0;
             reinterpret_cast<double*>(&begk[i])[sub] = bet;
             if (sub == 0) {
-              const double tau = 1.0 / (nrm * (nrm + aa));
+              const double tau = recip_nr(nrm * (nrm + aa));
               s_tau[kk] = tau;
               toutk[i] = tau;
             }

@@ -32,20 +32,6 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-// 1 / d by Newton-Raphson (r <- r + r (1 - d r), the relative error squaring each step) from
-// the hardware's approximate FP64 reciprocal (~2^-22): 2^-44, then below an ulp before the
-// final rounding.  Four FMAs after the estimate, where an IEEE division issues more FP64
-// instructions (the LU of every inverse-iteration vector takes W of these).  |d| stays in the
-// normal range here (pivots of T - lam I are at least eps ||T||).
-__device__ __forceinline__ double recip_nr(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
 // ------------------------------------------------------------------ inverse iteration
 // Persistent: CTA b handles k = b, b + gridDim.x, ...; block = ldt = W rounded up to a warp;
 // thread j handles the cluster starting at sorted index j.  Z: [n][W][W] real, column m =

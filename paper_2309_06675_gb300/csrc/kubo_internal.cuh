@@ -97,6 +97,21 @@ __device__ __forceinline__ void pow2_rescale(double* x, int n, size_t stride) {
   }
 }
 
+// 1 / d by Newton-Raphson (r <- r + r (1 - d r), the relative error squaring each step) from
+// the hardware's approximate FP64 reciprocal (~2^-22): 2^-44, then below an ulp before the
+// final rounding.  Four FMAs after the estimate, where an IEEE division issues more FP64
+// instructions (the LU of every inverse-iteration vector takes W of these, the Householder
+// reduction one per column).  For |d| and 1 / |d| in the normal range (the callers' pivots
+// are at least eps ||T||, the reduction's |x| (|x| + |alpha|) a positive sum of squares).
+__device__ __forceinline__ double recip_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // start vector of the inverse iterations: 0.5 + (h >> 8) 2^-24 in [0.5, 1.5) from an integer hash
 // of (row, vector); 1 + (h >> 8) 2^-24 is assembled from its bits (exponent of 1, the 24-bit
 // integer as the leading mantissa bits) and 0.5 subtracted exactly, instead of an integer ->
