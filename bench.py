@@ -56,7 +56,7 @@ DF_OPS_PER_MAC = 12
 # DRAM bytes (read + write) per k-point of the kernels that can dominate a step, by (path,
 # stage), from one ncu capture of the current kernel (profiles/, W = 64); a kernel that
 # changes after its capture leaves this table.
-DRAM_BYTES_PER_K = {("mixed", "tridiag"): 86.1e3, ("mixed_df", "tridiag"): 97.3e3}
+DRAM_BYTES_PER_K = {("mixed", "tridiag"): 87.0e3, ("mixed_df", "tridiag"): 97.3e3}
 # algorithmic flops per k-point by stage (useful work of each step of the method)
 def stage_flops(W, N_R, prec="fp64"):
     """Algorithmic flops per k-point of each stage (useful work, not issued slice products).
