@@ -597,7 +597,7 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
   const int nt = Npad / BN;
   // first column tile that lies entirely at or after red_n0
   const int rt = std::min(nt, (std::max(red_n0, 0) + BN - 1) / BN);
-  auto go = [&](auto kern, int t0, int tc) -> cudaError_t {
+  auto go = [&](auto kern, int t0, int tc, int gm) -> cudaError_t {
     if (tc <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -606,13 +606,19 @@ cudaError_t launch_fourier_tc(const void* A, const void* Bt, const int* col_exp,
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(tc * (Mpad / BM), std::max(nsm, 1));   // persistent: one per SM
     kern<<<grid, TC_THREADS, sm, s>>>(mA, mB, col_exp, Mpad, Npad, Kp / BK, n_rows, out, ldc, st,
-                                      t0, tc, group_m, vel0, vw2, vel32_x0(vel_w),
+                                      t0, tc, gm, vel0, vw2, vel32_x0(vel_w),
                                       vel32_yoff(vel_w));
     return cudaGetLastError();
   };
-  cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt);
+  // M tiles rasterised together: group_m for the H columns, four times that (at most 64) for the
+  // velocity columns, whose A tiles are three-quarters the size (3 slices) and whose basis is
+  // half again as large (8,192 vs 4,096 columns at W = 64).  Measured DRAM reads per 65,536-k
+  // launch at W = 64, N_R = 1331 (H / velocity kernel): groups of 8: 2.50 / 3.93 GB; of 32:
+  // 3.54 / 1.85 GB; of 1: 2.85 / 5.58 GB -- the same time in every case (the kernels are bound
+  // by their operand intake, not by DRAM).
+  cudaError_t e = go(fourier_tc_kernel<NSLICE>, 0, rt, group_m);
   if (e != cudaSuccess) return e;
-  return go(fourier_tc_kernel<NSLICE - 1>, rt, nt - rt);
+  return go(fourier_tc_kernel<NSLICE - 1>, rt, nt - rt, std::min(64, 4 * group_m));
 }
 
 }  // namespace kubo
