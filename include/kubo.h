@@ -346,7 +346,8 @@ typedef struct kubo_batch_schedule {
    * out: the values used).  The tuner first picks streams and chunk_k on the default kernel
    * parameters, then tries each parameter's alternatives in turn on that schedule. */
   int fourier_group_m;      /* tensor-core Fourier sum: 128-k tiles rasterised together per
-                               column tile (L2 reuse of the basis tiles); default 8, tuned over
+                               column tile of the H columns (L2 reuse of the basis tiles; the
+                               velocity columns use min(64, 4 x this)); default 8, tuned over
                                {4, 8, 16}; 1..64 */
   int symv_parts;           /* Householder reduction: cap on the column partitions per row of
                                its symv (W <= 64: the count up to the cap with the fewest FP64
