@@ -17,13 +17,14 @@
 // core applies.  The epilogue converts each level to an integer (exact), accumulates the K
 // blocks and levels exactly in one int64 per column, and scales once in FP64:
 //   C = 2^e_n sum_l 2^(-14-8l) I_l   (levels l <= 3: 10 slice pairs).
-// The result carries ~31 fractional bits relative to the operand scales (FP64 phases, FP64
-// basis), versus ~24 for a split-BF16 product with FP32 accumulation.
+// The result carries ~31 fractional bits relative to the operand scales (phases to ~2^-46,
+// FP64 basis), versus ~24 for a split-BF16 product with FP32 accumulation.
 //
 // Kernels:
 //   basis_scale_kernel  once per call: column exponents e_n of the stacked basis
 //   basis_slice_kernel  once per call: stacked basis -> Bt[4 slices][Npad][Kp] (K-major, bf16)
-//   coef_slice_kernel   per batch: FP64 phases with exact argument reduction -> A[4][Mpad][Kp]
+//   coef_slice_kernel   per batch: phases with exact integer argument reduction, the three
+//                       twiddles multiplied in FP32 pairs (~2^-46) -> A[4][Mpad][Kp]
 //   fourier_tc_kernel   per batch: tcgen05.mma (kind::f16, M=128, K=16; one MMA per A slice
 //                       against the stacked B slices, N = 64 x (slices - i)), operands staged
 //                       by TMA (128-byte swizzle, 2-stage mbarrier pipeline), 4 level
