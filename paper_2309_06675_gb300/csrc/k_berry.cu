@@ -986,8 +986,8 @@ __global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
 // scheme): every FP32 operand x is cut into hi = tf32(x) and lo = tf32(x - hi) (11 + 11
 // significant bits, the cut exact), and a product is formed as hi lo + lo hi + hi hi; the
 // dropped lo lo and the cut's residual are ~2^-24 relative: FP32-grade.  The tensor core's
-// additions into its FP32 accumulator truncate, so each K-quarter (12 MMAs, the small cross
-// terms first) starts a fresh accumulator and the quarters are summed in registers with
+// additions into its FP32 accumulator truncate, so each K phase of 32 (12 MMAs, the small
+// cross terms first) starts a fresh accumulator and the phases are summed in registers with
 // round-to-nearest: on the W = 64 workload this rotation is then slightly more accurate than
 // the SIMT FP32 one (all 48 MMAs in one accumulator were ten times less accurate).
 // The complex products are block-real GEMMs with M = 128, N = 64, K = 128 (W padded to 64):
@@ -995,8 +995,10 @@ __global__ void __launch_bounds__(RT_NT, 1) berry_tc_kernel(
 //   V = U^H T:  [V_r; V_i] = [[U_r^T, U_i^T], [-U_i^T, U_r^T]] [T_r; T_i]
 // T is held in registers (each thread 32 entries of one row of [T_r; T_i], which is one K
 // column of the second product's B operand); V^x waits in TMEM while V^y is formed.  The
-// operands are staged one K-quarter (32 TF32 = one 128-byte swizzle row) at a time, 48 KB for
-// A and B with their hi / lo parts, so that with U (FP32, assembled from the FP64 factors in
+// operands are staged one K phase (32 TF32 = one 128-byte swizzle row) at a time, 48 KB for
+// A and B with their hi / lo parts -- a phase pairs 16 K of the real-part half with the same 16
+// of the imaginary-part half, so that every block-real row pair is formed from one load and
+// one split per value -- so that with U (FP32, assembled from the FP64 factors in
 // shared memory) and the packed FP32 velocity rows (copied asynchronously into shared memory,
 // rows of W + 1 floats: X while U is assembled, Y while the second product of X runs) a CTA
 // needs ~100 KB and two CTAs share an SM: one stages operands while the other's MMAs run.
@@ -1094,7 +1096,7 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t
       : "memory");
 }
 
-// the 12 MMAs of one K-quarter: (hi, lo), (lo, hi), then (hi, hi), x 4 K8 steps.  The small
+// the 12 MMAs of one K phase: (hi, lo), (lo, hi), then (hi, hi), x 4 K8 steps.  The small
 // cross terms go first: each MMA's addition into the FP32 accumulator truncates at the
 // accumulator's magnitude, so they are added while it is still ~2^-11 of its final size and
 // only the four (hi, hi) steps truncate at full size.
@@ -1172,7 +1174,7 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
   uint32_t phase = 0;
   bool ok = true;
 
-  // the MMAs of the staged K-quarter into TMEM column d_col; bounded wait (false on timeout)
+  // the MMAs of the staged K phase into TMEM column d_col; bounded wait (false on timeout)
   auto mma_quarter = [&](uint32_t d_col, bool first) -> bool {
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -1214,9 +1216,9 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
     float vacc[32];   // this thread's 32 entries of row mrow of [V_r; V_i]
     for (int a = 0; a < 2 && ok; ++a) {
       const TIn* P = (a == 0 ? Xp : Yp) + k * ld;
-      // ---- product 1: [T_r; T_i] = A1 B1^T.  Each K-quarter accumulates into TMEM columns
+      // ---- product 1: [T_r; T_i] = A1 B1^T.  Each K phase accumulates into TMEM columns
       // 0..63 from zero and is added here in FP32 with round-to-nearest: the tensor core's
-      // FP32 accumulation truncates, and one accumulator per quarter keeps that to 12 steps
+      // FP32 accumulation truncates, and one accumulator per phase keeps that to 12 steps
       // (all 48 in one accumulator left the result ten times less accurate than the SIMT
       // rotation's).  tv: this thread's 32 entries of row mrow of [T_r; T_i].
       float tv[32];
@@ -1279,7 +1281,7 @@ __global__ void __launch_bounds__(TF_NT, 2) berry_tf32_kernel(
         tc::tc_fence_before();
       }
       if (!ok) break;
-      // ---- product 2: [V_r; V_i] = A2 B2^T, per K-quarter in TMEM columns 64..127, summed here
+      // ---- product 2: [V_r; V_i] = A2 B2^T, per K phase in TMEM columns 64..127, summed here
 #pragma unroll
       for (int j = 0; j < 32; ++j) vacc[j] = 0.f;
       for (int h = 0; h < 4 && ok; ++h) {
