@@ -541,9 +541,10 @@ __global__ void __launch_bounds__(NT) assemble_u_kernel(const double* __restrict
 }
 
 // Leading dimension (in float2) of the FP32 shared-memory matrices.  Padded: W + P with
-// W + P = 4 (mod 16), so that a row step moves 8 banks: the 4 rows x 2 columns of float2 that
-// a quarter of a warp touches in the reflector application, and the 16 consecutive columns of
-// a half warp elsewhere, fall on distinct banks.  Unpadded (the ablation): W.
+// W + P = 4 (mod 16), so that a row step moves 8 banks: the 4 rows x 4 columns of float2 that
+// a half warp touches in the reflector application (four row lanes per column), and the 16
+// consecutive columns of a half warp elsewhere, fall on distinct banks.  Unpadded (the
+// ablation): W.
 __host__ __device__ __forceinline__ int mixed_ld(int W, int pad) {
   return pad ? W + ((4 - W) & 15) : W;
 }
